@@ -1,0 +1,208 @@
+/*
+ * stab.h -- C interface of the GB300 Pauli-coefficient propagation library.
+ *
+ * The library implements the propagation stage ("Map", Sec. IV-B) of the
+ * extended stabilizer formalism of arXiv 2502.10685: every stabilizer
+ * generator Z_k of |0^n> (Eq. (1)) and every observable is held as a dense
+ * FP64 vector of its 4^n Pauli-string coefficients, and each gate of a
+ * parameterized circuit maps that vector to the coefficients of g P g^dagger
+ * (Sec. II-A: Clifford gates map strings to signed strings; R_x, R_y, R_z mix
+ * strings by cos/sin as in Table I).  Observables are propagated backward
+ * (U^dagger O U) and <0^n| O |0^n> is read from the strings made of I and Z.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns a status: STAB_OK (0) or a negative STAB_E_* code.
+ *    No C++ exception crosses this interface.  On an error the context keeps
+ *    the state it had before the call.
+ *  - Input arrays are owned by the caller and are copied or consumed before the
+ *    call returns, unless a parameter says it is a device pointer that must
+ *    stay valid until the next synchronizing call.
+ *  - Work is queued on the context's stream(s); results written to host
+ *    memory are complete when the call returns, results written to device
+ *    memory are complete after stab_synchronize() or an event on the stream.
+ *  - A context is used by one host thread at a time.
+ *
+ * Coefficient layout on the device and in every generator output:
+ *    index(P) = z | (x << n),  bit q of x (z) set iff the letter on qubit q is
+ *    X or Y (Z or Y);  I = (0,0), X = (1,0), Z = (0,1), Y = (1,1).
+ * The strings made of I and Z (x = 0) are the contiguous block [0, 2^n).
+ */
+#ifndef STAB_LIB_INTERFACE_H
+#define STAB_LIB_INTERFACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STAB_VERSION 1
+
+/* ---------------------------------------------------------------- status */
+#define STAB_OK 0
+#define STAB_E_INVAL (-1)     /* null pointer, unknown opcode, qubit >= n, q0 == q1, bad term */
+#define STAB_E_RANGE (-2)     /* n outside [1, STAB_MAX_QUBITS], slot outside [0, n_params), size */
+#define STAB_E_NOMEM (-3)     /* device allocation failed, or a request does not fit */
+#define STAB_E_TIMEOUT (-4)   /* a bounded device wait gave up (status read back on the host) */
+#define STAB_E_NONFINITE (-5) /* an angle or coefficient is NaN or infinite */
+#define STAB_E_CUDA (-6)      /* CUDA runtime error; stab_last_cuda_error() returns its code */
+#define STAB_E_STATE (-7)     /* call out of order (e.g. expectation before a circuit is loaded) */
+#define STAB_E_BUSY (-8)      /* server queue full */
+
+#define STAB_MAX_QUBITS 12
+
+/* ---------------------------------------------------------------- gates */
+/* Opcodes.  H, S and the rotations are Table I; CX is map_CX of Sec. III-C
+ * (q0 = control, q1 = target).  S^dagger, X, Y, Z and CZ are the standard
+ * Clifford gates; each is a composition of the paper's rules.  Rotations are
+ * R_s(theta) = exp(-i theta s / 2), the convention under which Table I and
+ * Example 1 hold. */
+enum stab_op {
+    STAB_H = 0, STAB_S = 1, STAB_SDG = 2, STAB_X = 3, STAB_Y = 4, STAB_Z = 5,
+    STAB_CX = 6, STAB_CZ = 7, STAB_RX = 8, STAB_RY = 9, STAB_RZ = 10
+};
+
+/* One instruction {g, w, theta} of Sec. III-A.  8 bytes.
+ *  op     stab_op
+ *  q0     wire (control of CX, first qubit of CZ)
+ *  q1     second wire of CX / CZ, else ignored
+ *  flags  reserved, must be 0
+ *  param  rotations: index of the angle in the thetas array (several gates may
+ *         share a slot; gradients sum over them); other gates: ignored (-1). */
+typedef struct stab_gate {
+    uint8_t op, q0, q1, flags;
+    int32_t param;
+} stab_gate;
+
+/* One observable term coeff * P(x, z); bit q of x / z as in the layout above. */
+typedef struct stab_term {
+    double coeff;
+    uint64_t x, z;
+} stab_term;
+
+/* ---------------------------------------------------------------- options */
+enum stab_kernel {
+    STAB_KERNEL_AUTO = 0,      /* autotuner choice per n */
+    STAB_KERNEL_RESIDENT = 1,  /* one CTA per vector, vector resident in shared memory (n <= 7) */
+    STAB_KERNEL_STREAMED = 2,  /* vector in HBM, one fused pass per launch (any n) */
+    STAB_KERNEL_PLAIN = 3      /* one launch per gate, no fusion: the comparison form */
+};
+
+/* Device allocator hooks.  With alloc == NULL the library uses cudaMallocAsync
+ * / cudaFreeAsync on its stream.  The Python binding passes PyTorch's caching
+ * allocator here. */
+typedef void *(*stab_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*stab_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct stab_opts {
+    int32_t device;        /* CUDA device ordinal, -1 = the current device */
+    int32_t kernel;        /* stab_kernel */
+    int32_t fuse;          /* 1 (default): group per-wire runs and CX runs (Sec. III-A) */
+    int32_t reserved;
+    void *stream;          /* cudaStream_t to queue on; NULL = a stream the context creates */
+    stab_alloc_fn alloc;
+    stab_free_fn free;
+    void *alloc_user;
+} stab_opts;
+
+/* Fills *opts with the defaults (device -1, AUTO, fuse 1, own stream, cudaMallocAsync). */
+void stab_default_opts(stab_opts *opts);
+
+/* ---------------------------------------------------------------- context */
+typedef struct stab_ctx stab_ctx;
+
+/* Creates a context for n qubits (1 <= n <= STAB_MAX_QUBITS).  opts may be
+ * NULL.  The context owns the device vectors: n generators of 4^n doubles and
+ * the work vectors of expectation and gradient calls.
+ * Errors: STAB_E_RANGE (n), STAB_E_INVAL (out NULL), STAB_E_CUDA, STAB_E_NOMEM. */
+int stab_create(int n, const stab_opts *opts, stab_ctx **out);
+
+/* Releases every device buffer and stream the context owns.  NULL is a no-op. */
+int stab_destroy(stab_ctx *ctx);
+
+/* Loads a circuit (Sec. III-A dividing + encoding): validates the m gate
+ * records (host memory), plans the fused passes, uploads them and encodes the
+ * n_params angles (host memory).  Replaces any previous circuit.  m = 0 is the
+ * identity circuit.  Errors: STAB_E_INVAL (bad opcode, qubit, q0 == q1),
+ * STAB_E_RANGE (param slot), STAB_E_NONFINITE (angle), STAB_E_CUDA. */
+int stab_load_circuit(stab_ctx *ctx, const stab_gate *gates, int64_t m, const double *thetas,
+                      int64_t n_params);
+
+/* Replaces the angles of the loaded circuit.  thetas has the loaded n_params
+ * entries, in host memory (is_device = 0) or device memory (is_device = 1,
+ * read on the context stream).  Errors: STAB_E_STATE (no circuit),
+ * STAB_E_NONFINITE (host angles only), STAB_E_CUDA. */
+int stab_set_params(stab_ctx *ctx, const double *thetas, int is_device);
+
+/* Evolves the n generators of |0^n> (Eq. (1)) through the loaded circuit:
+ * generator k becomes U Z_k U^dagger.  Asynchronous.  Errors: STAB_E_STATE. */
+int stab_run_generators(stab_ctx *ctx);
+
+/* stab_load_circuit followed by stab_run_generators. */
+int stab_apply_circuit(stab_ctx *ctx, const stab_gate *gates, int64_t m, const double *thetas,
+                       int64_t n_params);
+
+/* Copies the n evolved generators, n x 4^n doubles in the layout above, to
+ * out (host memory if out_is_device == 0, then synchronizing; device memory
+ * otherwise, queued on the context stream).  Errors: STAB_E_STATE (never run). */
+int stab_get_generators(stab_ctx *ctx, double *out, int out_is_device);
+
+/* Device pointer of the generator block (n x 4^n doubles), valid until the
+ * next load/run call or stab_destroy.  NULL before the first run. */
+const double *stab_generators_device(stab_ctx *ctx);
+
+/* <0^n| U^dagger O U |0^n> for O = sum of n_terms terms (host memory) and the
+ * loaded circuit U: O is propagated backward through the circuit and the
+ * coefficients of the strings made of I and Z are summed (fixed-order tree).
+ * *out (host) is written before return.  Errors: STAB_E_INVAL (x or z has a
+ * bit >= n), STAB_E_NONFINITE, STAB_E_STATE. */
+int stab_expect(stab_ctx *ctx, const stab_term *O, int64_t n_terms, double *out);
+
+/* Uploads an observable O = sum of n_terms terms (host memory) for the
+ * asynchronous calls below; equal strings are merged.  Errors: STAB_E_INVAL
+ * (x or z has a bit >= n), STAB_E_NONFINITE. */
+int stab_set_observable(stab_ctx *ctx, const stab_term *O, int64_t n_terms);
+
+/* <O> of the loaded observable and circuit, written to out_dev (device
+ * memory, one double).  Queued on an internal stream that the context stream
+ * then waits for, so work queued later on the context stream sees the value.
+ * Errors: STAB_E_STATE (no circuit or no observable). */
+int stab_expect_async(stab_ctx *ctx, double *out_dev);
+
+/* Adjoint gradient of the loaded observable: expect_dev (device, may be NULL)
+ * receives <O>, grads_dev (device) n_params doubles.  Queued like
+ * stab_expect_async. */
+int stab_grad_async(stab_ctx *ctx, double *expect_dev, double *grads_dev);
+
+/* Gradient of <O> with respect to every angle slot, by one adjoint reverse
+ * sweep.  expect_out (may be NULL) receives <O>; grads_out receives n_params
+ * doubles (host memory).  Errors as stab_expect. */
+int stab_grad(stab_ctx *ctx, const stab_term *O, int64_t n_terms, double *expect_out,
+              double *grads_out);
+
+/* Waits for all work queued by the context. */
+int stab_synchronize(stab_ctx *ctx);
+
+/* Number of qubits, loaded gates and fused passes of the current plan. */
+int stab_plan_info(stab_ctx *ctx, int64_t *n_gates, int64_t *n_passes, int32_t *kernel);
+
+/* Number of kernels this context launched since creation (all entry points). */
+int64_t stab_launch_count(stab_ctx *ctx);
+
+/* Bytes the context copied host -> device and device -> host since creation. */
+int stab_transfer_bytes(stab_ctx *ctx, int64_t *h2d, int64_t *d2h);
+
+/* Human-readable name of a status code (static storage). */
+const char *stab_error_string(int status);
+
+/* CUDA error code behind the last STAB_E_CUDA returned on this thread. */
+int stab_last_cuda_error(void);
+
+int stab_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STAB_LIB_INTERFACE_H */

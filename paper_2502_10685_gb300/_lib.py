@@ -1,0 +1,105 @@
+"""Loader of libstab.so, the CUDA library behind the C interface in include/stab.h.
+
+The library is built in-tree (``paper_2502_10685_gb300/libstab.so``).  There is
+no CPU fallback: if the library cannot be built or loaded, every entry point
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+STAB_OK = 0
+ERRORS = {
+    -1: "STAB_E_INVAL", -2: "STAB_E_RANGE", -3: "STAB_E_NOMEM", -4: "STAB_E_TIMEOUT",
+    -5: "STAB_E_NONFINITE", -6: "STAB_E_CUDA", -7: "STAB_E_STATE", -8: "STAB_E_BUSY",
+}
+
+
+class StabError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        name = ERRORS.get(code, str(code))
+        super().__init__("%s failed: %s%s" % (where, name, (" (" + detail + ")") if detail else ""))
+
+
+class StabGate(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint8), ("q0", ctypes.c_uint8), ("q1", ctypes.c_uint8),
+                ("flags", ctypes.c_uint8), ("param", ctypes.c_int32)]
+
+
+class StabTerm(ctypes.Structure):
+    _fields_ = [("coeff", ctypes.c_double), ("x", ctypes.c_uint64), ("z", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class StabOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("kernel", ctypes.c_int32), ("fuse", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libstab.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libstab.so is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        i32, i64, vp, dp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p
+        sig = {
+            "stab_default_opts": (None, [ctypes.POINTER(StabOpts)]),
+            "stab_create": (i32, [i32, ctypes.POINTER(StabOpts), ctypes.POINTER(vp)]),
+            "stab_destroy": (i32, [vp]),
+            "stab_load_circuit": (i32, [vp, vp, i64, dp, i64]),
+            "stab_set_params": (i32, [vp, dp, i32]),
+            "stab_run_generators": (i32, [vp]),
+            "stab_apply_circuit": (i32, [vp, vp, i64, dp, i64]),
+            "stab_get_generators": (i32, [vp, dp, i32]),
+            "stab_generators_device": (vp, [vp]),
+            "stab_expect": (i32, [vp, vp, i64, dp]),
+            "stab_grad": (i32, [vp, vp, i64, dp, dp]),
+            "stab_set_observable": (i32, [vp, vp, i64]),
+            "stab_expect_async": (i32, [vp, dp]),
+            "stab_grad_async": (i32, [vp, dp, dp]),
+            "stab_transfer_bytes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "stab_synchronize": (i32, [vp]),
+            "stab_plan_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_int32)]),
+            "stab_launch_count": (i64, [vp]),
+            "stab_error_string": (ctypes.c_char_p, [i32]),
+            "stab_last_cuda_error": (i32, []),
+            "stab_version": (i32, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def check(code: int, where: str) -> None:
+    if code != STAB_OK:
+        detail = ""
+        if code == -6 and _lib is not None:
+            detail = "cuda error %d" % _lib.stab_last_cuda_error()
+        raise StabError(code, where, detail)

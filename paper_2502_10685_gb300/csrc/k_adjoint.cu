@@ -1,0 +1,261 @@
+// k_adjoint.cu -- adjoint (reverse-mode) gradient of <O> in the Pauli basis.
+//
+// With rho_0 the coefficient vector of 2^n |0><0| (1 on every string of I and
+// Z) and M_j the orthogonal transfer map of gate j, <O> = <o, M_m ... M_1 rho_0>.
+// Let r_j = M_j ... M_1 rho_0 and l_j = M_{j+1}^T ... M_m^T o.  For a rotation
+// on a pair (u, v), d M_j / d theta = J M_j with J (u, v) = (-v, u), so
+//     d<O>/d theta_j = sum over the gate's pairs of  l_u * (-r_v) + l_v * r_u
+// evaluated on (l_j, r_j).  One reverse sweep carries l and r backward
+// together (r_{j-1} = M_j^T r_j, exact up to rounding because every map is
+// orthogonal), so no forward state is stored except r_m.
+#include <cuda_runtime.h>
+
+#include "resident.cuh"
+
+namespace stab {
+
+namespace {
+
+constexpr int R = kRotPerGradPass;
+
+__device__ __forceinline__ double pair_dot(int axis, double lx, double ly, double lz, double rx,
+                                           double ry, double rz) {
+    // (u, v) = (Y, Z) for R_x, (Z, X) for R_y, (X, Y) for R_z
+    if (axis == AX_X) return fma(lz, ry, -ly * rz);
+    if (axis == AX_Y) return fma(lx, rz, -lz * rx);
+    return fma(ly, rx, -lx * ry);
+}
+
+__device__ __forceinline__ void add_slot(double (&part)[R], int slot, double d) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (r == slot) part[r] += d;
+}
+
+// Walks one P_WIRE pass backward on a group: accumulates the gradient dot of
+// every rotation into part[] (slot = rotation's position within the pass) and
+// applies the inverse op to both vectors.
+__device__ __forceinline__ void adjoint_group(const DevPass &p, const DevOp *ops,
+                                              const DevMap3 *maps, double &lx, double &ly,
+                                              double &lz, double &rx, double &ry, double &rz,
+                                              double (&part)[R], int n_rot) {
+    int slot = n_rot - 1;
+    for (int j = p.n_ops - 1; j >= 0; --j) {
+        const DevOp op = ops[p.first + j];
+        if (op.kind == K_ROT) {
+            add_slot(part, slot, pair_dot(op.axis, lx, ly, lz, rx, ry, rz));
+            --slot;
+        }
+        apply_op1(lx, ly, lz, op, maps, 1);
+        apply_op1(rx, ry, rz, op, maps, 1);
+    }
+}
+
+__device__ __forceinline__ int count_rot(const DevPass &p, const DevOp *ops) {
+    int c = 0;
+    for (int j = 0; j < p.n_ops; ++j) c += ops[p.first + j].kind == K_ROT;
+    return c;
+}
+
+// Gradient slot of the r-th rotation of a pass.
+__device__ __forceinline__ int rot_gate(const DevPass &p, const DevOp *ops, int r) {
+    for (int j = 0; j < p.n_ops; ++j) {
+        if (ops[p.first + j].kind == K_ROT) {
+            if (r == 0) return ops[p.first + j].gate;
+            --r;
+        }
+    }
+    return -1;
+}
+
+template <int N>
+__global__ void __launch_bounds__(RCfg<N>::T) k_adjoint_resident(AdjointArgs a) {
+    using C = RCfg<N>;
+    extern __shared__ double smem[];
+    double *lam = smem;
+    double *rho = smem + C::E;
+    double *red = smem + 2 * C::E;   // (T / 32) x R partial sums
+    for (int i = threadIdx.x; i < C::E; i += C::T) {
+        rho[i] = i < (1 << N) ? 1.0 : 0.0;
+        lam[i] = 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.n_terms; k += C::T) lam[a.terms[k].idx] = a.terms[k].coeff;
+    __syncthreads();
+    resident_run<N>(rho, a.prog, 0);
+
+    const int np = a.prog.n_passes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int W = (C::T + 31) / 32;
+    for (int s = np - 1; s >= 0; --s) {
+        const DevPass p = a.prog.passes[s];
+        if (p.type == P_CLIFF) {
+            resident_cliff<N>(lam, p, a.prog.ops, 1);
+            resident_cliff<N>(rho, p, a.prog.ops, 1);
+            __syncthreads();
+            continue;
+        }
+        const int q = p.q;
+        const int n_rot = count_rot(p, a.prog.ops);
+        double part[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) part[r] = 0.0;
+#pragma unroll
+        for (int k = 0; k < C::GPT; ++k) {
+            const int g = threadIdx.x + k * C::T;
+            if (g < C::G) {
+                const uint32_t b = (uint32_t)group_base((uint64_t)g, N, q);
+                const uint32_t ix = b | (1u << (N + q)), iy = ix | (1u << q), iz = b | (1u << q);
+                double lx = lam[ix], ly = lam[iy], lz = lam[iz];
+                double rx = rho[ix], ry = rho[iy], rz = rho[iz];
+                adjoint_group(p, a.prog.ops, a.prog.maps, lx, ly, lz, rx, ry, rz, part, n_rot);
+                lam[ix] = lx; lam[iy] = ly; lam[iz] = lz;
+                rho[ix] = rx; rho[iy] = ry; rho[iz] = rz;
+            }
+        }
+        if (n_rot > 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                double v = part[r];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) red[warp * R + r] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < n_rot) {
+                double total = 0.0;
+                for (int w = 0; w < W; ++w) total += red[w * R + threadIdx.x];
+                a.grad_rot[rot_gate(p, a.prog.ops, threadIdx.x)] = total;
+            }
+        }
+        __syncthreads();
+    }
+    // <O>: x-free coefficients of the fully back-propagated observable
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
+    double total = block_sum<C::T>(acc, red);
+    if (threadIdx.x == 0 && a.expect_out) *a.expect_out = total;
+}
+
+template <int N>
+cudaError_t launch_adjoint_n(const AdjointArgs &a, cudaStream_t st) {
+    using C = RCfg<N>;
+    const size_t smem = (2 * (size_t)C::E + (size_t)((C::T + 31) / 32) * R + 32) * sizeof(double);
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        e = cudaFuncSetAttribute(k_adjoint_resident<N>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
+    }
+    k_adjoint_resident<N><<<1, C::T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- streamed
+
+constexpr int kAdjThreads = 256;
+
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, double *rho, int n,
+                                                              DevPass p, const DevOp *ops,
+                                                              double *partials) {
+    __shared__ double red[(kAdjThreads / 32) * R];
+    const int q = p.q;
+    const uint64_t G = 1ull << (2 * n - 2);
+    const uint64_t bx = 1ull << (n + q), bz = 1ull << q;
+    const int n_rot = count_rot(p, ops);
+    double part[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) part[r] = 0.0;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = group_base(g, n, q);
+        double *L = lam + b, *Rh = rho + b;
+        double lx = L[bx], ly = L[bx | bz], lz = L[bz];
+        double rx = Rh[bx], ry = Rh[bx | bz], rz = Rh[bz];
+        adjoint_group(p, ops, nullptr, lx, ly, lz, rx, ry, rz, part, n_rot);
+        L[bx] = lx; L[bx | bz] = ly; L[bz] = lz;
+        Rh[bx] = rx; Rh[bx | bz] = ry; Rh[bz] = rz;
+    }
+    if (n_rot == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        double v = part[r];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp * R + r] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < n_rot) {
+        double total = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) total += red[w * R + threadIdx.x];
+        partials[(size_t)rot_gate(p, ops, threadIdx.x) * gridDim.x + blockIdx.x] = total;
+    }
+}
+
+__global__ void k_reduce_partials(const double *partials, int n_rot, int n_blocks,
+                                  double *grad_rot) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rot) return;
+    double acc = 0.0;
+    for (int b = 0; b < n_blocks; ++b) acc += partials[(size_t)r * n_blocks + b];
+    grad_rot[r] = acc;
+}
+
+__global__ void k_gather_grads(const double *grad_rot, const int32_t *param_ptr,
+                               const int32_t *param_rot, int n_params, double *grads) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_params) return;
+    double acc = 0.0;
+    for (int k = param_ptr[p]; k < param_ptr[p + 1]; ++k) acc += grad_rot[param_rot[k]];
+    grads[p] = acc;
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_resident(int n, const AdjointArgs &a, cudaStream_t st) {
+    switch (n) {
+    case 1: return launch_adjoint_n<1>(a, st);
+    case 2: return launch_adjoint_n<2>(a, st);
+    case 3: return launch_adjoint_n<3>(a, st);
+    case 4: return launch_adjoint_n<4>(a, st);
+    case 5: return launch_adjoint_n<5>(a, st);
+    case 6: return launch_adjoint_n<6>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int adjoint_stream_blocks(int n) {
+    const long long G = 1ll << (2 * n - 2);
+    long long b = (G + kAdjThreads - 1) / kAdjThreads;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &p,
+                                const DevOp *ops, double *partials, int, int,
+                                cudaStream_t st) {
+    k_adjoint_wire<<<adjoint_stream_blocks(n), kAdjThreads, 0, st>>>(lam, rho, n, p, ops,
+                                                                      partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double *partials, int n_rot, int n_blocks,
+                                   double *grad_rot, cudaStream_t st) {
+    if (n_rot == 0) return cudaSuccess;
+    k_reduce_partials<<<(n_rot + 127) / 128, 128, 0, st>>>(partials, n_rot, n_blocks, grad_rot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_grads(const double *grad_rot, const int32_t *param_ptr,
+                                const int32_t *param_rot, int n_params, double *grads,
+                                cudaStream_t st) {
+    if (n_params == 0) return cudaSuccess;
+    k_gather_grads<<<(n_params + 127) / 128, 128, 0, st>>>(grad_rot, param_ptr, param_rot,
+                                                           n_params, grads);
+    return cudaGetLastError();
+}
+
+}  // namespace stab

@@ -1,0 +1,206 @@
+// k_stream.cu -- angle encoding and the streamed (HBM-resident) passes.
+//
+// Streamed passes keep the vectors in global memory and apply one fused pass
+// per launch to every vector of the batch: a P_WIRE pass reads each group of
+// the pass's wire once, runs all of the wire's ops on it in registers and
+// writes it back in place; a P_CLIFF pass gathers every entry through the
+// pass's signed permutation into a second buffer.
+#include <cuda_runtime.h>
+
+#include "device_ops.cuh"
+#include "launch.h"
+
+namespace stab {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(uint64_t work, int threads) {
+    uint64_t b = (work + threads - 1) / threads;
+    const uint64_t cap = 152ull * 16ull;  // grid-stride beyond 16 CTAs per SM
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// 3x3 maps on the (X, Y, Z) coefficients of one wire (new = M old), Table I
+// rows; Clifford gates as signed permutation matrices.
+__device__ void gate_matrix3(const RawGate &g, const double *thetas, double M[9]) {
+    for (int k = 0; k < 9; ++k) M[k] = 0.0;
+    double c = 1.0, s = 0.0;
+    if (g.op >= 8) sincos(thetas[g.param], &s, &c);
+    switch (g.op) {
+    case 0:  // H: X <- Z, Y <- -Y, Z <- X
+        M[2] = 1.0; M[4] = -1.0; M[6] = 1.0; break;
+    case 1:  // S: X <- -Y, Y <- X
+        M[1] = -1.0; M[3] = 1.0; M[8] = 1.0; break;
+    case 2:  // Sdg: X <- Y, Y <- -X
+        M[1] = 1.0; M[3] = -1.0; M[8] = 1.0; break;
+    case 3:  // X: Y, Z negated
+        M[0] = 1.0; M[4] = -1.0; M[8] = -1.0; break;
+    case 4:  // Y: X, Z negated
+        M[0] = -1.0; M[4] = 1.0; M[8] = -1.0; break;
+    case 5:  // Z: X, Y negated
+        M[0] = -1.0; M[4] = -1.0; M[8] = 1.0; break;
+    case 8:  // RX: Y' = cY - sZ, Z' = sY + cZ
+        M[0] = 1.0; M[4] = c; M[5] = -s; M[7] = s; M[8] = c; break;
+    case 9:  // RY: X' = cX + sZ, Z' = -sX + cZ
+        M[0] = c; M[2] = s; M[4] = 1.0; M[6] = -s; M[8] = c; break;
+    case 10: // RZ: X' = cX - sY, Y' = sX + cY
+        M[0] = c; M[1] = -s; M[3] = s; M[4] = c; M[8] = 1.0; break;
+    default:
+        M[0] = M[4] = M[8] = 1.0; break;
+    }
+}
+
+__global__ void k_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
+                         const int32_t *map_gate_idx, const RawGate *gates, const double *thetas) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_ops && ops[i].kind == K_ROT) {
+        // Reduce theta to phi in [-pi/2, pi/2] up to a factor R(pi) = -1 on
+        // the pair, then store the shear coefficients of R(phi).
+        const double two_pi = 6.283185307179586476925286766559;
+        const double pi = 3.1415926535897932384626433832795;
+        double phi = remainder(thetas[ops[i].param], two_pi);
+        uint16_t neg = 0;
+        if (phi > 0.5 * pi) { phi -= pi; neg = 1; }
+        else if (phi < -0.5 * pi) { phi += pi; neg = 1; }
+        ops[i].t = -tan(0.5 * phi);
+        ops[i].s = sin(phi);
+        ops[i].perm = neg;
+    }
+    if (i < n_maps) {
+        double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        const DevMap3 &mp = maps[i];
+        for (int k = 0; k < mp.count; ++k) {
+            double G[9], R[9];
+            gate_matrix3(gates[map_gate_idx[mp.first + k]], thetas, G);
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c)
+                    R[3 * r + c] = G[3 * r] * M[c] + G[3 * r + 1] * M[3 + c] + G[3 * r + 2] * M[6 + c];
+            for (int k2 = 0; k2 < 9; ++k2) M[k2] = R[k2];
+        }
+        for (int k = 0; k < 9; ++k) maps[i].m[k] = M[k];
+    }
+}
+
+__global__ void k_fill(double *vec, int n, int n_vec, int init) {
+    const uint64_t E = 1ull << (2 * n);
+    const uint64_t total = E * (uint64_t)n_vec;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = t >> (2 * n), i = t & (E - 1);
+        double val = 0.0;
+        if (init == INIT_RHO0) val = i < (1ull << n) ? 1.0 : 0.0;
+        else if (init == INIT_GENERATOR) val = (i == (1ull << v)) ? 1.0 : 0.0;
+        vec[t] = val;
+    }
+}
+
+__global__ void k_scatter_terms(double *vec, const DevTerm *terms, int n_terms) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_terms) vec[terms[k].idx] = terms[k].coeff;
+}
+
+__global__ void __launch_bounds__(kThreads) k_stream_wire(double *vec, int n, int n_vec, DevPass p,
+                                                          const DevOp *ops, const DevMap3 *maps,
+                                                          int inverse) {
+    const int q = p.q;
+    const uint64_t E = 1ull << (2 * n);
+    const uint64_t G = E >> 2;
+    const uint64_t total = G * (uint64_t)n_vec;
+    const uint64_t bx = 1ull << (n + q), bz = 1ull << q;
+    const int n_ops = p.n_ops;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = t >> (2 * n - 2), g = t & (G - 1);
+        double *base = vec + v * E + group_base(g, n, q);
+        double x = base[bx], y = base[bx | bz], z = base[bz];
+        for (int j = 0; j < n_ops; ++j) {
+            const DevOp op = ops[p.first + (inverse ? n_ops - 1 - j : j)];
+            apply_op1(x, y, z, op, maps, inverse);
+        }
+        base[bx] = x;
+        base[bx | bz] = y;
+        base[bz] = z;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_stream_cliff(const double *__restrict__ src,
+                                                           double *__restrict__ dst, int n,
+                                                           int n_vec, DevPass p, const DevOp *ops,
+                                                           int inverse) {
+    const uint64_t E = 1ull << (2 * n);
+    const uint64_t total = E * (uint64_t)n_vec;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = t >> (2 * n), i = t & (E - 1);
+        uint32_t neg = 0;
+        const uint64_t j = pull_pass(i, n, ops + p.first, p.n_ops, inverse, neg);
+        dst[t] = flip(src[v * E + j], neg);
+    }
+}
+
+// Deterministic sum of the 2^n x-free coefficients of each vector (one CTA
+// per vector, fixed order).
+__global__ void __launch_bounds__(kThreads) k_xfree_sum(const double *vec, int n, double *out) {
+    __shared__ double red[kThreads / 32];
+    const uint64_t E = 1ull << (2 * n);
+    const double *v = vec + blockIdx.x * E;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (1 << n); i += blockDim.x) acc += v[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double total = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) total += red[w];
+        out[blockIdx.x] = total;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
+                          const int32_t *map_gate_idx, const RawGate *gates, const double *thetas,
+                          cudaStream_t st) {
+    const int work = n_ops > n_maps ? n_ops : n_maps;
+    if (work == 0) return cudaSuccess;
+    k_encode<<<(work + 127) / 128, 128, 0, st>>>(ops, n_ops, maps, n_maps, map_gate_idx, gates,
+                                                 thetas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double *vec, int n, int n_vec, int init, const DevTerm *terms,
+                        int n_terms, cudaStream_t st) {
+    const uint64_t total = (1ull << (2 * n)) * (uint64_t)n_vec;
+    k_fill<<<grid_for(total, kThreads), kThreads, 0, st>>>(vec, n, n_vec, init);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || init != INIT_TERMS || n_terms == 0) return e;
+    k_scatter_terms<<<(n_terms + 127) / 128, 128, 0, st>>>(vec, terms, n_terms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_wire(double *vec, int n, int n_vec, const DevPass &p, const DevOp *ops,
+                               const DevMap3 *maps, int inverse, cudaStream_t st) {
+    const uint64_t total = (1ull << (2 * n - 2)) * (uint64_t)n_vec;
+    k_stream_wire<<<grid_for(total, kThreads), kThreads, 0, st>>>(vec, n, n_vec, p, ops, maps,
+                                                                   inverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_cliff(const double *src, double *dst, int n, int n_vec,
+                                const DevPass &p, const DevOp *ops, int inverse, cudaStream_t st) {
+    const uint64_t total = (1ull << (2 * n)) * (uint64_t)n_vec;
+    k_stream_cliff<<<grid_for(total, kThreads), kThreads, 0, st>>>(src, dst, n, n_vec, p, ops,
+                                                                    inverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xfree_sum(const double *vec, int n, int n_vec, double *out, cudaStream_t st) {
+    k_xfree_sum<<<n_vec, kThreads, 0, st>>>(vec, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace stab

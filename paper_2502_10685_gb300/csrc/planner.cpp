@@ -1,0 +1,274 @@
+// planner.cpp -- host-side validation, gate encoding and pass planning (see planner.h).
+#include "planner.h"
+
+#include "launch.h"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+namespace stab {
+
+namespace {
+
+bool is_two_qubit(int op) { return op == STAB_CX || op == STAB_CZ; }
+bool is_rotation(int op) { return op == STAB_RX || op == STAB_RY || op == STAB_RZ; }
+
+uint32_t make_perm(int s0, int n0, int s1, int n1, int s2, int n2) {
+    return (uint32_t)(s0 | (n0 << 2) | (s1 << 3) | (n1 << 5) | (s2 << 6) | (n2 << 8));
+}
+
+}  // namespace
+
+// Slots 0, 1, 2 = X, Y, Z; new[o] = (-1)^neg old[src] (Table I rows H and S;
+// S^dagger, X, Y, Z are the standard conjugations).
+uint32_t clifford_perm_code(int op) {
+    switch (op) {
+    case STAB_H: return make_perm(2, 0, 1, 1, 0, 0);    // X <- Z, Y <- -Y, Z <- X
+    case STAB_S: return make_perm(1, 1, 0, 0, 2, 0);    // X <- -Y, Y <- X
+    case STAB_SDG: return make_perm(1, 0, 0, 1, 2, 0);  // X <- Y, Y <- -X
+    case STAB_X: return make_perm(0, 0, 1, 1, 2, 1);    // Y, Z negated
+    case STAB_Y: return make_perm(0, 1, 1, 0, 2, 1);    // X, Z negated
+    case STAB_Z: return make_perm(0, 1, 1, 1, 2, 0);    // X, Y negated
+    default: return kPermIdentity;
+    }
+}
+
+uint32_t perm_compose(uint32_t first, uint32_t then) {
+    uint32_t out = 0;
+    for (int o = 0; o < 3; ++o) {
+        uint32_t s2 = (then >> (3 * o)) & 3u, n2 = (then >> (3 * o + 2)) & 1u;
+        uint32_t s1 = (first >> (3 * s2)) & 3u, n1 = (first >> (3 * s2 + 2)) & 1u;
+        out |= (s1 | ((n1 ^ n2) << 2)) << (3 * o);
+    }
+    return out;
+}
+
+uint32_t perm_inverse(uint32_t code) {
+    uint32_t out = 0;
+    for (int o = 0; o < 3; ++o) {
+        uint32_t s = (code >> (3 * o)) & 3u, ng = (code >> (3 * o + 2)) & 1u;
+        out |= (o | (ng << 2)) << (3 * s);
+    }
+    return out;
+}
+
+int validate_gates(int n, const stab_gate *gates, int64_t m, int64_t n_params, std::string *msg) {
+    if (m < 0 || n_params < 0) return STAB_E_RANGE;
+    if (m > 0 && gates == nullptr) return STAB_E_INVAL;
+    if (m > (int64_t)INT32_MAX / 2) return STAB_E_RANGE;
+    for (int64_t i = 0; i < m; ++i) {
+        const stab_gate &g = gates[i];
+        if (g.op > STAB_RZ || g.flags != 0 || g.q0 >= n) {
+            if (msg) *msg = "gate " + std::to_string(i) + ": bad opcode, flags or qubit";
+            return STAB_E_INVAL;
+        }
+        if (is_two_qubit(g.op) && (g.q1 >= n || g.q1 == g.q0)) {
+            if (msg) *msg = "gate " + std::to_string(i) + ": bad second qubit";
+            return STAB_E_INVAL;
+        }
+        if (is_rotation(g.op) && (g.param < 0 || g.param >= n_params)) {
+            if (msg) *msg = "gate " + std::to_string(i) + ": angle slot out of range";
+            return STAB_E_RANGE;
+        }
+    }
+    return STAB_OK;
+}
+
+int validate_thetas(const double *thetas, int64_t n_params) {
+    if (n_params > 0 && thetas == nullptr) return STAB_E_INVAL;
+    for (int64_t j = 0; j < n_params; ++j)
+        if (!std::isfinite(thetas[j])) return STAB_E_NONFINITE;
+    return STAB_OK;
+}
+
+namespace {
+
+struct Emitter {
+    HostPlan *P;
+    PlanMode mode;
+    const std::vector<int32_t> *rot_ordinal;
+
+    void emit_cliff(const stab_gate *gates, int64_t i0, int64_t i1) {
+        DevPass p{};
+        p.type = P_CLIFF;
+        p.first = (uint32_t)P->ops.size();
+        for (int64_t i = i0; i < i1; ++i) {
+            DevOp op{};
+            op.kind = gates[i].op == STAB_CX ? K_CX : K_CZ;
+            op.q = gates[i].q0;
+            op.q1 = gates[i].q1;
+            op.param = -1;
+            op.gate = -1;
+            P->ops.push_back(op);
+        }
+        p.n_ops = (uint16_t)(i1 - i0);
+        P->passes.push_back(p);
+    }
+
+    // One wire's run (gate indices in order) -> one or more P_WIRE passes.
+    void emit_wire(const stab_gate *gates, int q, const std::vector<int64_t> &run) {
+        int n_rot = 0;
+        for (int64_t i : run) n_rot += is_rotation(gates[i].op);
+        if (mode == PLAN_FUSED && n_rot > 3) {
+            DevMap3 mp{};
+            mp.first = (int32_t)P->map_gate_idx.size();
+            mp.count = (int32_t)run.size();
+            for (int64_t i : run) P->map_gate_idx.push_back((int32_t)i);
+            DevOp op{};
+            op.kind = K_MAP3;
+            op.q = (uint8_t)q;
+            op.param = (int32_t)P->maps.size();
+            op.gate = -1;
+            P->maps.push_back(mp);
+            DevPass p{};
+            p.type = P_WIRE;
+            p.q = (uint8_t)q;
+            p.first = (uint32_t)P->ops.size();
+            p.n_ops = 1;
+            P->ops.push_back(op);
+            P->passes.push_back(p);
+            return;
+        }
+        DevPass p{};
+        p.type = P_WIRE;
+        p.q = (uint8_t)q;
+        p.first = (uint32_t)P->ops.size();
+        int rot_in_pass = 0;
+        uint32_t pending = kPermIdentity;
+        auto flush_perm = [&]() {
+            if (pending != kPermIdentity) {
+                DevOp op{};
+                op.kind = K_PERM;
+                op.q = (uint8_t)q;
+                op.param = -1;
+                op.gate = -1;
+                op.perm = (uint16_t)pending;
+                op.perm_inv = (uint16_t)perm_inverse(pending);
+                P->ops.push_back(op);
+            }
+            pending = kPermIdentity;
+        };
+        auto close_pass = [&]() {
+            p.n_ops = (uint16_t)(P->ops.size() - p.first);
+            if (p.n_ops > 0) P->passes.push_back(p);
+            p.first = (uint32_t)P->ops.size();
+            rot_in_pass = 0;
+        };
+        for (int64_t i : run) {
+            const int op = gates[i].op;
+            if (!is_rotation(op)) {
+                pending = perm_compose(pending, clifford_perm_code(op));
+                if (mode == PLAN_PLAIN) {
+                    flush_perm();
+                    close_pass();
+                }
+                continue;
+            }
+            if (mode == PLAN_GRAD && rot_in_pass == kRotPerGradPass) {
+                flush_perm();
+                close_pass();
+            }
+            flush_perm();
+            DevOp r{};
+            r.kind = K_ROT;
+            r.q = (uint8_t)q;
+            r.axis = (uint8_t)(op == STAB_RX ? AX_X : op == STAB_RY ? AX_Y : AX_Z);
+            r.param = gates[i].param;
+            r.gate = (*rot_ordinal)[i];
+            P->ops.push_back(r);
+            ++rot_in_pass;
+            if (mode == PLAN_PLAIN) close_pass();
+        }
+        flush_perm();
+        close_pass();
+    }
+};
+
+}  // namespace
+
+void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
+                HostPlan *out) {
+    HostPlan &P = *out;
+    P = HostPlan();
+    P.n_params = n_params;
+    P.raw.resize((size_t)m);
+    for (int64_t i = 0; i < m; ++i) {
+        P.raw[i].op = gates[i].op;
+        P.raw[i].q0 = gates[i].q0;
+        P.raw[i].q1 = gates[i].q1;
+        P.raw[i].flags = 0;
+        P.raw[i].param = gates[i].param;
+    }
+    // rotation ordinals (gradient slots, gate order) and the slot -> ordinals CSR
+    std::vector<int32_t> rot_ordinal((size_t)m, -1);
+    std::vector<int32_t> count((size_t)n_params, 0);
+    int32_t nr = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (is_rotation(gates[i].op)) {
+            rot_ordinal[i] = nr++;
+            count[gates[i].param]++;
+        }
+    }
+    P.n_rot = nr;
+    P.param_ptr.assign((size_t)n_params + 1, 0);
+    for (int64_t j = 0; j < n_params; ++j) P.param_ptr[j + 1] = P.param_ptr[j] + count[j];
+    P.param_rot.assign((size_t)nr, 0);
+    {
+        std::vector<int32_t> fill(P.param_ptr.begin(), P.param_ptr.end() - 1);
+        for (int64_t i = 0; i < m; ++i)
+            if (is_rotation(gates[i].op)) P.param_rot[fill[gates[i].param]++] = rot_ordinal[i];
+    }
+
+    Emitter em{&P, mode, &rot_ordinal};
+    int64_t i = 0;
+    std::vector<std::vector<int64_t>> runs((size_t)n);
+    while (i < m) {
+        int64_t j = i;
+        if (is_two_qubit(gates[i].op)) {
+            while (j < m && is_two_qubit(gates[j].op)) ++j;
+            if (mode == PLAN_PLAIN) {
+                for (int64_t k = i; k < j; ++k) em.emit_cliff(gates, k, k + 1);
+            } else {
+                // a P_CLIFF pass holds at most 65535 ops
+                for (int64_t k = i; k < j; k += 65535) em.emit_cliff(gates, k, std::min(j, k + 65535));
+            }
+        } else {
+            while (j < m && !is_two_qubit(gates[j].op)) ++j;
+            if (mode == PLAN_PLAIN) {
+                for (int64_t k = i; k < j; ++k) em.emit_wire(gates, gates[k].q0, {k});
+            } else {
+                for (auto &r : runs) r.clear();
+                for (int64_t k = i; k < j; ++k) runs[gates[k].q0].push_back(k);
+                for (int q = 0; q < n; ++q) {
+                    if (runs[q].empty()) continue;
+                    // a P_WIRE pass holds at most 65535 ops; cut longer unfused runs
+                    const auto &r = runs[q];
+                    for (size_t k = 0; k < r.size(); k += 16384) {
+                        std::vector<int64_t> part(r.begin() + k,
+                                                  r.begin() + std::min(r.size(), k + 16384));
+                        em.emit_wire(gates, q, part);
+                    }
+                }
+            }
+        }
+        i = j;
+    }
+}
+
+int encode_terms(int n, const stab_term *O, int64_t n_terms, std::vector<DevTerm> *out) {
+    out->clear();
+    if (n_terms < 0) return STAB_E_RANGE;
+    if (n_terms > 0 && O == nullptr) return STAB_E_INVAL;
+    const uint64_t lim = 1ull << n;
+    std::map<uint64_t, double> acc;
+    for (int64_t k = 0; k < n_terms; ++k) {
+        if (O[k].x >= lim || O[k].z >= lim) return STAB_E_INVAL;
+        if (!std::isfinite(O[k].coeff)) return STAB_E_NONFINITE;
+        acc[O[k].z | (O[k].x << n)] += O[k].coeff;
+    }
+    for (auto &kv : acc) out->push_back(DevTerm{kv.second, kv.first});
+    return STAB_OK;
+}
+
+}  // namespace stab

@@ -1,0 +1,54 @@
+// planner.h -- host-side validation, encoding and pass planning.
+//
+// Dividing (Sec. III-A): the gate list is cut into maximal blocks of
+// single-qubit gates (the paper's U_k) and of two-qubit Clifford gates (V_k).
+// Inside a U_k block, the gates of each wire form the run U_{k,j}; gates on
+// different wires commute, so each run becomes one P_WIRE pass.  A run with
+// more than three rotations is composed into one 3x3 map (the paper's
+// LUT_non-CX entry, composed on the device from the angles); shorter runs keep
+// their rotations (three FMAs per pair each, fewer than the nine of a map)
+// with adjacent Clifford gates folded into signed permutations.  Each V_k
+// block becomes one P_CLIFF pass.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/stab.h"
+#include "stab_internal.h"
+
+namespace stab {
+
+enum PlanMode { PLAN_FUSED = 0, PLAN_GRAD = 1, PLAN_PLAIN = 2 };
+
+struct HostPlan {
+    std::vector<DevPass> passes;
+    std::vector<DevOp> ops;
+    std::vector<DevMap3> maps;
+    std::vector<int32_t> map_gate_idx;
+    std::vector<RawGate> raw;            // copy of the gate list (map composition reads it)
+    std::vector<int32_t> param_ptr;      // CSR: angle slot -> rotation ordinals
+    std::vector<int32_t> param_rot;
+    int32_t n_rot = 0;
+    int64_t n_params = 0;
+};
+
+// Returns STAB_OK or an error code; msg receives a description on error.
+int validate_gates(int n, const stab_gate *gates, int64_t m, int64_t n_params, std::string *msg);
+int validate_thetas(const double *thetas, int64_t n_params);
+
+// Builds the pass list.  gates must be valid.
+void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
+                HostPlan *out);
+
+// Signed permutation codes of the single-qubit Clifford opcodes on (X, Y, Z).
+uint32_t clifford_perm_code(int op);
+uint32_t perm_compose(uint32_t first, uint32_t then);   // apply first, then then
+uint32_t perm_inverse(uint32_t code);
+constexpr uint32_t kPermIdentity = 0u | (1u << 3) | (2u << 6);
+
+// Observable terms -> deduplicated device terms (index z | x << n).
+int encode_terms(int n, const stab_term *O, int64_t n_terms, std::vector<DevTerm> *out);
+
+}  // namespace stab

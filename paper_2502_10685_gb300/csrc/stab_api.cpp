@@ -1,0 +1,638 @@
+// stab_api.cpp -- the C interface (include/stab.h): contexts, device buffers,
+// circuit loading, and the launch sequences of every entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/stab.h"
+#include "launch.h"
+#include "planner.h"
+
+using namespace stab;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+#define CK(expr)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (expr);                                    \
+        if (e_ != cudaSuccess) {                                    \
+            g_last_cuda = (int)e_;                                  \
+            return STAB_E_CUDA;                                     \
+        }                                                           \
+    } while (0)
+
+#define RC(expr)                 \
+    do {                         \
+        int r_ = (expr);         \
+        if (r_ != STAB_OK) return r_; \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// A plan uploaded to the device: one buffer holding passes, ops, maps, map
+// gate indices, raw gates and the slot CSR.
+struct DevPlan {
+    HostPlan host;
+    DevBuf buf;
+    Program prog{};
+    const int32_t *map_gate_idx = nullptr;
+    const RawGate *raw = nullptr;
+    const int32_t *param_ptr = nullptr;
+    const int32_t *param_rot = nullptr;
+    bool built = false;
+    bool encoded = false;
+};
+
+}  // namespace
+
+struct stab_ctx {
+    int n = 0;
+    int device = 0;
+    int kernel = STAB_KERNEL_AUTO;
+    int fuse = 1;
+    cudaStream_t st = nullptr;
+    cudaStream_t aux = nullptr;
+    bool own_st = false;
+    cudaEvent_t ev_ready = nullptr;    // plan uploaded and encoded (on st)
+    cudaEvent_t ev_aux = nullptr;      // aux work done
+    cudaEvent_t ev_stage = nullptr;    // staging buffer free
+    stab_alloc_fn alloc = nullptr;
+    stab_free_fn free = nullptr;
+    void *user = nullptr;
+
+    bool loaded = false;
+    bool gens_valid = false;
+    std::vector<stab_gate> gates;
+    int64_t n_params = 0;
+
+    DevPlan fwd, grad;
+    DevBuf thetas, gens, gens_tmp, lam, rho, tmp, tmp2, terms, scal, grad_rot, partials, grads;
+    int32_t n_obs_terms = 0;
+    bool obs_loaded = false;
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+    double *gens_cur = nullptr;      // buffer holding the evolved generators
+
+    void *stage = nullptr;           // pinned host staging
+    size_t stage_bytes = 0;
+    void *aux_stage = nullptr;
+    size_t aux_stage_bytes = 0;
+    int64_t launches = 0;
+
+    int dalloc(DevBuf &b, size_t bytes, cudaStream_t s) {
+        if (b.bytes >= bytes && b.p) return STAB_OK;
+        dfree(b, s);
+        bytes = align256(bytes ? bytes : 256);
+        void *p = nullptr;
+        if (alloc) {
+            p = alloc(bytes, (void *)s, user);
+            if (!p) return STAB_E_NOMEM;
+        } else {
+            cudaError_t e = cudaMallocAsync(&p, bytes, s);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                return e == cudaErrorMemoryAllocation ? STAB_E_NOMEM : (g_last_cuda = (int)e, STAB_E_CUDA);
+            }
+        }
+        b.p = p;
+        b.bytes = bytes;
+        return STAB_OK;
+    }
+    void dfree(DevBuf &b, cudaStream_t s) {
+        if (!b.p) return;
+        // a buffer may be in use on either stream of the context
+        if (st) cudaStreamSynchronize(st);
+        if (aux) cudaStreamSynchronize(aux);
+        if (free) free(b.p, b.bytes, (void *)s, user);
+        else cudaFreeAsync(b.p, s);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    int host_stage(void *&buf, size_t &cap, size_t bytes) {
+        if (cap >= bytes && buf) return STAB_OK;
+        if (buf) cudaFreeHost(buf);
+        buf = nullptr;
+        cap = 0;
+        CK(cudaMallocHost(&buf, bytes));
+        cap = bytes;
+        return STAB_OK;
+    }
+    size_t vec_bytes() const { return (sizeof(double) << (2 * n)); }
+    bool use_resident() const {
+        return (kernel == STAB_KERNEL_AUTO || kernel == STAB_KERNEL_RESIDENT) &&
+               n <= kMaxResidentQubits;
+    }
+    bool use_resident_adjoint() const {
+        return (kernel == STAB_KERNEL_AUTO || kernel == STAB_KERNEL_RESIDENT) &&
+               n <= kMaxResidentAdjoint;
+    }
+    PlanMode fwd_mode() const {
+        return (kernel == STAB_KERNEL_PLAIN || !fuse) ? PLAN_PLAIN : PLAN_FUSED;
+    }
+};
+
+namespace {
+
+// Uploads a host plan into its device buffer (one copy from pinned staging).
+int upload_plan(stab_ctx *c, DevPlan &P) {
+    HostPlan &H = P.host;
+    const size_t b_pass = align256(H.passes.size() * sizeof(DevPass));
+    const size_t b_ops = align256(H.ops.size() * sizeof(DevOp));
+    const size_t b_maps = align256(H.maps.size() * sizeof(DevMap3));
+    const size_t b_midx = align256(H.map_gate_idx.size() * sizeof(int32_t));
+    const size_t b_raw = align256(H.raw.size() * sizeof(RawGate));
+    const size_t b_pptr = align256(H.param_ptr.size() * sizeof(int32_t));
+    const size_t b_prot = align256(H.param_rot.size() * sizeof(int32_t));
+    const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot;
+    RC(c->dalloc(P.buf, total, c->st));
+    CK(cudaEventSynchronize(c->ev_stage));
+    RC(c->host_stage(c->stage, c->stage_bytes, total));
+    char *h = (char *)c->stage;
+    char *d = (char *)P.buf.p;
+    size_t off = 0;
+    auto put = [&](const void *src, size_t bytes, size_t span) {
+        if (bytes) std::memcpy(h + off, src, bytes);
+        const size_t at = off;
+        off += span;
+        return d + at;
+    };
+    P.prog.passes = (const DevPass *)put(H.passes.data(), H.passes.size() * sizeof(DevPass), b_pass);
+    P.prog.ops = (const DevOp *)put(H.ops.data(), H.ops.size() * sizeof(DevOp), b_ops);
+    P.prog.maps = (const DevMap3 *)put(H.maps.data(), H.maps.size() * sizeof(DevMap3), b_maps);
+    P.map_gate_idx = (const int32_t *)put(H.map_gate_idx.data(), H.map_gate_idx.size() * 4, b_midx);
+    P.raw = (const RawGate *)put(H.raw.data(), H.raw.size() * sizeof(RawGate), b_raw);
+    P.param_ptr = (const int32_t *)put(H.param_ptr.data(), H.param_ptr.size() * 4, b_pptr);
+    P.param_rot = (const int32_t *)put(H.param_rot.data(), H.param_rot.size() * 4, b_prot);
+    P.prog.n_passes = (int32_t)H.passes.size();
+    P.prog.n_ops = (int32_t)H.ops.size();
+    CK(cudaMemcpyAsync(P.buf.p, h, total, cudaMemcpyHostToDevice, c->st));
+    CK(cudaEventRecord(c->ev_stage, c->st));
+    c->h2d_bytes += (int64_t)total;
+    P.built = true;
+    P.encoded = false;
+    return STAB_OK;
+}
+
+int encode_plan(stab_ctx *c, DevPlan &P) {
+    const int n_ops = P.prog.n_ops, n_maps = (int)P.host.maps.size();
+    if (n_ops == 0 && n_maps == 0) {
+        P.encoded = true;
+        return STAB_OK;
+    }
+    CK(launch_encode(const_cast<DevOp *>(P.prog.ops), n_ops, const_cast<DevMap3 *>(P.prog.maps),
+                     n_maps, P.map_gate_idx, P.raw, (const double *)c->thetas.p, c->st));
+    c->launches++;
+    P.encoded = true;
+    return STAB_OK;
+}
+
+int upload_thetas_host(stab_ctx *c, const double *thetas) {
+    const size_t bytes = (size_t)(c->n_params > 0 ? c->n_params : 1) * sizeof(double);
+    RC(c->dalloc(c->thetas, bytes, c->st));
+    if (c->n_params == 0) return STAB_OK;
+    CK(cudaEventSynchronize(c->ev_stage));
+    RC(c->host_stage(c->stage, c->stage_bytes, bytes));
+    std::memcpy(c->stage, thetas, (size_t)c->n_params * sizeof(double));
+    CK(cudaMemcpyAsync(c->thetas.p, c->stage, (size_t)c->n_params * sizeof(double),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaEventRecord(c->ev_stage, c->st));
+    c->h2d_bytes += c->n_params * (int64_t)sizeof(double);
+    return STAB_OK;
+}
+
+// Uploads deduplicated observable terms on the main stream (pinned staging).
+int upload_terms(stab_ctx *c, const stab_term *O, int64_t n_terms) {
+    std::vector<DevTerm> t;
+    RC(encode_terms(c->n, O, n_terms, &t));
+    const size_t bytes = (t.size() ? t.size() : 1) * sizeof(DevTerm);
+    // the aux stream may still read the previous terms
+    CK(cudaStreamSynchronize(c->aux));
+    RC(c->dalloc(c->terms, bytes, c->st));
+    if (!t.empty()) {
+        CK(cudaEventSynchronize(c->ev_stage));
+        RC(c->host_stage(c->stage, c->stage_bytes, bytes));
+        std::memcpy(c->stage, t.data(), t.size() * sizeof(DevTerm));
+        CK(cudaMemcpyAsync(c->terms.p, c->stage, t.size() * sizeof(DevTerm),
+                           cudaMemcpyHostToDevice, c->st));
+        CK(cudaEventRecord(c->ev_stage, c->st));
+        c->h2d_bytes += (int64_t)(t.size() * sizeof(DevTerm));
+    }
+    c->n_obs_terms = (int32_t)t.size();
+    return STAB_OK;
+}
+
+// Streamed propagation of n_vec vectors through a plan; *cur / *alt are the
+// ping-pong buffers (the result ends in *cur).
+int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int n_vec,
+                 int inverse, cudaStream_t s) {
+    const auto &passes = P.host.passes;
+    const int np = (int)passes.size();
+    for (int k = 0; k < np; ++k) {
+        const DevPass &p = passes[inverse ? np - 1 - k : k];
+        if (p.type == P_WIRE) {
+            CK(launch_stream_wire(*cur, c->n, n_vec, p, P.prog.ops, P.prog.maps, inverse, s));
+        } else {
+            CK(launch_stream_cliff(*cur, *alt, c->n, n_vec, p, P.prog.ops, inverse, s));
+            double *t = *cur;
+            *cur = *alt;
+            *alt = t;
+        }
+        c->launches++;
+    }
+    return STAB_OK;
+}
+
+int ensure_grad_plan(stab_ctx *c) {
+    if (!c->grad.built) {
+        build_plan(c->n, c->gates.data(), (int64_t)c->gates.size(), c->n_params, PLAN_GRAD,
+                   &c->grad.host);
+        RC(upload_plan(c, c->grad));
+    }
+    if (!c->grad.encoded) RC(encode_plan(c, c->grad));
+    CK(cudaEventRecord(c->ev_ready, c->st));
+    return STAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void stab_default_opts(stab_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->device = -1;
+    o->kernel = STAB_KERNEL_AUTO;
+    o->fuse = 1;
+}
+
+int stab_version(void) { return STAB_VERSION; }
+
+int stab_last_cuda_error(void) { return g_last_cuda; }
+
+const char *stab_error_string(int s) {
+    switch (s) {
+    case STAB_OK: return "ok";
+    case STAB_E_INVAL: return "invalid argument";
+    case STAB_E_RANGE: return "value out of range";
+    case STAB_E_NOMEM: return "out of device memory";
+    case STAB_E_TIMEOUT: return "device wait timed out";
+    case STAB_E_NONFINITE: return "non-finite angle or coefficient";
+    case STAB_E_CUDA: return "CUDA runtime error";
+    case STAB_E_STATE: return "call out of order";
+    case STAB_E_BUSY: return "queue full";
+    default: return "unknown status";
+    }
+}
+
+int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
+    if (!out) return STAB_E_INVAL;
+    *out = nullptr;
+    if (n < 1 || n > STAB_MAX_QUBITS) return STAB_E_RANGE;
+    stab_opts o;
+    stab_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.kernel < STAB_KERNEL_AUTO || o.kernel > STAB_KERNEL_PLAIN) return STAB_E_INVAL;
+    if (o.kernel == STAB_KERNEL_RESIDENT && n > kMaxResidentQubits) return STAB_E_RANGE;
+    if ((o.alloc == nullptr) != (o.free == nullptr)) return STAB_E_INVAL;
+    stab_ctx *c = new (std::nothrow) stab_ctx();
+    if (!c) return STAB_E_NOMEM;
+    c->n = n;
+    c->kernel = o.kernel;
+    c->fuse = o.fuse;
+    c->alloc = o.alloc;
+    c->free = o.free;
+    c->user = o.alloc_user;
+    int dev = o.device;
+    cudaError_t e = cudaSuccess;
+    if (dev < 0) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e == cudaSuccess) {
+        c->device = dev;
+        if (o.stream) {
+            c->st = (cudaStream_t)o.stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+            c->own_st = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_stage, c->st);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        stab_destroy(c);
+        return STAB_E_CUDA;
+    }
+    *out = c;
+    return STAB_OK;
+}
+
+int stab_destroy(stab_ctx *c) {
+    if (!c) return STAB_OK;
+    cudaSetDevice(c->device);
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->aux) cudaStreamSynchronize(c->aux);
+    DevBuf *bufs[] = {&c->fwd.buf, &c->grad.buf, &c->thetas, &c->gens, &c->gens_tmp, &c->lam,
+                      &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
+                      &c->partials, &c->grads};
+    for (DevBuf *b : bufs) c->dfree(*b, c->st);
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->stage) cudaFreeHost(c->stage);
+    if (c->aux_stage) cudaFreeHost(c->aux_stage);
+    if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+    if (c->ev_aux) cudaEventDestroy(c->ev_aux);
+    if (c->ev_stage) cudaEventDestroy(c->ev_stage);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->own_st && c->st) cudaStreamDestroy(c->st);
+    delete c;
+    return STAB_OK;
+}
+
+int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const double *thetas,
+                      int64_t n_params) {
+    if (!c) return STAB_E_INVAL;
+    std::string msg;
+    RC(validate_gates(c->n, gates, m, n_params, &msg));
+    RC(validate_thetas(thetas, n_params));
+    CK(cudaSetDevice(c->device));
+    // new state is built before the old one is dropped only where cheap; on an
+    // error below the context reports STAB_E_STATE until a load succeeds
+    c->loaded = false;
+    c->gens_valid = false;
+    c->gates.assign(gates, gates + m);
+    c->n_params = n_params;
+    c->grad.built = false;
+    c->grad.encoded = false;
+    build_plan(c->n, gates, m, n_params, c->fwd_mode(), &c->fwd.host);
+    RC(upload_thetas_host(c, thetas));
+    RC(upload_plan(c, c->fwd));
+    RC(encode_plan(c, c->fwd));
+    CK(cudaEventRecord(c->ev_ready, c->st));
+    c->loaded = true;
+    return STAB_OK;
+}
+
+int stab_set_params(stab_ctx *c, const double *thetas, int is_device) {
+    if (!c) return STAB_E_INVAL;
+    if (!c->loaded) return STAB_E_STATE;
+    CK(cudaSetDevice(c->device));
+    if (is_device) {
+        if (c->n_params > 0) {
+            if (!thetas) return STAB_E_INVAL;
+            CK(cudaMemcpyAsync(c->thetas.p, thetas, (size_t)c->n_params * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->st));
+        }
+    } else {
+        RC(validate_thetas(thetas, c->n_params));
+        RC(upload_thetas_host(c, thetas));
+    }
+    RC(encode_plan(c, c->fwd));
+    c->grad.encoded = false;
+    c->gens_valid = false;
+    CK(cudaEventRecord(c->ev_ready, c->st));
+    return STAB_OK;
+}
+
+int stab_run_generators(stab_ctx *c) {
+    if (!c) return STAB_E_INVAL;
+    if (!c->loaded) return STAB_E_STATE;
+    CK(cudaSetDevice(c->device));
+    const int n = c->n;
+    const size_t bytes = c->vec_bytes() * (size_t)n;
+    RC(c->dalloc(c->gens, bytes, c->st));
+    if (c->use_resident()) {
+        ResidentArgs a{};
+        a.prog = c->fwd.prog;
+        a.inverse = 0;
+        a.init = INIT_GENERATOR;
+        a.n_vec = n;
+        a.out = (double *)c->gens.p;
+        CK(launch_resident(n, a, c->st));
+        c->launches++;
+        c->gens_cur = (double *)c->gens.p;
+    } else {
+        RC(c->dalloc(c->gens_tmp, bytes, c->st));
+        double *cur = (double *)c->gens.p, *alt = (double *)c->gens_tmp.p;
+        CK(launch_fill(cur, n, n, INIT_GENERATOR, nullptr, 0, c->st));
+        c->launches++;
+        RC(run_streamed(c, c->fwd, &cur, &alt, n, 0, c->st));
+        c->gens_cur = cur;
+    }
+    c->gens_valid = true;
+    return STAB_OK;
+}
+
+int stab_apply_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const double *thetas,
+                       int64_t n_params) {
+    RC(stab_load_circuit(c, gates, m, thetas, n_params));
+    return stab_run_generators(c);
+}
+
+int stab_get_generators(stab_ctx *c, double *out, int out_is_device) {
+    if (!c || !out) return STAB_E_INVAL;
+    if (!c->gens_valid) return STAB_E_STATE;
+    CK(cudaSetDevice(c->device));
+    const size_t bytes = c->vec_bytes() * (size_t)c->n;
+    if (out_is_device) {
+        CK(cudaMemcpyAsync(out, c->gens_cur, bytes, cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        CK(cudaMemcpyAsync(out, c->gens_cur, bytes, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        c->d2h_bytes += (int64_t)bytes;
+    }
+    return STAB_OK;
+}
+
+const double *stab_generators_device(stab_ctx *c) {
+    if (!c || !c->gens_valid) return nullptr;
+    return c->gens_cur;
+}
+
+int stab_set_observable(stab_ctx *c, const stab_term *O, int64_t n_terms) {
+    if (!c) return STAB_E_INVAL;
+    CK(cudaSetDevice(c->device));
+    c->obs_loaded = false;
+    RC(upload_terms(c, O, n_terms));
+    CK(cudaEventRecord(c->ev_ready, c->st));
+    c->obs_loaded = true;
+    return STAB_OK;
+}
+
+int stab_expect_async(stab_ctx *c, double *out_dev) {
+    if (!c || !out_dev) return STAB_E_INVAL;
+    if (!c->loaded || !c->obs_loaded) return STAB_E_STATE;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->aux;
+    CK(cudaStreamWaitEvent(s, c->ev_ready, 0));
+    const int32_t nt = c->n_obs_terms;
+    if (c->use_resident()) {
+        ResidentArgs a{};
+        a.prog = c->fwd.prog;
+        a.inverse = 1;
+        a.init = INIT_TERMS;
+        a.terms = (const DevTerm *)c->terms.p;
+        a.n_terms = nt;
+        a.n_vec = 1;
+        a.xfree_out = out_dev;
+        CK(launch_resident(c->n, a, s));
+        c->launches++;
+    } else {
+        RC(c->dalloc(c->lam, c->vec_bytes(), s));
+        RC(c->dalloc(c->tmp, c->vec_bytes(), s));
+        double *cur = (double *)c->lam.p, *alt = (double *)c->tmp.p;
+        CK(launch_fill(cur, c->n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, s));
+        c->launches += nt ? 2 : 1;
+        RC(run_streamed(c, c->fwd, &cur, &alt, 1, 1, s));
+        CK(launch_xfree_sum(cur, c->n, 1, out_dev, s));
+        c->launches++;
+    }
+    // join: later work on the main stream sees the result
+    CK(cudaEventRecord(c->ev_aux, s));
+    CK(cudaStreamWaitEvent(c->st, c->ev_aux, 0));
+    return STAB_OK;
+}
+
+int stab_expect(stab_ctx *c, const stab_term *O, int64_t n_terms, double *out) {
+    if (!c || !out) return STAB_E_INVAL;
+    if (!c->loaded) return STAB_E_STATE;
+    RC(stab_set_observable(c, O, n_terms));
+    RC(c->dalloc(c->scal, 64 * sizeof(double), c->st));
+    RC(stab_expect_async(c, (double *)c->scal.p));
+    CK(cudaEventSynchronize(c->ev_stage));
+    RC(c->host_stage(c->stage, c->stage_bytes, 64 * sizeof(double)));
+    double *h = (double *)c->stage;
+    CK(cudaMemcpyAsync(h, c->scal.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->d2h_bytes += (int64_t)sizeof(double);
+    *out = *h;
+    return STAB_OK;
+}
+
+int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
+    if (!c) return STAB_E_INVAL;
+    if (!c->loaded || !c->obs_loaded) return STAB_E_STATE;
+    if (c->n_params > 0 && !grads_dev) return STAB_E_INVAL;
+    CK(cudaSetDevice(c->device));
+    RC(ensure_grad_plan(c));
+    cudaStream_t s = c->aux;
+    CK(cudaStreamWaitEvent(s, c->ev_ready, 0));
+    const int32_t nt = c->n_obs_terms;
+    const int n = c->n;
+    const int n_rot = c->grad.host.n_rot;
+    RC(c->dalloc(c->scal, 64 * sizeof(double), s));
+    RC(c->dalloc(c->grad_rot, (size_t)(n_rot ? n_rot : 1) * sizeof(double), s));
+    double *e_out = expect_dev ? expect_dev : (double *)c->scal.p + 1;
+    if (c->use_resident_adjoint()) {
+        AdjointArgs a{};
+        a.prog = c->grad.prog;
+        a.terms = (const DevTerm *)c->terms.p;
+        a.n_terms = nt;
+        a.grad_rot = (double *)c->grad_rot.p;
+        a.expect_out = e_out;
+        CK(launch_adjoint_resident(n, a, s));
+        c->launches++;
+    } else {
+        const size_t vb = c->vec_bytes();
+        RC(c->dalloc(c->lam, vb, s));
+        RC(c->dalloc(c->rho, vb, s));
+        RC(c->dalloc(c->tmp, vb, s));
+        RC(c->dalloc(c->tmp2, vb, s));
+        const int nb = adjoint_stream_blocks(n);
+        RC(c->dalloc(c->partials, (size_t)(n_rot ? n_rot : 1) * nb * sizeof(double), s));
+        double *rho = (double *)c->rho.p, *rho_alt = (double *)c->tmp2.p;
+        double *lam = (double *)c->lam.p, *lam_alt = (double *)c->tmp.p;
+        CK(launch_fill(rho, n, 1, INIT_RHO0, nullptr, 0, s));
+        c->launches++;
+        RC(run_streamed(c, c->grad, &rho, &rho_alt, 1, 0, s));
+        CK(launch_fill(lam, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, s));
+        c->launches += nt ? 2 : 1;
+        const auto &passes = c->grad.host.passes;
+        for (int k = (int)passes.size() - 1; k >= 0; --k) {
+            const DevPass &p = passes[k];
+            if (p.type == P_WIRE) {
+                CK(launch_adjoint_wire(lam, rho, n, p, c->grad.prog.ops, (double *)c->partials.p,
+                                       0, n_rot, s));
+                c->launches++;
+            } else {
+                CK(launch_stream_cliff(lam, lam_alt, n, 1, p, c->grad.prog.ops, 1, s));
+                CK(launch_stream_cliff(rho, rho_alt, n, 1, p, c->grad.prog.ops, 1, s));
+                c->launches += 2;
+                std::swap(lam, lam_alt);
+                std::swap(rho, rho_alt);
+            }
+        }
+        CK(launch_reduce_partials((const double *)c->partials.p, n_rot, nb,
+                                  (double *)c->grad_rot.p, s));
+        CK(launch_xfree_sum(lam, n, 1, e_out, s));
+        c->launches += 2;
+    }
+    if (c->n_params > 0) {
+        CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
+                               c->grad.param_rot, (int)c->n_params, grads_dev, s));
+        c->launches++;
+    }
+    CK(cudaEventRecord(c->ev_aux, s));
+    CK(cudaStreamWaitEvent(c->st, c->ev_aux, 0));
+    return STAB_OK;
+}
+
+int stab_grad(stab_ctx *c, const stab_term *O, int64_t n_terms, double *expect_out,
+              double *grads_out) {
+    if (!c) return STAB_E_INVAL;
+    if (!c->loaded) return STAB_E_STATE;
+    if (c->n_params > 0 && !grads_out) return STAB_E_INVAL;
+    RC(stab_set_observable(c, O, n_terms));
+    RC(c->dalloc(c->grads, (size_t)(c->n_params ? c->n_params : 1) * sizeof(double), c->st));
+    RC(c->dalloc(c->scal, 64 * sizeof(double), c->st));
+    RC(stab_grad_async(c, (double *)c->scal.p, (double *)c->grads.p));
+    const size_t gbytes = (size_t)c->n_params * sizeof(double);
+    CK(cudaEventSynchronize(c->ev_stage));
+    RC(c->host_stage(c->stage, c->stage_bytes, gbytes + 64 * sizeof(double)));
+    double *h = (double *)c->stage;
+    CK(cudaMemcpyAsync(h, c->scal.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (gbytes) CK(cudaMemcpyAsync(h + 8, c->grads.p, gbytes, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->d2h_bytes += (int64_t)(gbytes + sizeof(double));
+    if (expect_out) *expect_out = h[0];
+    if (gbytes) std::memcpy(grads_out, h + 8, gbytes);
+    return STAB_OK;
+}
+
+int stab_synchronize(stab_ctx *c) {
+    if (!c) return STAB_E_INVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaStreamSynchronize(c->aux));
+    return STAB_OK;
+}
+
+int stab_plan_info(stab_ctx *c, int64_t *n_gates, int64_t *n_passes, int32_t *kernel) {
+    if (!c) return STAB_E_INVAL;
+    if (n_gates) *n_gates = (int64_t)c->gates.size();
+    if (n_passes) *n_passes = (int64_t)c->fwd.host.passes.size();
+    if (kernel) *kernel = c->use_resident() ? STAB_KERNEL_RESIDENT : STAB_KERNEL_STREAMED;
+    return STAB_OK;
+}
+
+int64_t stab_launch_count(stab_ctx *c) { return c ? c->launches : 0; }
+
+int stab_transfer_bytes(stab_ctx *c, int64_t *h2d, int64_t *d2h) {
+    if (!c) return STAB_E_INVAL;
+    if (h2d) *h2d = c->h2d_bytes;
+    if (d2h) *d2h = c->d2h_bytes;
+    return STAB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+"""Python binding of the C interface (include/stab.h): argument marshalling only.
+
+Every computation runs in libstab.so.  The module exposes the C entry points
+under their own names (``stab_create``, ``stab_apply_circuit``, ...) and a
+small ``Stab`` class that owns one context, routes its device allocations
+through PyTorch's caching allocator and queues its work on a PyTorch stream.
+
+Observables are lists of ``(coeff, string)`` (one letter per qubit, qubit 0
+first).  Generator outputs use the library layout index = z | (x << n).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Iterable, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _lib
+from ._lib import StabError, StabGate, StabOpts, StabTerm, check
+
+KERNELS = {"auto": 0, "resident": 1, "streamed": 2, "plain": 3}
+GATE_DTYPE = np.dtype([("op", "u1"), ("q0", "u1"), ("q1", "u1"), ("flags", "u1"),
+                       ("param", "<i4")])
+
+
+def _gates_ptr(gates) -> Tuple[np.ndarray, int]:
+    g = np.ascontiguousarray(gates)
+    if g.dtype.itemsize != 8 or g.dtype.names is None:
+        raise TypeError("gates must be records of the 8-byte stab_gate layout")
+    return g, g.ctypes.data
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def terms_from_observable(n: int, observable: Iterable[Tuple[float, str]]) -> np.ndarray:
+    """[(coeff, "XZIY"...)] -> stab_term records (coeff, x mask, z mask)."""
+    obs = list(observable)
+    out = np.zeros(len(obs), dtype=[("coeff", "<f8"), ("x", "<u8"), ("z", "<u8")])
+    for k, (c, s) in enumerate(obs):
+        if len(s) != n:
+            raise ValueError("observable string %r has %d letters, expected %d" % (s, len(s), n))
+        x = z = 0
+        for q, ch in enumerate(s):
+            if ch in "XY":
+                x |= 1 << q
+            if ch in "ZY":
+                z |= 1 << q
+            if ch not in "IXYZ":
+                raise ValueError("bad Pauli letter %r" % ch)
+        out[k] = (float(c), x, z)
+    return out
+
+
+# ---------------------------------------------------------------- C names
+
+def stab_default_opts() -> StabOpts:
+    o = StabOpts()
+    _lib.load().stab_default_opts(ctypes.byref(o))
+    return o
+
+
+def stab_create(n: int, opts: Optional[StabOpts] = None) -> ctypes.c_void_p:
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    check(L.stab_create(n, ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
+          "stab_create")
+    return h
+
+
+def stab_destroy(h) -> None:
+    check(_lib.load().stab_destroy(h), "stab_destroy")
+
+
+def stab_load_circuit(h, gates, thetas) -> None:
+    g, gp = _gates_ptr(gates)
+    t = _f64(thetas)
+    check(_lib.load().stab_load_circuit(h, gp, g.shape[0], t.ctypes.data if t.size else None,
+                                        t.size), "stab_load_circuit")
+
+
+def stab_set_params(h, thetas, is_device: bool = False) -> None:
+    if is_device:
+        ptr = thetas.data_ptr()
+        check(_lib.load().stab_set_params(h, ptr, 1), "stab_set_params")
+    else:
+        t = _f64(thetas)
+        check(_lib.load().stab_set_params(h, t.ctypes.data if t.size else None, 0),
+              "stab_set_params")
+
+
+def stab_run_generators(h) -> None:
+    check(_lib.load().stab_run_generators(h), "stab_run_generators")
+
+
+def stab_apply_circuit(h, gates, thetas) -> None:
+    g, gp = _gates_ptr(gates)
+    t = _f64(thetas)
+    check(_lib.load().stab_apply_circuit(h, gp, g.shape[0], t.ctypes.data if t.size else None,
+                                         t.size), "stab_apply_circuit")
+
+
+def stab_get_generators(h, n: int, out=None):
+    """Host numpy (n, 4^n) by default; a CUDA torch tensor ``out`` is filled on device."""
+    if out is None:
+        arr = np.empty((n, 4 ** n), dtype=np.float64)
+        check(_lib.load().stab_get_generators(h, arr.ctypes.data, 0), "stab_get_generators")
+        return arr
+    if hasattr(out, "data_ptr"):
+        if out.numel() != n * 4 ** n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous tensor of n * 4^n doubles")
+        check(_lib.load().stab_get_generators(h, out.data_ptr(), 1 if out.is_cuda else 0),
+              "stab_get_generators")
+        return out
+    arr = out
+    if arr.dtype != np.float64 or arr.size != n * 4 ** n or not arr.flags.c_contiguous:
+        raise ValueError("out must be a contiguous float64 array of n * 4^n entries")
+    check(_lib.load().stab_get_generators(h, arr.ctypes.data, 0), "stab_get_generators")
+    return arr
+
+
+def stab_expect(h, terms: np.ndarray) -> float:
+    out = ctypes.c_double()
+    t = np.ascontiguousarray(terms)
+    check(_lib.load().stab_expect(h, t.ctypes.data if t.size else None, t.shape[0],
+                                  ctypes.byref(out)), "stab_expect")
+    return out.value
+
+
+def stab_grad(h, terms: np.ndarray, n_params: int) -> Tuple[float, np.ndarray]:
+    out = ctypes.c_double()
+    grads = np.zeros(max(n_params, 1))
+    t = np.ascontiguousarray(terms)
+    check(_lib.load().stab_grad(h, t.ctypes.data if t.size else None, t.shape[0],
+                                ctypes.byref(out), grads.ctypes.data), "stab_grad")
+    return out.value, grads[:n_params]
+
+
+def stab_set_observable(h, terms: np.ndarray) -> None:
+    t = np.ascontiguousarray(terms)
+    check(_lib.load().stab_set_observable(h, t.ctypes.data if t.size else None, t.shape[0]),
+          "stab_set_observable")
+
+
+def stab_expect_async(h, out_dev) -> None:
+    """``out_dev``: a CUDA float64 tensor (first element receives <O>)."""
+    check(_lib.load().stab_expect_async(h, out_dev.data_ptr()), "stab_expect_async")
+
+
+def stab_grad_async(h, expect_dev, grads_dev) -> None:
+    check(_lib.load().stab_grad_async(h, expect_dev.data_ptr() if expect_dev is not None else None,
+                                      grads_dev.data_ptr()), "stab_grad_async")
+
+
+def stab_transfer_bytes(h) -> Tuple[int, int]:
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    check(_lib.load().stab_transfer_bytes(h, ctypes.byref(a), ctypes.byref(b)),
+          "stab_transfer_bytes")
+    return a.value, b.value
+
+
+def stab_synchronize(h) -> None:
+    check(_lib.load().stab_synchronize(h), "stab_synchronize")
+
+
+def stab_plan_info(h) -> Tuple[int, int, int]:
+    a, b, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    check(_lib.load().stab_plan_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)),
+          "stab_plan_info")
+    return a.value, b.value, k.value
+
+
+def stab_launch_count(h) -> int:
+    return int(_lib.load().stab_launch_count(h))
+
+
+# ---------------------------------------------------------------- class
+
+class Stab:
+    """One context: n qubits, a loaded circuit, its generators and observables.
+
+    ``torch_memory=True`` routes device allocations through PyTorch's caching
+    allocator and queues work on the current PyTorch stream of ``device``.
+    """
+
+    def __init__(self, n: int, kernel: str = "auto", fuse: bool = True, device: int = 0,
+                 torch_memory: bool = True, stream=None):
+        self.n = n
+        self.n_params = 0
+        self._keep = []
+        opts = stab_default_opts()
+        opts.device = device
+        opts.kernel = KERNELS[kernel]
+        opts.fuse = 1 if fuse else 0
+        if torch_memory or stream is not None:
+            import torch
+            dev = torch.device("cuda", device)
+            if stream is None:
+                stream = torch.cuda.current_stream(dev)
+            opts.stream = ctypes.c_void_p(stream.cuda_stream)
+            self._stream = stream
+        if torch_memory:
+            import torch
+
+            def _alloc(nbytes, st, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), device,
+                                                                  self._stream))
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, st, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            a, f = _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
+            self._keep += [a, f]
+            opts.alloc = a
+            opts.free = f
+        self.h = stab_create(n, opts)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            stab_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_circuit(self, gates, thetas) -> None:
+        stab_load_circuit(self.h, gates, thetas)
+        self.n_params = int(np.asarray(thetas).size)
+
+    def set_params(self, thetas) -> None:
+        if hasattr(thetas, "is_cuda") and thetas.is_cuda:
+            import torch
+            t = thetas.detach().to(torch.float64).contiguous()
+            if t.numel() != self.n_params:
+                raise ValueError("expected %d angles" % self.n_params)
+            stab_set_params(self.h, t, True)
+            self._keep_params = t
+        else:
+            t = np.asarray(thetas.detach().cpu() if hasattr(thetas, "detach") else thetas,
+                           dtype=np.float64)
+            if t.size != self.n_params:
+                raise ValueError("expected %d angles" % self.n_params)
+            stab_set_params(self.h, t, False)
+
+    def run_generators(self) -> None:
+        stab_run_generators(self.h)
+
+    def apply_circuit(self, gates, thetas) -> None:
+        stab_apply_circuit(self.h, gates, thetas)
+        self.n_params = int(np.asarray(thetas).size)
+
+    def generators(self, out=None):
+        return stab_get_generators(self.h, self.n, out)
+
+    def expect(self, observable) -> float:
+        return stab_expect(self.h, terms_from_observable(self.n, observable))
+
+    def grad(self, observable) -> Tuple[float, np.ndarray]:
+        return stab_grad(self.h, terms_from_observable(self.n, observable), self.n_params)
+
+    def set_observable(self, observable) -> None:
+        stab_set_observable(self.h, terms_from_observable(self.n, observable))
+
+    def expect_async(self, out_dev) -> None:
+        stab_expect_async(self.h, out_dev)
+
+    def grad_async(self, expect_dev, grads_dev) -> None:
+        stab_grad_async(self.h, expect_dev, grads_dev)
+
+    def transfer_bytes(self):
+        return stab_transfer_bytes(self.h)
+
+    def synchronize(self) -> None:
+        stab_synchronize(self.h)
+
+    def plan_info(self):
+        return stab_plan_info(self.h)
+
+    def launch_count(self) -> int:
+        return stab_launch_count(self.h)

@@ -1,0 +1,232 @@
+"""CUDA path vs the CPU oracle, element by element, through the C interface.
+
+Tolerances (from the spec reading, applied per vector): generators
+max |a - b| <= tol * ||b||_2 (= tol, generators have unit norm); <O> within
+tol * sum |o_P|; tol = 1e-12, or 1e-10 for circuits of 60K gates and more.
+Clifford-only circuits must match bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import layout
+import oracle
+from paper_2502_10685_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stab():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2502_10685_gb300 import stab as S
+    return S
+
+
+def tol_for(m):
+    return 1e-10 if m >= 60000 else 1e-12
+
+
+def run_gens(S, c, kernel="auto", fuse=True):
+    s = S.Stab(c.n, kernel=kernel, fuse=fuse)
+    s.apply_circuit(c.gates, c.thetas)
+    g = s.generators()
+    s.close()
+    return layout.lib_to_paper(c.n, g)
+
+
+def obs_l1(obs):
+    return sum(abs(a) for a, _ in obs)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("kernel", ["auto", "streamed", "plain"])
+def test_generators_random_circuits(stab, n, kernel):
+    m = 150 if n <= 6 else 60
+    c = W.random_circuit(n, m, seed=1000 + n)
+    ref = oracle.generators(n, c.gates, c.thetas)
+    got = run_gens(stab, c, kernel)
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 4, 6, 7, 8, 9])
+def test_clifford_circuits_bit_exact(stab, n):
+    c = W.random_circuit(n, 200, seed=2000 + n, clifford_only=True)
+    ref = oracle.generators(n, c.gates, c.thetas)
+    for kernel in ("auto", "streamed"):
+        got = run_gens(stab, c, kernel)
+        np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7, 8])
+def test_expectation_random(stab, n):
+    m = 200 if n <= 6 else 60
+    c = W.random_circuit(n, m, seed=3000 + n)
+    obs = W.random_observable(n, 6, seed=n)
+    ref = oracle.expect(n, c.gates, c.thetas, obs)
+    for kernel in ("auto", "streamed", "plain"):
+        s = stab.Stab(n, kernel=kernel)
+        s.load_circuit(c.gates, c.thetas)
+        got = s.expect(obs)
+        s.close()
+        assert abs(got - ref) <= 1e-12 * obs_l1(obs), kernel
+
+
+def test_config_small_layered_n4_2000(stab):
+    """n=4, 2,000-gate layered ansatz: all 4 x 256 coefficients and <Z_0>."""
+    c = W.layered_ansatz(4, 2000, seed=1001)
+    ref = oracle.generators(4, c.gates, c.thetas)
+    s = stab.Stab(4)
+    s.apply_circuit(c.gates, c.thetas)
+    got = layout.lib_to_paper(4, s.generators())
+    assert np.abs(got - ref).max() <= 1e-12
+    obs = W.obs_z(4, 0)
+    assert abs(s.expect(obs) - oracle.expect(4, c.gates, c.thetas, obs)) <= 1e-12
+    s.close()
+
+
+def test_config_paper_scale_n4_60200(stab):
+    """n=4, 60,200 gates: generators and <Z_0 Z_1> within 1e-10."""
+    c = W.layered_ansatz(4, 60200, seed=1002)
+    ref = oracle.generators(4, c.gates, c.thetas)
+    s = stab.Stab(4)
+    s.apply_circuit(c.gates, c.thetas)
+    got = layout.lib_to_paper(4, s.generators())
+    assert np.abs(got - ref).max() <= 1e-10
+    obs = W.obs_zz(4, 0, 1)
+    assert abs(s.expect(obs) - oracle.expect(4, c.gates, c.thetas, obs)) <= 1e-10
+    s.close()
+
+
+def test_paper_shaped_ansatz_fused_maps(stab):
+    """W_chain + ZXZ with many repeats: wire runs compose into 3x3 maps."""
+    c = W.paper_shaped_ansatz(4, 5, 20, seed=7)
+    ref = oracle.generators(4, c.gates, c.thetas)
+    for kernel in ("auto", "streamed", "plain"):
+        got = run_gens(stab, c, kernel)
+        assert np.abs(got - ref).max() <= 1e-12, kernel
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7])
+def test_gradient_matches_psr(stab, n):
+    c = W.random_circuit(n, 60, seed=4000 + n)
+    obs = W.random_observable(n, 5, seed=40 + n)
+    gref = oracle.psr_grad(n, c.gates, c.thetas, obs)
+    eref = oracle.expect(n, c.gates, c.thetas, obs)
+    for kernel in ("auto", "streamed"):
+        s = stab.Stab(n, kernel=kernel)
+        s.load_circuit(c.gates, c.thetas)
+        e, g = s.grad(obs)
+        s.close()
+        assert abs(e - eref) <= 1e-12 * obs_l1(obs)
+        assert np.abs(g - gref).max() <= 1e-12 * obs_l1(obs), kernel
+
+
+def test_gradient_shared_parameters(stab):
+    c = W.random_circuit(4, 80, seed=51, shared_params=5)
+    obs = W.obs_chain(4)
+    gref = oracle.psr_grad(4, c.gates, c.thetas, obs)
+    s = stab.Stab(4)
+    s.load_circuit(c.gates, c.thetas)
+    _, g = s.grad(obs)
+    s.close()
+    assert np.abs(g - gref).max() <= 1e-12 * obs_l1(obs)
+
+
+def test_gradient_n8_sampled_psr_and_fd(stab):
+    """n=8 layered ansatz, chain observable: adjoint vs oracle PSR on sampled
+    gates, and vs central finite differences (h = 1e-6) of the GPU <O>."""
+    c = W.layered_ansatz(8, 600, seed=1004)
+    obs = W.obs_chain(8)
+    s = stab.Stab(8)
+    s.load_circuit(c.gates, c.thetas)
+    e, g = s.grad(obs)
+    assert abs(e - oracle.expect(8, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
+    rot = [i for i in range(c.m) if c.gates[i]["op"] >= 8]
+    rng = np.random.default_rng(0)
+    for i in rng.choice(rot, size=3, replace=False):
+        j = int(c.gates[i]["param"])
+        gp = oracle.psr_grad_gate(8, c.gates, c.thetas, obs, int(i))
+        assert abs(g[j] - gp) <= 1e-12 * obs_l1(obs)
+    h = 1e-6
+    for j in rng.choice(c.n_params, size=3, replace=False):
+        tp, tm = c.thetas.copy(), c.thetas.copy()
+        tp[j] += h
+        tm[j] -= h
+        s.set_params(tp)
+        fp = s.expect(obs)
+        s.set_params(tm)
+        fm = s.expect(obs)
+        assert abs(g[j] - (fp - fm) / (2 * h)) <= 1e-6 * obs_l1(obs)
+    s.close()
+
+
+def test_identity_circuit_and_n1(stab):
+    c = W.Circuit(3, np.zeros(0, dtype=W.GATE_DTYPE), np.zeros(0))
+    got = run_gens(stab, c)
+    ref = oracle.generators(3, c.gates, c.thetas)
+    np.testing.assert_array_equal(got, ref)
+    c1 = W.random_circuit(1, 50, seed=3)
+    np.testing.assert_allclose(run_gens(stab, c1), oracle.generators(1, c1.gates, c1.thetas),
+                               atol=1e-14)
+
+
+def test_n12_one_generator_sampled(stab):
+    """Largest register: n = 12 (4^12 coefficients per vector), short circuit."""
+    n = 12
+    c = W.layered_ansatz(n, 40, seed=12)
+    s = stab.Stab(n)
+    s.apply_circuit(c.gates, c.thetas)
+    g = s.generators()
+    s.close()
+    ref = oracle.forward(n, c.gates, c.thetas, oracle.generator(n, 5))
+    got = layout.lib_to_paper(n, g[5])
+    assert np.abs(got - ref).max() <= 1e-12
+    for k in range(n):
+        assert abs(np.dot(g[k], g[k]) - 1.0) < 1e-12
+
+
+def test_set_params_device_tensor(stab):
+    import torch
+    c = W.layered_ansatz(5, 300, seed=77)
+    obs = W.obs_chain(5)
+    s = stab.Stab(5)
+    s.load_circuit(c.gates, c.thetas)
+    th2 = c.thetas + 0.3
+    s.set_params(torch.tensor(th2, device="cuda"))
+    got = s.expect(obs)
+    s.close()
+    assert abs(got - oracle.expect(5, c.gates, th2, obs)) <= 1e-12 * obs_l1(obs)
+
+
+def test_invalid_inputs_return_errors(stab):
+    from paper_2502_10685_gb300._lib import StabError
+    s = stab.Stab(3)
+    bad = W.gates_from_list([("CX", 1, 1)])
+    with pytest.raises(StabError) as ei:
+        s.load_circuit(bad, np.zeros(0))
+    assert ei.value.code == -1
+    bad = W.gates_from_list([("RX", 0, 4)])
+    with pytest.raises(StabError) as ei:
+        s.load_circuit(bad, np.zeros(2))
+    assert ei.value.code == -2
+    bad = W.gates_from_list([("RX", 0, 0)])
+    with pytest.raises(StabError) as ei:
+        s.load_circuit(bad, np.array([np.nan]))
+    assert ei.value.code == -5
+    with pytest.raises(StabError) as ei:
+        s.expect([(1.0, "ZII")])
+    assert ei.value.code == -7
+    s.close()
+    with pytest.raises(StabError):
+        stab.Stab(13)
+
+
+def test_deterministic_repeat(stab):
+    c = W.layered_ansatz(6, 1000, seed=5)
+    a = run_gens(stab, c)
+    b = run_gens(stab, c)
+    np.testing.assert_array_equal(a, b)
