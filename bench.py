@@ -215,6 +215,8 @@ def run_ours(args):
 
     from paper_2502_10685_gb300 import stab
     c, obs = workload_spec(args.workload)
+    # all work of this process is queued on one dedicated stream
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
     s = stab.Stab(c.n, device=local)
     s.load_circuit(c.gates, c.thetas)
     s.set_observable(obs)

@@ -99,8 +99,10 @@ typedef struct stab_opts {
     int32_t device;        /* CUDA device ordinal, -1 = the current device */
     int32_t kernel;        /* stab_kernel */
     int32_t fuse;          /* 1 (default): group per-wire runs and CX runs (Sec. III-A) */
-    int32_t reserved;
-    void *stream;          /* cudaStream_t to queue on; NULL = a stream the context creates */
+    int32_t stream_given;  /* 1: queue on `stream` even when it is NULL (the legacy default
+                              stream); 0: on `stream` if non-NULL, else on a stream the
+                              context creates */
+    void *stream;          /* cudaStream_t */
     stab_alloc_fn alloc;
     stab_free_fn free;
     void *alloc_user;

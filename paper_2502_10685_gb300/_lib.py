@@ -44,7 +44,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 class StabOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("kernel", ctypes.c_int32), ("fuse", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
+                ("stream_given", ctypes.c_int32), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 

@@ -318,7 +318,7 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
     if (e == cudaSuccess) e = cudaSetDevice(dev);
     if (e == cudaSuccess) {
         c->device = dev;
-        if (o.stream) {
+        if (o.stream || o.stream_given) {
             c->st = (cudaStream_t)o.stream;
         } else {
             e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);

@@ -199,6 +199,7 @@ class Stab:
             if stream is None:
                 stream = torch.cuda.current_stream(dev)
             opts.stream = ctypes.c_void_p(stream.cuda_stream)
+            opts.stream_given = 1
             self._stream = stream
         if torch_memory:
             import torch
