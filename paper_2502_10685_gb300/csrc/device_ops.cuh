@@ -104,9 +104,9 @@ __device__ __forceinline__ void apply_op1(double &x, double &y, double &z, const
 //   CX(c -> t): x_t ^= x_c, z_c ^= z_t; minus iff x_c & z_t & !(x_t ^ z_c)
 //     (the map_CX list of Sec. III-C, XZ <-> -YY);
 //   CZ(a, b):   z_a ^= x_b, z_b ^= x_a; minus iff x_a & x_b & (z_a ^ z_b).
-__device__ __forceinline__ uint64_t pull_2q(uint64_t i, int n, const DevOp &op, uint32_t &neg) {
-    const int a = op.q, b = op.q1;
-    if (op.kind == K_CX) {
+__device__ __forceinline__ uint64_t pull_2q_ab(uint64_t i, int n, bool is_cx, int a, int b,
+                                               uint32_t &neg) {
+    if (is_cx) {
         uint64_t xc = (i >> (n + a)) & 1ull, zt = (i >> b) & 1ull;
         uint64_t j = i ^ (xc << (n + b)) ^ (zt << a);
         uint32_t xt = (uint32_t)((j >> (n + b)) & 1ull), zc = (uint32_t)((j >> a) & 1ull);
@@ -118,6 +118,38 @@ __device__ __forceinline__ uint64_t pull_2q(uint64_t i, int n, const DevOp &op, 
         uint32_t za = (uint32_t)((j >> a) & 1ull), zb = (uint32_t)((j >> b) & 1ull);
         neg ^= (uint32_t)(xa & xb) & (za ^ zb);
         return j;
+    }
+}
+
+__device__ __forceinline__ uint64_t pull_2q(uint64_t i, int n, const DevOp &op, uint32_t &neg) {
+    return pull_2q_ab(i, n, op.kind == K_CX, op.q, op.q1, neg);
+}
+
+// Source of output index i through the pull records of a stream pass (stored
+// in pull order).
+__device__ __forceinline__ uint32_t pull_recs(uint32_t i, int n, const Rec *pulls, int n_pull,
+                                              uint32_t &neg) {
+    uint64_t j = i;
+    for (int k = 0; k < n_pull; ++k) {
+        const Rec &p = pulls[k];
+        j = pull_2q_ab(j, n, p.kind == R_CX, p.q, p.q1, neg);
+    }
+    return (uint32_t)j;
+}
+
+// Applies the op records of a stream pass to a group held in registers.
+__device__ __forceinline__ void apply_recs(double &x, double &y, double &z, const Rec *ops,
+                                           int n_recs) {
+    for (int k = 0; k < n_recs; ++k) {
+        const Rec &op = ops[k];
+        if (op.kind == R_ROT) {
+            apply_rot(x, y, z, op.axis, op.t, op.s, op.code);
+        } else if (op.kind == R_PERM) {
+            apply_perm(x, y, z, op.code);
+        } else if (op.kind == R_MAP3) {
+            apply_map3(x, y, z, reinterpret_cast<const double *>(&ops[k + 1]), false);
+            k += 3;
+        }
     }
 }
 

@@ -1,4 +1,6 @@
-// k_adjoint.cu -- adjoint (reverse-mode) gradient of <O> in the Pauli basis.
+// k_adjoint.cu -- adjoint (reverse-mode) gradient of <O> in the Pauli basis,
+// streamed form (vectors in global memory; the shared-memory form is in
+// k_resident.cu).
 //
 // With rho_0 the coefficient vector of 2^n |0><0| (1 on every string of I and
 // Z) and M_j the orthogonal transfer map of gate j, <O> = <o, M_m ... M_1 rho_0>.
@@ -10,7 +12,8 @@
 // orthogonal), so no forward state is stored except r_m.
 #include <cuda_runtime.h>
 
-#include "resident.cuh"
+#include "device_ops.cuh"
+#include "launch.h"
 
 namespace stab {
 
@@ -66,92 +69,6 @@ __device__ __forceinline__ int rot_gate(const DevPass &p, const DevOp *ops, int 
         }
     }
     return -1;
-}
-
-template <int N>
-__global__ void __launch_bounds__(RCfg<N>::T) k_adjoint_resident(AdjointArgs a) {
-    using C = RCfg<N>;
-    extern __shared__ double smem[];
-    double *lam = smem;
-    double *rho = smem + C::E;
-    double *red = smem + 2 * C::E;   // (T / 32) x R partial sums
-    for (int i = threadIdx.x; i < C::E; i += C::T) {
-        rho[i] = i < (1 << N) ? 1.0 : 0.0;
-        lam[i] = 0.0;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < a.n_terms; k += C::T) lam[a.terms[k].idx] = a.terms[k].coeff;
-    __syncthreads();
-    resident_run<N>(rho, a.prog, 0);
-
-    const int np = a.prog.n_passes;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int W = (C::T + 31) / 32;
-    for (int s = np - 1; s >= 0; --s) {
-        const DevPass p = a.prog.passes[s];
-        if (p.type == P_CLIFF) {
-            resident_cliff<N>(lam, p, a.prog.ops, 1);
-            resident_cliff<N>(rho, p, a.prog.ops, 1);
-            __syncthreads();
-            continue;
-        }
-        const int q = p.q;
-        const int n_rot = count_rot(p, a.prog.ops);
-        double part[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) part[r] = 0.0;
-#pragma unroll
-        for (int k = 0; k < C::GPT; ++k) {
-            const int g = threadIdx.x + k * C::T;
-            if (g < C::G) {
-                const uint32_t b = (uint32_t)group_base((uint64_t)g, N, q);
-                const uint32_t ix = b | (1u << (N + q)), iy = ix | (1u << q), iz = b | (1u << q);
-                double lx = lam[ix], ly = lam[iy], lz = lam[iz];
-                double rx = rho[ix], ry = rho[iy], rz = rho[iz];
-                adjoint_group(p, a.prog.ops, a.prog.maps, lx, ly, lz, rx, ry, rz, part, n_rot);
-                lam[ix] = lx; lam[iy] = ly; lam[iz] = lz;
-                rho[ix] = rx; rho[iy] = ry; rho[iz] = rz;
-            }
-        }
-        if (n_rot > 0) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                double v = part[r];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                if (lane == 0) red[warp * R + r] = v;
-            }
-            __syncthreads();
-            if (threadIdx.x < n_rot) {
-                double total = 0.0;
-                for (int w = 0; w < W; ++w) total += red[w * R + threadIdx.x];
-                a.grad_rot[rot_gate(p, a.prog.ops, threadIdx.x)] = total;
-            }
-        }
-        __syncthreads();
-    }
-    // <O>: x-free coefficients of the fully back-propagated observable
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
-    double total = block_sum<C::T>(acc, red);
-    if (threadIdx.x == 0 && a.expect_out) *a.expect_out = total;
-}
-
-template <int N>
-cudaError_t launch_adjoint_n(const AdjointArgs &a, cudaStream_t st) {
-    using C = RCfg<N>;
-    const size_t smem = (2 * (size_t)C::E + (size_t)((C::T + 31) / 32) * R + 32) * sizeof(double);
-    static bool configured[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(k_adjoint_resident<N>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) configured[dev] = true;
-    }
-    k_adjoint_resident<N><<<1, C::T, smem, st>>>(a);
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- streamed
@@ -214,18 +131,6 @@ __global__ void k_gather_grads(const double *grad_rot, const int32_t *param_ptr,
 }
 
 }  // namespace
-
-cudaError_t launch_adjoint_resident(int n, const AdjointArgs &a, cudaStream_t st) {
-    switch (n) {
-    case 1: return launch_adjoint_n<1>(a, st);
-    case 2: return launch_adjoint_n<2>(a, st);
-    case 3: return launch_adjoint_n<3>(a, st);
-    case 4: return launch_adjoint_n<4>(a, st);
-    case 5: return launch_adjoint_n<5>(a, st);
-    case 6: return launch_adjoint_n<6>(a, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 int adjoint_stream_blocks(int n) {
     const long long G = 1ll << (2 * n - 2);

@@ -1,65 +1,388 @@
 // k_resident.cu -- propagation with the whole 4^n coefficient vector resident
-// in shared memory, one CTA per vector (n <= 7).
+// in shared memory, one CTA per vector (n <= 6), reading an instruction stream
+// staged chunk by chunk with bulk copies (see tma.cuh).
 //
-// The CTA walks the pass list of the loaded circuit (the Map stage of
-// Sec. IV-B, sequential by nature) and applies each pass to its vector in
-// place: a P_WIRE pass gives each thread whole groups of one wire and runs the
-// wire's ops on them in registers (Table I rows, lifting form for rotations);
-// a P_CLIFF pass pulls every entry through the pass's two-qubit Clifford
-// permutation (map_CX of Sec. III-C and CZ).  Only rotations use the FP64 pipe.
+// The CTA walks the passes of the loaded circuit (the sequential Map stage of
+// Sec. IV-B).  Each pass reads its wire's groups from one shared buffer --
+// pulling every entry through the preceding run of two-qubit Clifford gates
+// (map_CX of Sec. III-C, and CZ) -- applies the wire's ops and writes the
+// other buffer; the buffers then swap.  Two thread mappings:
+//   LPG = 3 (n <= 4): the wire run is one composed 3x3 map and three lanes
+//     share a group, each computing one output row: three dependent FP64
+//     instructions per pass.  An FP64 instruction costs ~68 cycles per warp on
+//     this GPU whatever the active-lane mask, so this is the shortest pass.
+//   LPG = 1 (n = 5, 6): one lane per group running the ops in registers
+//     (lifting rotations, 3 FMAs per rotation): the fewest FP64 instructions.
+// The adjoint kernel carries the cotangent and the forward vector backward
+// together and reduces each rotation's gradient dot at the end of its pass.
 #include <cuda_runtime.h>
 
-#include "resident.cuh"
+#include "device_ops.cuh"
+#include "launch.h"
+#include "tma.cuh"
 
 namespace stab {
 
+namespace {
+
+template <int N, int LPG>
+struct SCfg {
+    static constexpr int E = 1 << (2 * N);   // coefficients per vector
+    static constexpr int G = E / 4;          // groups of one wire
+    static constexpr int L = G * LPG;        // working lanes
+    static constexpr int T = L < 32 ? 32 : (L > 1024 ? 1024 : ((L + 31) / 32) * 32);
+    static constexpr int GPT = (G + T - 1) / T;   // groups per thread (LPG = 1)
+    static constexpr int W = T / 32;
+};
+
+constexpr int R = kRotPerGradPass;
+
+// Shared memory: [chunks 2 x 4 KiB][mbarriers 16 B | flag | gradient slots][reduction][vectors]
+constexpr int kOffBar = 2 * kChunkRecs * (int)sizeof(Rec);
+constexpr int kOffFlag = kOffBar + 16;
+constexpr int kOffSlot = kOffBar + 32;
+constexpr int kOffRed = kOffBar + 128;
+constexpr int kSmemHeader = kOffRed + 32 * 8 * R;
+
 template <int N>
-__global__ void __launch_bounds__(RCfg<N>::T) k_resident(ResidentArgs a) {
-    using C = RCfg<N>;
-    extern __shared__ double smem[];
-    double *vec = smem;
-    double *red = smem + C::E;
-    resident_init<N>(vec, a);
-    resident_run<N>(vec, a.prog, a.inverse);
-    if (a.out) {
-        double *o = a.out + (size_t)blockIdx.x * C::E;
-        for (int i = threadIdx.x; i < C::E; i += C::T) o[i] = vec[i];
-    }
-    if (a.xfree_out) {
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += vec[i];
-        double total = block_sum<C::T>(acc, red);
-        if (threadIdx.x == 0) a.xfree_out[blockIdx.x] = total;
-    }
+__device__ __forceinline__ void group_idx(uint32_t g, int q, uint32_t &ii, uint32_t &ix,
+                                          uint32_t &iy, uint32_t &iz) {
+    ii = (uint32_t)group_base(g, N, q);
+    iz = ii | (1u << q);
+    ix = ii | (1u << (N + q));
+    iy = ix | (1u << q);
 }
 
 template <int N>
-static cudaError_t launch_resident_n(const ResidentArgs &a, cudaStream_t st) {
-    using C = RCfg<N>;
-    const size_t smem = (size_t)C::E * sizeof(double) + 32 * sizeof(double);
-    static bool configured[64] = {};  // the attribute is set once per device
+__device__ __forceinline__ double pulled(const double *src, uint32_t i, const Rec *pulls,
+                                         int n_pull) {
+    uint32_t neg = 0;
+    const uint32_t j = pull_recs(i, N, pulls, n_pull, neg);
+    return flip(src[j], neg);
+}
+
+// One wire pass, LPG = 1: cur -> nxt.
+template <int N>
+__device__ __forceinline__ void pass_groups(const double *cur, double *nxt, int q,
+                                            const Rec *pulls, int n_pull, const Rec *ops,
+                                            int n_ops) {
+    using C = SCfg<N, 1>;
+#pragma unroll
+    for (int k = 0; k < C::GPT; ++k) {
+        const uint32_t g = threadIdx.x + k * C::T;
+        if (g < (uint32_t)C::G) {
+            uint32_t ii, ix, iy, iz;
+            group_idx<N>(g, q, ii, ix, iy, iz);
+            const double vi = pulled<N>(cur, ii, pulls, n_pull);
+            double x = pulled<N>(cur, ix, pulls, n_pull);
+            double y = pulled<N>(cur, iy, pulls, n_pull);
+            double z = pulled<N>(cur, iz, pulls, n_pull);
+            apply_recs(x, y, z, ops, n_ops);
+            nxt[ii] = vi;
+            nxt[ix] = x;
+            nxt[iy] = y;
+            nxt[iz] = z;
+        }
+    }
+}
+
+// One wire pass, LPG = 3: lane (g, r) writes output row r of group g.  The
+// pass holds no op (identity) or one R_MAP3 and its matrix.
+template <int N>
+__device__ __forceinline__ void pass_rows(const double *cur, double *nxt, int q,
+                                          const Rec *pulls, int n_pull, const Rec *ops,
+                                          int n_ops) {
+    using C = SCfg<N, 3>;
+    const uint32_t l = threadIdx.x;
+    if (l >= (uint32_t)C::L) return;
+    const uint32_t g = l / 3, r = l - 3 * g;
+    uint32_t ii, ix, iy, iz;
+    group_idx<N>(g, q, ii, ix, iy, iz);
+    const double x = pulled<N>(cur, ix, pulls, n_pull);
+    const double y = pulled<N>(cur, iy, pulls, n_pull);
+    const double z = pulled<N>(cur, iz, pulls, n_pull);
+    double out;
+    if (n_ops == 0) {
+        out = r == 0 ? x : (r == 1 ? y : z);
+    } else {
+        const double *m = reinterpret_cast<const double *>(&ops[1]) + 3 * r;
+        out = fma(m[2], z, fma(m[1], y, m[0] * x));
+    }
+    nxt[r == 0 ? ix : (r == 1 ? iy : iz)] = out;
+    if (r == 0) nxt[ii] = pulled<N>(cur, ii, pulls, n_pull);
+}
+
+template <int T>
+__device__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double total = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < T / 32; ++w) total += red[w];
+    return total;
+}
+
+__device__ __forceinline__ void stager_setup(Stager &st, unsigned char *smem) {
+    st.buf = reinterpret_cast<Rec *>(smem);
+    st.bar = reinterpret_cast<uint64_t *>(smem + kOffBar);
+    st.flag = reinterpret_cast<int *>(smem + kOffFlag);
+}
+
+// Runs the passes of chunks [c0, c1) on one vector; returns the buffer that
+// holds the result, or nullptr when a staging wait gave up.
+template <int N, int LPG>
+__device__ double *run_stream(Stager &st, int c0, int c1, double *cur, double *nxt,
+                              int32_t *status) {
+    for (int c = c0; c < c1; ++c) {
+        if (!st.wait(c, status)) return nullptr;
+        const Rec *Rr = st.chunk(c);
+        int r = 0;
+        while (true) {
+            const Rec h = Rr[r];
+            if (h.kind != R_PASS) break;   // R_NEXT or R_END
+            const Rec *pulls = Rr + r + 1;
+            const Rec *ops = pulls + h.param;
+            if constexpr (LPG == 1) pass_groups<N>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
+            else pass_rows<N>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
+            double *t = cur;
+            cur = nxt;
+            nxt = t;
+            __syncthreads();
+            r += 1 + h.param + h.gate;
+        }
+        st.release(c);
+    }
+    return cur;
+}
+
+template <int N, int LPG>
+__global__ void __launch_bounds__(SCfg<N, LPG>::T) k_resident_stream(StreamArgs a) {
+    using C = SCfg<N, LPG>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    Stager st;
+    st.s0 = a.stream;
+    st.s1 = nullptr;
+    st.n0 = a.n_chunks;
+    st.n_total = a.n_chunks;
+    stager_setup(st, smem);
+    double *red = reinterpret_cast<double *>(smem + kOffRed);
+    double *bufA = reinterpret_cast<double *>(smem + kSmemHeader);
+    double *bufB = bufA + C::E;
+    st.start();
+
+    const int b = blockIdx.x;
+    for (int i = threadIdx.x; i < C::E; i += C::T) {
+        double v = 0.0;
+        if (a.init == INIT_RHO0) v = (i < (1 << N)) ? 1.0 : 0.0;
+        else if (a.init == INIT_LOAD) v = a.in[(size_t)b * C::E + i];
+        bufA[i] = v;
+    }
+    __syncthreads();
+    if (a.init == INIT_GENERATOR) {
+        if (threadIdx.x == 0) bufA[1u << b] = 1.0;   // Z_b: z bit b set
+    } else if (a.init == INIT_TERMS) {
+        for (int k = threadIdx.x; k < a.n_terms; k += C::T) bufA[a.terms[k].idx] = a.terms[k].coeff;
+    }
+    __syncthreads();
+
+    double *res = run_stream<N, LPG>(st, 0, a.n_chunks, bufA, bufB, a.status);
+    if (res == nullptr) return;
+    if (a.out) {
+        double *o = a.out + (size_t)b * C::E;
+        for (int i = threadIdx.x; i < C::E; i += C::T) o[i] = res[i];
+    }
+    if (a.xfree_out) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += res[i];
+        const double total = block_sum<C::T>(acc, red);
+        if (threadIdx.x == 0) a.xfree_out[b] = total;
+    }
+}
+
+// ---------------------------------------------------------------- adjoint
+
+__device__ __forceinline__ double pair_dot(int axis, double lx, double ly, double lz, double rx,
+                                           double ry, double rz) {
+    // d<O>/d theta on the pair (u, v): l_v r_u - l_u r_v; (u, v) = (Y, Z) for
+    // R_x, (Z, X) for R_y, (X, Y) for R_z
+    if (axis == AX_X) return fma(lz, ry, -ly * rz);
+    if (axis == AX_Y) return fma(lx, rz, -lz * rx);
+    return fma(ly, rx, -lx * ry);
+}
+
+template <int N>
+__global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamArgs a) {
+    using C = SCfg<N, 1>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    Stager st;
+    st.s0 = a.fwd;
+    st.s1 = a.bwd;
+    st.n0 = a.n_fwd_chunks;
+    st.n_total = a.n_fwd_chunks + a.n_bwd_chunks;
+    stager_setup(st, smem);
+    int *gslot = reinterpret_cast<int *>(smem + kOffSlot);
+    double *red = reinterpret_cast<double *>(smem + kOffRed);
+    double *rA = reinterpret_cast<double *>(smem + kSmemHeader);
+    double *rB = rA + C::E, *lA = rB + C::E, *lB = lA + C::E;
+    st.start();
+    for (int i = threadIdx.x; i < C::E; i += C::T) {
+        rA[i] = i < (1 << N) ? 1.0 : 0.0;
+        lA[i] = 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.n_terms; k += C::T) lA[a.terms[k].idx] = a.terms[k].coeff;
+    __syncthreads();
+
+    // forward: r_m = M_m ... M_1 rho_0
+    double *rho = run_stream<N, 1>(st, 0, a.n_fwd_chunks, rA, rB, a.status);
+    if (rho == nullptr) return;
+    double *rho_n = rho == rA ? rB : rA;
+    double *lam = lA, *lam_n = lB;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = a.n_fwd_chunks; c < st.n_total; ++c) {
+        if (!st.wait(c, a.status)) return;
+        const Rec *Rr = st.chunk(c);
+        int r = 0;
+        while (true) {
+            const Rec h = Rr[r];
+            if (h.kind != R_PASS) break;
+            const Rec *pulls = Rr + r + 1;
+            const Rec *ops = pulls + h.param;
+            const int n_pull = h.param, n_ops = h.gate, q = h.q;
+            double part[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) part[k] = 0.0;
+#pragma unroll
+            for (int k = 0; k < C::GPT; ++k) {
+                const uint32_t g = threadIdx.x + k * C::T;
+                if (g < (uint32_t)C::G) {
+                    uint32_t ii, ix, iy, iz;
+                    group_idx<N>(g, q, ii, ix, iy, iz);
+                    const double li = pulled<N>(lam, ii, pulls, n_pull);
+                    const double ri = pulled<N>(rho, ii, pulls, n_pull);
+                    double lx = pulled<N>(lam, ix, pulls, n_pull);
+                    double ly = pulled<N>(lam, iy, pulls, n_pull);
+                    double lz = pulled<N>(lam, iz, pulls, n_pull);
+                    double rx = pulled<N>(rho, ix, pulls, n_pull);
+                    double ry = pulled<N>(rho, iy, pulls, n_pull);
+                    double rz = pulled<N>(rho, iz, pulls, n_pull);
+                    int slot = 0;
+                    for (int j = 0; j < n_ops; ++j) {
+                        if (ops[j].kind == R_ROT) {
+                            const double d = pair_dot(ops[j].axis, lx, ly, lz, rx, ry, rz);
+#pragma unroll
+                            for (int s = 0; s < R; ++s)
+                                if (s == slot) part[s] += d;
+                            ++slot;
+                        }
+                        apply_recs(lx, ly, lz, ops + j, 1);
+                        apply_recs(rx, ry, rz, ops + j, 1);
+                    }
+                    lam_n[ii] = li; lam_n[ix] = lx; lam_n[iy] = ly; lam_n[iz] = lz;
+                    rho_n[ii] = ri; rho_n[ix] = rx; rho_n[iy] = ry; rho_n[iz] = rz;
+                }
+            }
+            int n_rot = 0;
+            for (int j = 0; j < n_ops; ++j) {
+                if (ops[j].kind == R_ROT) {
+                    if (threadIdx.x == 0) gslot[n_rot] = ops[j].gate;
+                    ++n_rot;
+                }
+            }
+            if (n_rot > 0) {
+#pragma unroll
+                for (int s = 0; s < R; ++s) {
+                    double v = part[s];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                    if (lane == 0) red[warp * R + s] = v;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < n_rot) {
+                double total = 0.0;
+                for (int w = 0; w < C::W; ++w) total += red[w * R + threadIdx.x];
+                a.grad_rot[gslot[threadIdx.x]] = total;
+            }
+            double *t = lam;
+            lam = lam_n;
+            lam_n = t;
+            t = rho;
+            rho = rho_n;
+            rho_n = t;
+            __syncthreads();
+            r += 1 + n_pull + n_ops;
+        }
+        st.release(c);
+    }
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
+    const double total = block_sum<C::T>(acc, red);
+    if (threadIdx.x == 0 && a.expect_out) *a.expect_out = total;
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t smem, bool *configured) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(k_resident<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    k_resident<N><<<a.n_vec, C::T, smem, st>>>(a);
+    return cudaSuccess;
+}
+
+template <int N, int LPG>
+cudaError_t launch_stream_n(const StreamArgs &a, cudaStream_t s) {
+    using C = SCfg<N, LPG>;
+    const size_t smem = kSmemHeader + 2 * (size_t)C::E * sizeof(double);
+    static bool configured[64] = {};
+    cudaError_t e = set_smem(k_resident_stream<N, LPG>, smem, configured);
+    if (e != cudaSuccess) return e;
+    k_resident_stream<N, LPG><<<a.n_vec, C::T, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_resident(int n, const ResidentArgs &a, cudaStream_t st) {
+template <int N>
+cudaError_t launch_adjoint_stream_n(const AdjointStreamArgs &a, cudaStream_t s) {
+    using C = SCfg<N, 1>;
+    const size_t smem = kSmemHeader + 4 * (size_t)C::E * sizeof(double);
+    static bool configured[64] = {};
+    cudaError_t e = set_smem(k_adjoint_stream<N>, smem, configured);
+    if (e != cudaSuccess) return e;
+    k_adjoint_stream<N><<<1, C::T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int resident_lanes_per_group(int n) { return n <= 4 ? 3 : 1; }
+
+cudaError_t launch_resident_stream(int n, const StreamArgs &a, cudaStream_t s) {
     switch (n) {
-    case 1: return launch_resident_n<1>(a, st);
-    case 2: return launch_resident_n<2>(a, st);
-    case 3: return launch_resident_n<3>(a, st);
-    case 4: return launch_resident_n<4>(a, st);
-    case 5: return launch_resident_n<5>(a, st);
-    case 6: return launch_resident_n<6>(a, st);
-    case 7: return launch_resident_n<7>(a, st);
+    case 1: return launch_stream_n<1, 3>(a, s);
+    case 2: return launch_stream_n<2, 3>(a, s);
+    case 3: return launch_stream_n<3, 3>(a, s);
+    case 4: return launch_stream_n<4, 3>(a, s);
+    case 5: return launch_stream_n<5, 1>(a, s);
+    case 6: return launch_stream_n<6, 1>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_t s) {
+    switch (n) {
+    case 1: return launch_adjoint_stream_n<1>(a, s);
+    case 2: return launch_adjoint_stream_n<2>(a, s);
+    case 3: return launch_adjoint_stream_n<3>(a, s);
+    case 4: return launch_adjoint_stream_n<4>(a, s);
+    case 5: return launch_adjoint_stream_n<5>(a, s);
+    case 6: return launch_adjoint_stream_n<6>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

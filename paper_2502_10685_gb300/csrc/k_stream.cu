@@ -54,35 +54,67 @@ __device__ void gate_matrix3(const RawGate &g, const double *thetas, double M[9]
     }
 }
 
+// Shear coefficients of an angle: theta is reduced to phi in [-pi/2, pi/2] up
+// to a factor R(pi) = -1 on the pair (neg), so that t = -tan(phi/2) stays in
+// [-1, 1].
+__device__ void shear_coeffs(double theta, double &t, double &s, uint16_t &neg) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const double pi = 3.1415926535897932384626433832795;
+    double phi = remainder(theta, two_pi);
+    neg = 0;
+    if (phi > 0.5 * pi) { phi -= pi; neg = 1; }
+    else if (phi < -0.5 * pi) { phi += pi; neg = 1; }
+    t = -tan(0.5 * phi);
+    s = sin(phi);
+}
+
+__device__ void compose_map(const DevMap3 &mp, const int32_t *map_gate_idx, const RawGate *gates,
+                            const double *thetas, double M[9]) {
+    for (int k = 0; k < 9; ++k) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    for (int k = 0; k < mp.count; ++k) {
+        double G[9], R[9];
+        gate_matrix3(gates[map_gate_idx[mp.first + k]], thetas, G);
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                R[3 * r + c] = G[3 * r] * M[c] + G[3 * r + 1] * M[3 + c] + G[3 * r + 2] * M[6 + c];
+        for (int k2 = 0; k2 < 9; ++k2) M[k2] = R[k2];
+    }
+}
+
+__global__ void k_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const DevMap3 *maps,
+                                const int32_t *map_gate_idx, const RawGate *gates,
+                                const double *thetas) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_enc) return;
+    Rec &r = recs[enc[k]];
+    if (r.kind == R_ROT) {
+        double t, s;
+        uint16_t neg;
+        shear_coeffs(thetas[r.param], t, s, neg);
+        r.t = r.inv ? -t : t;
+        r.s = r.inv ? -s : s;
+        r.code = neg;
+    } else if (r.kind == R_MAP3) {
+        double M[9];
+        compose_map(maps[r.param], map_gate_idx, gates, thetas, M);
+        double *dst = reinterpret_cast<double *>(&r + 1);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) dst[3 * i + j] = r.inv ? M[3 * j + i] : M[3 * i + j];
+    }
+}
+
 __global__ void k_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
                          const int32_t *map_gate_idx, const RawGate *gates, const double *thetas) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_ops && ops[i].kind == K_ROT) {
-        // Reduce theta to phi in [-pi/2, pi/2] up to a factor R(pi) = -1 on
-        // the pair, then store the shear coefficients of R(phi).
-        const double two_pi = 6.283185307179586476925286766559;
-        const double pi = 3.1415926535897932384626433832795;
-        double phi = remainder(thetas[ops[i].param], two_pi);
-        uint16_t neg = 0;
-        if (phi > 0.5 * pi) { phi -= pi; neg = 1; }
-        else if (phi < -0.5 * pi) { phi += pi; neg = 1; }
-        ops[i].t = -tan(0.5 * phi);
-        ops[i].s = sin(phi);
+        double t, s;
+        uint16_t neg;
+        shear_coeffs(thetas[ops[i].param], t, s, neg);
+        ops[i].t = t;
+        ops[i].s = s;
         ops[i].perm = neg;
     }
-    if (i < n_maps) {
-        double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-        const DevMap3 &mp = maps[i];
-        for (int k = 0; k < mp.count; ++k) {
-            double G[9], R[9];
-            gate_matrix3(gates[map_gate_idx[mp.first + k]], thetas, G);
-            for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 3; ++c)
-                    R[3 * r + c] = G[3 * r] * M[c] + G[3 * r + 1] * M[3 + c] + G[3 * r + 2] * M[6 + c];
-            for (int k2 = 0; k2 < 9; ++k2) M[k2] = R[k2];
-        }
-        for (int k = 0; k < 9; ++k) maps[i].m[k] = M[k];
-    }
+    if (i < n_maps) compose_map(maps[i], map_gate_idx, gates, thetas, maps[i].m);
 }
 
 __global__ void k_fill(double *vec, int n, int n_vec, int init) {
@@ -169,6 +201,15 @@ cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
     if (work == 0) return cudaSuccess;
     k_encode<<<(work + 127) / 128, 128, 0, st>>>(ops, n_ops, maps, n_maps, map_gate_idx, gates,
                                                  thetas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const DevMap3 *maps,
+                                 const int32_t *map_gate_idx, const RawGate *gates,
+                                 const double *thetas, cudaStream_t st) {
+    if (n_enc == 0) return cudaSuccess;
+    k_encode_stream<<<(n_enc + 127) / 128, 128, 0, st>>>(recs, enc, n_enc, maps, map_gate_idx,
+                                                         gates, thetas);
     return cudaGetLastError();
 }
 

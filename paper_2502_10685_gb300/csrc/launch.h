@@ -9,20 +9,33 @@
 
 namespace stab {
 
-constexpr int kMaxResidentQubits = 7;   // 4^7 doubles = 128 KiB of shared memory
-constexpr int kMaxResidentAdjoint = 6;  // two vectors: 2 x 4^6 doubles = 64 KiB
+constexpr int kMaxResidentQubits = 6;   // two buffers of 4^6 doubles = 64 KiB of shared memory
+constexpr int kMaxResidentAdjoint = 6;  // four buffers of 4^6 doubles = 128 KiB
 constexpr int kRotPerGradPass = 8;      // rotations per P_WIRE pass in gradient plans
 
-struct ResidentArgs {
-    Program prog;
-    int32_t inverse;         // 0: forward (U P U^dagger), 1: backward (U^dagger P U)
+struct StreamArgs {
+    const Rec *stream;       // instruction stream (device), n_chunks x kChunkRecs records
+    int32_t n_chunks;
     int32_t init;            // InitMode
     const DevTerm *terms;    // INIT_TERMS
     int32_t n_terms;
-    int32_t n_vec;           // vectors (blocks)
+    int32_t n_vec;           // vectors (blocks); block b starts as Z_b for INIT_GENERATOR
     const double *in;        // INIT_LOAD: block b reads in + b * 4^n
     double *out;             // final vector of block b at out + b * 4^n (may be null)
     double *xfree_out;       // block b: sum of its x-free coefficients (may be null)
+    int32_t *status;         // set to a nonzero code when a bounded wait gives up
+};
+
+struct AdjointStreamArgs {
+    const Rec *fwd;          // forward stream of the gradient plan
+    const Rec *bwd;          // backward stream of the gradient plan
+    int32_t n_fwd_chunks;
+    int32_t n_bwd_chunks;
+    const DevTerm *terms;
+    int32_t n_terms;
+    double *grad_rot;        // one entry per rotation ordinal
+    double *expect_out;      // <O>
+    int32_t *status;
 };
 
 // Encode kernel: lifting coefficients of every rotation op and composed 3x3
@@ -31,8 +44,15 @@ cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
                           const int32_t *map_gate_idx, const RawGate *gates, const double *thetas,
                           cudaStream_t st);
 
-// Shared-memory-resident propagation, one CTA per vector (n <= 7).
-cudaError_t launch_resident(int n, const ResidentArgs &a, cudaStream_t st);
+// Stream encode: shear coefficients of the R_ROT records and matrices of the
+// R_MAP3 records listed in enc (indices into recs).
+cudaError_t launch_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const DevMap3 *maps,
+                                 const int32_t *map_gate_idx, const RawGate *gates,
+                                 const double *thetas, cudaStream_t st);
+
+// Shared-memory-resident propagation, one CTA per vector (n <= kMaxResidentQubits).
+cudaError_t launch_resident_stream(int n, const StreamArgs &a, cudaStream_t st);
+int resident_lanes_per_group(int n);
 
 // Streamed passes over n_vec vectors of 4^n doubles in global memory.
 cudaError_t launch_fill(double *vec, int n, int n_vec, int init, const DevTerm *terms,
@@ -43,15 +63,8 @@ cudaError_t launch_stream_cliff(const double *src, double *dst, int n, int n_vec
                                 const DevPass &p, const DevOp *ops, int inverse, cudaStream_t st);
 cudaError_t launch_xfree_sum(const double *vec, int n, int n_vec, double *out, cudaStream_t st);
 
-// Adjoint gradient.
-struct AdjointArgs {
-    Program prog;              // gradient plan: no K_MAP3, <= kRotPerGradPass rotations per pass
-    const DevTerm *terms;
-    int32_t n_terms;
-    double *grad_rot;          // one entry per rotation ordinal
-    double *expect_out;        // <O>
-};
-cudaError_t launch_adjoint_resident(int n, const AdjointArgs &a, cudaStream_t st);
+// Adjoint gradient, shared-memory resident (n <= kMaxResidentAdjoint).
+cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_t st);
 
 // Streamed adjoint pieces.
 int adjoint_stream_blocks(int n);

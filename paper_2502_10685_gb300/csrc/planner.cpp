@@ -110,7 +110,7 @@ struct Emitter {
     void emit_wire(const stab_gate *gates, int q, const std::vector<int64_t> &run) {
         int n_rot = 0;
         for (int64_t i : run) n_rot += is_rotation(gates[i].op);
-        if (mode == PLAN_FUSED && n_rot > 3) {
+        if ((mode == PLAN_FUSED && n_rot > 3) || mode == PLAN_ROWS) {
             DevMap3 mp{};
             mp.first = (int32_t)P->map_gate_idx.size();
             mp.count = (int32_t)run.size();
@@ -254,6 +254,113 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
         }
         i = j;
     }
+}
+
+namespace {
+
+constexpr int kMaxPullPerPass = 64;
+
+struct StreamWriter {
+    std::vector<Rec> *out;
+    int fill = 0;   // records used in the current chunk
+
+    void pass(int q, const std::vector<Rec> &pulls, const std::vector<Rec> &ops) {
+        const int need = 1 + (int)pulls.size() + (int)ops.size();
+        if (fill + need > kChunkRecs - 1) {
+            Rec nx{};
+            nx.kind = R_NEXT;
+            out->push_back(nx);
+            while (out->size() % kChunkRecs) out->push_back(Rec{});
+            fill = 0;
+        }
+        Rec h{};
+        h.kind = R_PASS;
+        h.q = (uint8_t)q;
+        h.param = (int32_t)pulls.size();
+        h.gate = (int32_t)ops.size();
+        out->push_back(h);
+        out->insert(out->end(), pulls.begin(), pulls.end());
+        out->insert(out->end(), ops.begin(), ops.end());
+        fill += need;
+    }
+    void end() {
+        Rec e{};
+        e.kind = R_END;
+        out->push_back(e);
+        while (out->size() % kChunkRecs) out->push_back(Rec{});
+    }
+};
+
+Rec pull_rec(const DevOp &op) {
+    Rec r{};
+    r.kind = op.kind == K_CX ? R_CX : R_CZ;
+    r.q = op.q;
+    r.q1 = op.q1;
+    return r;
+}
+
+}  // namespace
+
+void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out) {
+    out->clear();
+    StreamWriter w{out};
+    // two-qubit Clifford gates waiting to be pulled, in application order
+    std::vector<Rec> applied;
+    auto emit = [&](int q, const std::vector<Rec> &ops) {
+        // all but the last kMaxPullPerPass-segment go into identity passes
+        size_t k = 0;
+        while (applied.size() - k > (size_t)kMaxPullPerPass) {
+            std::vector<Rec> seg(applied.begin() + k, applied.begin() + k + kMaxPullPerPass);
+            std::reverse(seg.begin(), seg.end());
+            w.pass(0, seg, {});
+            k += kMaxPullPerPass;
+        }
+        std::vector<Rec> seg(applied.begin() + k, applied.end());
+        std::reverse(seg.begin(), seg.end());   // a pull walks the last applied gate first
+        w.pass(q, seg, ops);
+        applied.clear();
+    };
+    const int np = (int)P.passes.size();
+    for (int k = 0; k < np; ++k) {
+        const DevPass &p = P.passes[backward ? np - 1 - k : k];
+        if (p.type == P_CLIFF) {
+            for (int j = 0; j < p.n_ops; ++j) {
+                const int jj = backward ? p.n_ops - 1 - j : j;
+                applied.push_back(pull_rec(P.ops[p.first + jj]));
+            }
+            continue;
+        }
+        std::vector<Rec> ops;
+        for (int j = 0; j < p.n_ops; ++j) {
+            const DevOp &op = P.ops[p.first + (backward ? p.n_ops - 1 - j : j)];
+            Rec r{};
+            r.q = op.q;
+            r.inv = backward ? 1 : 0;
+            if (op.kind == K_ROT) {
+                r.kind = R_ROT;
+                r.axis = op.axis;
+                r.param = op.param;
+                r.gate = op.gate;
+                ops.push_back(r);
+            } else if (op.kind == K_PERM) {
+                r.kind = R_PERM;
+                r.code = backward ? op.perm_inv : op.perm;
+                ops.push_back(r);
+            } else {
+                r.kind = R_MAP3;
+                r.param = op.param;
+                ops.push_back(r);
+                Rec d{};
+                d.kind = R_DATA;
+                ops.push_back(d);
+                ops.push_back(d);
+                ops.push_back(d);
+            }
+        }
+        emit(p.q, ops);
+    }
+    if (!applied.empty()) emit(0, {});
+    w.end();
 }
 
 int encode_terms(int n, const stab_term *O, int64_t n_terms, std::vector<DevTerm> *out) {

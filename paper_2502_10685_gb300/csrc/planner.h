@@ -20,7 +20,12 @@
 
 namespace stab {
 
-enum PlanMode { PLAN_FUSED = 0, PLAN_GRAD = 1, PLAN_PLAIN = 2 };
+enum PlanMode {
+    PLAN_FUSED = 0,  // runs with more than three rotations become one 3x3 map
+    PLAN_GRAD = 1,   // no maps (every rotation kept for its gradient), <= kRotPerGradPass per pass
+    PLAN_PLAIN = 2,  // one pass per gate
+    PLAN_ROWS = 3,   // every wire run becomes one 3x3 map (latency-optimised resident kernel)
+};
 
 struct HostPlan {
     std::vector<DevPass> passes;
@@ -41,6 +46,10 @@ int validate_thetas(const double *thetas, int64_t n_params);
 // Builds the pass list.  gates must be valid.
 void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
                 HostPlan *out);
+
+// Instruction stream of a plan for the resident kernels (see stab_internal.h):
+// forward (backward = false) or for the inverse circuit (backward = true).
+void build_stream(const HostPlan &plan, bool backward, std::vector<Rec> *out);
 
 // Signed permutation codes of the single-qubit Clifford opcodes on (X, Y, Z).
 uint32_t clifford_perm_code(int op);

@@ -40,10 +40,23 @@ struct DevBuf {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Instruction stream of a plan for the resident kernels, with the indices of
+// the records the encode kernel fills (rotations and maps).
+struct DevStreamBuf {
+    std::vector<Rec> host;
+    std::vector<int32_t> enc;
+    Rec *dev = nullptr;
+    const int32_t *enc_dev = nullptr;
+    int n_chunks = 0;
+};
+
 // A plan uploaded to the device: one buffer holding passes, ops, maps, map
-// gate indices, raw gates and the slot CSR.
+// gate indices, raw gates, the slot CSR and (resident plans) the forward and
+// backward instruction streams.
 struct DevPlan {
     HostPlan host;
+    bool streams = false;
+    DevStreamBuf sf, sb;
     DevBuf buf;
     Program prog{};
     const int32_t *map_gate_idx = nullptr;
@@ -78,6 +91,7 @@ struct stab_ctx {
 
     DevPlan fwd, grad;
     DevBuf thetas, gens, gens_tmp, lam, rho, tmp, tmp2, terms, scal, grad_rot, partials, grads;
+    DevBuf status;                   // int32 set by kernels whose bounded waits gave up
     int32_t n_obs_terms = 0;
     bool obs_loaded = false;
     int64_t h2d_bytes = 0, d2h_bytes = 0;
@@ -137,7 +151,9 @@ struct stab_ctx {
                n <= kMaxResidentAdjoint;
     }
     PlanMode fwd_mode() const {
-        return (kernel == STAB_KERNEL_PLAIN || !fuse) ? PLAN_PLAIN : PLAN_FUSED;
+        if (kernel == STAB_KERNEL_PLAIN || !fuse) return PLAN_PLAIN;
+        if (use_resident() && resident_lanes_per_group(n) == 3) return PLAN_ROWS;
+        return PLAN_FUSED;
     }
 };
 
@@ -153,7 +169,12 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     const size_t b_raw = align256(H.raw.size() * sizeof(RawGate));
     const size_t b_pptr = align256(H.param_ptr.size() * sizeof(int32_t));
     const size_t b_prot = align256(H.param_rot.size() * sizeof(int32_t));
-    const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot;
+    const size_t b_sf = align256(P.sf.host.size() * sizeof(Rec));
+    const size_t b_sfe = align256(P.sf.enc.size() * sizeof(int32_t));
+    const size_t b_sb = align256(P.sb.host.size() * sizeof(Rec));
+    const size_t b_sbe = align256(P.sb.enc.size() * sizeof(int32_t));
+    const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot + b_sf +
+                         b_sfe + b_sb + b_sbe;
     RC(c->dalloc(P.buf, total, c->st));
     CK(cudaEventSynchronize(c->ev_stage));
     RC(c->host_stage(c->stage, c->stage_bytes, total));
@@ -173,6 +194,10 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     P.raw = (const RawGate *)put(H.raw.data(), H.raw.size() * sizeof(RawGate), b_raw);
     P.param_ptr = (const int32_t *)put(H.param_ptr.data(), H.param_ptr.size() * 4, b_pptr);
     P.param_rot = (const int32_t *)put(H.param_rot.data(), H.param_rot.size() * 4, b_prot);
+    P.sf.dev = (Rec *)put(P.sf.host.data(), P.sf.host.size() * sizeof(Rec), b_sf);
+    P.sf.enc_dev = (const int32_t *)put(P.sf.enc.data(), P.sf.enc.size() * 4, b_sfe);
+    P.sb.dev = (Rec *)put(P.sb.host.data(), P.sb.host.size() * sizeof(Rec), b_sb);
+    P.sb.enc_dev = (const int32_t *)put(P.sb.enc.data(), P.sb.enc.size() * 4, b_sbe);
     P.prog.n_passes = (int32_t)H.passes.size();
     P.prog.n_ops = (int32_t)H.ops.size();
     CK(cudaMemcpyAsync(P.buf.p, h, total, cudaMemcpyHostToDevice, c->st));
@@ -184,15 +209,63 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
 }
 
 int encode_plan(stab_ctx *c, DevPlan &P) {
+    const double *th = (const double *)c->thetas.p;
+    if (P.streams) {
+        // resident plans: only the instruction streams are read by kernels
+        for (DevStreamBuf *S : {&P.sf, &P.sb}) {
+            if (S->enc.empty()) continue;
+            CK(launch_encode_stream(S->dev, S->enc_dev, (int)S->enc.size(), P.prog.maps,
+                                    P.map_gate_idx, P.raw, th, c->st));
+            c->launches++;
+        }
+        P.encoded = true;
+        return STAB_OK;
+    }
     const int n_ops = P.prog.n_ops, n_maps = (int)P.host.maps.size();
     if (n_ops == 0 && n_maps == 0) {
         P.encoded = true;
         return STAB_OK;
     }
     CK(launch_encode(const_cast<DevOp *>(P.prog.ops), n_ops, const_cast<DevMap3 *>(P.prog.maps),
-                     n_maps, P.map_gate_idx, P.raw, (const double *)c->thetas.p, c->st));
+                     n_maps, P.map_gate_idx, P.raw, th, c->st));
     c->launches++;
     P.encoded = true;
+    return STAB_OK;
+}
+
+void make_streams(DevPlan &P) {
+    P.streams = true;
+    for (int b = 0; b < 2; ++b) {
+        DevStreamBuf &S = b ? P.sb : P.sf;
+        build_stream(P.host, b == 1, &S.host);
+        S.enc.clear();
+        for (size_t i = 0; i < S.host.size(); ++i) {
+            const uint8_t k = S.host[i].kind;
+            if (k == R_ROT || k == R_MAP3) S.enc.push_back((int32_t)i);
+            if (k == R_MAP3) i += 3;   // its data records are not kinds
+        }
+        S.n_chunks = (int)(S.host.size() / kChunkRecs);
+    }
+}
+
+void no_streams(DevPlan &P) {
+    P.streams = false;
+    P.sf = DevStreamBuf();
+    P.sb = DevStreamBuf();
+}
+
+// Reads and clears the kernels' status word (synchronizes the context).
+int check_status(stab_ctx *c) {
+    if (!c->status.p) return STAB_OK;
+    int32_t h = 0;
+    CK(cudaStreamSynchronize(c->aux));
+    CK(cudaMemcpyAsync(&h, c->status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h != 0) {
+        CK(cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->st));
+        CK(cudaStreamSynchronize(c->st));
+        return STAB_E_TIMEOUT;
+    }
     return STAB_OK;
 }
 
@@ -256,6 +329,8 @@ int ensure_grad_plan(stab_ctx *c) {
     if (!c->grad.built) {
         build_plan(c->n, c->gates.data(), (int64_t)c->gates.size(), c->n_params, PLAN_GRAD,
                    &c->grad.host);
+        if (c->use_resident_adjoint()) make_streams(c->grad);
+        else no_streams(c->grad);
         RC(upload_plan(c, c->grad));
     }
     if (!c->grad.encoded) RC(encode_plan(c, c->grad));
@@ -330,6 +405,14 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_stage, c->st);
+    if (e == cudaSuccess) {
+        const int r = c->dalloc(c->status, 256, c->st);
+        if (r != STAB_OK) {
+            stab_destroy(c);
+            return r;
+        }
+        e = cudaMemsetAsync(c->status.p, 0, 256, c->st);
+    }
     if (e != cudaSuccess) {
         g_last_cuda = (int)e;
         stab_destroy(c);
@@ -346,7 +429,7 @@ int stab_destroy(stab_ctx *c) {
     if (c->aux) cudaStreamSynchronize(c->aux);
     DevBuf *bufs[] = {&c->fwd.buf, &c->grad.buf, &c->thetas, &c->gens, &c->gens_tmp, &c->lam,
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
-                      &c->partials, &c->grads};
+                      &c->partials, &c->grads, &c->status};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -376,6 +459,8 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
     c->grad.built = false;
     c->grad.encoded = false;
     build_plan(c->n, gates, m, n_params, c->fwd_mode(), &c->fwd.host);
+    if (c->use_resident()) make_streams(c->fwd);
+    else no_streams(c->fwd);
     RC(upload_thetas_host(c, thetas));
     RC(upload_plan(c, c->fwd));
     RC(encode_plan(c, c->fwd));
@@ -413,13 +498,14 @@ int stab_run_generators(stab_ctx *c) {
     const size_t bytes = c->vec_bytes() * (size_t)n;
     RC(c->dalloc(c->gens, bytes, c->st));
     if (c->use_resident()) {
-        ResidentArgs a{};
-        a.prog = c->fwd.prog;
-        a.inverse = 0;
+        StreamArgs a{};
+        a.stream = c->fwd.sf.dev;
+        a.n_chunks = c->fwd.sf.n_chunks;
         a.init = INIT_GENERATOR;
         a.n_vec = n;
         a.out = (double *)c->gens.p;
-        CK(launch_resident(n, a, c->st));
+        a.status = (int32_t *)c->status.p;
+        CK(launch_resident_stream(n, a, c->st));
         c->launches++;
         c->gens_cur = (double *)c->gens.p;
     } else {
@@ -451,6 +537,7 @@ int stab_get_generators(stab_ctx *c, double *out, int out_is_device) {
         CK(cudaMemcpyAsync(out, c->gens_cur, bytes, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
         c->d2h_bytes += (int64_t)bytes;
+        RC(check_status(c));
     }
     return STAB_OK;
 }
@@ -478,15 +565,16 @@ int stab_expect_async(stab_ctx *c, double *out_dev) {
     CK(cudaStreamWaitEvent(s, c->ev_ready, 0));
     const int32_t nt = c->n_obs_terms;
     if (c->use_resident()) {
-        ResidentArgs a{};
-        a.prog = c->fwd.prog;
-        a.inverse = 1;
+        StreamArgs a{};
+        a.stream = c->fwd.sb.dev;
+        a.n_chunks = c->fwd.sb.n_chunks;
         a.init = INIT_TERMS;
         a.terms = (const DevTerm *)c->terms.p;
         a.n_terms = nt;
         a.n_vec = 1;
         a.xfree_out = out_dev;
-        CK(launch_resident(c->n, a, s));
+        a.status = (int32_t *)c->status.p;
+        CK(launch_resident_stream(c->n, a, s));
         c->launches++;
     } else {
         RC(c->dalloc(c->lam, c->vec_bytes(), s));
@@ -517,6 +605,7 @@ int stab_expect(stab_ctx *c, const stab_term *O, int64_t n_terms, double *out) {
     CK(cudaStreamSynchronize(c->st));
     c->d2h_bytes += (int64_t)sizeof(double);
     *out = *h;
+    RC(check_status(c));
     return STAB_OK;
 }
 
@@ -535,13 +624,17 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
     RC(c->dalloc(c->grad_rot, (size_t)(n_rot ? n_rot : 1) * sizeof(double), s));
     double *e_out = expect_dev ? expect_dev : (double *)c->scal.p + 1;
     if (c->use_resident_adjoint()) {
-        AdjointArgs a{};
-        a.prog = c->grad.prog;
+        AdjointStreamArgs a{};
+        a.fwd = c->grad.sf.dev;
+        a.bwd = c->grad.sb.dev;
+        a.n_fwd_chunks = c->grad.sf.n_chunks;
+        a.n_bwd_chunks = c->grad.sb.n_chunks;
         a.terms = (const DevTerm *)c->terms.p;
         a.n_terms = nt;
         a.grad_rot = (double *)c->grad_rot.p;
         a.expect_out = e_out;
-        CK(launch_adjoint_resident(n, a, s));
+        a.status = (int32_t *)c->status.p;
+        CK(launch_adjoint_stream(n, a, s));
         c->launches++;
     } else {
         const size_t vb = c->vec_bytes();
@@ -607,6 +700,7 @@ int stab_grad(stab_ctx *c, const stab_term *O, int64_t n_terms, double *expect_o
     c->d2h_bytes += (int64_t)(gbytes + sizeof(double));
     if (expect_out) *expect_out = h[0];
     if (gbytes) std::memcpy(grads_out, h + 8, gbytes);
+    RC(check_status(c));
     return STAB_OK;
 }
 
@@ -615,7 +709,7 @@ int stab_synchronize(stab_ctx *c) {
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->st));
     CK(cudaStreamSynchronize(c->aux));
-    return STAB_OK;
+    return check_status(c);
 }
 
 int stab_plan_info(stab_ctx *c, int64_t *n_gates, int64_t *n_passes, int32_t *kernel) {

@@ -78,6 +78,43 @@ struct Program {
     int32_t n_ops;
 };
 
+// ---------------------------------------------------------------- streams
+//
+// The shared-memory-resident kernels read a forward-only instruction stream
+// of 32-byte records, packed by the host into chunks of kChunkRecs records
+// that the kernel stages into shared memory with bulk copies.  A pass never
+// straddles a chunk.  Runs of two-qubit Clifford gates are not separate
+// passes: their records (R_CX, R_CZ) precede the next wire pass and are
+// applied while that pass reads its inputs (each entry is pulled through the
+// permutation).  The backward stream lists passes, pulls and ops in the order
+// the inverse circuit needs them, with rotations and maps flagged inverse, so
+// kernels never walk a stream backward.
+constexpr int kChunkRecs = 128;            // 4 KiB per chunk
+
+enum RecKind : uint8_t {
+    R_END = 0,    // end of the program
+    R_NEXT = 1,   // the rest of this chunk is unused: continue with the next chunk
+    R_PASS = 2,   // wire pass on qubit q: param = number of pull records, gate = op records
+    R_CX = 3,     // pull record CX(q -> q1)
+    R_CZ = 4,     // pull record CZ(q, q1)
+    R_ROT = 5,    // rotation (axis, param = angle slot, gate = gradient slot)
+    R_PERM = 6,   // signed permutation of (X, Y, Z); code = permutation code
+    R_MAP3 = 7,   // composed 3x3 map, param = index of the run; 3 R_DATA records follow
+    R_DATA = 8,   // raw storage of the 9 matrix entries of the preceding R_MAP3
+};
+
+struct Rec {            // 32 bytes
+    uint8_t kind;       // RecKind
+    uint8_t q, q1;      // qubits
+    uint8_t axis;       // R_ROT: Axis
+    int32_t param;
+    int32_t gate;
+    uint16_t code;      // R_PERM: permutation code; R_ROT: 1 when a factor R(pi) applies (device)
+    uint16_t inv;       // R_ROT / R_MAP3: 1 = apply the inverse (set by the host)
+    double t, s;        // R_ROT: shear coefficients (device)
+};
+static_assert(sizeof(Rec) == 32, "Rec layout");
+
 struct DevTerm {         // deduplicated observable term: index in the device layout
     double coeff;
     uint64_t idx;

@@ -230,3 +230,51 @@ def test_deterministic_repeat(stab):
     a = run_gens(stab, c)
     b = run_gens(stab, c)
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 7])
+def test_long_two_qubit_clifford_runs(stab, n):
+    """Runs of 150 consecutive CX/CZ gates between rotation layers (the
+    resident kernels split them across several pull passes)."""
+    rng = np.random.default_rng(n)
+    items, slot = [], 0
+    for _ in range(3):
+        for _ in range(150):
+            a = int(rng.integers(n))
+            b = int((a + 1 + rng.integers(n - 1)) % n)
+            items.append(("CX" if rng.random() < 0.7 else "CZ", a, b))
+        for q in range(n):
+            items.append(("RY", q, slot))
+            slot += 1
+    c = W.Circuit(n, W.gates_from_list(items), rng.uniform(0, 2 * math.pi, slot))
+    ref = oracle.generators(n, c.gates, c.thetas)
+    for kernel in ("auto", "streamed"):
+        got = run_gens(stab, c, kernel)
+        assert np.abs(got - ref).max() <= 1e-12, kernel
+    obs = W.obs_chain(n)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    e, g = s.grad(obs)
+    s.close()
+    assert abs(e - oracle.expect(n, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
+    gref = oracle.psr_grad(n, c.gates, c.thetas, obs)
+    assert np.abs(g - gref).max() <= 1e-12 * obs_l1(obs)
+
+
+def test_autograd_function_matches_psr(stab):
+    import torch
+    from paper_2502_10685_gb300.autograd import ExpectationLayer
+    c = W.layered_ansatz(4, 300, seed=8)
+    obs = W.obs_chain(4)
+    layer = ExpectationLayer(c, obs)
+    f = layer()
+    f.backward()
+    g = layer.thetas.grad.detach().cpu().numpy()
+    gref = oracle.psr_grad(4, c.gates, c.thetas, obs)
+    assert abs(float(f) - oracle.expect(4, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
+    assert np.abs(g - gref).max() <= 1e-12 * obs_l1(obs)
+    # one optimizer step moves <O> the way the gradient says
+    opt = torch.optim.SGD([layer.thetas], lr=1e-3)
+    opt.step()
+    f2 = float(layer())
+    assert f2 < float(f) + 1e-15
