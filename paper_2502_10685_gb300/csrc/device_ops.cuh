@@ -125,16 +125,39 @@ __device__ __forceinline__ uint64_t pull_2q(uint64_t i, int n, const DevOp &op, 
     return pull_2q_ab(i, n, op.kind == K_CX, op.q, op.q1, neg);
 }
 
+// 32-bit forms for the resident kernels (an index has at most 2n <= 24 bits).
+__device__ __forceinline__ uint32_t insert0_32(uint32_t v, int p) {
+    return ((v >> p) << (p + 1)) | (v & ((1u << p) - 1u));
+}
+
+__device__ __forceinline__ uint32_t group_base32(uint32_t g, int n, int q) {
+    return insert0_32(insert0_32(g, q), n + q);
+}
+
+__device__ __forceinline__ uint32_t pull_2q_32(uint32_t i, int n, bool is_cx, int a, int b,
+                                               uint32_t &neg) {
+    if (is_cx) {
+        const uint32_t xc = (i >> (n + a)) & 1u, zt = (i >> b) & 1u;
+        const uint32_t j = i ^ (xc << (n + b)) ^ (zt << a);
+        neg ^= xc & zt & (1u ^ (((j >> (n + b)) ^ (j >> a)) & 1u));
+        return j;
+    } else {
+        const uint32_t xa = (i >> (n + a)) & 1u, xb = (i >> (n + b)) & 1u;
+        const uint32_t j = i ^ (xb << a) ^ (xa << b);
+        neg ^= xa & xb & (((j >> a) ^ (j >> b)) & 1u);
+        return j;
+    }
+}
+
 // Source of output index i through the pull records of a stream pass (stored
 // in pull order).
 __device__ __forceinline__ uint32_t pull_recs(uint32_t i, int n, const Rec *pulls, int n_pull,
                                               uint32_t &neg) {
-    uint64_t j = i;
     for (int k = 0; k < n_pull; ++k) {
         const Rec &p = pulls[k];
-        j = pull_2q_ab(j, n, p.kind == R_CX, p.q, p.q1, neg);
+        i = pull_2q_32(i, n, p.kind == R_CX, p.q, p.q1, neg);
     }
-    return (uint32_t)j;
+    return i;
 }
 
 // Applies the op records of a stream pass to a group held in registers.

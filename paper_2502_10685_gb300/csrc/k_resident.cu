@@ -7,156 +7,26 @@
 // pulling every entry through the preceding run of two-qubit Clifford gates
 // (map_CX of Sec. III-C, and CZ) -- applies the wire's ops and writes the
 // other buffer; the buffers then swap.  Two thread mappings:
-//   LPG = 3 (n <= 4): the wire run is one composed 3x3 map and three lanes
-//     share a group, each computing one output row: three dependent FP64
-//     instructions per pass.  An FP64 instruction costs ~68 cycles per warp on
-//     this GPU whatever the active-lane mask, so this is the shortest pass.
+//   LPG = 4 (n <= 4): the wire run is one composed 3x3 map and a quad of
+//     lanes holds a group (slots I, X, Y, Z); each lane pulls its own entry,
+//     gets the other two through warp shuffles and computes its output row:
+//     three dependent FP64 instructions per pass.  An FP64 instruction costs
+//     ~68 cycles per warp on this GPU whatever the active-lane mask, so this is
+//     the shortest pass; the next pass's source index is computed while the
+//     current pass's FP64 chain is in flight.
 //   LPG = 1 (n = 5, 6): one lane per group running the ops in registers
 //     (lifting rotations, 3 FMAs per rotation): the fewest FP64 instructions.
 // The adjoint kernel carries the cotangent and the forward vector backward
 // together and reduces each rotation's gradient dot at the end of its pass.
 #include <cuda_runtime.h>
 
-#include "device_ops.cuh"
-#include "launch.h"
-#include "tma.cuh"
+#include "resident.cuh"
 
 namespace stab {
 
 namespace {
 
-template <int N, int LPG>
-struct SCfg {
-    static constexpr int E = 1 << (2 * N);   // coefficients per vector
-    static constexpr int G = E / 4;          // groups of one wire
-    static constexpr int L = G * LPG;        // working lanes
-    static constexpr int T = L < 32 ? 32 : (L > 1024 ? 1024 : ((L + 31) / 32) * 32);
-    static constexpr int GPT = (G + T - 1) / T;   // groups per thread (LPG = 1)
-    static constexpr int W = T / 32;
-};
-
-constexpr int R = kRotPerGradPass;
-
-// Shared memory: [chunks 2 x 4 KiB][mbarriers 16 B | flag | gradient slots][reduction][vectors]
-constexpr int kOffBar = 2 * kChunkRecs * (int)sizeof(Rec);
-constexpr int kOffFlag = kOffBar + 16;
-constexpr int kOffSlot = kOffBar + 32;
-constexpr int kOffRed = kOffBar + 128;
-constexpr int kSmemHeader = kOffRed + 32 * 8 * R;
-
-template <int N>
-__device__ __forceinline__ void group_idx(uint32_t g, int q, uint32_t &ii, uint32_t &ix,
-                                          uint32_t &iy, uint32_t &iz) {
-    ii = (uint32_t)group_base(g, N, q);
-    iz = ii | (1u << q);
-    ix = ii | (1u << (N + q));
-    iy = ix | (1u << q);
-}
-
-template <int N>
-__device__ __forceinline__ double pulled(const double *src, uint32_t i, const Rec *pulls,
-                                         int n_pull) {
-    uint32_t neg = 0;
-    const uint32_t j = pull_recs(i, N, pulls, n_pull, neg);
-    return flip(src[j], neg);
-}
-
-// One wire pass, LPG = 1: cur -> nxt.
-template <int N>
-__device__ __forceinline__ void pass_groups(const double *cur, double *nxt, int q,
-                                            const Rec *pulls, int n_pull, const Rec *ops,
-                                            int n_ops) {
-    using C = SCfg<N, 1>;
-#pragma unroll
-    for (int k = 0; k < C::GPT; ++k) {
-        const uint32_t g = threadIdx.x + k * C::T;
-        if (g < (uint32_t)C::G) {
-            uint32_t ii, ix, iy, iz;
-            group_idx<N>(g, q, ii, ix, iy, iz);
-            const double vi = pulled<N>(cur, ii, pulls, n_pull);
-            double x = pulled<N>(cur, ix, pulls, n_pull);
-            double y = pulled<N>(cur, iy, pulls, n_pull);
-            double z = pulled<N>(cur, iz, pulls, n_pull);
-            apply_recs(x, y, z, ops, n_ops);
-            nxt[ii] = vi;
-            nxt[ix] = x;
-            nxt[iy] = y;
-            nxt[iz] = z;
-        }
-    }
-}
-
-// One wire pass, LPG = 3: lane (g, r) writes output row r of group g.  The
-// pass holds no op (identity) or one R_MAP3 and its matrix.
-template <int N>
-__device__ __forceinline__ void pass_rows(const double *cur, double *nxt, int q,
-                                          const Rec *pulls, int n_pull, const Rec *ops,
-                                          int n_ops) {
-    using C = SCfg<N, 3>;
-    const uint32_t l = threadIdx.x;
-    if (l >= (uint32_t)C::L) return;
-    const uint32_t g = l / 3, r = l - 3 * g;
-    uint32_t ii, ix, iy, iz;
-    group_idx<N>(g, q, ii, ix, iy, iz);
-    const double x = pulled<N>(cur, ix, pulls, n_pull);
-    const double y = pulled<N>(cur, iy, pulls, n_pull);
-    const double z = pulled<N>(cur, iz, pulls, n_pull);
-    double out;
-    if (n_ops == 0) {
-        out = r == 0 ? x : (r == 1 ? y : z);
-    } else {
-        const double *m = reinterpret_cast<const double *>(&ops[1]) + 3 * r;
-        out = fma(m[2], z, fma(m[1], y, m[0] * x));
-    }
-    nxt[r == 0 ? ix : (r == 1 ? iy : iz)] = out;
-    if (r == 0) nxt[ii] = pulled<N>(cur, ii, pulls, n_pull);
-}
-
-template <int T>
-__device__ double block_sum(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double total = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < T / 32; ++w) total += red[w];
-    return total;
-}
-
-__device__ __forceinline__ void stager_setup(Stager &st, unsigned char *smem) {
-    st.buf = reinterpret_cast<Rec *>(smem);
-    st.bar = reinterpret_cast<uint64_t *>(smem + kOffBar);
-    st.flag = reinterpret_cast<int *>(smem + kOffFlag);
-}
-
-// Runs the passes of chunks [c0, c1) on one vector; returns the buffer that
-// holds the result, or nullptr when a staging wait gave up.
-template <int N, int LPG>
-__device__ double *run_stream(Stager &st, int c0, int c1, double *cur, double *nxt,
-                              int32_t *status) {
-    for (int c = c0; c < c1; ++c) {
-        if (!st.wait(c, status)) return nullptr;
-        const Rec *Rr = st.chunk(c);
-        int r = 0;
-        while (true) {
-            const Rec h = Rr[r];
-            if (h.kind != R_PASS) break;   // R_NEXT or R_END
-            const Rec *pulls = Rr + r + 1;
-            const Rec *ops = pulls + h.param;
-            if constexpr (LPG == 1) pass_groups<N>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
-            else pass_rows<N>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
-            double *t = cur;
-            cur = nxt;
-            nxt = t;
-            __syncthreads();
-            r += 1 + h.param + h.gate;
-        }
-        st.release(c);
-    }
-    return cur;
-}
+using namespace resident;
 
 template <int N, int LPG>
 __global__ void __launch_bounds__(SCfg<N, LPG>::T) k_resident_stream(StreamArgs a) {
@@ -361,14 +231,14 @@ cudaError_t launch_adjoint_stream_n(const AdjointStreamArgs &a, cudaStream_t s) 
 
 }  // namespace
 
-int resident_lanes_per_group(int n) { return n <= 4 ? 3 : 1; }
+int resident_lanes_per_group(int n) { return n <= 4 ? 4 : 1; }
 
 cudaError_t launch_resident_stream(int n, const StreamArgs &a, cudaStream_t s) {
     switch (n) {
-    case 1: return launch_stream_n<1, 3>(a, s);
-    case 2: return launch_stream_n<2, 3>(a, s);
-    case 3: return launch_stream_n<3, 3>(a, s);
-    case 4: return launch_stream_n<4, 3>(a, s);
+    case 1: return launch_stream_n<1, 4>(a, s);
+    case 2: return launch_stream_n<2, 4>(a, s);
+    case 3: return launch_stream_n<3, 4>(a, s);
+    case 4: return launch_stream_n<4, 4>(a, s);
     case 5: return launch_stream_n<5, 1>(a, s);
     case 6: return launch_stream_n<6, 1>(a, s);
     default: return cudaErrorInvalidValue;

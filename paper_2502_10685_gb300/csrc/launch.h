@@ -38,6 +38,9 @@ struct AdjointStreamArgs {
     int32_t *status;
 };
 
+// Records the CUDA error behind a STAB_E_CUDA status (stab_last_cuda_error).
+void record_cuda_error(cudaError_t e);
+
 // Encode kernel: lifting coefficients of every rotation op and composed 3x3
 // maps, from the angle array on the device.
 cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,

@@ -1,0 +1,190 @@
+// resident.cuh -- device building blocks of the shared-memory-resident
+// kernels (k_resident.cu) and the persistent batch kernel (k_batch.cu): pass
+// loops over a staged instruction stream on one vector held by one CTA.  The
+// vector buffers may live in shared memory or, for larger n, in a per-CTA
+// slab of global memory; the code is the same.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device_ops.cuh"
+#include "launch.h"
+#include "tma.cuh"
+
+namespace stab {
+namespace resident {
+
+template <int N, int LPG>
+struct SCfg {
+    static constexpr int E = 1 << (2 * N);   // coefficients per vector
+    static constexpr int G = E / 4;          // groups of one wire
+    static constexpr int L = G * LPG;        // working lanes
+    static constexpr int T = L < 32 ? 32 : (L > 1024 ? 1024 : ((L + 31) / 32) * 32);
+    static constexpr int GPT = (G + T - 1) / T;   // groups per thread (LPG = 1)
+    static constexpr int W = T / 32;
+};
+
+constexpr int R = kRotPerGradPass;
+
+// Shared memory: [chunks 2 x 4 KiB][mbarriers 16 B | flag | gradient slots][reduction][vectors]
+constexpr int kOffBar = 2 * kChunkRecs * (int)sizeof(Rec);
+constexpr int kOffFlag = kOffBar + 16;
+constexpr int kOffSlot = kOffBar + 32;
+constexpr int kOffRed = kOffBar + 128;
+constexpr int kSmemHeader = kOffRed + 32 * 8 * R;
+
+template <int N>
+__device__ __forceinline__ void group_idx(uint32_t g, int q, uint32_t &ii, uint32_t &ix,
+                                          uint32_t &iy, uint32_t &iz) {
+    ii = group_base32(g, N, q);
+    iz = ii | (1u << q);
+    ix = ii | (1u << (N + q));
+    iy = ix | (1u << q);
+}
+
+template <int N>
+__device__ __forceinline__ double pulled(const double *src, uint32_t i, const Rec *pulls,
+                                         int n_pull) {
+    uint32_t neg = 0;
+    const uint32_t j = pull_recs(i, N, pulls, n_pull, neg);
+    return flip(src[j], neg);
+}
+
+// One wire pass, LPG = 1: cur -> nxt, T threads, groups strided by T.
+template <int N, int T = SCfg<N, 1>::T>
+__device__ __forceinline__ void pass_groups(const double *cur, double *nxt, int q,
+                                            const Rec *pulls, int n_pull, const Rec *ops,
+                                            int n_ops) {
+    constexpr int G = (1 << (2 * N)) / 4;
+    constexpr int GPT = (G + T - 1) / T;
+#pragma unroll(GPT <= 8 ? GPT : 1)
+    for (int k = 0; k < GPT; ++k) {
+        const uint32_t g = threadIdx.x + k * T;
+        if (g < (uint32_t)G) {
+            uint32_t ii, ix, iy, iz;
+            group_idx<N>(g, q, ii, ix, iy, iz);
+            const double vi = pulled<N>(cur, ii, pulls, n_pull);
+            double x = pulled<N>(cur, ix, pulls, n_pull);
+            double y = pulled<N>(cur, iy, pulls, n_pull);
+            double z = pulled<N>(cur, iz, pulls, n_pull);
+            apply_recs(x, y, z, ops, n_ops);
+            nxt[ii] = vi;
+            nxt[ix] = x;
+            nxt[iy] = y;
+            nxt[iz] = z;
+        }
+    }
+}
+
+// Slot index of lane (g, slot) for a pass on wire q, and its pulled source.
+template <int N>
+__device__ __forceinline__ void quad_index(uint32_t g, uint32_t slot, int q, const Rec *pulls,
+                                           int n_pull, uint32_t &i, uint32_t &j, uint32_t &neg) {
+    const uint32_t b = group_base32(g, N, q);
+    // slot 0 = I, 1 = X, 2 = Y, 3 = Z
+    const uint32_t xb = (slot == 1u || slot == 2u) ? (1u << (N + q)) : 0u;
+    const uint32_t zb = (slot >= 2u) ? (1u << q) : 0u;
+    i = b | xb | zb;
+    neg = 0;
+    j = pull_recs(i, N, pulls, n_pull, neg);
+}
+
+template <int T>
+__device__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double total = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < T / 32; ++w) total += red[w];
+    return total;
+}
+
+__device__ __forceinline__ void stager_setup(Stager &st, unsigned char *smem) {
+    st.buf = reinterpret_cast<Rec *>(smem);
+    st.bar = reinterpret_cast<uint64_t *>(smem + kOffBar);
+    st.flag = reinterpret_cast<int *>(smem + kOffFlag);
+}
+
+// Runs the passes of chunks [c0, c1) on one vector; returns the buffer that
+// holds the result, or nullptr when a staging wait gave up.
+// LPG = 4 pass loop (see the file comment).
+template <int N>
+__device__ double *run_stream_quads(Stager &st, int c0, int c1, double *cur, double *nxt,
+                                    int32_t *status) {
+    constexpr int L = (1 << (2 * N));   // 4 lanes per group of 4 entries
+    const uint32_t l = threadIdx.x;
+    const bool active = l < (uint32_t)L;
+    const uint32_t g = l >> 2, slot = l & 3u;
+    const uint32_t lane = l & 31u, qbase = lane & ~3u;
+    for (int c = c0; c < c1; ++c) {
+        if (!st.wait(c, status)) return nullptr;
+        const Rec *Rr = st.chunk(c);
+        int r = 0;
+        Rec h = Rr[0];
+        uint32_t i = 0, j = 0, neg = 0;
+        if (h.kind == R_PASS && active) quad_index<N>(g, slot, h.q, Rr + 1, h.param, i, j, neg);
+        while (h.kind == R_PASS) {
+            const int r_next = r + 1 + h.param + h.gate;
+            const Rec hn = Rr[r_next];
+            double v = 0.0;
+            if (active) v = flip(cur[j], neg);
+            const double x = __shfl_sync(0xffffffffu, v, qbase + 1);
+            const double y = __shfl_sync(0xffffffffu, v, qbase + 2);
+            const double z = __shfl_sync(0xffffffffu, v, qbase + 3);
+            double out = v;
+            if (h.gate != 0 && slot != 0u) {
+                const double *m =
+                    reinterpret_cast<const double *>(Rr + r + 2 + h.param) + 3 * (slot - 1u);
+                out = fma(m[2], z, fma(m[1], y, m[0] * x));
+            }
+            // source of the next pass, computed while the FP64 chain above runs
+            uint32_t i2 = 0, j2 = 0, neg2 = 0;
+            if (hn.kind == R_PASS && active)
+                quad_index<N>(g, slot, hn.q, Rr + r_next + 1, hn.param, i2, j2, neg2);
+            if (active) nxt[i] = out;
+            double *t = cur;
+            cur = nxt;
+            nxt = t;
+            __syncthreads();
+            h = hn;
+            r = r_next;
+            i = i2;
+            j = j2;
+            neg = neg2;
+        }
+        st.release(c);
+    }
+    return cur;
+}
+
+// The block must have at least 4^n threads for LPG = 4.
+template <int N, int LPG, int T = SCfg<N, LPG>::T>
+__device__ double *run_stream(Stager &st, int c0, int c1, double *cur, double *nxt,
+                              int32_t *status) {
+    if constexpr (LPG == 4) return run_stream_quads<N>(st, c0, c1, cur, nxt, status);
+    for (int c = c0; c < c1; ++c) {
+        if (!st.wait(c, status)) return nullptr;
+        const Rec *Rr = st.chunk(c);
+        int r = 0;
+        while (true) {
+            const Rec h = Rr[r];
+            if (h.kind != R_PASS) break;   // R_NEXT or R_END
+            const Rec *pulls = Rr + r + 1;
+            const Rec *ops = pulls + h.param;
+            pass_groups<N, T>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
+            double *t = cur;
+            cur = nxt;
+            nxt = t;
+            __syncthreads();
+            r += 1 + h.param + h.gate;
+        }
+        st.release(c);
+    }
+    return cur;
+}
+
+}  // namespace resident
+}  // namespace stab

@@ -18,6 +18,12 @@ namespace {
 
 thread_local int g_last_cuda = 0;
 
+}  // namespace
+
+void stab::record_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
+
+namespace {
+
 #define CK(expr)                                                    \
     do {                                                            \
         cudaError_t e_ = (expr);                                    \
@@ -152,7 +158,7 @@ struct stab_ctx {
     }
     PlanMode fwd_mode() const {
         if (kernel == STAB_KERNEL_PLAIN || !fuse) return PLAN_PLAIN;
-        if (use_resident() && resident_lanes_per_group(n) == 3) return PLAN_ROWS;
+        if (use_resident() && resident_lanes_per_group(n) == 4) return PLAN_ROWS;
         return PLAN_FUSED;
     }
 };

@@ -75,6 +75,25 @@ struct Stager {
     Rec *buf;          // 2 x kChunkRecs records in shared memory
     uint64_t *bar;     // 2 mbarriers in shared memory
     int *flag;         // shared flag: 1 = chunk ready, 0 = gave up
+    uint32_t ph0 = 0, ph1 = 0;   // phases each barrier completed before this sequence
+
+    __device__ uint32_t parity(int c) const {
+        return ((c & 1 ? ph1 : ph0) + (uint32_t)(c >> 1)) & 1u;
+    }
+    // Phases completed once all n_total chunks of this sequence are consumed.
+    __device__ void advance_phases() {
+        ph0 += (uint32_t)((n_total + 1) / 2);
+        ph1 += (uint32_t)(n_total / 2);
+    }
+    // Later sequences on the same barriers (persistent kernels): issue the
+    // first chunks without re-initialising the barriers.
+    __device__ void restart() {
+        if (threadIdx.x == 0) {
+            if (n_total > 0) issue(0);
+            if (n_total > 1) issue(1);
+        }
+        __syncthreads();
+    }
 
     __device__ const Rec *src(int c) const {
         return c < n0 ? s0 + (size_t)c * kChunkRecs : s1 + (size_t)(c - n0) * kChunkRecs;
@@ -99,14 +118,13 @@ struct Stager {
     // every thread) when the bounded wait gave up; *status is then set.
     __device__ bool wait(int c, int32_t *status) {
         if (threadIdx.x == 0) {
-            bool ok = mbar_wait_bounded(bar + (c & 1), (uint32_t)((c >> 1) & 1));
+            bool ok = mbar_wait_bounded(bar + (c & 1), parity(c));
             *flag = ok ? 1 : 0;
             if (!ok) {
                 if (status) atomicExch(status, STAB_KSTATUS_TIMEOUT);
                 // let the copies in flight land before the block exits (bounded)
-                mbar_wait_bounded(bar + (c & 1), (uint32_t)((c >> 1) & 1));
-                if (c + 1 < n_total)
-                    mbar_wait_bounded(bar + ((c + 1) & 1), (uint32_t)(((c + 1) >> 1) & 1));
+                mbar_wait_bounded(bar + (c & 1), parity(c));
+                if (c + 1 < n_total) mbar_wait_bounded(bar + ((c + 1) & 1), parity(c + 1));
             }
         }
         __syncthreads();
