@@ -183,6 +183,31 @@ int stab_grad_async(stab_ctx *ctx, double *expect_dev, double *grads_dev);
 int stab_grad(stab_ctx *ctx, const stab_term *O, int64_t n_terms, double *expect_out,
               double *grads_out);
 
+/* <0^n| U^dagger O U |0^n> without any device allocation, for callers that
+ * must not allocate device memory (a program that reserves its device budget
+ * at start-up and allows no growth later, or code running inside a framework
+ * whose allocator owns the device).  The paper has no counterpart: this is a
+ * deployment entry point around the same propagation as stab_expect with
+ * STAB_KERNEL_STREAMED.
+ *  n, gates (m records), thetas (n_params), O (n_terms terms): host memory,
+ *    meaning as in stab_load_circuit and stab_expect; out: host double.
+ *  stream: cudaStream_t to queue on (NULL = the legacy default stream); the
+ *    call waits for its own work before returning.
+ * Everything the call needs on the device -- the planned passes, the angles,
+ * the terms and two working vectors of 4^n doubles -- lives in one 16 MiB
+ * workspace that the library holds as a static device array on every GPU
+ * that loads it, until the process exits.  A problem that does not fit
+ * (roughly n <= 9 for short circuits; fewer qubits for very long ones)
+ * returns STAB_E_RANGE.  The first call on a device looks up the workspace's
+ * device address with that device current; make that first call before any
+ * stream capture.  All calls share the workspace: calls whose work overlaps
+ * on the GPU (other threads, other streams) race and give wrong results, so
+ * serialize them.  Errors: as stab_load_circuit and stab_expect, STAB_E_RANGE
+ * (too large), STAB_E_CUDA. */
+int stab_expect_static(int n, const stab_gate *gates, int64_t m, const double *thetas,
+                       int64_t n_params, const stab_term *O, int64_t n_terms, double *out,
+                       void *stream);
+
 /* Waits for all work queued by the context. */
 int stab_synchronize(stab_ctx *ctx);
 

@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
             "stab_expect_async": (i32, [vp, dp]),
             "stab_grad_async": (i32, [vp, dp, dp]),
             "stab_transfer_bytes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "stab_expect_static": (i32, [i32, vp, i64, dp, i64, vp, i64, dp, vp]),
             "stab_synchronize": (i32, [vp]),
             "stab_plan_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_int32)]),
