@@ -1,6 +1,6 @@
 """CUDA path vs the CPU oracle, element by element, through the C interface.
 
-Tolerances (from the spec reading, applied per vector): generators
+Tolerances (the stated 1e-12 relative, 1e-10 after 60K gates, applied per vector): generators
 max |a - b| <= tol * ||b||_2 (= tol, generators have unit norm); <O> within
 tol * sum |o_P|; tol = 1e-12, or 1e-10 for circuits of 60K gates and more.
 Clifford-only circuits must match bit for bit.
