@@ -38,6 +38,37 @@ struct AdjointStreamArgs {
     int32_t *status;
 };
 
+// One unit of the persistent batch kernel: one vector of one circuit.
+struct BatchUnit {             // 64 bytes
+    const Rec *stream;         // the circuit's forward (generators) or backward (<O>) stream
+    int32_t n_chunks;
+    int8_t n;                  // qubits (1 .. 8)
+    int8_t init;               // INIT_GENERATOR or INIT_TERMS
+    int16_t gen;               // generator index for INIT_GENERATOR
+    const DevTerm *terms;      // INIT_TERMS
+    int32_t n_terms;
+    int32_t pad;
+    double *out;               // final vector (may be null)
+    double *xfree_out;         // <O> (may be null)
+    int64_t cost;              // host-side ordering key
+    int64_t reserved;
+};
+static_assert(sizeof(BatchUnit) == 64, "BatchUnit layout");
+
+struct BatchArgs {
+    const BatchUnit *units;
+    int32_t n_units;
+    int32_t *counter;          // next unit to take (zeroed before the launch)
+    int32_t *status;
+    double *slab;              // per-CTA global vectors for n > kMaxResidentQubits (may be null)
+    size_t slab_doubles;       // doubles per CTA slab
+};
+
+size_t batch_smem_bytes(int max_n_in_smem);
+int batch_threads();
+cudaError_t batch_occupancy(size_t smem, int *ctas_per_sm);
+cudaError_t launch_batch(const BatchArgs &a, int grid, size_t smem, cudaStream_t s);
+
 // Records the CUDA error behind a STAB_E_CUDA status (stab_last_cuda_error).
 void record_cuda_error(cudaError_t e);
 
