@@ -208,6 +208,55 @@ int stab_expect_static(int n, const stab_gate *gates, int64_t m, const double *t
                        int64_t n_params, const stab_term *O, int64_t n_terms, double *out,
                        void *stream);
 
+/* ---------------------------------------------------------------- batches */
+/* Many independent circuits of different sizes evaluated by one persistent
+ * launch (replayed from a CUDA graph): every generator of a generator item
+ * and the observable of an expectation item is one unit of work; CTAs take
+ * units longest first.  The 2m parameter-shift copies of a circuit (Sec. I)
+ * are expectation items that differ only in their angles. */
+#define STAB_BATCH_MAX_QUBITS 8
+
+enum stab_item_kind { STAB_ITEM_GENERATORS = 0, STAB_ITEM_EXPECT = 1 };
+
+typedef struct stab_batch_item {
+    int32_t n;               /* qubits, 1 <= n <= STAB_BATCH_MAX_QUBITS */
+    int32_t kind;            /* stab_item_kind */
+    const stab_gate *gates;  /* m records, host memory, rules of stab_load_circuit */
+    int64_t m;
+    const double *thetas;    /* n_params angles, host memory */
+    int64_t n_params;
+    const stab_term *obs;    /* STAB_ITEM_EXPECT: n_terms terms, host memory */
+    int64_t n_terms;
+} stab_batch_item;
+
+typedef struct stab_batch stab_batch;
+
+/* Validates, plans and uploads count items (all host arrays are copied before
+ * return).  opts may be NULL; with kernel = STAB_KERNEL_AUTO the number of
+ * CTAs per SM is picked by timing candidate launches on a sample of the
+ * units.  Errors: as stab_load_circuit / stab_expect, STAB_E_RANGE (n > 8 or
+ * count < 1), STAB_E_NOMEM, STAB_E_CUDA. */
+int stab_batch_create(const stab_batch_item *items, int64_t count, const stab_opts *opts,
+                      stab_batch **out);
+
+/* Queues one evaluation of every item (asynchronous). */
+int stab_batch_run(stab_batch *b);
+
+/* After stab_batch_run: <O> of every item into out[0 .. count) (host; NaN for
+ * generator items).  Synchronizes.  Errors: STAB_E_STATE (never run),
+ * STAB_E_TIMEOUT. */
+int stab_batch_expectations(stab_batch *b, double *out);
+
+/* After stab_batch_run: the n x 4^n generators of generator item `item`
+ * (host memory if out_is_device == 0, synchronizing; else device memory). */
+int stab_batch_generators(stab_batch *b, int64_t item, double *out, int out_is_device);
+
+/* units: vectors in the batch; grid: CTAs of the persistent launch;
+ * ctas_per_sm: the chosen residency.  Any pointer may be NULL. */
+int stab_batch_info(stab_batch *b, int64_t *units, int32_t *grid, int32_t *ctas_per_sm);
+
+int stab_batch_destroy(stab_batch *b);
+
 /* Waits for all work queued by the context. */
 int stab_synchronize(stab_ctx *ctx);
 

@@ -48,6 +48,12 @@ class StabOpts(ctypes.Structure):
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 
+class StabBatchItem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("kind", ctypes.c_int32), ("gates", ctypes.c_void_p),
+                ("m", ctypes.c_int64), ("thetas", ctypes.c_void_p), ("n_params", ctypes.c_int64),
+                ("obs", ctypes.c_void_p), ("n_terms", ctypes.c_int64)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -82,6 +88,14 @@ def load(build_if_missing: bool = True):
             "stab_grad_async": (i32, [vp, dp, dp]),
             "stab_transfer_bytes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "stab_expect_static": (i32, [i32, vp, i64, dp, i64, vp, i64, dp, vp]),
+            "stab_batch_create": (i32, [ctypes.POINTER(StabBatchItem), i64,
+                                        ctypes.POINTER(StabOpts), ctypes.POINTER(vp)]),
+            "stab_batch_run": (i32, [vp]),
+            "stab_batch_expectations": (i32, [vp, dp]),
+            "stab_batch_generators": (i32, [vp, i64, dp, i32]),
+            "stab_batch_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+            "stab_batch_destroy": (i32, [vp]),
             "stab_synchronize": (i32, [vp]),
             "stab_plan_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_int32)]),

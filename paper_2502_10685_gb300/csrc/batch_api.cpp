@@ -1,0 +1,450 @@
+// batch_api.cpp -- stab_batch_*: many uneven circuits in one persistent launch.
+//
+// Create plans every item, concatenates all instruction streams, angle
+// arrays, map gate lists and observable terms into one device buffer (one
+// host-to-device copy), encodes every rotation and map with one launch, and
+// builds the unit table (one unit per propagated vector) sorted longest
+// first.  Run replays a CUDA graph holding the counter reset and the
+// persistent launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/stab.h"
+#include "launch.h"
+#include "planner.h"
+
+using namespace stab;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct stab_batch {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_st = false;
+    stab_alloc_fn alloc = nullptr;
+    stab_free_fn free = nullptr;
+    void *user = nullptr;
+
+    int64_t count = 0;
+    std::vector<int32_t> item_n, item_kind;
+    std::vector<int64_t> gen_off;     // doubles into the generator buffer (-1: none)
+    int n_units = 0;
+    int max_n = 1;
+    int grid = 0;
+    int ctas_per_sm = 1;
+    size_t smem = 0;
+
+    Buf data, gens, exps, slab, counter;   // counter also holds the status word
+    const BatchUnit *units_dev = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool ran = false;
+
+    int dalloc(Buf &b, size_t bytes) {
+        bytes = up256(bytes ? bytes : 256);
+        void *p = nullptr;
+        if (alloc) {
+            p = alloc(bytes, (void *)st, user);
+            if (!p) return STAB_E_NOMEM;
+        } else {
+            cudaError_t e = cudaMallocAsync(&p, bytes, st);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                if (e == cudaErrorMemoryAllocation) return STAB_E_NOMEM;
+                record_cuda_error(e);
+                return STAB_E_CUDA;
+            }
+        }
+        b.p = p;
+        b.bytes = bytes;
+        return STAB_OK;
+    }
+    void dfree(Buf &b) {
+        if (!b.p) return;
+        if (free) free(b.p, b.bytes, (void *)st, user);
+        else cudaFreeAsync(b.p, st);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+};
+
+namespace {
+
+#define BCK(expr)                       \
+    do {                                \
+        cudaError_t e_ = (expr);        \
+        if (e_ != cudaSuccess) {        \
+            record_cuda_error(e_);      \
+            return STAB_E_CUDA;         \
+        }                               \
+    } while (0)
+
+#define BRC(expr)                        \
+    do {                                 \
+        int r_ = (expr);                 \
+        if (r_ != STAB_OK) return r_;    \
+    } while (0)
+
+int launch_graph_or_direct(stab_batch *b, const BatchArgs &a, int grid, bool use_graph) {
+    if (!use_graph) {
+        BCK(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), b->st));
+        BCK(launch_batch(a, grid, b->smem, b->st));
+        return STAB_OK;
+    }
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), b->st);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_batch(a, grid, b->smem, b->st) : e1;
+        cudaError_t e3 = cudaStreamEndCapture(b->st, &g);
+        if (e2 != cudaSuccess || e3 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            record_cuda_error(e2 != cudaSuccess ? e2 : e3);
+            return STAB_E_CUDA;
+        }
+        cudaError_t e4 = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        BCK(e4);
+    }
+    BCK(cudaGraphLaunch(b->graph, b->st));
+    return STAB_OK;
+}
+
+BatchArgs make_args(stab_batch *b, int n_units) {
+    BatchArgs a{};
+    a.units = b->units_dev;
+    a.n_units = n_units;
+    a.counter = (int32_t *)b->counter.p;
+    a.status = (int32_t *)b->counter.p + 32;
+    a.slab = (double *)b->slab.p;
+    a.slab_doubles = b->max_n > kMaxResidentQubits ? (size_t)2 << (2 * b->max_n) : 0;
+    return a;
+}
+
+// Picks CTAs per SM by timing the persistent launch on a prefix of the unit
+// table (the longest units) for each candidate residency.
+int autotune(stab_batch *b, int sms, int max_occ) {
+    const int sample = std::min(b->n_units, 2 * sms * max_occ);
+    float best = 1e30f;
+    int best_occ = max_occ;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    std::vector<int> cands;
+    for (int occ : {1, 2, 4, max_occ})
+        if (occ <= max_occ && std::find(cands.begin(), cands.end(), occ) == cands.end())
+            cands.push_back(occ);
+    for (int occ : cands) {
+        const BatchArgs a = make_args(b, sample);
+        BRC(launch_graph_or_direct(b, a, sms * occ, false));   // warm-up
+        BCK(cudaEventRecord(e0, b->st));
+        BRC(launch_graph_or_direct(b, a, sms * occ, false));
+        BCK(cudaEventRecord(e1, b->st));
+        BCK(cudaEventSynchronize(e1));
+        float ms = 0;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_occ = occ;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->ctas_per_sm = best_occ;
+    return STAB_OK;
+}
+
+int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel) {
+    std::vector<Rec> recs;
+    std::vector<int32_t> enc;
+    std::vector<DevMap3> maps;
+    std::vector<int32_t> midx;
+    std::vector<RawGate> raw;
+    std::vector<double> thetas;
+    std::vector<DevTerm> terms;
+    struct UnitPlan {
+        int64_t rec_off, n_chunks, term_off, n_terms, item;
+        int n, init, gen;
+        int64_t cost;
+    };
+    std::vector<UnitPlan> ups;
+    b->item_n.resize(count);
+    b->item_kind.resize(count);
+    b->gen_off.assign(count, -1);
+    int64_t gens_doubles = 0;
+    for (int64_t it = 0; it < count; ++it) {
+        const stab_batch_item &I = items[it];
+        if (I.n < 1 || I.n > STAB_BATCH_MAX_QUBITS) return STAB_E_RANGE;
+        if (I.kind != STAB_ITEM_GENERATORS && I.kind != STAB_ITEM_EXPECT) return STAB_E_INVAL;
+        BRC(validate_gates(I.n, I.gates, I.m, I.n_params, nullptr));
+        BRC(validate_thetas(I.thetas, I.n_params));
+        std::vector<DevTerm> t;
+        if (I.kind == STAB_ITEM_EXPECT) BRC(encode_terms(I.n, I.obs, I.n_terms, &t));
+        b->item_n[it] = I.n;
+        b->item_kind[it] = I.kind;
+        b->max_n = std::max(b->max_n, (int)I.n);
+
+        HostPlan P;
+        build_plan(I.n, I.gates, I.m, I.n_params, I.n <= 4 ? PLAN_ROWS : PLAN_FUSED, &P);
+        std::vector<Rec> S;
+        build_stream(P, I.kind == STAB_ITEM_EXPECT, &S);
+        const int64_t th_off = (int64_t)thetas.size(), raw_off = (int64_t)raw.size();
+        const int64_t map_off = (int64_t)maps.size(), midx_off = (int64_t)midx.size();
+        const int64_t rec_off = (int64_t)recs.size();
+        for (size_t i = 0; i < S.size(); ++i) {
+            Rec r = S[i];
+            if (r.kind == R_ROT) {
+                r.param += (int32_t)th_off;
+                enc.push_back((int32_t)(rec_off + (int64_t)i));
+            } else if (r.kind == R_MAP3) {
+                r.param += (int32_t)map_off;
+                enc.push_back((int32_t)(rec_off + (int64_t)i));
+                recs.push_back(r);
+                for (int k = 1; k <= 3; ++k) recs.push_back(S[i + k]);
+                i += 3;
+                continue;
+            }
+            recs.push_back(r);
+        }
+        for (DevMap3 mp : P.maps) {
+            mp.first += (int32_t)midx_off;
+            maps.push_back(mp);
+        }
+        for (int32_t g : P.map_gate_idx) midx.push_back(g + (int32_t)raw_off);
+        for (RawGate g : P.raw) {
+            if (g.op >= STAB_RX) g.param += (int32_t)th_off;
+            raw.push_back(g);
+        }
+        thetas.insert(thetas.end(), I.thetas, I.thetas + I.n_params);
+        const int64_t n_chunks = (int64_t)S.size() / kChunkRecs;
+        const int64_t cost = n_chunks * ((int64_t)1 << (2 * I.n));
+        if (I.kind == STAB_ITEM_GENERATORS) {
+            b->gen_off[it] = gens_doubles;
+            for (int k = 0; k < I.n; ++k)
+                ups.push_back({rec_off, n_chunks, 0, 0, it, I.n, INIT_GENERATOR, k, cost});
+            gens_doubles += (int64_t)I.n << (2 * I.n);
+        } else {
+            const int64_t toff = (int64_t)terms.size();
+            terms.insert(terms.end(), t.begin(), t.end());
+            ups.push_back({rec_off, n_chunks, toff, (int64_t)t.size(), it, I.n, INIT_TERMS, 0,
+                           cost});
+        }
+        if (recs.size() > (size_t)INT32_MAX / 2) return STAB_E_RANGE;
+    }
+    std::stable_sort(ups.begin(), ups.end(),
+                     [](const UnitPlan &x, const UnitPlan &y) { return x.cost > y.cost; });
+    b->n_units = (int)ups.size();
+
+    // one device buffer: recs | enc | maps | midx | raw | thetas | terms | units
+    const size_t o_recs = 0;
+    const size_t o_enc = o_recs + up256(recs.size() * sizeof(Rec));
+    const size_t o_maps = o_enc + up256(enc.size() * 4);
+    const size_t o_midx = o_maps + up256(maps.size() * sizeof(DevMap3));
+    const size_t o_raw = o_midx + up256(midx.size() * 4);
+    const size_t o_th = o_raw + up256(raw.size() * sizeof(RawGate));
+    const size_t o_terms = o_th + up256(thetas.size() * 8);
+    const size_t o_units = o_terms + up256(terms.size() * sizeof(DevTerm));
+    const size_t total = o_units + up256(ups.size() * sizeof(BatchUnit));
+    BRC(b->dalloc(b->data, total));
+    BRC(b->dalloc(b->gens, (size_t)std::max<int64_t>(gens_doubles, 1) * 8));
+    BRC(b->dalloc(b->exps, (size_t)count * 8));
+    BRC(b->dalloc(b->counter, 256));
+    BCK(cudaMemsetAsync(b->counter.p, 0, 256, b->st));
+    char *d = (char *)b->data.p;
+    std::vector<BatchUnit> units(ups.size());
+    for (size_t k = 0; k < ups.size(); ++k) {
+        const UnitPlan &u = ups[k];
+        BatchUnit U{};
+        U.stream = (const Rec *)(d + o_recs) + u.rec_off;
+        U.n_chunks = (int32_t)u.n_chunks;
+        U.n = (int8_t)u.n;
+        U.init = (int8_t)u.init;
+        U.gen = (int16_t)u.gen;
+        U.terms = (const DevTerm *)(d + o_terms) + u.term_off;
+        U.n_terms = (int32_t)u.n_terms;
+        if (u.init == INIT_GENERATOR) {
+            U.out = (double *)b->gens.p + b->gen_off[u.item] + ((int64_t)u.gen << (2 * u.n));
+        } else {
+            U.xfree_out = (double *)b->exps.p + u.item;
+        }
+        U.cost = u.cost;
+        units[k] = U;
+    }
+    void *h = nullptr;
+    BCK(cudaMallocHost(&h, total));
+    char *hc = (char *)h;
+    auto put = [&](size_t off, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(hc + off, src, bytes);
+    };
+    put(o_recs, recs.data(), recs.size() * sizeof(Rec));
+    put(o_enc, enc.data(), enc.size() * 4);
+    put(o_maps, maps.data(), maps.size() * sizeof(DevMap3));
+    put(o_midx, midx.data(), midx.size() * 4);
+    put(o_raw, raw.data(), raw.size() * sizeof(RawGate));
+    put(o_th, thetas.data(), thetas.size() * 8);
+    put(o_terms, terms.data(), terms.size() * sizeof(DevTerm));
+    put(o_units, units.data(), units.size() * sizeof(BatchUnit));
+    cudaError_t e = cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess && !enc.empty())
+        e = launch_encode_stream((Rec *)(d + o_recs), (const int32_t *)(d + o_enc), (int)enc.size(),
+                                 (const DevMap3 *)(d + o_maps), (const int32_t *)(d + o_midx),
+                                 (const RawGate *)(d + o_raw), (const double *)(d + o_th), b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    cudaFreeHost(h);
+    BCK(e);
+    b->units_dev = (const BatchUnit *)(d + o_units);
+
+    // residency: shared memory for the vectors of n <= 6, a global slab above
+    const int smem_n = std::min(b->max_n, kMaxResidentQubits);
+    b->smem = batch_smem_bytes(smem_n);
+    int max_occ = 1, sms = 0;
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    BCK(batch_occupancy(b->smem, &max_occ));
+    if (max_occ < 1) return STAB_E_RANGE;
+    max_occ = std::min(max_occ, 8);
+    if (b->max_n > kMaxResidentQubits) {
+        // the slabs of all resident CTAs: 2 x 4^max_n doubles each
+        const size_t per = (size_t)2 << (2 * b->max_n);
+        BRC(b->dalloc(b->slab, per * 8 * (size_t)sms * max_occ));
+    }
+    b->ctas_per_sm = max_occ;
+    if (kernel == STAB_KERNEL_AUTO && max_occ > 1) BRC(autotune(b, sms, max_occ));
+    b->grid = sms * b->ctas_per_sm;
+    return STAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stab_batch_create(const stab_batch_item *items, int64_t count, const stab_opts *opts,
+                      stab_batch **out) {
+    if (!out) return STAB_E_INVAL;
+    *out = nullptr;
+    if (count < 1 || count > (int64_t)INT32_MAX / 16) return STAB_E_RANGE;
+    if (!items) return STAB_E_INVAL;
+    stab_opts o;
+    stab_default_opts(&o);
+    if (opts) o = *opts;
+    if ((o.alloc == nullptr) != (o.free == nullptr)) return STAB_E_INVAL;
+    stab_batch *b = new (std::nothrow) stab_batch();
+    if (!b) return STAB_E_NOMEM;
+    b->alloc = o.alloc;
+    b->free = o.free;
+    b->user = o.alloc_user;
+    b->count = count;
+    int dev = o.device;
+    cudaError_t e = cudaSuccess;
+    if (dev < 0) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e == cudaSuccess) {
+        b->device = dev;
+        if (o.stream || o.stream_given) {
+            b->st = (cudaStream_t)o.stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+            b->own_st = e == cudaSuccess;
+        }
+    }
+    if (e != cudaSuccess) {
+        record_cuda_error(e);
+        stab_batch_destroy(b);
+        return STAB_E_CUDA;
+    }
+    const int rc = build(b, items, count, o.kernel);
+    if (rc != STAB_OK) {
+        stab_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return STAB_OK;
+}
+
+int stab_batch_run(stab_batch *b) {
+    if (!b) return STAB_E_INVAL;
+    BCK(cudaSetDevice(b->device));
+    const BatchArgs a = make_args(b, b->n_units);
+    BRC(launch_graph_or_direct(b, a, b->grid, true));
+    b->ran = true;
+    return STAB_OK;
+}
+
+static int batch_status(stab_batch *b) {
+    int32_t h = 0;
+    BCK(cudaMemcpyAsync(&h, (int32_t *)b->counter.p + 32, 4, cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    if (h != 0) {
+        BCK(cudaMemsetAsync((int32_t *)b->counter.p + 32, 0, 4, b->st));
+        return STAB_E_TIMEOUT;
+    }
+    return STAB_OK;
+}
+
+int stab_batch_expectations(stab_batch *b, double *out) {
+    if (!b || !out) return STAB_E_INVAL;
+    if (!b->ran) return STAB_E_STATE;
+    BCK(cudaSetDevice(b->device));
+    std::vector<double> h((size_t)b->count);
+    BCK(cudaMemcpyAsync(h.data(), b->exps.p, (size_t)b->count * 8, cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    BRC(batch_status(b));
+    for (int64_t i = 0; i < b->count; ++i)
+        out[i] = b->item_kind[i] == STAB_ITEM_EXPECT ? h[i] : std::nan("");
+    return STAB_OK;
+}
+
+int stab_batch_generators(stab_batch *b, int64_t item, double *out, int out_is_device) {
+    if (!b || !out || item < 0 || item >= b->count) return STAB_E_INVAL;
+    if (b->gen_off[item] < 0) return STAB_E_INVAL;
+    if (!b->ran) return STAB_E_STATE;
+    BCK(cudaSetDevice(b->device));
+    const int n = b->item_n[item];
+    const size_t bytes = ((size_t)n << (2 * n)) * 8;
+    const double *src = (const double *)b->gens.p + b->gen_off[item];
+    if (out_is_device) {
+        BCK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, b->st));
+        return STAB_OK;
+    }
+    BCK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    return batch_status(b);
+}
+
+int stab_batch_info(stab_batch *b, int64_t *units, int32_t *grid, int32_t *ctas_per_sm) {
+    if (!b) return STAB_E_INVAL;
+    if (units) *units = b->n_units;
+    if (grid) *grid = b->grid;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    return STAB_OK;
+}
+
+int stab_batch_destroy(stab_batch *b) {
+    if (!b) return STAB_OK;
+    cudaSetDevice(b->device);
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->dfree(b->data);
+    b->dfree(b->gens);
+    b->dfree(b->exps);
+    b->dfree(b->slab);
+    b->dfree(b->counter);
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->own_st && b->st) cudaStreamDestroy(b->st);
+    delete b;
+    return STAB_OK;
+}
+
+}  // extern "C"

@@ -111,10 +111,8 @@ cudaError_t batch_occupancy(size_t smem, int *ctas_per_sm) {
                                                          smem);
 }
 
+// batch_occupancy() sets the kernel's shared-memory limit before the first launch.
 cudaError_t launch_batch(const BatchArgs &a, int grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     k_batch<<<grid, kBatchThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

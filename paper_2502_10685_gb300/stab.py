@@ -16,7 +16,7 @@ from typing import Iterable, Optional, Sequence, Tuple
 import numpy as np
 
 from . import _lib
-from ._lib import StabError, StabGate, StabOpts, StabTerm, check
+from ._lib import StabBatchItem, StabError, StabGate, StabOpts, StabTerm, check
 
 KERNELS = {"auto": 0, "resident": 1, "streamed": 2, "plain": 3}
 GATE_DTYPE = np.dtype([("op", "u1"), ("q0", "u1"), ("q1", "u1"), ("flags", "u1"),
@@ -286,3 +286,102 @@ class Stab:
 
     def launch_count(self) -> int:
         return stab_launch_count(self.h)
+
+
+# ---------------------------------------------------------------- batches
+
+ITEM_KINDS = {"generators": 0, "expect": 1}
+
+
+def _torch_alloc_opts(opts, device, holder):
+    import torch
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    opts.stream = ctypes.c_void_p(stream.cuda_stream)
+    opts.stream_given = 1
+
+    def _alloc(nbytes, st, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, stream))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, st, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
+    holder += [a, f, stream]
+    opts.alloc = a
+    opts.free = f
+
+
+class Batch:
+    """Many uneven circuits evaluated by one persistent launch.
+
+    ``items``: objects with ``circuit`` (workloads.Circuit), ``kind``
+    ("generators" or "expect") and ``observable`` (for "expect").
+    """
+
+    def __init__(self, items, device: int = 0, kernel: str = "auto", torch_memory: bool = True):
+        self._keep = []
+        self.items = list(items)
+        arr = (StabBatchItem * len(self.items))()
+        for k, it in enumerate(self.items):
+            c = it.circuit
+            g = np.ascontiguousarray(c.gates)
+            th = np.ascontiguousarray(c.thetas if c.n_params else np.zeros(1), dtype=np.float64)
+            self._keep += [g, th]
+            arr[k].n = c.n
+            arr[k].kind = ITEM_KINDS[it.kind]
+            arr[k].gates = g.ctypes.data if c.m else None
+            arr[k].m = c.m
+            arr[k].thetas = th.ctypes.data
+            arr[k].n_params = c.n_params
+            if it.kind == "expect":
+                t = terms_from_observable(c.n, it.observable)
+                self._keep.append(t)
+                arr[k].obs = t.ctypes.data if len(t) else None
+                arr[k].n_terms = len(t)
+        opts = stab_default_opts()
+        opts.device = device
+        opts.kernel = KERNELS[kernel]
+        if torch_memory:
+            _torch_alloc_opts(opts, device, self._keep)
+        h = ctypes.c_void_p()
+        check(_lib.load().stab_batch_create(arr, len(self.items), ctypes.byref(opts),
+                                            ctypes.byref(h)), "stab_batch_create")
+        self.h = h
+        self._keep = [x for x in self._keep if not isinstance(x, np.ndarray)]
+
+    def run(self) -> None:
+        check(_lib.load().stab_batch_run(self.h), "stab_batch_run")
+
+    def expectations(self) -> np.ndarray:
+        out = np.empty(len(self.items))
+        check(_lib.load().stab_batch_expectations(self.h, out.ctypes.data),
+              "stab_batch_expectations")
+        return out
+
+    def generators(self, item: int) -> np.ndarray:
+        n = self.items[item].circuit.n
+        out = np.empty((n, 4 ** n))
+        check(_lib.load().stab_batch_generators(self.h, item, out.ctypes.data, 0),
+              "stab_batch_generators")
+        return out
+
+    def info(self):
+        u, g, o = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        check(_lib.load().stab_batch_info(self.h, ctypes.byref(u), ctypes.byref(g),
+                                          ctypes.byref(o)), "stab_batch_info")
+        return {"units": u.value, "grid": g.value, "ctas_per_sm": o.value}
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            _lib.load().stab_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,94 @@
+"""Persistent batched launch vs the oracle: uneven circuits (n = 1..8), both
+generator and expectation items, and the 2m parameter-shift copies of one
+circuit whose shifted expectations must reproduce the adjoint gradient."""
+import math
+
+import numpy as np
+import pytest
+
+import layout
+import oracle
+from paper_2502_10685_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def l1(obs):
+    return sum(abs(a) for a, _ in obs)
+
+
+@pytest.fixture(scope="module")
+def stab():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2502_10685_gb300 import stab as S
+    return S
+
+
+def mixed_items(seed):
+    rng = np.random.default_rng(seed)
+    items = []
+    for k in range(40):
+        n = int(rng.integers(1, 9))
+        m = int(rng.integers(10, 160 if n <= 6 else 60))
+        if rng.random() < 0.5:
+            c = W.layered_ansatz(n, m, seed=seed * 1000 + k)
+        else:
+            c = W.random_circuit(n, m, seed=seed * 1000 + k)
+        if rng.random() < 0.5:
+            items.append(W.BatchItem(c, "generators"))
+        else:
+            items.append(W.BatchItem(c, "expect", W.random_observable(n, 4, seed=k)))
+    return items
+
+
+def test_batch_mixed_sizes_against_oracle(stab):
+    items = mixed_items(1)
+    b = stab.Batch(items)
+    b.run()
+    ex = b.expectations()
+    for k, it in enumerate(items):
+        c = it.circuit
+        if it.kind == "expect":
+            ref = oracle.expect(c.n, c.gates, c.thetas, it.observable)
+            assert abs(ex[k] - ref) <= 1e-12 * l1(it.observable), k
+        else:
+            assert math.isnan(ex[k])
+            ref = oracle.generators(c.n, c.gates, c.thetas)
+            got = layout.lib_to_paper(c.n, b.generators(k))
+            assert np.abs(got - ref).max() <= 1e-12, k
+    # the graph replay gives bit-identical results
+    b.run()
+    ex2 = b.expectations()
+    np.testing.assert_array_equal(np.nan_to_num(ex), np.nan_to_num(ex2))
+    b.close()
+
+
+def test_batch_parameter_shift_equals_adjoint(stab):
+    base = W.layered_ansatz(5, 120, seed=77)
+    obs = W.obs_chain(5)
+    variants = W.psr_variants(base)
+    items = [W.BatchItem(v, "expect", obs) for v in variants]
+    items += mixed_items(2)[:10]
+    b = stab.Batch(items)
+    b.run()
+    ex = b.expectations()
+    m = base.n_params
+    psr = np.array([(ex[2 * j] - ex[2 * j + 1]) / 2 for j in range(m)])
+    s = stab.Stab(5)
+    s.load_circuit(base.gates, base.thetas)
+    _, g = s.grad(obs)
+    s.close()
+    assert np.abs(psr - g).max() <= 1e-12 * l1(obs)
+    assert np.abs(psr - oracle.psr_grad(5, base.gates, base.thetas, obs)).max() <= 1e-12 * l1(obs)
+    info = b.info()
+    assert info["units"] == sum(1 if it.kind == "expect" else it.circuit.n for it in items)
+    b.close()
+
+
+def test_batch_rejects_too_many_qubits(stab):
+    from paper_2502_10685_gb300._lib import StabError
+    c = W.layered_ansatz(9, 20, seed=1)
+    with pytest.raises(StabError):
+        stab.Batch([W.BatchItem(c, "generators")])
