@@ -33,7 +33,10 @@ size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct stab_batch {
     int device = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr;        // internal stream: capture and launches
+    cudaStream_t user_st = nullptr;   // caller's stream, joined by events
+    bool has_user_st = false;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     bool own_st = false;
     stab_alloc_fn alloc = nullptr;
     stab_free_fn free = nullptr;
@@ -352,13 +355,16 @@ int stab_batch_create(const stab_batch_item *items, int64_t count, const stab_op
     if (e == cudaSuccess) e = cudaSetDevice(dev);
     if (e == cudaSuccess) {
         b->device = dev;
-        if (o.stream || o.stream_given) {
-            b->st = (cudaStream_t)o.stream;
-        } else {
-            e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
-            b->own_st = e == cudaSuccess;
-        }
+        // the persistent launch is captured into a graph, which the legacy
+        // default stream cannot do: run on an own stream and join the
+        // caller's stream with events
+        b->has_user_st = o.stream != nullptr || o.stream_given;
+        b->user_st = (cudaStream_t)o.stream;
+        e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+        b->own_st = e == cudaSuccess;
     }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         record_cuda_error(e);
         stab_batch_destroy(b);
@@ -377,7 +383,15 @@ int stab_batch_run(stab_batch *b) {
     if (!b) return STAB_E_INVAL;
     BCK(cudaSetDevice(b->device));
     const BatchArgs a = make_args(b, b->n_units);
+    if (b->has_user_st) {
+        BCK(cudaEventRecord(b->ev_in, b->user_st));
+        BCK(cudaStreamWaitEvent(b->st, b->ev_in, 0));
+    }
     BRC(launch_graph_or_direct(b, a, b->grid, true));
+    if (b->has_user_st) {
+        BCK(cudaEventRecord(b->ev_out, b->st));
+        BCK(cudaStreamWaitEvent(b->user_st, b->ev_out, 0));
+    }
     b->ran = true;
     return STAB_OK;
 }
@@ -442,6 +456,8 @@ int stab_batch_destroy(stab_batch *b) {
     b->dfree(b->slab);
     b->dfree(b->counter);
     if (b->st) cudaStreamSynchronize(b->st);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->own_st && b->st) cudaStreamDestroy(b->st);
     delete b;
     return STAB_OK;
