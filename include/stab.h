@@ -257,6 +257,74 @@ int stab_batch_info(stab_batch *b, int64_t *units, int32_t *grid, int32_t *ctas_
 
 int stab_batch_destroy(stab_batch *b);
 
+/* ---------------------------------------------------------------- serving */
+/* A request server with continuous batching: requests (an expectation value
+ * or an adjoint gradient of one circuit) are queued as they arrive and
+ * admitted, first come first served, whenever a slot and enough HBM budget
+ * are free; each admitted request runs on its own pooled context and
+ * streams, so the work of all admitted requests overlaps on the device, and
+ * requests join and leave while others are running.  Contexts keep their
+ * device vectors between requests.  The paper has no counterpart (it
+ * evaluates one circuit per call). */
+typedef struct stab_server stab_server;
+
+typedef struct stab_server_opts {
+    int32_t device;        /* CUDA device ordinal, -1 = current */
+    int32_t max_active;    /* requests admitted at once (0 = 64) */
+    int64_t hbm_budget;    /* bytes of request state admitted at once (0 = 32 GiB) */
+    int32_t planners;      /* host threads that plan and launch requests (0 = 4) */
+    int32_t reserved;
+} stab_server_opts;
+
+enum stab_request_kind { STAB_REQ_EXPECT = 0, STAB_REQ_GRAD = 1 };
+
+typedef struct stab_request {
+    int32_t n;               /* 1 <= n <= STAB_MAX_QUBITS */
+    int32_t kind;            /* stab_request_kind */
+    const stab_gate *gates;  /* host memory, copied by stab_server_submit */
+    int64_t m;
+    const double *thetas;
+    int64_t n_params;
+    const stab_term *obs;
+    int64_t n_terms;
+} stab_request;
+
+typedef struct stab_result {
+    int32_t status;          /* STAB_OK or this request's error */
+    int32_t n_params;
+    double expect;           /* <O> */
+    double submit_s;         /* server clock (seconds since creation) */
+    double admit_s;          /* admitted: planning and launch started */
+    double done_s;           /* results on the host */
+} stab_result;
+
+/* Admission footprint of a request: max(n 4^n 8, 4^n 8 x (2 for <O>, 4 for a
+ * gradient)) bytes plus 64 bytes per gate. */
+int64_t stab_request_footprint(const stab_request *req);
+
+int stab_server_create(const stab_server_opts *opts, stab_server **out);
+
+/* Queues a copy of *req; *id identifies it.  Invalid requests are accepted
+ * and complete with their error status.  A request whose footprint exceeds
+ * the whole budget completes with STAB_E_NOMEM. */
+int stab_server_submit(stab_server *s, const stab_request *req, int64_t *id);
+
+/* Waits up to timeout_s (< 0: forever) for request id.  grads (host, may be
+ * NULL) receives the n_params gradient entries of a gradient request.
+ * Errors: STAB_E_INVAL (unknown id), STAB_E_TIMEOUT (not done in time). */
+int stab_server_wait(stab_server *s, int64_t id, double timeout_s, stab_result *out,
+                     double *grads);
+
+/* *done = 1 when request id has completed. */
+int stab_server_poll(stab_server *s, int64_t id, int32_t *done);
+
+/* Counters: requests submitted, completed, admitted now, bytes admitted now. */
+int stab_server_stats(stab_server *s, int64_t *submitted, int64_t *completed, int64_t *active,
+                      int64_t *bytes_in_use);
+
+/* Waits for every queued request, then releases the server. */
+int stab_server_destroy(stab_server *s);
+
 /* Waits for all work queued by the context. */
 int stab_synchronize(stab_ctx *ctx);
 

@@ -54,6 +54,24 @@ class StabBatchItem(ctypes.Structure):
                 ("obs", ctypes.c_void_p), ("n_terms", ctypes.c_int64)]
 
 
+class StabServerOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64), ("planners", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class StabRequest(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("kind", ctypes.c_int32), ("gates", ctypes.c_void_p),
+                ("m", ctypes.c_int64), ("thetas", ctypes.c_void_p), ("n_params", ctypes.c_int64),
+                ("obs", ctypes.c_void_p), ("n_terms", ctypes.c_int64)]
+
+
+class StabResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_params", ctypes.c_int32),
+                ("expect", ctypes.c_double), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -96,6 +114,14 @@ def load(build_if_missing: bool = True):
             "stab_batch_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
             "stab_batch_destroy": (i32, [vp]),
+            "stab_request_footprint": (i64, [ctypes.POINTER(StabRequest)]),
+            "stab_server_create": (i32, [ctypes.POINTER(StabServerOpts), ctypes.POINTER(vp)]),
+            "stab_server_submit": (i32, [vp, ctypes.POINTER(StabRequest), ctypes.POINTER(i64)]),
+            "stab_server_wait": (i32, [vp, i64, ctypes.c_double, ctypes.POINTER(StabResult), dp]),
+            "stab_server_poll": (i32, [vp, i64, ctypes.POINTER(ctypes.c_int32)]),
+            "stab_server_stats": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                        ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "stab_server_destroy": (i32, [vp]),
             "stab_synchronize": (i32, [vp]),
             "stab_plan_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_int32)]),

@@ -69,6 +69,16 @@ int batch_threads();
 cudaError_t batch_occupancy(size_t smem, int *ctas_per_sm);
 cudaError_t launch_batch(const BatchArgs &a, int grid, size_t smem, cudaStream_t s);
 
+}  // namespace stab
+
+typedef struct stab_ctx stab_ctx;
+
+namespace stab {
+
+// The context's main stream (work queued by the asynchronous entry points is
+// complete once this stream is).
+cudaStream_t ctx_stream(stab_ctx *ctx);
+
 // Records the CUDA error behind a STAB_E_CUDA status (stab_last_cuda_error).
 void record_cuda_error(cudaError_t e);
 

@@ -346,6 +346,8 @@ int ensure_grad_plan(stab_ctx *c) {
 
 }  // namespace
 
+cudaStream_t stab::ctx_stream(stab_ctx *c) { return c ? c->st : nullptr; }
+
 extern "C" {
 
 void stab_default_opts(stab_opts *o) {

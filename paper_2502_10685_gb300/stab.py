@@ -16,7 +16,8 @@ from typing import Iterable, Optional, Sequence, Tuple
 import numpy as np
 
 from . import _lib
-from ._lib import StabBatchItem, StabError, StabGate, StabOpts, StabTerm, check
+from ._lib import (StabBatchItem, StabError, StabGate, StabOpts, StabRequest, StabResult,
+                   StabServerOpts, StabTerm, check)
 
 KERNELS = {"auto": 0, "resident": 1, "streamed": 2, "plain": 3}
 GATE_DTYPE = np.dtype([("op", "u1"), ("q0", "u1"), ("q1", "u1"), ("flags", "u1"),
@@ -378,6 +379,99 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "h", None) is not None:
             _lib.load().stab_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving
+
+REQUEST_KINDS = {"expect": 0, "grad": 1}
+
+
+class Server:
+    """Continuous-batching request server (stab_server_*).
+
+    ``submit`` copies the request and returns its id immediately; ``wait``
+    blocks for its result: a dict with ``status``, ``expect``, ``grads`` (for
+    gradient requests) and the server-clock times ``submit_s``, ``admit_s``,
+    ``done_s``.
+    """
+
+    def __init__(self, device: int = 0, max_active: int = 0, hbm_budget: int = 0,
+                 planners: int = 0):
+        o = StabServerOpts()
+        o.device = device
+        o.max_active = max_active
+        o.hbm_budget = hbm_budget
+        o.planners = planners
+        h = ctypes.c_void_p()
+        check(_lib.load().stab_server_create(ctypes.byref(o), ctypes.byref(h)),
+              "stab_server_create")
+        self.h = h
+        self._n_params = {}
+
+    @staticmethod
+    def _request(circuit, kind, observable, keep):
+        r = StabRequest()
+        g = np.ascontiguousarray(circuit.gates)
+        th = np.ascontiguousarray(circuit.thetas if circuit.n_params else np.zeros(1),
+                                  dtype=np.float64)
+        t = terms_from_observable(circuit.n, observable)
+        keep += [g, th, t]
+        r.n = circuit.n
+        r.kind = REQUEST_KINDS[kind]
+        r.gates = g.ctypes.data if circuit.m else None
+        r.m = circuit.m
+        r.thetas = th.ctypes.data
+        r.n_params = circuit.n_params
+        r.obs = t.ctypes.data if len(t) else None
+        r.n_terms = len(t)
+        return r
+
+    @staticmethod
+    def footprint(circuit, kind: str, observable) -> int:
+        keep = []
+        r = Server._request(circuit, kind, observable, keep)
+        return int(_lib.load().stab_request_footprint(ctypes.byref(r)))
+
+    def submit(self, circuit, kind: str, observable) -> int:
+        keep = []
+        r = self._request(circuit, kind, observable, keep)
+        i = ctypes.c_int64()
+        check(_lib.load().stab_server_submit(self.h, ctypes.byref(r), ctypes.byref(i)),
+              "stab_server_submit")
+        self._n_params[i.value] = circuit.n_params
+        return i.value
+
+    def wait(self, rid: int, timeout_s: float = -1.0) -> dict:
+        res = StabResult()
+        npar = self._n_params.get(rid, 0)
+        grads = np.zeros(max(npar, 1))
+        check(_lib.load().stab_server_wait(self.h, rid, timeout_s, ctypes.byref(res),
+                                           grads.ctypes.data), "stab_server_wait")
+        return {"status": res.status, "expect": res.expect, "grads": grads[:npar],
+                "submit_s": res.submit_s, "admit_s": res.admit_s, "done_s": res.done_s}
+
+    def done(self, rid: int) -> bool:
+        d = ctypes.c_int32()
+        check(_lib.load().stab_server_poll(self.h, rid, ctypes.byref(d)), "stab_server_poll")
+        return bool(d.value)
+
+    def stats(self) -> dict:
+        a, b, c, d = (ctypes.c_int64() for _ in range(4))
+        check(_lib.load().stab_server_stats(self.h, ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.byref(c), ctypes.byref(d)), "stab_server_stats")
+        return {"submitted": a.value, "completed": b.value, "active": c.value,
+                "bytes_in_use": d.value}
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            _lib.load().stab_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
