@@ -305,6 +305,34 @@ def run_ours(args):
                 "kernel": "k_resident<4> (generators)", "launch_ms": gen_avg_s * 1e3,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock"}
 
+    # the plain GPU form: one launch per gate, no fusion, same step
+    plain = None
+    if not args.no_plain:
+        sp = stab.Stab(c.n, kernel="plain", device=local)
+        sp.load_circuit(c.gates, c.thetas)
+        sp.set_observable(obs)
+        out_p = torch.zeros(8, dtype=torch.float64, device=dev)
+
+        def pstep():
+            sp.set_params(th_dev)
+            sp.run_generators()
+            sp.expect_async(out_p)
+        pstep()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(st)
+        for _ in range(reps):
+            pstep()
+        e1.record(st)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / reps
+        assert abs(float(out_p[0].item()) - got) <= 1e-10
+        plain = {"value": units_per_step(c) / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                 "speedup": pms / (total_ms / args.steps),
+                 "form": "one launch per gate, no fusion (STAB_KERNEL_PLAIN)"}
+        sp.close()
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -317,6 +345,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": (h1 - h0) // e2e_steps,
                 "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
         "gpu_launches": launches,
+        "vs_plain_form": plain,
         "roofline": roofline,
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                    "reasons": clk.get("reasons"), "samples": clk.get("samples")},
@@ -332,6 +361,181 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- other configurations
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batch(args):
+    """Uneven batch: 4,096 circuits (n ~ U{2..8}, depth ~ U[100, 20000]) including
+    the 2m parameter-shift copies of a 6-qubit 2,000-gate circuit, one
+    persistent launch per step; compared with one fused launch per circuit and
+    one launch per gate (both timed on a seeded sample, scaled by updates)."""
+    import numpy as np
+    import torch
+    from paper_2502_10685_gb300 import stab, workloads as W
+    torch.cuda.set_stream(torch.cuda.Stream())
+    st = torch.cuda.current_stream()
+    items = W.uneven_batch(4096, seed=1003)
+    t0 = time.perf_counter()
+    b = stab.Batch(items)
+    create_s = time.perf_counter() - t0
+    upd = sum((it.circuit.n if it.kind == "generators" else 1) * it.circuit.m * 4 ** it.circuit.n
+              for it in items)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = _events()
+        e0.record(st)
+        b.run()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    forms = {}
+    rng = np.random.default_rng(0)
+    sample = [items[i] for i in rng.choice(len(items), size=16, replace=False)]
+    s_upd = sum((it.circuit.n if it.kind == "generators" else 1) * it.circuit.m * 4 ** it.circuit.n
+                for it in sample)
+    for kernel in ("auto", "plain"):
+        tot = 0.0
+        for it in sample:
+            c = it.circuit
+            sx = stab.Stab(c.n, kernel=kernel)
+            sx.load_circuit(c.gates, c.thetas)
+            out = torch.zeros(8, dtype=torch.float64, device="cuda")
+            if it.kind == "expect":
+                sx.set_observable(it.observable)
+                fn = lambda: sx.expect_async(out)
+            else:
+                fn = sx.run_generators
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+            sx.close()
+        est = tot * upd / s_upd
+        forms["fused_per_circuit" if kernel == "auto" else "plain_per_gate"] = {
+            "extrapolated_ms": est, "batch_speedup": est / ms, "sample_circuits": len(sample)}
+    info = b.info()
+    b.close()
+    print(json.dumps({
+        "metric": "circuits/s", "value": len(items) / (ms / 1e3), "unit": "circuits/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batch-c3", "circuits": len(items), "units": info["units"],
+                   "grid": info["grid"], "ctas_per_sm": info["ctas_per_sm"],
+                   "l2": "flushed between steps"},
+        "updates_per_s": upd / (ms / 1e3), "create_s": create_s, "vs_forms": forms}))
+    return 0
+
+
+def run_grad(args):
+    """n=8, 10,000-gate layered ansatz, O = sum Z_i Z_{i+1} + 0.5 sum X_i: all
+    gradients by one adjoint sweep, vs parameter shift (2 evaluations per
+    slot) in one batched launch, timed on 64 slots and scaled to all."""
+    import numpy as np
+    import torch
+    from paper_2502_10685_gb300 import stab, workloads as W
+    torch.cuda.set_stream(torch.cuda.Stream())
+    st = torch.cuda.current_stream()
+    c = W.layered_ansatz(8, 10000, seed=1004)
+    obs = W.obs_chain(8)
+    s = stab.Stab(8)
+    s.load_circuit(c.gates, c.thetas)
+    s.set_observable(obs)
+    g = torch.zeros(c.n_params, dtype=torch.float64, device="cuda")
+    e = torch.zeros(8, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        s.grad_async(e, g)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = _events()
+        e0.record(st)
+        s.grad_async(e, g)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    adj_ms = sum(times) / len(times)
+    grads = g.cpu().numpy()
+    # parameter shift on a sample of slots, batched
+    rng = np.random.default_rng(1)
+    js = rng.choice(c.n_params, size=64, replace=False)
+    items = []
+    for j in js:
+        for sgn in (1.0, -1.0):
+            th = c.thetas.copy()
+            th[j] += sgn * math.pi / 2
+            items.append(W.BatchItem(c.with_thetas(th), "expect", obs))
+    b = stab.Batch(items)
+    b.run()
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(st)
+    b.run()
+    e1.record(st)
+    torch.cuda.synchronize()
+    psr_ms = e0.elapsed_time(e1)
+    ex = b.expectations()
+    b.close()
+    psr = np.array([(ex[2 * k] - ex[2 * k + 1]) / 2 for k in range(len(js))])
+    err = float(np.abs(psr - grads[js]).max())
+    l1 = sum(abs(a) for a, _ in obs)
+    assert err <= 1e-10 * l1, err
+    psr_all_ms = psr_ms * c.n_params / len(js)
+    s.close()
+    print(json.dumps({
+        "metric": "gradient time", "value": adj_ms, "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": adj_ms,
+        "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "grad-c4", "n": 8, "gates": c.m, "params": c.n_params},
+        "psr_batched_ms_all_params": psr_all_ms, "adjoint_speedup": psr_all_ms / adj_ms,
+        "max_abs_diff_vs_psr_sample": err}))
+    return 0
+
+
+def run_serve(args):
+    """Poisson trace (2,000 req/s), n ~ U{4..12}, depth log-uniform [100, 60000],
+    50/50 <O> / gradient requests, submitted at their arrival times to the
+    continuous-batching server; latency = completion - arrival."""
+    import numpy as np
+    from paper_2502_10685_gb300 import stab, workloads as W
+    reqs = W.serving_trace(args.requests, seed=1005)
+    srv = stab.Server(max_active=args.max_active)
+    t0 = time.perf_counter()
+    ids = []
+    for r in reqs:
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(r.circuit, r.kind, r.observable))
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    assert all(x["status"] == 0 for x in res)
+    lat = np.array([x["done_s"] - x["submit_s"] for x in res])
+    span = max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)
+    upd = sum((1 if r.kind == "expect" else 2) * r.circuit.m * 4 ** r.circuit.n for r in reqs)
+    print(json.dumps({
+        "metric": "p50/p99 latency", "value": float(np.percentile(lat, 50)), "unit": "s",
+        "p99_s": float(np.percentile(lat, 99)), "n_gpus": 1, "higher_is_better": False,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve-c5", "requests": len(reqs), "rate_per_s": 2000,
+                   "max_active": args.max_active},
+        "circuits_per_s": len(reqs) / span, "updates_per_s": upd / span, "makespan_s": span}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,11 +545,20 @@ def main():
     ap.add_argument("--workload", default="layered-n4-60200")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--requests", type=int, default=200, help="serve-c5: trace length")
+    ap.add_argument("--max-active", type=int, default=64, help="serve-c5: admitted at once")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch-c3":
+        return run_batch(args)
+    if args.workload == "grad-c4":
+        return run_grad(args)
+    if args.workload == "serve-c5":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -86,31 +86,46 @@ def layered_ansatz(n: int, m: int, seed: int, p_replace: float = 0.1) -> Circuit
     (50/50).  The ring is CX(q -> q+1 mod n) for q = 0..n-1 (none for n = 1).
     Every surviving rotation gets its own slot with theta ~ U[0, 2 pi).  The
     list is cut at exactly ``m`` gates, so the last layer may be partial.
+    Draws (PCG64): one uniform per rotation slot for the replacement test, one
+    for the H/S choice and one angle, each as an array over all slots.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
+    ring = n if n >= 2 else 0
+    per_layer = 3 * n + ring
+    layers = -(-m // per_layer) if m > 0 else 0
+    # one layer's template
+    t_op = np.empty(per_layer, dtype=np.uint8)
+    t_q0 = np.empty(per_layer, dtype=np.uint8)
+    t_q1 = np.zeros(per_layer, dtype=np.uint8)
+    rot = np.zeros(per_layer, dtype=bool)
+    k = 0
+    for q in range(n):
+        for r in ("RX", "RY", "RZ"):
+            t_op[k], t_q0[k], rot[k] = OPS[r], q, True
+            k += 1
+    for q in range(ring):
+        t_op[k], t_q0[k], t_q1[k] = OPS["CX"], q, (q + 1) % n
+        k += 1
+    op = np.tile(t_op, layers)[:m]
+    q0 = np.tile(t_q0, layers)[:m]
+    q1 = np.tile(t_q1, layers)[:m]
+    is_rot = np.tile(rot, layers)[:m]
+    n_slots = int(is_rot.sum())
+    u = rng.random(n_slots)
+    hs = rng.random(n_slots) < 0.5
+    theta = rng.uniform(0.0, 2.0 * math.pi, n_slots)
+    replaced = u < p_replace
+    slot_ops = op[is_rot].copy()
+    slot_ops[replaced] = np.where(hs[replaced], OPS["H"], OPS["S"])
+    op[is_rot] = slot_ops
+    param = np.full(m, -1, dtype=np.int32)
+    keep = ~replaced
+    slot_param = np.full(n_slots, -1, dtype=np.int32)
+    slot_param[keep] = np.arange(int(keep.sum()), dtype=np.int32)
+    param[is_rot] = slot_param
     recs = np.zeros(m, dtype=GATE_DTYPE)
-    thetas: List[float] = []
-    i = 0
-    ring = [(q, (q + 1) % n) for q in range(n)] if n >= 2 else []
-    while i < m:
-        for q in range(n):
-            for rot in ("RX", "RY", "RZ"):
-                if i >= m:
-                    break
-                u = rng.random()
-                if u < p_replace:
-                    op = OPS["H"] if rng.random() < 0.5 else OPS["S"]
-                    recs[i] = (op, q, 0, 0, -1)
-                else:
-                    recs[i] = (OPS[rot], q, 0, 0, len(thetas))
-                    thetas.append(rng.uniform(0.0, 2.0 * math.pi))
-                i += 1
-        for (c, t) in ring:
-            if i >= m:
-                break
-            recs[i] = (OPS["CX"], c, t, 0, -1)
-            i += 1
-    return Circuit(n, recs, np.asarray(thetas, dtype=np.float64))
+    recs["op"], recs["q0"], recs["q1"], recs["param"] = op, q0, q1, param
+    return Circuit(n, recs, np.ascontiguousarray(theta[keep], dtype=np.float64))
 
 
 def paper_shaped_ansatz(n: int, layers: int, repeats: int, seed: int) -> Circuit:
