@@ -198,6 +198,19 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- ranks
+
+def combine_ranks(local_ms, units_per_rank, world, dist=None, device=None):
+    """Whole-job figures for replicas: the slowest rank's time (barrier-bounded
+    region, max over ranks) and the units of all ranks divided by it."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1 and dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    return total_ms, units_per_rank * world / (total_ms / 1e3)
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -264,12 +277,8 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     gen_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = units_per_step(c) * args.steps * world / (total_ms / 1e3)
+    total_ms, value = combine_ranks(sum(step_ms), units_per_step(c) * args.steps, world,
+                                    dist if world > 1 else None, dev)
 
     # check the device result against the host path once (same circuit)
     got = float(out_dev[0].item())
@@ -300,10 +309,18 @@ def run_ours(args):
     peak = SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     gen_avg_s = statistics.mean(gen_ms) / 1e3
     achieved = algorithmic_flops_generators(c) / gen_avg_s / 1e12
+    # DRAM bytes per launch from one ncu capture of k_resident_stream<4,4> on the
+    # 2,000-gate case (125,440 B read, 0 B written: the staged instruction stream),
+    # scaled by gates (the stream grows in proportion); see profiles/.
+    traffic = 125440.0 * c.m / 2000.0 if c.n == 4 else None
+    active_sms = c.n + 1
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_resident<4> (generators)", "launch_ms": gen_avg_s * 1e3,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock"}
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_resident_stream<4,4> (generators)", "launch_ms": gen_avg_s * 1e3,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock",
+                "active_sms": active_sms,
+                "frac_of_active_sms": achieved / (peak * active_sms / SMS),
+                "note": "one circuit: 5 independent vectors, one CTA each; passes are sequential"}
 
     # the plain GPU form: one launch per gate, no fusion, same step
     plain = None

@@ -345,6 +345,14 @@ int stab_last_cuda_error(void);
 
 int stab_version(void);
 
+/* Self-test of failure reporting: runs one small kernel whose thread 0 waits
+ * on a shared-memory barrier that nothing ever completes, giving up after
+ * `polls` polls exactly as every bounded wait of the library does, and
+ * returns what the host reads back: STAB_E_TIMEOUT when the bound was reached
+ * (any polls > 0), STAB_OK for polls == 0.  The device stays usable.
+ * Errors: STAB_E_RANGE (polls < 0), STAB_E_CUDA. */
+int stab_selftest_bounded_wait(int64_t polls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True):
             "stab_error_string": (ctypes.c_char_p, [i32]),
             "stab_last_cuda_error": (i32, []),
             "stab_version": (i32, []),
+            "stab_selftest_bounded_wait": (i32, [i64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -9,6 +9,7 @@
 
 #include "device_ops.cuh"
 #include "launch.h"
+#include "tma.cuh"
 
 namespace stab {
 
@@ -192,7 +193,24 @@ __global__ void __launch_bounds__(kThreads) k_xfree_sum(const double *vec, int n
     }
 }
 
+// Waits on a barrier nothing completes, with a poll bound; records a timeout.
+__global__ void k_bounded_wait(int64_t polls, int32_t *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        bool ok = polls == 0;
+        for (int64_t i = 0; i < polls && !ok; ++i) ok = mbar_try_wait(&bar, 0);
+        *status = ok ? 0 : STAB_KSTATUS_TIMEOUT;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_bounded_wait(int64_t polls, int32_t *status, cudaStream_t st) {
+    k_bounded_wait<<<1, 32, 0, st>>>(polls, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
                           const int32_t *map_gate_idx, const RawGate *gates, const double *thetas,

@@ -79,6 +79,9 @@ namespace stab {
 // complete once this stream is).
 cudaStream_t ctx_stream(stab_ctx *ctx);
 
+// Kernel that waits on a barrier nothing completes (bounded), for the self-test.
+cudaError_t launch_bounded_wait(int64_t polls, int32_t *status, cudaStream_t st);
+
 // Records the CUDA error behind a STAB_E_CUDA status (stab_last_cuda_error).
 void record_cuda_error(cudaError_t e);
 

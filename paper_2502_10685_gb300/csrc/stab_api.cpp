@@ -360,6 +360,24 @@ void stab_default_opts(stab_opts *o) {
 
 int stab_version(void) { return STAB_VERSION; }
 
+int stab_selftest_bounded_wait(int64_t polls) {
+    if (polls < 0) return STAB_E_RANGE;
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int32_t *d = nullptr;
+    int32_t h = -1;
+    cudaError_t e = cudaMallocAsync(&d, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_bounded_wait(polls, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (d) cudaFreeAsync(d, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e == cudaSuccess) e = e2;
+    CK(e);
+    return h == 0 ? STAB_OK : STAB_E_TIMEOUT;
+}
+
 int stab_last_cuda_error(void) { return g_last_cuda; }
 
 const char *stab_error_string(int s) {

@@ -278,3 +278,15 @@ def test_autograd_function_matches_psr(stab):
     opt.step()
     f2 = float(layer())
     assert f2 < float(f) + 1e-15
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable(stab):
+    """A device wait that nothing completes gives up after its poll bound and
+    the host reads STAB_E_TIMEOUT; later work on the device is unaffected."""
+    from paper_2502_10685_gb300 import _lib
+    L = _lib.load()
+    assert L.stab_selftest_bounded_wait(0) == 0
+    assert L.stab_selftest_bounded_wait(20000) == -4      # STAB_E_TIMEOUT
+    c = W.layered_ansatz(3, 100, seed=9)
+    got = run_gens(stab, c)
+    assert np.abs(got - oracle.generators(3, c.gates, c.thetas)).max() <= 1e-12
