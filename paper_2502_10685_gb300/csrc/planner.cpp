@@ -110,7 +110,7 @@ struct Emitter {
     void emit_wire(const stab_gate *gates, int q, const std::vector<int64_t> &run) {
         int n_rot = 0;
         for (int64_t i : run) n_rot += is_rotation(gates[i].op);
-        if ((mode == PLAN_FUSED && n_rot > 3) || mode == PLAN_ROWS) {
+        if ((mode == PLAN_FUSED && n_rot > 3) || mode == PLAN_ROWS || mode == PLAN_PLAIN_ROWS) {
             DevMap3 mp{};
             mp.first = (int32_t)P->map_gate_idx.size();
             mp.count = (int32_t)run.size();
@@ -192,6 +192,7 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
     HostPlan &P = *out;
     P = HostPlan();
     P.n_params = n_params;
+    P.mode = mode;
     P.raw.resize((size_t)m);
     for (int64_t i = 0; i < m; ++i) {
         P.raw[i].op = gates[i].op;
@@ -227,7 +228,7 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
         int64_t j = i;
         if (is_two_qubit(gates[i].op)) {
             while (j < m && is_two_qubit(gates[j].op)) ++j;
-            if (mode == PLAN_PLAIN) {
+            if (mode == PLAN_PLAIN || mode == PLAN_PLAIN_ROWS) {
                 for (int64_t k = i; k < j; ++k) em.emit_cliff(gates, k, k + 1);
             } else {
                 // a P_CLIFF pass holds at most 65535 ops
@@ -235,7 +236,7 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
             }
         } else {
             while (j < m && !is_two_qubit(gates[j].op)) ++j;
-            if (mode == PLAN_PLAIN) {
+            if (mode == PLAN_PLAIN || mode == PLAN_PLAIN_ROWS) {
                 for (int64_t k = i; k < j; ++k) em.emit_wire(gates, gates[k].q0, {k});
             } else {
                 for (auto &r : runs) r.clear();
@@ -328,6 +329,8 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out) {
                 const int jj = backward ? p.n_ops - 1 - j : j;
                 applied.push_back(pull_rec(P.ops[p.first + jj]));
             }
+            // the gate-by-gate forms keep each two-qubit gate a pass of its own
+            if (P.mode == PLAN_PLAIN || P.mode == PLAN_PLAIN_ROWS) emit(0, {});
             continue;
         }
         std::vector<Rec> ops;

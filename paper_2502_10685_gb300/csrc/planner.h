@@ -25,6 +25,7 @@ enum PlanMode {
     PLAN_GRAD = 1,   // no maps (every rotation kept for its gradient), <= kRotPerGradPass per pass
     PLAN_PLAIN = 2,  // one pass per gate
     PLAN_ROWS = 3,   // every wire run becomes one 3x3 map (latency-optimised resident kernel)
+    PLAN_PLAIN_ROWS = 4,  // one pass per gate, every single-qubit gate a 3x3 map
 };
 
 struct HostPlan {
@@ -37,6 +38,7 @@ struct HostPlan {
     std::vector<int32_t> param_rot;
     int32_t n_rot = 0;
     int64_t n_params = 0;
+    PlanMode mode = PLAN_FUSED;
 };
 
 // Returns STAB_OK or an error code; msg receives a description on error.

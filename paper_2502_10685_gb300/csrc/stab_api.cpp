@@ -73,6 +73,21 @@ struct DevPlan {
     bool encoded = false;
 };
 
+// A captured sequence of streamed launches, valid while its key is unchanged.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> key;
+    int64_t launches = 0;            // kernels in the graph
+    void *result = nullptr;          // buffer that ends up holding the result
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+        launches = 0;
+        result = nullptr;
+    }
+};
+
 }  // namespace
 
 struct stab_ctx {
@@ -97,7 +112,10 @@ struct stab_ctx {
 
     DevPlan fwd, grad;
     DevBuf thetas, gens, gens_tmp, lam, rho, tmp, tmp2, terms, scal, grad_rot, partials, grads;
+    DevBuf gbuf;                     // gradients written inside captured graphs
     DevBuf status;                   // int32 set by kernels whose bounded waits gave up
+    GraphCache g_gens, g_expect, g_grad; // streamed launch sequences (n > resident sizes)
+    int64_t plan_gen = 0;            // bumped whenever a plan is rebuilt
     int32_t n_obs_terms = 0;
     bool obs_loaded = false;
     int64_t h2d_bytes = 0, d2h_bytes = 0;
@@ -149,7 +167,8 @@ struct stab_ctx {
     }
     size_t vec_bytes() const { return (sizeof(double) << (2 * n)); }
     bool use_resident() const {
-        return (kernel == STAB_KERNEL_AUTO || kernel == STAB_KERNEL_RESIDENT) &&
+        return (kernel == STAB_KERNEL_AUTO || kernel == STAB_KERNEL_RESIDENT ||
+                kernel == STAB_KERNEL_PLAIN) &&
                n <= kMaxResidentQubits;
     }
     bool use_resident_adjoint() const {
@@ -157,9 +176,9 @@ struct stab_ctx {
                n <= kMaxResidentAdjoint;
     }
     PlanMode fwd_mode() const {
-        if (kernel == STAB_KERNEL_PLAIN || !fuse) return PLAN_PLAIN;
-        if (use_resident() && resident_lanes_per_group(n) == 4) return PLAN_ROWS;
-        return PLAN_FUSED;
+        const bool rows = use_resident() && resident_lanes_per_group(n) == 4;
+        if (kernel == STAB_KERNEL_PLAIN || !fuse) return rows ? PLAN_PLAIN_ROWS : PLAN_PLAIN;
+        return rows ? PLAN_ROWS : PLAN_FUSED;
     }
 };
 
@@ -331,12 +350,54 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
     return STAB_OK;
 }
 
+// Replays the launch sequence `body` (queued on s) from a graph cached under
+// `key`, capturing it first when the key changed.  s is the context's own
+// non-blocking stream (the legacy default stream cannot be captured).  All
+// buffers the body uses must be allocated before the call.
+template <class F>
+int run_graph(stab_ctx *c, GraphCache &g, const std::vector<const void *> &key, cudaStream_t s,
+              F body) {
+    if (!g.exec || g.key != key) {
+        g.reset();
+        cudaGraph_t graph = nullptr;
+        const int64_t l0 = c->launches;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = body(s, &g.result);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        g.launches = c->launches - l0;
+        c->launches = l0;
+        if (rc != STAB_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            g.reset();
+            if (rc != STAB_OK) return rc;
+            CK(e);
+        }
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) g.reset();
+        CK(e);
+        g.key = key;
+    }
+    CK(cudaGraphLaunch(g.exec, s));
+    c->launches += g.launches;
+    return STAB_OK;
+}
+
+void reset_graphs(stab_ctx *c) {
+    c->g_gens.reset();
+    c->g_expect.reset();
+    c->g_grad.reset();
+    c->plan_gen++;
+}
+
 int ensure_grad_plan(stab_ctx *c) {
     if (!c->grad.built) {
         build_plan(c->n, c->gates.data(), (int64_t)c->gates.size(), c->n_params, PLAN_GRAD,
                    &c->grad.host);
         if (c->use_resident_adjoint()) make_streams(c->grad);
         else no_streams(c->grad);
+        c->g_grad.reset();
+        c->plan_gen++;
         RC(upload_plan(c, c->grad));
     }
     if (!c->grad.encoded) RC(encode_plan(c, c->grad));
@@ -453,9 +514,12 @@ int stab_destroy(stab_ctx *c) {
     cudaSetDevice(c->device);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->aux) cudaStreamSynchronize(c->aux);
+    c->g_gens.reset();
+    c->g_expect.reset();
+    c->g_grad.reset();
     DevBuf *bufs[] = {&c->fwd.buf, &c->grad.buf, &c->thetas, &c->gens, &c->gens_tmp, &c->lam,
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
-                      &c->partials, &c->grads, &c->status};
+                      &c->partials, &c->grads, &c->status, &c->gbuf};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -484,6 +548,7 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
     c->n_params = n_params;
     c->grad.built = false;
     c->grad.encoded = false;
+    reset_graphs(c);
     build_plan(c->n, gates, m, n_params, c->fwd_mode(), &c->fwd.host);
     if (c->use_resident()) make_streams(c->fwd);
     else no_streams(c->fwd);
@@ -536,11 +601,21 @@ int stab_run_generators(stab_ctx *c) {
         c->gens_cur = (double *)c->gens.p;
     } else {
         RC(c->dalloc(c->gens_tmp, bytes, c->st));
-        double *cur = (double *)c->gens.p, *alt = (double *)c->gens_tmp.p;
-        CK(launch_fill(cur, n, n, INIT_GENERATOR, nullptr, 0, c->st));
-        c->launches++;
-        RC(run_streamed(c, c->fwd, &cur, &alt, n, 0, c->st));
-        c->gens_cur = cur;
+        cudaStream_t s = c->aux;
+        CK(cudaStreamWaitEvent(s, c->ev_ready, 0));
+        const std::vector<const void *> key = {(const void *)c->plan_gen, c->gens.p,
+                                               c->gens_tmp.p};
+        RC(run_graph(c, c->g_gens, key, s, [&](cudaStream_t gs, void **result) {
+            double *cur = (double *)c->gens.p, *alt = (double *)c->gens_tmp.p;
+            CK(launch_fill(cur, n, n, INIT_GENERATOR, nullptr, 0, gs));
+            c->launches++;
+            RC(run_streamed(c, c->fwd, &cur, &alt, n, 0, gs));
+            *result = cur;
+            return STAB_OK;
+        }));
+        c->gens_cur = (double *)c->g_gens.result;
+        CK(cudaEventRecord(c->ev_aux, s));
+        CK(cudaStreamWaitEvent(c->st, c->ev_aux, 0));
     }
     c->gens_valid = true;
     return STAB_OK;
@@ -605,12 +680,20 @@ int stab_expect_async(stab_ctx *c, double *out_dev) {
     } else {
         RC(c->dalloc(c->lam, c->vec_bytes(), s));
         RC(c->dalloc(c->tmp, c->vec_bytes(), s));
-        double *cur = (double *)c->lam.p, *alt = (double *)c->tmp.p;
-        CK(launch_fill(cur, c->n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, s));
-        c->launches += nt ? 2 : 1;
-        RC(run_streamed(c, c->fwd, &cur, &alt, 1, 1, s));
-        CK(launch_xfree_sum(cur, c->n, 1, out_dev, s));
-        c->launches++;
+        RC(c->dalloc(c->scal, 64 * sizeof(double), s));
+        double *res = (double *)c->scal.p + 2;
+        const std::vector<const void *> key = {(const void *)c->plan_gen, c->lam.p, c->tmp.p,
+                                               c->terms.p, (const void *)(intptr_t)nt, res};
+        RC(run_graph(c, c->g_expect, key, s, [&](cudaStream_t gs, void **) {
+            double *cur = (double *)c->lam.p, *alt = (double *)c->tmp.p;
+            CK(launch_fill(cur, c->n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, gs));
+            c->launches += nt ? 2 : 1;
+            RC(run_streamed(c, c->fwd, &cur, &alt, 1, 1, gs));
+            CK(launch_xfree_sum(cur, c->n, 1, res, gs));
+            c->launches++;
+            return STAB_OK;
+        }));
+        CK(cudaMemcpyAsync(out_dev, res, sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     // join: later work on the main stream sees the result
     CK(cudaEventRecord(c->ev_aux, s));
@@ -662,45 +745,63 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         a.status = (int32_t *)c->status.p;
         CK(launch_adjoint_stream(n, a, s));
         c->launches++;
+        if (c->n_params > 0) {
+            CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
+                                   c->grad.param_rot, (int)c->n_params, grads_dev, s));
+            c->launches++;
+        }
     } else {
         const size_t vb = c->vec_bytes();
         RC(c->dalloc(c->lam, vb, s));
         RC(c->dalloc(c->rho, vb, s));
         RC(c->dalloc(c->tmp, vb, s));
         RC(c->dalloc(c->tmp2, vb, s));
+        RC(c->dalloc(c->gbuf, (size_t)(c->n_params ? c->n_params : 1) * sizeof(double), s));
         const int nb = adjoint_stream_blocks(n);
         RC(c->dalloc(c->partials, (size_t)(n_rot ? n_rot : 1) * nb * sizeof(double), s));
-        double *rho = (double *)c->rho.p, *rho_alt = (double *)c->tmp2.p;
-        double *lam = (double *)c->lam.p, *lam_alt = (double *)c->tmp.p;
-        CK(launch_fill(rho, n, 1, INIT_RHO0, nullptr, 0, s));
-        c->launches++;
-        RC(run_streamed(c, c->grad, &rho, &rho_alt, 1, 0, s));
-        CK(launch_fill(lam, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, s));
-        c->launches += nt ? 2 : 1;
-        const auto &passes = c->grad.host.passes;
-        for (int k = (int)passes.size() - 1; k >= 0; --k) {
-            const DevPass &p = passes[k];
-            if (p.type == P_WIRE) {
-                CK(launch_adjoint_wire(lam, rho, n, p, c->grad.prog.ops, (double *)c->partials.p,
-                                       0, n_rot, s));
-                c->launches++;
-            } else {
-                CK(launch_stream_cliff(lam, lam_alt, n, 1, p, c->grad.prog.ops, 1, s));
-                CK(launch_stream_cliff(rho, rho_alt, n, 1, p, c->grad.prog.ops, 1, s));
-                c->launches += 2;
-                std::swap(lam, lam_alt);
-                std::swap(rho, rho_alt);
+        double *res = (double *)c->scal.p + 3;
+        const std::vector<const void *> key = {
+            (const void *)c->plan_gen, c->lam.p, c->rho.p, c->tmp.p, c->tmp2.p, c->partials.p,
+            c->grad_rot.p, c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
+        RC(run_graph(c, c->g_grad, key, s, [&](cudaStream_t gs, void **) {
+            double *rho = (double *)c->rho.p, *rho_alt = (double *)c->tmp2.p;
+            double *lam = (double *)c->lam.p, *lam_alt = (double *)c->tmp.p;
+            CK(launch_fill(rho, n, 1, INIT_RHO0, nullptr, 0, gs));
+            c->launches++;
+            RC(run_streamed(c, c->grad, &rho, &rho_alt, 1, 0, gs));
+            CK(launch_fill(lam, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, gs));
+            c->launches += nt ? 2 : 1;
+            const auto &passes = c->grad.host.passes;
+            for (int k = (int)passes.size() - 1; k >= 0; --k) {
+                const DevPass &p = passes[k];
+                if (p.type == P_WIRE) {
+                    CK(launch_adjoint_wire(lam, rho, n, p, c->grad.prog.ops,
+                                           (double *)c->partials.p, 0, n_rot, gs));
+                    c->launches++;
+                } else {
+                    CK(launch_stream_cliff(lam, lam_alt, n, 1, p, c->grad.prog.ops, 1, gs));
+                    CK(launch_stream_cliff(rho, rho_alt, n, 1, p, c->grad.prog.ops, 1, gs));
+                    c->launches += 2;
+                    std::swap(lam, lam_alt);
+                    std::swap(rho, rho_alt);
+                }
             }
-        }
-        CK(launch_reduce_partials((const double *)c->partials.p, n_rot, nb,
-                                  (double *)c->grad_rot.p, s));
-        CK(launch_xfree_sum(lam, n, 1, e_out, s));
-        c->launches += 2;
-    }
-    if (c->n_params > 0) {
-        CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
-                               c->grad.param_rot, (int)c->n_params, grads_dev, s));
-        c->launches++;
+            CK(launch_reduce_partials((const double *)c->partials.p, n_rot, nb,
+                                      (double *)c->grad_rot.p, gs));
+            CK(launch_xfree_sum(lam, n, 1, res, gs));
+            c->launches += 2;
+            if (c->n_params > 0) {
+                CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
+                                       c->grad.param_rot, (int)c->n_params, (double *)c->gbuf.p,
+                                       gs));
+                c->launches++;
+            }
+            return STAB_OK;
+        }));
+        CK(cudaMemcpyAsync(e_out, res, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (c->n_params > 0)
+            CK(cudaMemcpyAsync(grads_dev, c->gbuf.p, (size_t)c->n_params * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
     }
     CK(cudaEventRecord(c->ev_aux, s));
     CK(cudaStreamWaitEvent(c->st, c->ev_aux, 0));
