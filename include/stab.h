@@ -325,6 +325,15 @@ int stab_server_stats(stab_server *s, int64_t *submitted, int64_t *completed, in
 /* Waits for every queued request, then releases the server. */
 int stab_server_destroy(stab_server *s);
 
+/* Density matrix rho = |psi><psi| of psi = U|0^n> for the loaded circuit (the
+ * paper's decoding and toDM() step, Sec. III-D and IV-C): the coefficients of
+ * 2^n |0><0| are propagated forward and decoded as rho = 2^-n sum_P r_P P.
+ * out: 2^n x 2^n complex entries as interleaved (re, im) doubles, row-major,
+ * 2 x 4^n doubles; row and column index bit q is qubit q.  Host memory if
+ * out_is_device == 0 (synchronizing), else device memory (queued).
+ * Errors: STAB_E_STATE (no circuit), STAB_E_CUDA, STAB_E_NOMEM. */
+int stab_density_matrix(stab_ctx *ctx, double *out, int out_is_device);
+
 /* Waits for all work queued by the context. */
 int stab_synchronize(stab_ctx *ctx);
 

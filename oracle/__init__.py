@@ -59,6 +59,7 @@ def lib():
             L.orc_psr_grad_gate.argtypes = [c_int, i64, vp, vp, i64, vp, i64, vp]
             L.orc_expand.argtypes = [c_int, c_int, vp, vp]
             L.orc_map_noncx.argtypes = [c_int, ctypes.c_double, ctypes.c_double, vp, vp]
+            L.orc_density_matrix.argtypes = [c_int, i64, vp, vp, i64, vp, vp]
             _lib = L
     return _lib
 
@@ -201,3 +202,17 @@ def map_noncx(op: int, w, c: float = 1.0, s: float = 0.0) -> np.ndarray:
     out = np.empty(4)
     lib().orc_map_noncx(op, c, s, _p(w), _p(out))
     return out
+
+
+def density_matrix(n: int, gates, thetas) -> np.ndarray:
+    """rho = |psi><psi| of U|0^n> decoded from the Pauli coefficients (Sec. III-D,
+    Eq. (3)); complex (2^n, 2^n), qubit 0 the most significant bit."""
+    g, t = _gates(gates), _thetas(thetas)
+    D = 2 ** n
+    re = np.empty((D, D))
+    im = np.empty((D, D))
+    rc = lib().orc_density_matrix(n, g.shape[0], _p(g), _p(t), len(np.atleast_1d(thetas)),
+                                  _p(re), _p(im))
+    if rc != 0:
+        raise ValueError("oracle: invalid circuit")
+    return re + 1j * im

@@ -406,3 +406,60 @@ void orc_map_noncx(int op, double c, double s, const double w[4], double out[4])
 }
 
 int orc_num_ops(void) { return ORC_NUM_OPS; }
+
+/* ---------------- density matrix (Sec. III-D decoding, Sec. IV-C, Eq. (3)) ----------------
+ *
+ * rho = 2^-n sum_P r_P P, where r is the forward-evolved coefficient vector of
+ * 2^n |0><0| = sum over strings of I and Z (Eq. (3) with the state's own Pauli
+ * weights).  Each string P is decoded as in Sec. III-D: every row a of P has a
+ * single nonzero entry, at the column b obtained by flipping the qubits that
+ * carry X or Y, with the value prod_q <a_q| p_q |b_q> (I, X, Y, Z 2x2 entries).
+ * Rows and columns index basis states with qubit 0 as the most significant bit.
+ * out_re / out_im: 2^n x 2^n, row-major. */
+int orc_density_matrix(int n, int64_t m, const orc_gate *gates, const double *thetas,
+                       int64_t n_params, double *out_re, double *out_im) {
+    if (n < 1 || n > 10) return ORC_EINVAL;
+    const int64_t N = pow4(n), D = (int64_t)1 << n;
+    double *r = (double *)malloc((size_t)N * sizeof(double));
+    if (!r) return ORC_EINVAL;
+    for (int64_t i = 0; i < N; ++i) {
+        int xfree = 1;
+        for (int q = 0; q < n; ++q) {
+            int d = digit(i, n, q);
+            if (d == 1 || d == 2) { xfree = 0; break; }
+        }
+        r[i] = xfree ? 1.0 : 0.0;
+    }
+    int rc = orc_forward(n, m, gates, thetas, n_params, r);
+    if (rc != ORC_OK) { free(r); return rc; }
+    /* 2x2 entries <a|p|b> of I, X, Y, Z as (re, im) */
+    static const double pre[4][2][2] = {{{1, 0}, {0, 1}}, {{0, 1}, {1, 0}}, {{0, 0}, {0, 0}},
+                                        {{1, 0}, {0, -1}}};
+    static const double pim[4][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}, {{0, -1}, {1, 0}},
+                                        {{0, 0}, {0, 0}}};
+    for (int64_t k = 0; k < D * D; ++k) { out_re[k] = 0.0; out_im[k] = 0.0; }
+    const double scale = 1.0 / (double)D;
+    for (int64_t i = 0; i < N; ++i) {
+        if (r[i] == 0.0) continue;
+        int64_t flip = 0;
+        for (int q = 0; q < n; ++q) {
+            int d = digit(i, n, q);
+            if (d == 1 || d == 2) flip |= (int64_t)1 << (n - 1 - q);
+        }
+        for (int64_t a = 0; a < D; ++a) {
+            int64_t b = a ^ flip;
+            double vr = 1.0, vi = 0.0;
+            for (int q = 0; q < n; ++q) {
+                int d = digit(i, n, q);
+                int aq = (int)((a >> (n - 1 - q)) & 1), bq = (int)((b >> (n - 1 - q)) & 1);
+                double er = pre[d][aq][bq], ei = pim[d][aq][bq];
+                double tr = vr * er - vi * ei, ti = vr * ei + vi * er;
+                vr = tr; vi = ti;
+            }
+            out_re[a * D + b] += scale * r[i] * vr;
+            out_im[a * D + b] += scale * r[i] * vi;
+        }
+    }
+    free(r);
+    return ORC_OK;
+}

@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
             "stab_server_stats": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                         ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "stab_server_destroy": (i32, [vp]),
+            "stab_density_matrix": (i32, [vp, dp, i32]),
             "stab_synchronize": (i32, [vp]),
             "stab_plan_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_int32)]),

@@ -79,6 +79,10 @@ namespace stab {
 // complete once this stream is).
 cudaStream_t ctx_stream(stab_ctx *ctx);
 
+// Density matrix from the forward-evolved coefficients of 2^n |0><0|:
+// rho (device, 2 x 4^n doubles, interleaved complex, row-major).
+cudaError_t launch_decode_rho(const double *r, int n, double *rho, cudaStream_t st);
+
 // Kernel that waits on a barrier nothing completes (bounded), for the self-test.
 cudaError_t launch_bounded_wait(int64_t polls, int32_t *status, cudaStream_t st);
 

@@ -831,6 +831,47 @@ int stab_grad(stab_ctx *c, const stab_term *O, int64_t n_terms, double *expect_o
     return STAB_OK;
 }
 
+int stab_density_matrix(stab_ctx *c, double *out, int out_is_device) {
+    if (!c || !out) return STAB_E_INVAL;
+    if (!c->loaded) return STAB_E_STATE;
+    CK(cudaSetDevice(c->device));
+    const int n = c->n;
+    const size_t vb = c->vec_bytes();
+    RC(c->dalloc(c->rho, vb, c->st));
+    double *r = (double *)c->rho.p;
+    if (c->use_resident()) {
+        StreamArgs a{};
+        a.stream = c->fwd.sf.dev;
+        a.n_chunks = c->fwd.sf.n_chunks;
+        a.init = INIT_RHO0;
+        a.n_vec = 1;
+        a.out = r;
+        a.status = (int32_t *)c->status.p;
+        CK(launch_resident_stream(n, a, c->st));
+        c->launches++;
+    } else {
+        RC(c->dalloc(c->tmp2, vb, c->st));
+        double *cur = r, *alt = (double *)c->tmp2.p;
+        CK(launch_fill(cur, n, 1, INIT_RHO0, nullptr, 0, c->st));
+        c->launches++;
+        RC(run_streamed(c, c->fwd, &cur, &alt, 1, 0, c->st));
+        r = cur;
+    }
+    const size_t rho_bytes = 2 * vb;
+    if (out_is_device) {
+        CK(launch_decode_rho(r, n, out, c->st));
+        c->launches++;
+        return STAB_OK;
+    }
+    RC(c->dalloc(c->tmp, rho_bytes, c->st));
+    CK(launch_decode_rho(r, n, (double *)c->tmp.p, c->st));
+    c->launches++;
+    CK(cudaMemcpyAsync(out, c->tmp.p, rho_bytes, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->d2h_bytes += (int64_t)rho_bytes;
+    return check_status(c);
+}
+
 int stab_synchronize(stab_ctx *c) {
     if (!c) return STAB_E_INVAL;
     CK(cudaSetDevice(c->device));

@@ -279,6 +279,13 @@ class Stab:
     def transfer_bytes(self):
         return stab_transfer_bytes(self.h)
 
+    def density_matrix(self) -> np.ndarray:
+        """rho of U|0^n>, complex (2^n, 2^n); row/column bit q is qubit q."""
+        D = 2 ** self.n
+        out = np.empty((D, D), dtype=np.complex128)
+        check(_lib.load().stab_density_matrix(self.h, out.ctypes.data, 0), "stab_density_matrix")
+        return out
+
     def synchronize(self) -> None:
         stab_synchronize(self.h)
 

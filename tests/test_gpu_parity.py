@@ -290,3 +290,27 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(stab):
     c = W.layered_ansatz(3, 100, seed=9)
     got = run_gens(stab, c)
     assert np.abs(got - oracle.generators(3, c.gates, c.thetas)).max() <= 1e-12
+
+
+def _bitrev_perm(n):
+    idx = np.arange(2 ** n)
+    out = np.zeros_like(idx)
+    for q in range(n):
+        out |= ((idx >> q) & 1) << (n - 1 - q)
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 5, 6, 7, 8])
+def test_density_matrix_against_oracle(stab, n):
+    """Decoded rho (library: bit q = qubit q) vs the oracle's Sec. III-D decode
+    (qubit 0 most significant)."""
+    c = W.layered_ansatz(n, 40 * n, seed=600 + n) if n > 1 else W.random_circuit(1, 30, seed=6)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    rho = s.density_matrix()
+    s.close()
+    perm = _bitrev_perm(n)
+    got = rho[np.ix_(perm, perm)]
+    ref = oracle.density_matrix(n, c.gates, c.thetas)
+    assert np.abs(got - ref).max() <= 1e-12
+    assert abs(np.trace(rho) - 1) <= 1e-12

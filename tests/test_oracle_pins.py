@@ -379,3 +379,30 @@ def test_invalid_circuits_rejected():
     g = W.gates_from_list([("RX", 0, 5)])
     with pytest.raises(ValueError):
         oracle.forward(2, g, np.zeros(1), np.zeros(16))
+
+
+# ---------------------------------------------------------------- density matrix
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+def test_density_matrix_against_statevector(n):
+    c = W.random_circuit(n, 25 * n, seed=500 + n)
+    rho = oracle.density_matrix(n, c.gates, c.thetas)
+    U = D.circuit_unitary(n, c.gates, c.thetas)
+    psi = U[:, 0]
+    np.testing.assert_allclose(rho, np.outer(psi, psi.conj()), atol=1e-12)
+    assert abs(np.trace(rho) - 1) < 1e-12
+    np.testing.assert_allclose(rho, rho.conj().T, atol=1e-13)
+    np.testing.assert_allclose(rho @ rho, rho, atol=1e-12)
+
+
+def test_density_matrix_equals_product_of_generators_eq2():
+    """Eq. (2): rho = 2^-n prod_j (I + S_j) with S_j the evolved generators."""
+    n = 3
+    c = W.layered_ansatz(n, 60, seed=8)
+    gens = oracle.generators(n, c.gates, c.thetas)
+    prod = np.eye(2 ** n, dtype=complex)
+    for k in range(n):
+        Sk = D.coeffs_to_matrix(n, gens[k])
+        prod = prod @ (np.eye(2 ** n) + Sk)
+    np.testing.assert_allclose(oracle.density_matrix(n, c.gates, c.thetas), prod / 2 ** n,
+                               atol=1e-12)
