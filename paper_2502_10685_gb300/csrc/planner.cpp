@@ -107,14 +107,14 @@ struct Emitter {
     }
 
     // One wire's run (gate indices in order) -> one or more P_WIRE passes.
-    void emit_wire(const stab_gate *gates, int q, const std::vector<int64_t> &run) {
+    void emit_wire(const stab_gate *gates, int q, const int64_t *run, size_t run_len) {
         int n_rot = 0;
-        for (int64_t i : run) n_rot += is_rotation(gates[i].op);
+        for (size_t k = 0; k < run_len; ++k) n_rot += is_rotation(gates[run[k]].op);
         if ((mode == PLAN_FUSED && n_rot > 3) || mode == PLAN_ROWS || mode == PLAN_PLAIN_ROWS) {
             DevMap3 mp{};
             mp.first = (int32_t)P->map_gate_idx.size();
-            mp.count = (int32_t)run.size();
-            for (int64_t i : run) P->map_gate_idx.push_back((int32_t)i);
+            mp.count = (int32_t)run_len;
+            for (size_t k = 0; k < run_len; ++k) P->map_gate_idx.push_back((int32_t)run[k]);
             DevOp op{};
             op.kind = K_MAP3;
             op.q = (uint8_t)q;
@@ -155,7 +155,8 @@ struct Emitter {
             p.first = (uint32_t)P->ops.size();
             rot_in_pass = 0;
         };
-        for (int64_t i : run) {
+        for (size_t k = 0; k < run_len; ++k) {
+            const int64_t i = run[k];
             const int op = gates[i].op;
             if (!is_rotation(op)) {
                 pending = perm_compose(pending, clifford_perm_code(op));
@@ -221,6 +222,8 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
             if (is_rotation(gates[i].op)) P.param_rot[fill[gates[i].param]++] = rot_ordinal[i];
     }
 
+    P.passes.reserve((size_t)m + 1);
+    P.ops.reserve((size_t)m + 1);
     Emitter em{&P, mode, &rot_ordinal};
     int64_t i = 0;
     std::vector<std::vector<int64_t>> runs((size_t)n);
@@ -237,7 +240,7 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
         } else {
             while (j < m && !is_two_qubit(gates[j].op)) ++j;
             if (mode == PLAN_PLAIN || mode == PLAN_PLAIN_ROWS) {
-                for (int64_t k = i; k < j; ++k) em.emit_wire(gates, gates[k].q0, {k});
+                for (int64_t k = i; k < j; ++k) em.emit_wire(gates, gates[k].q0, &k, 1);
             } else {
                 for (auto &r : runs) r.clear();
                 for (int64_t k = i; k < j; ++k) runs[gates[k].q0].push_back(k);
@@ -245,11 +248,8 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
                     if (runs[q].empty()) continue;
                     // a P_WIRE pass holds at most 65535 ops; cut longer unfused runs
                     const auto &r = runs[q];
-                    for (size_t k = 0; k < r.size(); k += 16384) {
-                        std::vector<int64_t> part(r.begin() + k,
-                                                  r.begin() + std::min(r.size(), k + 16384));
-                        em.emit_wire(gates, q, part);
-                    }
+                    for (size_t k = 0; k < r.size(); k += 16384)
+                        em.emit_wire(gates, q, r.data() + k, std::min(r.size() - k, (size_t)16384));
                 }
             }
         }
@@ -306,19 +306,20 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out) {
     out->clear();
     StreamWriter w{out};
     // two-qubit Clifford gates waiting to be pulled, in application order
-    std::vector<Rec> applied;
-    auto emit = [&](int q, const std::vector<Rec> &ops) {
+    std::vector<Rec> applied, seg, none, ops;
+    out->reserve(P.passes.size() * 4 + P.ops.size() * 2 + kChunkRecs);
+    auto emit = [&](int q, const std::vector<Rec> &pass_ops) {
         // all but the last kMaxPullPerPass-segment go into identity passes
         size_t k = 0;
         while (applied.size() - k > (size_t)kMaxPullPerPass) {
-            std::vector<Rec> seg(applied.begin() + k, applied.begin() + k + kMaxPullPerPass);
+            seg.assign(applied.begin() + k, applied.begin() + k + kMaxPullPerPass);
             std::reverse(seg.begin(), seg.end());
-            w.pass(0, seg, {});
+            w.pass(0, seg, none);
             k += kMaxPullPerPass;
         }
-        std::vector<Rec> seg(applied.begin() + k, applied.end());
+        seg.assign(applied.begin() + k, applied.end());
         std::reverse(seg.begin(), seg.end());   // a pull walks the last applied gate first
-        w.pass(q, seg, ops);
+        w.pass(q, seg, pass_ops);
         applied.clear();
     };
     const int np = (int)P.passes.size();
@@ -330,10 +331,10 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out) {
                 applied.push_back(pull_rec(P.ops[p.first + jj]));
             }
             // the gate-by-gate forms keep each two-qubit gate a pass of its own
-            if (P.mode == PLAN_PLAIN || P.mode == PLAN_PLAIN_ROWS) emit(0, {});
+            if (P.mode == PLAN_PLAIN || P.mode == PLAN_PLAIN_ROWS) emit(0, none);
             continue;
         }
-        std::vector<Rec> ops;
+        ops.clear();
         for (int j = 0; j < p.n_ops; ++j) {
             const DevOp &op = P.ops[p.first + (backward ? p.n_ops - 1 - j : j)];
             Rec r{};
@@ -362,7 +363,7 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out) {
         }
         emit(p.q, ops);
     }
-    if (!applied.empty()) emit(0, {});
+    if (!applied.empty()) emit(0, none);
     w.end();
 }
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/stab.h"
@@ -187,8 +188,11 @@ namespace {
 // Uploads a host plan into its device buffer (one copy from pinned staging).
 int upload_plan(stab_ctx *c, DevPlan &P) {
     HostPlan &H = P.host;
-    const size_t b_pass = align256(H.passes.size() * sizeof(DevPass));
-    const size_t b_ops = align256(H.ops.size() * sizeof(DevOp));
+    // resident plans read only their streams (plus maps and raw gates for encoding)
+    const size_t n_pass = P.streams ? 0 : H.passes.size();
+    const size_t n_ops = P.streams ? 0 : H.ops.size();
+    const size_t b_pass = align256(n_pass * sizeof(DevPass));
+    const size_t b_ops = align256(n_ops * sizeof(DevOp));
     const size_t b_maps = align256(H.maps.size() * sizeof(DevMap3));
     const size_t b_midx = align256(H.map_gate_idx.size() * sizeof(int32_t));
     const size_t b_raw = align256(H.raw.size() * sizeof(RawGate));
@@ -212,8 +216,8 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
         off += span;
         return d + at;
     };
-    P.prog.passes = (const DevPass *)put(H.passes.data(), H.passes.size() * sizeof(DevPass), b_pass);
-    P.prog.ops = (const DevOp *)put(H.ops.data(), H.ops.size() * sizeof(DevOp), b_ops);
+    P.prog.passes = (const DevPass *)put(H.passes.data(), n_pass * sizeof(DevPass), b_pass);
+    P.prog.ops = (const DevOp *)put(H.ops.data(), n_ops * sizeof(DevOp), b_ops);
     P.prog.maps = (const DevMap3 *)put(H.maps.data(), H.maps.size() * sizeof(DevMap3), b_maps);
     P.map_gate_idx = (const int32_t *)put(H.map_gate_idx.data(), H.map_gate_idx.size() * 4, b_midx);
     P.raw = (const RawGate *)put(H.raw.data(), H.raw.size() * sizeof(RawGate), b_raw);
@@ -223,8 +227,8 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     P.sf.enc_dev = (const int32_t *)put(P.sf.enc.data(), P.sf.enc.size() * 4, b_sfe);
     P.sb.dev = (Rec *)put(P.sb.host.data(), P.sb.host.size() * sizeof(Rec), b_sb);
     P.sb.enc_dev = (const int32_t *)put(P.sb.enc.data(), P.sb.enc.size() * 4, b_sbe);
-    P.prog.n_passes = (int32_t)H.passes.size();
-    P.prog.n_ops = (int32_t)H.ops.size();
+    P.prog.n_passes = (int32_t)n_pass;
+    P.prog.n_ops = (int32_t)n_ops;
     CK(cudaMemcpyAsync(P.buf.p, h, total, cudaMemcpyHostToDevice, c->st));
     CK(cudaEventRecord(c->ev_stage, c->st));
     c->h2d_bytes += (int64_t)total;
@@ -258,19 +262,24 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
     return STAB_OK;
 }
 
+void make_stream(DevPlan &P, bool backward) {
+    DevStreamBuf &S = backward ? P.sb : P.sf;
+    build_stream(P.host, backward, &S.host);
+    S.enc.clear();
+    for (size_t i = 0; i < S.host.size(); ++i) {
+        const uint8_t k = S.host[i].kind;
+        if (k == R_ROT || k == R_MAP3) S.enc.push_back((int32_t)i);
+        if (k == R_MAP3) i += 3;   // its data records are not kinds
+    }
+    S.n_chunks = (int)(S.host.size() / kChunkRecs);
+}
+
+// Forward and backward streams, built concurrently on two host threads.
 void make_streams(DevPlan &P) {
     P.streams = true;
-    for (int b = 0; b < 2; ++b) {
-        DevStreamBuf &S = b ? P.sb : P.sf;
-        build_stream(P.host, b == 1, &S.host);
-        S.enc.clear();
-        for (size_t i = 0; i < S.host.size(); ++i) {
-            const uint8_t k = S.host[i].kind;
-            if (k == R_ROT || k == R_MAP3) S.enc.push_back((int32_t)i);
-            if (k == R_MAP3) i += 3;   // its data records are not kinds
-        }
-        S.n_chunks = (int)(S.host.size() / kChunkRecs);
-    }
+    std::thread bwd([&P] { make_stream(P, true); });
+    make_stream(P, false);
+    bwd.join();
 }
 
 void no_streams(DevPlan &P) {
