@@ -553,6 +553,87 @@ def run_serve(args):
     return 0
 
 
+def run_expect(args):
+    """<O> only (one vector propagated backward) on the layered ansatz with
+    n, m from the workload name expect-n<N>-<M>; device-resident steps timed
+    with CUDA events, L2 flushed between steps."""
+    import torch
+    from paper_2502_10685_gb300 import stab, workloads as W
+    n, m = (int(v) for v in args.workload[len("expect-n"):].split("-"))
+    torch.cuda.set_stream(torch.cuda.Stream())
+    st = torch.cuda.current_stream()
+    c = W.layered_ansatz(n, m, seed=1000 + n)
+    obs = W.obs_chain(n)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    s.set_observable(obs)
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        s.expect_async(out)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = _events()
+        e0.record(st)
+        s.expect_async(out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / args.steps
+    n_rot = int(sum(1 for g in c.gates if g["op"] in W.ROTATIONS))
+    flops = n_rot * 1.5 * 4 ** n
+    peak = SMS * FP64_FLOP_PER_CLK_SM * 2070.0e6 / 1e12
+    s.close()
+    print(json.dumps({
+        "metric": METRIC, "value": m * 4 ** n / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "gates": m, "vectors_per_step": 1},
+        "fp64_tflops": flops / (ms / 1e3) / 1e12, "fp64_frac_of_peak": flops / (ms / 1e3) / 1e12 / peak}))
+    return 0
+
+
+def run_paper_sweep(args):
+    """The paper's experiment shape (Sec. V): time to the density matrix of
+    the W_chain + ZXZ ansatz, n = 2, 3, 4, over #Layers (Repeats = 1) and
+    #Repeats (Layers = 50), through the host-buffer calls (stab_load_circuit +
+    stab_density_matrix to host memory), beside the CPU oracle's decode."""
+    import numpy as np
+    import oracle
+    from paper_2502_10685_gb300 import stab, workloads as W
+    oracle.build()
+    rows = []
+    points = [(L, 1) for L in (1, 10, 100, 1000)] + [(50, R) for R in (1, 10, 50, 100)]
+    for n in (2, 3, 4):
+        s = stab.Stab(n)
+        for (layers, repeats) in points:
+            c = W.paper_shaped_ansatz(n, layers, repeats, seed=7 + n)
+            s.load_circuit(c.gates, c.thetas)
+            s.density_matrix()
+            reps = 5
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                s.load_circuit(c.gates, c.thetas)
+                rho = s.density_matrix()
+            gpu_s = (time.perf_counter() - t0) / reps
+            t0 = time.perf_counter()
+            ref = oracle.density_matrix(n, c.gates, c.thetas)
+            cpu_s = time.perf_counter() - t0
+            perm = np.zeros(2 ** n, dtype=int)
+            for i in range(2 ** n):
+                perm[i] = int(format(i, "0%db" % n)[::-1], 2)
+            err = float(np.abs(rho[np.ix_(perm, perm)] - ref).max())
+            rows.append({"n": n, "layers": layers, "repeats": repeats, "gates": c.m,
+                         "todm_s": gpu_s, "oracle_todm_s": cpu_s, "max_abs_err": err})
+        s.close()
+    print(json.dumps({"metric": "time to density matrix", "unit": "s",
+                      "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "paper-sweep"}, "points": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -576,6 +657,10 @@ def main():
         return run_grad(args)
     if args.workload == "serve-c5":
         return run_serve(args)
+    if args.workload.startswith("expect-n"):
+        return run_expect(args)
+    if args.workload == "paper-sweep":
+        return run_paper_sweep(args)
     return run_ours(args)
 
 
