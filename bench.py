@@ -385,6 +385,12 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def shard(items, rank, world):
+    """Units of a batch for one rank: every world-th item, starting at rank
+    (items are independent, so ranks need no collective on the data path)."""
+    return items[rank::world]
+
+
 def run_batch(args):
     """Uneven batch: 4,096 circuits (n ~ U{2..8}, depth ~ U[100, 20000]) including
     the 2m parameter-shift copies of a 6-qubit 2,000-gate circuit, one
@@ -392,12 +398,20 @@ def run_batch(args):
     one launch per gate (both timed on a seeded sample, scaled by updates)."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     from paper_2502_10685_gb300 import stab, workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_stream(torch.cuda.Stream())
     st = torch.cuda.current_stream()
-    items = W.uneven_batch(4096, seed=1003)
+    all_items = W.uneven_batch(4096 * world, seed=1003)   # weak scaling: 4,096 per GPU
+    items = shard(all_items, rank, world)
     t0 = time.perf_counter()
-    b = stab.Batch(items)
+    b = stab.Batch(items, device=local)
     create_s = time.perf_counter() - t0
     upd = sum((it.circuit.n if it.kind == "generators" else 1) * it.circuit.m * 4 ** it.circuit.n
               for it in items)
@@ -414,7 +428,8 @@ def run_batch(args):
         e1.record(st)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    ms = sum(times) / len(times)
+    ms, _ = combine_ranks(sum(times) / len(times), 0, world, dist if world > 1 else None,
+                          torch.device("cuda", local))
     forms = {}
     rng = np.random.default_rng(0)
     sample = [items[i] for i in rng.choice(len(items), size=16, replace=False)]
@@ -446,14 +461,19 @@ def run_batch(args):
             "extrapolated_ms": est, "batch_speedup": est / ms, "sample_circuits": len(sample)}
     info = b.info()
     b.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     print(json.dumps({
-        "metric": "circuits/s", "value": len(items) / (ms / 1e3), "unit": "circuits/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "metric": "circuits/s", "value": len(items) * world / (ms / 1e3), "unit": "circuits/s",
+        "n_gpus": world, "scaling": "weak", "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms,
         "higher_is_better": True, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "batch-c3", "circuits": len(items), "units": info["units"],
                    "grid": info["grid"], "ctas_per_sm": info["ctas_per_sm"],
                    "l2": "flushed between steps"},
-        "updates_per_s": upd / (ms / 1e3), "create_s": create_s, "vs_forms": forms}))
+        "updates_per_s": upd * world / (ms / 1e3), "create_s": create_s, "vs_forms": forms}))
     return 0
 
 

@@ -50,3 +50,11 @@ def test_combine_ranks_single():
     import bench
     total_ms, value = bench.combine_ranks(50.0, 10, 1)
     assert total_ms == 50.0 and abs(value - 200.0) < 1e-12
+
+
+def test_batch_shards_cover_every_item_once():
+    import bench
+    items = list(range(4096 * 3))
+    shards = [bench.shard(items, r, 3) for r in range(3)]
+    assert sorted(x for sh in shards for x in sh) == items
+    assert max(len(sh) for sh in shards) - min(len(sh) for sh in shards) <= 1
