@@ -175,6 +175,51 @@ __global__ void __launch_bounds__(kThreads) k_stream_cliff(const double *__restr
     }
 }
 
+__device__ __forceinline__ uint64_t deposit_runs(uint64_t v, const BitRuns &r) {
+    uint64_t out = 0;
+    for (int k = 0; k < r.n; ++k)
+        out |= ((v >> r.src[k]) & ((1ull << r.len[k]) - 1ull)) << r.dst[k];
+    return out;
+}
+
+__global__ void __launch_bounds__(kThreads) k_stream_tile(double *vec, int n, int n_vec,
+                                                          TileGroup tg, const DevOp *ops,
+                                                          const DevMap3 *maps) {
+    extern __shared__ double tile[];
+    const uint32_t T = 1u << tg.tile_bits;
+    const uint64_t E = 1ull << (2 * n);
+    const uint64_t tiles = (uint64_t)n_vec << tg.rest_bits;
+    for (uint64_t tb = blockIdx.x; tb < tiles; tb += gridDim.x) {
+        const uint64_t v = tb >> tg.rest_bits, t = tb & ((1ull << tg.rest_bits) - 1ull);
+        double *V = vec + v * E + deposit_runs(t, tg.rest_runs);
+        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
+            tile[e] = V[deposit_runs(e, tg.tile_runs)];
+        __syncthreads();
+        for (int j = 0; j < tg.n_pass; ++j) {
+            const int lz = tg.lz[j], lx = tg.lx[j];
+            const int lo = lz < lx ? lz : lx, hi = lz < lx ? lx : lz;
+            const uint32_t bz = 1u << lz, bx = 1u << lx;
+            const int n_ops = tg.n_ops[j];
+            for (uint32_t g = threadIdx.x; g < T / 4; g += blockDim.x) {
+                uint32_t b = ((g >> lo) << (lo + 1)) | (g & ((1u << lo) - 1u));
+                b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1u));
+                double x = tile[b | bx], y = tile[b | bx | bz], z = tile[b | bz];
+                for (int k = 0; k < n_ops; ++k) {
+                    const DevOp op = ops[tg.first[j] + (tg.inverse ? n_ops - 1 - k : k)];
+                    apply_op1(x, y, z, op, maps, tg.inverse);
+                }
+                tile[b | bx] = x;
+                tile[b | bx | bz] = y;
+                tile[b | bz] = z;
+            }
+            __syncthreads();
+        }
+        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
+            V[deposit_runs(e, tg.tile_runs)] = tile[e];
+        __syncthreads();
+    }
+}
+
 // Deterministic sum of the 2^n x-free coefficients of each vector (one CTA
 // per vector, fixed order).
 __global__ void __launch_bounds__(kThreads) k_xfree_sum(const double *vec, int n, double *out) {
@@ -254,6 +299,19 @@ cudaError_t launch_stream_cliff(const double *src, double *dst, int n, int n_vec
     const uint64_t total = (1ull << (2 * n)) * (uint64_t)n_vec;
     k_stream_cliff<<<grid_for(total, kThreads), kThreads, 0, st>>>(src, dst, n, n_vec, p, ops,
                                                                     inverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_tile(double *vec, int n, int n_vec, const TileGroup &tg,
+                               const DevOp *ops, const DevMap3 *maps, cudaStream_t st) {
+    const uint32_t T = 1u << tg.tile_bits;
+    const uint64_t tiles = (uint64_t)n_vec << tg.rest_bits;
+    int threads = (int)(T / 4);
+    if (threads > kThreads) threads = kThreads;
+    if (threads < 32) threads = 32;
+    uint64_t grid = tiles;
+    if (grid > 152ull * 8ull) grid = 152ull * 8ull;
+    k_stream_tile<<<(int)grid, threads, T * sizeof(double), st>>>(vec, n, n_vec, tg, ops, maps);
     return cudaGetLastError();
 }
 

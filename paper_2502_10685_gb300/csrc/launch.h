@@ -114,6 +114,34 @@ cudaError_t launch_stream_cliff(const double *src, double *dst, int n, int n_vec
                                 const DevPass &p, const DevOp *ops, int inverse, cudaStream_t st);
 cudaError_t launch_xfree_sum(const double *vec, int n, int n_vec, double *out, cudaStream_t st);
 
+// Several consecutive wire passes on at most kTileWires wires fused into one
+// streamed launch: each CTA loads a tile (all 4^|Q| slots of the wires Q times
+// some of the lowest other index bits) into shared memory, applies the passes
+// in order and writes it back.
+constexpr int kTileWires = 3;
+constexpr int kTileMaxPasses = 8;
+constexpr int kTileMaxBits = 12;        // 4096 doubles = 32 KiB of shared memory
+
+struct BitRuns {                        // deposit of a packed integer into index bits
+    uint8_t n;
+    uint8_t src[16], dst[16], len[16];
+};
+
+struct TileGroup {
+    int32_t n_pass;
+    int32_t tile_bits;                  // log2 entries per tile
+    int32_t rest_bits;                  // 2n - tile_bits: log2 tiles per vector
+    int32_t inverse;
+    uint8_t lz[kTileMaxPasses], lx[kTileMaxPasses];   // tile-local bits of each pass's wire
+    uint16_t n_ops[kTileMaxPasses];
+    uint32_t first[kTileMaxPasses];
+    BitRuns tile_runs;                  // local entry -> global index bits
+    BitRuns rest_runs;                  // tile id -> global index bits
+};
+
+cudaError_t launch_stream_tile(double *vec, int n, int n_vec, const TileGroup &tg,
+                               const DevOp *ops, const DevMap3 *maps, cudaStream_t st);
+
 // Adjoint gradient, shared-memory resident (n <= kMaxResidentAdjoint).
 cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_t st);
 

@@ -2,6 +2,7 @@
 // circuit loading, and the launch sequences of every entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -338,25 +339,106 @@ int upload_terms(stab_ctx *c, const stab_term *O, int64_t n_terms) {
     return STAB_OK;
 }
 
+void bit_runs(const std::vector<int> &bits, BitRuns *r) {
+    // bit k of a packed integer goes to index bit bits[k] (bits ascending)
+    std::memset(r, 0, sizeof(*r));
+    for (size_t k = 0; k < bits.size();) {
+        size_t j = k + 1;
+        while (j < bits.size() && bits[j] == bits[j - 1] + 1) ++j;
+        r->src[r->n] = (uint8_t)k;
+        r->dst[r->n] = (uint8_t)bits[k];
+        r->len[r->n] = (uint8_t)(j - k);
+        r->n++;
+        k = j;
+    }
+}
+
+// Tile geometry for wire passes on `wires`: the wires' x and z bits plus as
+// many of the lowest other bits as keep at least 256 tiles (and 4096 entries).
+void make_tile_group(int n, int n_vec, const std::vector<const DevPass *> &group, int inverse,
+                     TileGroup *tg) {
+    std::memset(tg, 0, sizeof(*tg));
+    std::vector<int> wires;
+    for (const DevPass *p : group)
+        if (std::find(wires.begin(), wires.end(), (int)p->q) == wires.end()) wires.push_back(p->q);
+    std::vector<int> qbits;
+    for (int q : wires) {
+        qbits.push_back(q);
+        qbits.push_back(n + q);
+    }
+    std::vector<int> others;
+    for (int b = 0; b < 2 * n; ++b)
+        if (std::find(qbits.begin(), qbits.end(), b) == qbits.end()) others.push_back(b);
+    int c = 0;
+    while (c < (int)others.size() && (int)qbits.size() + c + 1 <= kTileMaxBits &&
+           ((int64_t)n_vec << (2 * n - ((int)qbits.size() + c + 1))) >= 256)
+        ++c;
+    std::vector<int> tile(qbits);
+    tile.insert(tile.end(), others.begin(), others.begin() + c);
+    std::sort(tile.begin(), tile.end());
+    std::vector<int> rest(others.begin() + c, others.end());
+    tg->n_pass = (int32_t)group.size();
+    tg->tile_bits = (int32_t)tile.size();
+    tg->rest_bits = (int32_t)rest.size();
+    tg->inverse = inverse;
+    for (size_t j = 0; j < group.size(); ++j) {
+        const int q = group[j]->q;
+        tg->lz[j] = (uint8_t)(std::find(tile.begin(), tile.end(), q) - tile.begin());
+        tg->lx[j] = (uint8_t)(std::find(tile.begin(), tile.end(), n + q) - tile.begin());
+        tg->n_ops[j] = group[j]->n_ops;
+        tg->first[j] = group[j]->first;
+    }
+    bit_runs(tile, &tg->tile_runs);
+    bit_runs(rest, &tg->rest_runs);
+}
+
 // Streamed propagation of n_vec vectors through a plan; *cur / *alt are the
-// ping-pong buffers (the result ends in *cur).
+// ping-pong buffers (the result ends in *cur).  Consecutive wire passes on at
+// most kTileWires wires run as one tile-fused launch (fused plans only; the
+// gate-by-gate forms keep one launch per gate).
 int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int n_vec,
                  int inverse, cudaStream_t s) {
     const auto &passes = P.host.passes;
     const int np = (int)passes.size();
+    const bool fuse_tiles = P.host.mode != PLAN_PLAIN && P.host.mode != PLAN_PLAIN_ROWS;
+    std::vector<const DevPass *> group;
+    std::vector<int> wires;
+    auto flush = [&]() -> int {
+        if (group.empty()) return STAB_OK;
+        if (group.size() == 1) {
+            CK(launch_stream_wire(*cur, c->n, n_vec, *group[0], P.prog.ops, P.prog.maps, inverse,
+                                  s));
+        } else {
+            TileGroup tg;
+            make_tile_group(c->n, n_vec, group, inverse, &tg);
+            CK(launch_stream_tile(*cur, c->n, n_vec, tg, P.prog.ops, P.prog.maps, s));
+        }
+        c->launches++;
+        group.clear();
+        wires.clear();
+        return STAB_OK;
+    };
     for (int k = 0; k < np; ++k) {
         const DevPass &p = passes[inverse ? np - 1 - k : k];
         if (p.type == P_WIRE) {
-            CK(launch_stream_wire(*cur, c->n, n_vec, p, P.prog.ops, P.prog.maps, inverse, s));
-        } else {
-            CK(launch_stream_cliff(*cur, *alt, c->n, n_vec, p, P.prog.ops, inverse, s));
-            double *t = *cur;
-            *cur = *alt;
-            *alt = t;
+            const bool known = std::find(wires.begin(), wires.end(), (int)p.q) != wires.end();
+            if (!fuse_tiles || (int)group.size() == kTileMaxPasses ||
+                (!known && (int)wires.size() == kTileWires)) {
+                RC(flush());
+            }
+            group.push_back(&p);
+            if (std::find(wires.begin(), wires.end(), (int)p.q) == wires.end())
+                wires.push_back(p.q);
+            continue;
         }
+        RC(flush());
+        CK(launch_stream_cliff(*cur, *alt, c->n, n_vec, p, P.prog.ops, inverse, s));
+        double *t = *cur;
+        *cur = *alt;
+        *alt = t;
         c->launches++;
     }
-    return STAB_OK;
+    return flush();
 }
 
 // Replays the launch sequence `body` (queued on s) from a graph cached under
