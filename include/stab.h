@@ -310,12 +310,14 @@ int stab_server_create(const stab_server_opts *opts, stab_server **out);
 int stab_server_submit(stab_server *s, const stab_request *req, int64_t *id);
 
 /* Waits up to timeout_s (< 0: forever) for request id.  grads (host, may be
- * NULL) receives the n_params gradient entries of a gradient request.
- * Errors: STAB_E_INVAL (unknown id), STAB_E_TIMEOUT (not done in time). */
+ * NULL) receives the n_params gradient entries of a gradient request.  A
+ * successful wait hands the results out and releases the request: its id is
+ * unknown afterwards.  Errors: STAB_E_INVAL (unknown id), STAB_E_TIMEOUT (not
+ * done in time; the request stays queued or running). */
 int stab_server_wait(stab_server *s, int64_t id, double timeout_s, stab_result *out,
                      double *grads);
 
-/* *done = 1 when request id has completed. */
+/* *done = 1 when request id has completed (it stays known until waited for). */
 int stab_server_poll(stab_server *s, int64_t id, int32_t *done);
 
 /* Counters: requests submitted, completed, admitted now, bytes admitted now. */

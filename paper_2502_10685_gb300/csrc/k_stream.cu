@@ -187,13 +187,17 @@ __global__ void __launch_bounds__(kThreads) k_stream_tile(double *vec, int n, in
                                                           const DevMap3 *maps) {
     extern __shared__ double tile[];
     const uint32_t T = 1u << tg.tile_bits;
+    // tile-local entry -> offset from the tile's base, the same for every tile
+    uint32_t *offs = reinterpret_cast<uint32_t *>(tile + T);
+    for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
+        offs[e] = (uint32_t)deposit_runs(e, tg.tile_runs);
+    __syncthreads();
     const uint64_t E = 1ull << (2 * n);
     const uint64_t tiles = (uint64_t)n_vec << tg.rest_bits;
     for (uint64_t tb = blockIdx.x; tb < tiles; tb += gridDim.x) {
         const uint64_t v = tb >> tg.rest_bits, t = tb & ((1ull << tg.rest_bits) - 1ull);
         double *V = vec + v * E + deposit_runs(t, tg.rest_runs);
-        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
-            tile[e] = V[deposit_runs(e, tg.tile_runs)];
+        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) tile[e] = V[offs[e]];
         __syncthreads();
         for (int j = 0; j < tg.n_pass; ++j) {
             const int lz = tg.lz[j], lx = tg.lx[j];
@@ -214,8 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_stream_tile(double *vec, int n, in
             }
             __syncthreads();
         }
-        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
-            V[deposit_runs(e, tg.tile_runs)] = tile[e];
+        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) V[offs[e]] = tile[e];
         __syncthreads();
     }
 }
@@ -311,7 +314,14 @@ cudaError_t launch_stream_tile(double *vec, int n, int n_vec, const TileGroup &t
     if (threads < 32) threads = 32;
     uint64_t grid = tiles;
     if (grid > 152ull * 8ull) grid = 152ull * 8ull;
-    k_stream_tile<<<(int)grid, threads, T * sizeof(double), st>>>(vec, n, n_vec, tg, ops, maps);
+    const size_t smem = T * (sizeof(double) + sizeof(uint32_t));
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_stream_tile,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_stream_tile<<<(int)grid, threads, smem, st>>>(vec, n, n_vec, tg, ops, maps);
     return cudaGetLastError();
 }
 

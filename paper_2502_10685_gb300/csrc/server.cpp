@@ -343,6 +343,9 @@ int stab_server_wait(stab_server *s, int64_t id, double timeout_s, stab_result *
     }
     if (out) *out = r->res;
     if (grads && !r->grads.empty()) std::memcpy(grads, r->grads.data(), r->grads.size() * 8);
+    // the results are handed out: the request is released
+    s->all.erase(it);
+    delete r;
     return STAB_OK;
 }
 
