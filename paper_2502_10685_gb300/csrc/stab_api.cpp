@@ -400,7 +400,10 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
                  int inverse, cudaStream_t s) {
     const auto &passes = P.host.passes;
     const int np = (int)passes.size();
-    const bool fuse_tiles = P.host.mode != PLAN_PLAIN && P.host.mode != PLAN_PLAIN_ROWS;
+    // tiles pay where a launch is small (launch-bound: few vectors, n <= 8); larger
+    // launches are FP64-bound and run faster one wire per launch
+    const bool fuse_tiles = P.host.mode != PLAN_PLAIN && P.host.mode != PLAN_PLAIN_ROWS &&
+                            ((uint64_t)n_vec << (2 * c->n)) <= (1ull << 17);
     std::vector<const DevPass *> group;
     std::vector<int> wires;
     auto flush = [&]() -> int {
