@@ -29,6 +29,13 @@ __device__ __forceinline__ double pair_dot(int axis, double lx, double ly, doubl
     return fma(ly, rx, -lx * ry);
 }
 
+__device__ __forceinline__ uint64_t deposit_runs(uint64_t v, const BitRuns &r) {
+    uint64_t out = 0;
+    for (int k = 0; k < r.n; ++k)
+        out |= ((v >> r.src[k]) & ((1ull << r.len[k]) - 1ull)) << r.dst[k];
+    return out;
+}
+
 __device__ __forceinline__ void add_slot(double (&part)[R], int slot, double d) {
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -112,6 +119,87 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, doubl
     }
 }
 
+// Tile-fused reverse sweep: up to kTileMaxPasses wire passes on at most
+// kTileWires wires, applied backward to the pair (lambda, rho) held as two
+// shared-memory tiles (pair[0 .. 4^n) = lambda, pair[4^n ..) = rho).  Every
+// rotation's gradient dot is reduced over the CTA in a fixed order, summed
+// over the CTA's tiles in tile order, and written to partials[gate][block].
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(double *pair, int n, TileGroup tg,
+                                                              const DevOp *ops,
+                                                              double *partials) {
+    extern __shared__ double sm[];
+    constexpr int W = kAdjThreads / 32;
+    const uint32_t T = 1u << tg.tile_bits;
+    double *tl = sm, *tr = sm + T;
+    double *red = tr + T;                            // W x R
+    double *acc = red + W * R;                       // kTileMaxPasses x R
+    uint32_t *offs = reinterpret_cast<uint32_t *>(acc + kTileMaxPasses * R);
+    for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
+        offs[e] = (uint32_t)deposit_runs(e, tg.tile_runs);
+    for (int k = threadIdx.x; k < kTileMaxPasses * R; k += blockDim.x) acc[k] = 0.0;
+    __syncthreads();
+    const uint64_t E = 1ull << (2 * n);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t tiles = 1ull << tg.rest_bits;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t base = deposit_runs(t, tg.rest_runs);
+        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+            tl[e] = pair[base + offs[e]];
+            tr[e] = pair[E + base + offs[e]];
+        }
+        __syncthreads();
+        for (int j = 0; j < tg.n_pass; ++j) {
+            const int lz = tg.lz[j], lx = tg.lx[j];
+            const int lo = lz < lx ? lz : lx, hi = lz < lx ? lx : lz;
+            const uint32_t bz = 1u << lz, bx = 1u << lx;
+            DevPass p{};
+            p.n_ops = tg.n_ops[j];
+            p.first = tg.first[j];
+            const int n_rot = count_rot(p, ops);
+            double part[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) part[r] = 0.0;
+            for (uint32_t g = threadIdx.x; g < T / 4; g += blockDim.x) {
+                uint32_t b = ((g >> lo) << (lo + 1)) | (g & ((1u << lo) - 1u));
+                b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1u));
+                double lx_ = tl[b | bx], ly_ = tl[b | bx | bz], lz_ = tl[b | bz];
+                double rx_ = tr[b | bx], ry_ = tr[b | bx | bz], rz_ = tr[b | bz];
+                adjoint_group(p, ops, nullptr, lx_, ly_, lz_, rx_, ry_, rz_, part, n_rot);
+                tl[b | bx] = lx_; tl[b | bx | bz] = ly_; tl[b | bz] = lz_;
+                tr[b | bx] = rx_; tr[b | bx | bz] = ry_; tr[b | bz] = rz_;
+            }
+            if (n_rot > 0) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double v = part[r];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                    if (lane == 0) red[warp * R + r] = v;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < n_rot) {
+                double total = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += red[w * R + threadIdx.x];
+                acc[j * R + threadIdx.x] += total;
+            }
+            __syncthreads();
+        }
+        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+            pair[base + offs[e]] = tl[e];
+            pair[E + base + offs[e]] = tr[e];
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < tg.n_pass * R; k += blockDim.x) {
+        const int j = k / R, r = k % R;
+        DevPass p{};
+        p.n_ops = tg.n_ops[j];
+        p.first = tg.first[j];
+        if (r < count_rot(p, ops))
+            partials[(size_t)rot_gate(p, ops, r) * gridDim.x + blockIdx.x] = acc[k];
+    }
+}
+
 __global__ void k_reduce_partials(const double *partials, int n_rot, int n_blocks,
                                   double *grad_rot) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,6 +232,22 @@ cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &
                                 cudaStream_t st) {
     k_adjoint_wire<<<adjoint_stream_blocks(n), kAdjThreads, 0, st>>>(lam, rho, n, p, ops,
                                                                       partials);
+    return cudaGetLastError();
+}
+
+size_t adjoint_tile_smem(int tile_bits) {
+    const size_t T = (size_t)1 << tile_bits;
+    return 2 * T * sizeof(double) + (kAdjThreads / 32) * R * sizeof(double) +
+           kTileMaxPasses * R * sizeof(double) + T * sizeof(uint32_t);
+}
+
+cudaError_t launch_adjoint_tile(double *pair, int n, const TileGroup &tg, const DevOp *ops,
+                                double *partials, cudaStream_t st) {
+    int threads = (int)((1u << tg.tile_bits) / 4);
+    if (threads > kAdjThreads) threads = kAdjThreads;
+    if (threads < 32) threads = 32;
+    k_adjoint_tile<<<adjoint_stream_blocks(n), threads, adjoint_tile_smem(tg.tile_bits), st>>>(
+        pair, n, tg, ops, partials);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,12 @@ int adjoint_stream_blocks(int n);
 cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &p,
                                 const DevOp *ops, double *partials, int rot_base, int n_rot_total,
                                 cudaStream_t st);
+// Tile-fused reverse sweep on the contiguous pair (lambda, rho); grid =
+// adjoint_stream_blocks(n), partials[gate][block] as launch_adjoint_wire.
+constexpr int kAdjTileMaxBits = 11;   // shared memory stays under 48 KiB
+size_t adjoint_tile_smem(int tile_bits);
+cudaError_t launch_adjoint_tile(double *pair, int n, const TileGroup &tg, const DevOp *ops,
+                                double *partials, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, int n_rot, int n_blocks,
                                    double *grad_rot, cudaStream_t st);
 cudaError_t launch_gather_grads(const double *grad_rot, const int32_t *param_ptr,

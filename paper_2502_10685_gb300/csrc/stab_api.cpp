@@ -356,7 +356,7 @@ void bit_runs(const std::vector<int> &bits, BitRuns *r) {
 // Tile geometry for wire passes on `wires`: the wires' x and z bits plus as
 // many of the lowest other bits as keep at least 256 tiles (and 4096 entries).
 void make_tile_group(int n, int n_vec, const std::vector<const DevPass *> &group, int inverse,
-                     TileGroup *tg) {
+                     TileGroup *tg, int min_tiles = 256, int max_bits = kTileMaxBits) {
     std::memset(tg, 0, sizeof(*tg));
     std::vector<int> wires;
     for (const DevPass *p : group)
@@ -370,8 +370,8 @@ void make_tile_group(int n, int n_vec, const std::vector<const DevPass *> &group
     for (int b = 0; b < 2 * n; ++b)
         if (std::find(qbits.begin(), qbits.end(), b) == qbits.end()) others.push_back(b);
     int c = 0;
-    while (c < (int)others.size() && (int)qbits.size() + c + 1 <= kTileMaxBits &&
-           ((int64_t)n_vec << (2 * n - ((int)qbits.size() + c + 1))) >= 256)
+    while (c < (int)others.size() && (int)qbits.size() + c + 1 <= max_bits &&
+           ((int64_t)n_vec << (2 * n - ((int)qbits.size() + c + 1))) >= min_tiles)
         ++c;
     std::vector<int> tile(qbits);
     tile.insert(tile.end(), others.begin(), others.begin() + c);
@@ -845,44 +845,72 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
             c->launches++;
         }
     } else {
+        // lambda and rho are one contiguous pair (lambda first), ping-ponged
+        // with a second pair, so a Clifford gather moves both in one launch
         const size_t vb = c->vec_bytes();
-        RC(c->dalloc(c->lam, vb, s));
-        RC(c->dalloc(c->rho, vb, s));
-        RC(c->dalloc(c->tmp, vb, s));
-        RC(c->dalloc(c->tmp2, vb, s));
+        const uint64_t E = 1ull << (2 * n);
+        RC(c->dalloc(c->lam, 2 * vb, s));
+        RC(c->dalloc(c->tmp, 2 * vb, s));
         RC(c->dalloc(c->gbuf, (size_t)(c->n_params ? c->n_params : 1) * sizeof(double), s));
         const int nb = adjoint_stream_blocks(n);
         RC(c->dalloc(c->partials, (size_t)(n_rot ? n_rot : 1) * nb * sizeof(double), s));
         double *res = (double *)c->scal.p + 3;
+        const bool tiles = n <= 8;
         const std::vector<const void *> key = {
-            (const void *)c->plan_gen, c->lam.p, c->rho.p, c->tmp.p, c->tmp2.p, c->partials.p,
-            c->grad_rot.p, c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
+            (const void *)c->plan_gen, c->lam.p, c->tmp.p, c->partials.p, c->grad_rot.p,
+            c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
         RC(run_graph(c, c->g_grad, key, s, [&](cudaStream_t gs, void **) {
-            double *rho = (double *)c->rho.p, *rho_alt = (double *)c->tmp2.p;
-            double *lam = (double *)c->lam.p, *lam_alt = (double *)c->tmp.p;
+            double *pa = (double *)c->lam.p, *pb = (double *)c->tmp.p;
+            double *rho = pa + E, *rho_alt = pb + E;
             CK(launch_fill(rho, n, 1, INIT_RHO0, nullptr, 0, gs));
             c->launches++;
             RC(run_streamed(c, c->grad, &rho, &rho_alt, 1, 0, gs));
-            CK(launch_fill(lam, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, gs));
+            double *pair = rho - E, *alt = (pair == pa) ? pb : pa;
+            CK(launch_fill(pair, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, gs));
             c->launches += nt ? 2 : 1;
             const auto &passes = c->grad.host.passes;
+            std::vector<const DevPass *> group;
+            std::vector<int> wires;
+            auto flush = [&]() -> int {
+                if (group.empty()) return STAB_OK;
+                if (!tiles) {
+                    for (const DevPass *p : group) {
+                        CK(launch_adjoint_wire(pair, pair + E, n, *p, c->grad.prog.ops,
+                                               (double *)c->partials.p, 0, n_rot, gs));
+                        c->launches++;
+                    }
+                } else {
+                    TileGroup tg;
+                    make_tile_group(n, 1, group, 1, &tg, nb, kAdjTileMaxBits);
+                    CK(launch_adjoint_tile(pair, n, tg, c->grad.prog.ops, (double *)c->partials.p,
+                                           gs));
+                    c->launches++;
+                }
+                group.clear();
+                wires.clear();
+                return STAB_OK;
+            };
             for (int k = (int)passes.size() - 1; k >= 0; --k) {
                 const DevPass &p = passes[k];
                 if (p.type == P_WIRE) {
-                    CK(launch_adjoint_wire(lam, rho, n, p, c->grad.prog.ops,
-                                           (double *)c->partials.p, 0, n_rot, gs));
-                    c->launches++;
-                } else {
-                    CK(launch_stream_cliff(lam, lam_alt, n, 1, p, c->grad.prog.ops, 1, gs));
-                    CK(launch_stream_cliff(rho, rho_alt, n, 1, p, c->grad.prog.ops, 1, gs));
-                    c->launches += 2;
-                    std::swap(lam, lam_alt);
-                    std::swap(rho, rho_alt);
+                    const bool known =
+                        std::find(wires.begin(), wires.end(), (int)p.q) != wires.end();
+                    if ((int)group.size() == kTileMaxPasses ||
+                        (!known && (int)wires.size() == kTileWires))
+                        RC(flush());
+                    group.push_back(&p);
+                    if (!known) wires.push_back(p.q);
+                    continue;
                 }
+                RC(flush());
+                CK(launch_stream_cliff(pair, alt, n, 2, p, c->grad.prog.ops, 1, gs));
+                c->launches++;
+                std::swap(pair, alt);
             }
+            RC(flush());
             CK(launch_reduce_partials((const double *)c->partials.p, n_rot, nb,
                                       (double *)c->grad_rot.p, gs));
-            CK(launch_xfree_sum(lam, n, 1, res, gs));
+            CK(launch_xfree_sum(pair, n, 1, res, gs));
             c->launches += 2;
             if (c->n_params > 0) {
                 CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
