@@ -408,7 +408,12 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_stream(torch.cuda.Stream())
     st = torch.cuda.current_stream()
-    all_items = W.uneven_batch(4096 * world, seed=1003)   # weak scaling: 4,096 per GPU
+    if args.workload == "batch-small":
+        # a small batch for profiler captures: 96 circuits, n ~ U{6..8}, 300..600 gates
+        all_items = W.uneven_batch(96 * world, seed=1013, n_range=(6, 8), depth_range=(300, 600),
+                                   psr_base=None)
+    else:
+        all_items = W.uneven_batch(4096 * world, seed=1003)   # weak scaling: 4,096 per GPU
     items = shard(all_items, rank, world)
     t0 = time.perf_counter()
     b = stab.Batch(items, device=local)
@@ -470,7 +475,7 @@ def run_batch(args):
         "n_gpus": world, "scaling": "weak", "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms,
         "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batch-c3", "circuits": len(items), "units": info["units"],
+        "config": {"workload": args.workload, "circuits": len(items), "units": info["units"],
                    "grid": info["grid"], "ctas_per_sm": info["ctas_per_sm"],
                    "l2": "flushed between steps"},
         "updates_per_s": upd * world / (ms / 1e3), "create_s": create_s, "vs_forms": forms}))
@@ -671,7 +676,7 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch-c3":
+    if args.workload in ("batch-c3", "batch-small"):
         return run_batch(args)
     if args.workload == "grad-c4":
         return run_grad(args)

@@ -221,6 +221,11 @@ __global__ void k_gather_grads(const double *grad_rot, const int32_t *param_ptr,
 }  // namespace
 
 int adjoint_stream_blocks(int n) {
+    if (n <= kAdjTileMaxN) {
+        // tile-fused sweep: one tile of 2^kAdjTileBits entries per CTA
+        const int bits = 2 * n - kAdjTileBits;
+        return bits > 0 ? 1 << bits : 1;
+    }
     const long long G = 1ll << (2 * n - 2);
     long long b = (G + kAdjThreads - 1) / kAdjThreads;
     if (b > 152 * 8) b = 152 * 8;

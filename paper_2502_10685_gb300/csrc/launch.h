@@ -150,9 +150,12 @@ int adjoint_stream_blocks(int n);
 cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &p,
                                 const DevOp *ops, double *partials, int rot_base, int n_rot_total,
                                 cudaStream_t st);
-// Tile-fused reverse sweep on the contiguous pair (lambda, rho); grid =
-// adjoint_stream_blocks(n), partials[gate][block] as launch_adjoint_wire.
-constexpr int kAdjTileMaxBits = 11;   // shared memory stays under 48 KiB
+// Tile-fused reverse sweep on the contiguous pair (lambda, rho) for n <=
+// kAdjTileMaxN: tiles of 2^kAdjTileBits entries, one per CTA and one group per
+// thread, grid = adjoint_stream_blocks(n); partials[gate][block] as
+// launch_adjoint_wire.
+constexpr int kAdjTileMaxN = 8;
+constexpr int kAdjTileBits = 9;
 size_t adjoint_tile_smem(int tile_bits);
 cudaError_t launch_adjoint_tile(double *pair, int n, const TileGroup &tg, const DevOp *ops,
                                 double *partials, cudaStream_t st);

@@ -855,7 +855,7 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         const int nb = adjoint_stream_blocks(n);
         RC(c->dalloc(c->partials, (size_t)(n_rot ? n_rot : 1) * nb * sizeof(double), s));
         double *res = (double *)c->scal.p + 3;
-        const bool tiles = n <= 8;
+        const bool tiles = n <= kAdjTileMaxN;
         const std::vector<const void *> key = {
             (const void *)c->plan_gen, c->lam.p, c->tmp.p, c->partials.p, c->grad_rot.p,
             c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
@@ -881,7 +881,7 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                     }
                 } else {
                     TileGroup tg;
-                    make_tile_group(n, 1, group, 1, &tg, nb, kAdjTileMaxBits);
+                    make_tile_group(n, 1, group, 1, &tg, nb, std::min(kAdjTileBits, 2 * n));
                     CK(launch_adjoint_tile(pair, n, tg, c->grad.prog.ops, (double *)c->partials.p,
                                            gs));
                     c->launches++;
