@@ -1,0 +1,134 @@
+"""Edge cases through the C interface: identity circuits, n = 1, empty and
+degenerate observables, circuits without angles, parameter updates from the
+device, and batches holding all of these."""
+import math
+
+import numpy as np
+import pytest
+
+import layout
+import oracle
+from paper_2502_10685_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stab():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2502_10685_gb300 import stab as S
+    return S
+
+
+def empty_circuit(n):
+    return W.Circuit(n, np.zeros(0, dtype=W.GATE_DTYPE), np.zeros(0))
+
+
+@pytest.mark.parametrize("n", [1, 3, 7])
+def test_observable_identity_duplicates_and_empty(stab, n):
+    c = W.layered_ansatz(n, 60, seed=n) if n > 1 else W.random_circuit(1, 20, seed=1)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    ident = "I" * n
+    assert abs(s.expect([(2.5, ident)]) - 2.5) <= 1e-14          # <I> = 1 for any U
+    zz = "Z" + "I" * (n - 1)
+    dup = s.expect([(0.5, zz), (0.25, zz), (0.25, zz)])          # equal strings are merged
+    assert abs(dup - s.expect([(1.0, zz)])) <= 1e-14
+    assert abs(dup - oracle.expect(n, c.gates, c.thetas, [(1.0, zz)])) <= 1e-12
+    assert s.expect([]) == 0.0                                    # empty observable
+    s.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8])
+def test_identity_circuit_all_entry_points(stab, n):
+    c = empty_circuit(n)
+    s = stab.Stab(n)
+    s.apply_circuit(c.gates, c.thetas)
+    g = layout.lib_to_paper(n, s.generators())
+    np.testing.assert_array_equal(g, oracle.generators(n, c.gates, c.thetas))
+    obs = [(1.0, "Z" * n)]
+    assert s.expect(obs) == 1.0
+    e, grads = s.grad(obs)
+    assert e == 1.0 and grads.size == 0
+    rho = s.density_matrix()
+    assert rho[0, 0] == 1.0 and np.count_nonzero(rho) == 1
+    s.close()
+
+
+def test_clifford_only_gradient_has_no_slots(stab):
+    c = W.random_circuit(4, 100, seed=3, clifford_only=True)
+    s = stab.Stab(4)
+    s.load_circuit(c.gates, c.thetas)
+    e, g = s.grad(W.obs_chain(4))
+    s.close()
+    assert g.size == 0
+    assert abs(e - oracle.expect(4, c.gates, c.thetas, W.obs_chain(4))) <= 1e-12 * 7.5
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_device_parameter_updates_then_generators(stab, n):
+    import torch
+    c = W.layered_ansatz(n, 80 * (9 - n), seed=40 + n)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    for shift in (0.0, 0.7, -1.9):
+        th = c.thetas + shift
+        s.set_params(torch.tensor(th, device="cuda"))
+        s.run_generators()
+        got = layout.lib_to_paper(n, s.generators())
+        assert np.abs(got - oracle.generators(n, c.gates, th)).max() <= 1e-12
+    s.close()
+
+
+def test_angles_far_outside_one_turn(stab):
+    """Angle reduction: theta and theta + 2 pi k give the same map (to the
+    rounding of the reduction), at both signs and large |k|."""
+    c = W.layered_ansatz(3, 90, seed=5)
+    s = stab.Stab(3)
+    s.load_circuit(c.gates, c.thetas)
+    ref = s.expect(W.obs_chain(3))
+    for k in (-40, -1, 1, 40):
+        s.set_params(c.thetas + 2 * math.pi * k)
+        assert abs(s.expect(W.obs_chain(3)) - ref) <= 1e-11
+    s.close()
+
+
+def test_batch_with_degenerate_items(stab):
+    items = [
+        W.BatchItem(empty_circuit(1), "generators"),
+        W.BatchItem(empty_circuit(6), "expect", [(1.0, "Z" * 6)]),
+        W.BatchItem(W.random_circuit(1, 40, seed=2), "expect", [(1.0, "Z")]),
+        W.BatchItem(W.layered_ansatz(8, 30, seed=3), "generators"),
+        W.BatchItem(W.layered_ansatz(5, 200, seed=4), "expect", []),
+    ]
+    b = stab.Batch(items)
+    b.run()
+    ex = b.expectations()
+    assert ex[1] == 1.0 and ex[4] == 0.0
+    c = items[2].circuit
+    assert abs(ex[2] - oracle.expect(1, c.gates, c.thetas, [(1.0, "Z")])) <= 1e-12
+    for k in (0, 3):
+        c = items[k].circuit
+        got = layout.lib_to_paper(c.n, b.generators(k))
+        assert np.abs(got - oracle.generators(c.n, c.gates, c.thetas)).max() <= 1e-12
+    b.close()
+
+
+def test_server_small_and_large_requests_mixed(stab):
+    srv = stab.Server(max_active=16)
+    reqs = []
+    for k in range(12):
+        n = 1 if k % 3 == 0 else (10 if k % 3 == 1 else 5)
+        c = W.random_circuit(1, 30, seed=k) if n == 1 else W.layered_ansatz(n, 30 + k, seed=k)
+        kind = "grad" if k % 2 else "expect"
+        reqs.append((c, kind, W.obs_chain(n) if n > 1 else [(1.0, "Z")]))
+    ids = [srv.submit(*r) for r in reqs]
+    res = [srv.wait(i, timeout_s=300) for i in ids]
+    srv.close()
+    for (c, kind, obs), r in zip(reqs, res):
+        assert r["status"] == 0
+        ref = oracle.expect(c.n, c.gates, c.thetas, obs) if c.n <= 6 else None
+        if ref is not None:
+            assert abs(r["expect"] - ref) <= 1e-12 * sum(abs(a) for a, _ in obs)
