@@ -1,4 +1,5 @@
-"""ctypes front end of the plain FP64 CPU oracle (``pauli_oracle.c``).
+"""ctypes front end of the plain FP64 CPU oracle (``pauli_oracle.c``, dense
+4^n vectors, and ``sparse_oracle.c``, lists of (coefficient, string) terms).
 
 TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
 cpu_baseline / reference legs of ``bench.py`` use it; the CUDA library never
@@ -15,7 +16,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "pauli_oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("pauli_oracle.c", "sparse_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -28,10 +29,12 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(
+        os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS)
+    if force or stale:
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +63,11 @@ def lib():
             L.orc_expand.argtypes = [c_int, c_int, vp, vp]
             L.orc_map_noncx.argtypes = [c_int, ctypes.c_double, ctypes.c_double, vp, vp]
             L.orc_density_matrix.argtypes = [c_int, i64, vp, vp, i64, vp, vp]
+            L.orc_sparse_propagate.argtypes = [c_int, i64, vp, vp, i64, c_int, i64, vp, vp,
+                                               i64, vp, vp, vp]
+            L.orc_sparse_sum_xfree.argtypes = [c_int, i64, vp, vp]
+            L.orc_sparse_sum_xfree.restype = ctypes.c_double
+            L.orc_sparse_expect.argtypes = [c_int, i64, vp, vp, i64, i64, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -216,3 +224,68 @@ def density_matrix(n: int, gates, thetas) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle: invalid circuit")
     return re + 1j * im
+
+
+# ---------------------------------------------------------------- sparse lists
+
+def sparse_terms(n: int, terms):
+    """[(coeff, string)] -> (keys uint64, coeffs float64) in the base-4 encoding
+    (qubit 0 the most significant digit); works for n <= 32."""
+    keys = np.zeros(len(terms), dtype=np.uint64)
+    vals = np.zeros(len(terms))
+    for i, (c, s) in enumerate(terms):
+        if len(s) != n:
+            raise ValueError("observable string length must equal n")
+        k = 0
+        for ch in s:
+            d = "IXYZ".find(ch)
+            if d < 0:
+                raise ValueError("bad Pauli letter in %r" % s)
+            k = k * 4 + d
+        keys[i] = k
+        vals[i] = c
+    return keys, vals
+
+
+def sparse_propagate(n: int, gates, thetas, keys, vals, backward: bool = False,
+                     cap: int = 1 << 22):
+    """Propagate a term list through the circuit (forward: U P U^dagger; backward:
+    U^dagger P U).  Returns (keys, coeffs) sorted by key, exact zeros dropped."""
+    g, t = _gates(gates), _thetas(thetas)
+    k_in = np.ascontiguousarray(keys, dtype=np.uint64)
+    v_in = np.ascontiguousarray(vals, dtype=np.float64)
+    k_out = np.zeros(max(cap, 1), dtype=np.uint64)
+    v_out = np.zeros(max(cap, 1))
+    n_out = ctypes.c_int64()
+    rc = lib().orc_sparse_propagate(n, g.shape[0], _p(g), _p(t), len(np.atleast_1d(thetas)),
+                                    int(backward), k_in.size, _p(k_in), _p(v_in), cap,
+                                    _p(k_out), _p(v_out), ctypes.byref(n_out))
+    if rc == -2:
+        raise OverflowError("oracle: %d terms exceed cap %d" % (n_out.value, cap))
+    if rc != 0:
+        raise ValueError("oracle: invalid circuit or input (%d)" % rc)
+    return k_out[:n_out.value].copy(), v_out[:n_out.value].copy()
+
+
+def sparse_generator(n: int, gates, thetas, k: int):
+    """U Z_k U^dagger as a term list (keys, coeffs)."""
+    keys, vals = sparse_terms(n, [(1.0, "I" * k + "Z" + "I" * (n - k - 1))])
+    return sparse_propagate(n, gates, thetas, keys, vals, backward=False)
+
+
+def sparse_sum_xfree(n: int, keys, vals) -> float:
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    v = np.ascontiguousarray(vals, dtype=np.float64)
+    return float(lib().orc_sparse_sum_xfree(n, k.size, _p(k), _p(v)))
+
+
+def sparse_expect(n: int, gates, thetas, terms) -> float:
+    """<0^n| U^dagger O U |0^n> on term lists (any n <= 32)."""
+    g, t = _gates(gates), _thetas(thetas)
+    k, v = sparse_terms(n, terms)
+    out = ctypes.c_double()
+    rc = lib().orc_sparse_expect(n, g.shape[0], _p(g), _p(t), len(np.atleast_1d(thetas)),
+                                 k.size, _p(k), _p(v), ctypes.byref(out))
+    if rc != 0:
+        raise ValueError("oracle: invalid circuit or input (%d)" % rc)
+    return out.value

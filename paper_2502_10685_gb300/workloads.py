@@ -184,6 +184,37 @@ def random_circuit(n: int, m: int, seed: int, clifford_only: bool = False,
     return Circuit(n, recs, np.asarray(thetas, dtype=np.float64))
 
 
+
+def clifford_plus_rotations(n: int, m: int, n_rot: int, seed: int,
+                            two_qubit_fraction: float = 0.4) -> Circuit:
+    """``m`` gates: random Clifford gates (H, S, S^dagger, X, Y, Z, CX, CZ) with
+    ``n_rot`` rotations (R_x, R_y, R_z, own slot each, theta ~ U[0, 2 pi)) at
+    random positions.  The stabilizer order of a generator grows at most by
+    a factor 2 per rotation (Sec. II-B), so these circuits stay sparse for
+    any n; they are the workload of the sparse representation."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_rot = min(n_rot, m)
+    rot_at = set(int(i) for i in rng.choice(m, size=n_rot, replace=False)) if n_rot else set()
+    one_q = ["H", "S", "SDG", "X", "Y", "Z"]
+    recs = np.zeros(m, dtype=GATE_DTYPE)
+    thetas: List[float] = []
+    for i in range(m):
+        q0 = int(rng.integers(n))
+        q1, param = 0, -1
+        if i in rot_at:
+            op = OPS[("RX", "RY", "RZ")[int(rng.integers(3))]]
+            param = len(thetas)
+            thetas.append(rng.uniform(0.0, 2.0 * math.pi))
+        elif n > 1 and rng.uniform() < two_qubit_fraction:
+            op = OPS["CX"] if rng.uniform() < 0.75 else OPS["CZ"]
+            q1 = int(rng.integers(n - 1))
+            if q1 >= q0:
+                q1 += 1
+        else:
+            op = OPS[one_q[int(rng.integers(len(one_q)))]]
+        recs[i] = (op, q0, q1, 0, param)
+    return Circuit(n, recs, np.asarray(thetas, dtype=np.float64))
+
 # ---------------------------------------------------------------- observables
 
 def obs_z(n: int, k: int) -> Observable:
