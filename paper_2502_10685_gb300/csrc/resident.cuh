@@ -174,10 +174,18 @@ __device__ double *run_stream(Stager &st, int c0, int c1, double *cur, double *n
             if (h.kind != R_PASS) break;   // R_NEXT or R_END
             const Rec *pulls = Rr + r + 1;
             const Rec *ops = pulls + h.param;
-            pass_groups<N, T>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
-            double *t = cur;
-            cur = nxt;
-            nxt = t;
+            // Without pulls a thread reads and writes only its own groups, so
+            // the pass runs in place; a pull pass permutes and needs the
+            // second buffer.  (In place keeps one vector hot in L2 when the
+            // buffers are in global memory.)
+            if (h.param == 0) {
+                pass_groups<N, T>(cur, cur, h.q, pulls, 0, ops, h.gate);
+            } else {
+                pass_groups<N, T>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
+                double *t = cur;
+                cur = nxt;
+                nxt = t;
+            }
             __syncthreads();
             r += 1 + h.param + h.gate;
         }
