@@ -339,6 +339,73 @@ int stab_density_matrix(stab_ctx *ctx, double *out, int out_is_device);
 /* Waits for all work queued by the context. */
 int stab_synchronize(stab_ctx *ctx);
 
+/* ---------------------------------------------------------------- sparse term lists */
+/* The sparse representation of Sec. II-B: a stabilizer or observable held as
+ * its list of terms lambda * P (the (lambda, I) pairs), whose length is the
+ * stabilizer order n' of Fig. 1.  The list is propagated on the device while
+ * n' stays small, so n may go up to STAB_SPARSE_MAX_QUBITS: Clifford gates map
+ * each term to one signed term, a rotation gives each anticommuting term its
+ * partner string (u' = c u - s v, v' = s u + c v, Table I), so n' at most
+ * doubles per rotation.  Keys use the layout above (z | x << n).  Terms whose
+ * coefficient is exactly zero are dropped.  The order of the list is
+ * deterministic (the images of each term in input order).
+ * Expectations switch to the dense path (stab_ctx) once n' exceeds a
+ * threshold, for n <= STAB_MAX_QUBITS. */
+#define STAB_SPARSE_MAX_QUBITS 32
+
+typedef struct stab_sparse stab_sparse;
+
+typedef struct stab_sparse_info {
+    int64_t order_final;   /* terms in the list when the sparse path ended */
+    int64_t order_max;     /* longest list seen */
+    int64_t steps;         /* steps run on the list (Clifford runs + rotations) */
+    int64_t dense_gates;   /* gates left to the dense path at the switch; -1: no switch */
+    int32_t regrows;       /* times the list capacity was enlarged */
+    int32_t reserved;
+} stab_sparse_info;
+
+/* Creates a sparse context for n qubits (1 <= n <= STAB_SPARSE_MAX_QUBITS)
+ * holding up to max_terms terms (1 <= max_terms <= 2^30); the buffers start
+ * small and grow by 8x when a step would overflow them (the step is then
+ * re-run), up to max_terms.  Device memory is about 64 bytes per term of
+ * capacity.  opts as for stab_create (kernel and fuse apply to the dense
+ * path it switches to).
+ * Errors: STAB_E_RANGE (n, max_terms), STAB_E_INVAL, STAB_E_CUDA, STAB_E_NOMEM. */
+int stab_sparse_create(int n, int64_t max_terms, const stab_opts *opts, stab_sparse **out);
+int stab_sparse_destroy(stab_sparse *s);
+
+/* Validates and copies a gate list and its angles (host memory), as
+ * stab_load_circuit.  Errors: STAB_E_INVAL, STAB_E_RANGE, STAB_E_NONFINITE. */
+int stab_sparse_load_circuit(stab_sparse *s, const stab_gate *gates, int64_t m,
+                             const double *thetas, int64_t n_params);
+
+/* Order above which an expectation continues on the dense 4^n vector (the
+ * rest of the circuit through the dense path); 0 = never.  Only for
+ * n <= STAB_MAX_QUBITS.  Default: 4^n / 16 for n <= 12, else 0.
+ * Errors: STAB_E_RANGE (negative, or nonzero with n > STAB_MAX_QUBITS). */
+int stab_sparse_set_dense_threshold(stab_sparse *s, int64_t order);
+
+/* <0^n| U^dagger O U |0^n>: O (host terms, duplicates summed) is propagated
+ * backward as a list, then its x-free coefficients are summed in list order.
+ * info may be NULL.  Synchronizing.
+ * Errors: STAB_E_STATE (no circuit), STAB_E_INVAL (bad term), STAB_E_RANGE
+ * (the list outgrew max_terms and no dense switch was possible), STAB_E_CUDA,
+ * STAB_E_NOMEM. */
+int stab_sparse_expect(stab_sparse *s, const stab_term *O, int64_t n_terms, double *out,
+                       stab_sparse_info *info);
+
+/* U Z_k U^dagger as a term list: writes up to max_out terms to out (host)
+ * and the number of terms to *n_out; when *n_out > max_out nothing is
+ * written and STAB_E_RANGE is returned.  Synchronizing.
+ * Errors: STAB_E_STATE, STAB_E_RANGE (k, list size), STAB_E_CUDA, STAB_E_NOMEM. */
+int stab_sparse_generator(stab_sparse *s, int k, int64_t max_out, stab_term *out,
+                          int64_t *n_out, stab_sparse_info *info);
+
+/* The order after each step of the last expect / generator call (the
+ * stabilizer order curve of Fig. 1): writes min(count, max) values and sets
+ * *count to the number of steps run. */
+int stab_sparse_order_history(stab_sparse *s, int64_t *orders, int64_t max, int64_t *count);
+
 /* Number of qubits, loaded gates and fused passes of the current plan. */
 int stab_plan_info(stab_ctx *ctx, int64_t *n_gates, int64_t *n_passes, int32_t *kernel);
 

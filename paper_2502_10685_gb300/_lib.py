@@ -72,6 +72,12 @@ class StabResult(ctypes.Structure):
                 ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
 
 
+class StabSparseInfo(ctypes.Structure):
+    _fields_ = [("order_final", ctypes.c_int64), ("order_max", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("dense_gates", ctypes.c_int64),
+                ("regrows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -131,6 +137,14 @@ def load(build_if_missing: bool = True):
             "stab_last_cuda_error": (i32, []),
             "stab_version": (i32, []),
             "stab_selftest_bounded_wait": (i32, [i64]),
+            "stab_sparse_create": (i32, [i32, i64, ctypes.POINTER(StabOpts), ctypes.POINTER(vp)]),
+            "stab_sparse_destroy": (i32, [vp]),
+            "stab_sparse_load_circuit": (i32, [vp, vp, i64, dp, i64]),
+            "stab_sparse_set_dense_threshold": (i32, [vp, i64]),
+            "stab_sparse_expect": (i32, [vp, vp, i64, dp, ctypes.POINTER(StabSparseInfo)]),
+            "stab_sparse_generator": (i32, [vp, i32, i64, vp, ctypes.POINTER(i64),
+                                            ctypes.POINTER(StabSparseInfo)]),
+            "stab_sparse_order_history": (i32, [vp, vp, i64, ctypes.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -165,4 +165,50 @@ cudaError_t launch_gather_grads(const double *grad_rot, const int32_t *param_ptr
                                 const int32_t *param_rot, int n_params, double *grads,
                                 cudaStream_t st);
 
+// ---------------------------------------------------------------- sparse term lists (k_sparse.cu)
+
+constexpr int kSpMaxBlocks = 608;        // 4 CTAs per SM on 152 SMs
+
+struct SpGate {                          // one Clifford gate of a run, already inverted for
+    uint8_t op, q0, q1, pad;             // backward runs (S <-> S^dagger)
+};
+
+struct SpRotArgs {
+    const uint64_t *keys;                // input list (keys z | x << n, coefficients)
+    const double *vals;
+    uint64_t *keys_out;                  // output list (the other buffer)
+    double *vals_out;
+    int64_t *counts;                     // counts[step] = order before step
+    int32_t *flags;                      // [0] stop code (1 overflow, 2 threshold), [1] step
+    int32_t step, n, q, axis;            // axis 0/1/2 = R_x/R_y/R_z
+    const double *thetas;
+    int32_t param, inverse;
+    int32_t *hpos;                       // table: position of the term in a slot, -1 free
+    uint64_t *hkey;                      // table: key in a slot
+    int32_t log_h;
+    int32_t *slot_of;                    // per term: its table slot
+    int32_t *partner;                    // per term: position of its partner, -1 absent
+    int64_t *blk;                        // per block: emitted terms, then their offsets
+    int32_t *err;                        // set when a table probe runs out (never expected)
+    int64_t cap;                         // list capacity
+    int64_t threshold;                   // stop above this order (0: never)
+    int64_t bound;                       // host bound on counts[step] (sizes the grid)
+};
+
+cudaError_t launch_sp_cliff(uint64_t *keys, double *vals, int64_t *counts, const int32_t *flags,
+                            int step, int n, const SpGate *gates, int n_gates, int64_t bound,
+                            cudaStream_t st);
+cudaError_t launch_sp_rotation(const SpRotArgs &a, cudaStream_t st);
+cudaError_t launch_sp_xfree(const uint64_t *keys, const double *vals, const int64_t *counts,
+                            int step, int n, double *partial, double *out, cudaStream_t st);
+cudaError_t launch_sp_to_terms(const uint64_t *keys, const double *vals, const int64_t *counts,
+                               int step, DevTerm *out, int64_t bound, cudaStream_t st);
+
+}  // namespace stab
+
+struct stab_ctx;
+namespace stab {
+// <0^n| U^dagger O U |0^n> for the loaded circuit, O given as nt deduplicated
+// device terms (stab_api.cpp); blocks until the value is on the host.
+int expect_device_terms(stab_ctx *c, const DevTerm *terms, int64_t nt, double *out);
 }  // namespace stab

@@ -1020,3 +1020,32 @@ int stab_transfer_bytes(stab_ctx *c, int64_t *h2d, int64_t *d2h) {
 }
 
 }  // extern "C"
+
+// Expectation of an observable already on the device as deduplicated terms
+// (the sparse path's list when it switches to the dense vector).
+int stab::expect_device_terms(stab_ctx *c, const DevTerm *terms, int64_t nt, double *out) {
+    if (!c || !out || nt < 0 || nt > INT32_MAX || (nt > 0 && !terms)) return STAB_E_INVAL;
+    if (!c->loaded) return STAB_E_STATE;
+    CK(cudaSetDevice(c->device));
+    c->obs_loaded = false;
+    CK(cudaStreamSynchronize(c->aux));
+    RC(c->dalloc(c->terms, (size_t)(nt ? nt : 1) * sizeof(DevTerm), c->st));
+    if (nt)
+        CK(cudaMemcpyAsync(c->terms.p, terms, (size_t)nt * sizeof(DevTerm),
+                           cudaMemcpyDeviceToDevice, c->st));
+    c->n_obs_terms = (int32_t)nt;
+    CK(cudaEventRecord(c->ev_ready, c->st));
+    c->obs_loaded = true;
+    RC(c->dalloc(c->scal, 64 * sizeof(double), c->st));
+    RC(stab_expect_async(c, (double *)c->scal.p));
+    CK(cudaEventSynchronize(c->ev_stage));
+    RC(c->host_stage(c->stage, c->stage_bytes, 64 * sizeof(double)));
+    double *h = (double *)c->stage;
+    CK(cudaMemcpyAsync(h, c->scal.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->d2h_bytes += (int64_t)sizeof(double);
+    *out = *h;
+    RC(check_status(c));
+    return STAB_OK;
+}
+

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (StabBatchItem, StabError, StabGate, StabOpts, StabRequest, StabResult,
-                   StabServerOpts, StabTerm, check)
+                   StabServerOpts, StabSparseInfo, StabTerm, check)
 
 KERNELS = {"auto": 0, "resident": 1, "streamed": 2, "plain": 3}
 GATE_DTYPE = np.dtype([("op", "u1"), ("q0", "u1"), ("q1", "u1"), ("flags", "u1"),
@@ -386,6 +386,93 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "h", None) is not None:
             _lib.load().stab_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- sparse term lists
+
+TERM_DTYPE = np.dtype([("coeff", "<f8"), ("x", "<u8"), ("z", "<u8")])
+
+
+def _info_dict(info: StabSparseInfo) -> dict:
+    return {"order_final": info.order_final, "order_max": info.order_max, "steps": info.steps,
+            "dense_gates": info.dense_gates, "regrows": info.regrows}
+
+
+class Sparse:
+    """A stabilizer or observable held as its list of Pauli terms (stab_sparse_*),
+    for up to 32 qubits while the stabilizer order stays below ``max_terms``.
+
+    ``expect`` returns ``(value, info)``; ``generator`` returns the term records
+    (``coeff``, ``x``, ``z`` masks, bit q = qubit q) and ``info``.  With
+    ``torch_memory`` the device buffers come from PyTorch's caching allocator
+    and the work is queued on its current stream.
+    """
+
+    def __init__(self, n: int, max_terms: int = 1 << 24, device: int = 0,
+                 torch_memory: bool = True):
+        self.n = n
+        self._keep = []
+        o = StabOpts()
+        _lib.load().stab_default_opts(ctypes.byref(o))
+        o.device = device
+        if torch_memory:
+            _torch_alloc_opts(o, device, self._keep)
+        h = ctypes.c_void_p()
+        check(_lib.load().stab_sparse_create(n, int(max_terms), ctypes.byref(o), ctypes.byref(h)),
+              "stab_sparse_create")
+        self.h = h
+
+    def load_circuit(self, gates, thetas) -> None:
+        g, gp = _gates_ptr(gates)
+        m = int(g.shape[0])
+        th = _f64(thetas)
+        self._n_params = int(th.size)
+        check(_lib.load().stab_sparse_load_circuit(self.h, gp if m else None, m,
+                                                   th.ctypes.data if th.size else None, th.size),
+              "stab_sparse_load_circuit")
+
+    def set_dense_threshold(self, order: int) -> None:
+        check(_lib.load().stab_sparse_set_dense_threshold(self.h, int(order)),
+              "stab_sparse_set_dense_threshold")
+
+    def expect(self, observable):
+        t = terms_from_observable(self.n, observable)
+        out = ctypes.c_double()
+        info = StabSparseInfo()
+        check(_lib.load().stab_sparse_expect(self.h, t.ctypes.data if len(t) else None, len(t),
+                                             ctypes.byref(out), ctypes.byref(info)),
+              "stab_sparse_expect")
+        return out.value, _info_dict(info)
+
+    def generator(self, k: int, max_out: int = 1 << 22):
+        out = np.zeros(max(1, max_out), dtype=TERM_DTYPE)
+        cnt = ctypes.c_int64()
+        info = StabSparseInfo()
+        check(_lib.load().stab_sparse_generator(self.h, k, max_out, out.ctypes.data,
+                                                ctypes.byref(cnt), ctypes.byref(info)),
+              "stab_sparse_generator")
+        return out[:cnt.value].copy(), _info_dict(info)
+
+    def order_history(self) -> np.ndarray:
+        cnt = ctypes.c_int64()
+        check(_lib.load().stab_sparse_order_history(self.h, None, 0, ctypes.byref(cnt)),
+              "stab_sparse_order_history")
+        out = np.zeros(max(1, cnt.value), dtype=np.int64)
+        check(_lib.load().stab_sparse_order_history(self.h, out.ctypes.data, cnt.value,
+                                                    ctypes.byref(cnt)),
+              "stab_sparse_order_history")
+        return out[:cnt.value]
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            _lib.load().stab_sparse_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -31,3 +31,17 @@ def lib_to_paper(n: int, v: np.ndarray) -> np.ndarray:
 def paper_to_lib(n: int, v: np.ndarray) -> np.ndarray:
     perm = lib_to_paper_index(n)
     return v[..., perm]
+
+
+def term_key_paper(n: int, x: int, z: int) -> int:
+    """Base-4 key (qubit 0 most significant digit) of the string with masks x, z."""
+    k = 0
+    for q in range(n):
+        xb, zb = (x >> q) & 1, (z >> q) & 1
+        k = k * 4 + (2 if xb and zb else 1 if xb else 3 if zb else 0)
+    return k
+
+
+def terms_to_paper_dict(n: int, terms) -> dict:
+    """Library term records (coeff, x, z) -> {base-4 key: coeff}."""
+    return {term_key_paper(n, int(t["x"]), int(t["z"])): float(t["coeff"]) for t in terms}
