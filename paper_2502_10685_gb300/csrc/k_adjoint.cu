@@ -81,6 +81,7 @@ __device__ __forceinline__ int rot_gate(const DevPass &p, const DevOp *ops, int 
 // ---------------------------------------------------------------- streamed
 
 constexpr int kAdjThreads = 256;
+constexpr int kAdjStagedOps = 96;   // ops of a tile group staged in shared memory (3 KiB)
 
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, double *rho, int n,
                                                               DevPass p, const DevOp *ops,
@@ -121,31 +122,72 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, doubl
 
 // Tile-fused reverse sweep: up to kTileMaxPasses wire passes on at most
 // kTileWires wires, applied backward to the pair (lambda, rho) held as two
-// shared-memory tiles (pair[0 .. 4^n) = lambda, pair[4^n ..) = rho).  Every
-// rotation's gradient dot is reduced over the CTA in a fixed order, summed
-// over the CTA's tiles in tile order, and written to partials[gate][block].
-__global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(double *pair, int n, TileGroup tg,
+// shared-memory tiles (pair[0 .. 4^n) = lambda, pair[4^n ..) = rho).  The
+// group's ops are staged in shared memory once per launch.  Every rotation's
+// gradient dot is reduced within each warp per pass (lane 0 adds it to its
+// warp's slot, tile after tile), and over the warps in a fixed order at the
+// end; the result goes to partials[gate][block].
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src, double *pair,
+                                                              int n, TileGroup tg,
                                                               const DevOp *ops,
                                                               double *partials) {
     extern __shared__ double sm[];
     constexpr int W = kAdjThreads / 32;
     const uint32_t T = 1u << tg.tile_bits;
     double *tl = sm, *tr = sm + T;
-    double *red = tr + T;                            // W x R
-    double *acc = red + W * R;                       // kTileMaxPasses x R
-    uint32_t *offs = reinterpret_cast<uint32_t *>(acc + kTileMaxPasses * R);
+    double *red = tr + T;                            // kTileMaxPasses x R x W
+    DevOp *sops = reinterpret_cast<DevOp *>(red + kTileMaxPasses * R * W);   // kAdjStagedOps
+    uint32_t *offs = reinterpret_cast<uint32_t *>(sops + kAdjStagedOps);
+    __shared__ int s_first[kTileMaxPasses], s_nrot[kTileMaxPasses];
+    __shared__ int s_staged;
     for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
         offs[e] = (uint32_t)deposit_runs(e, tg.tile_runs);
-    for (int k = threadIdx.x; k < kTileMaxPasses * R; k += blockDim.x) acc[k] = 0.0;
+    for (int k = threadIdx.x; k < kTileMaxPasses * R * W; k += blockDim.x) red[k] = 0.0;
+    if (threadIdx.x == 0) {
+        int total = 0;
+        for (int j = 0; j < tg.n_pass; ++j) total += tg.n_ops[j];
+        s_staged = total <= kAdjStagedOps;
+        int at = 0;
+        for (int j = 0; j < tg.n_pass; ++j) {
+            s_first[j] = s_staged ? at : (int)tg.first[j];
+            at += tg.n_ops[j];
+            DevPass p{};
+            p.n_ops = tg.n_ops[j];
+            p.first = tg.first[j];
+            s_nrot[j] = count_rot(p, ops);
+        }
+    }
     __syncthreads();
+    const bool staged = s_staged != 0;
+    if (staged) {
+        int at = 0;
+        for (int j = 0; j < tg.n_pass; ++j) {
+            for (int k = threadIdx.x; k < (int)tg.n_ops[j]; k += blockDim.x)
+                sops[at + k] = ops[tg.first[j] + k];
+            at += tg.n_ops[j];
+        }
+    }
+    __syncthreads();
+    const DevOp *pops = staged ? sops : ops;
     const uint64_t E = 1ull << (2 * n);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t tiles = 1ull << tg.rest_bits;
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const uint64_t base = deposit_runs(t, tg.rest_runs);
-        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
-            tl[e] = pair[base + offs[e]];
-            tr[e] = pair[E + base + offs[e]];
+        if (tg.pull_n == 0) {
+            for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+                tl[e] = src[base + offs[e]];
+                tr[e] = src[E + base + offs[e]];
+            }
+        } else {
+            // the Clifford gather that precedes the group, on both vectors
+            for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+                uint32_t neg = 0;
+                const uint64_t j = pull_pass(base + offs[e], n, ops + tg.pull_first, tg.pull_n,
+                                             tg.pull_inverse, neg);
+                tl[e] = flip(src[j], neg);
+                tr[e] = flip(src[E + j], neg);
+            }
         }
         __syncthreads();
         for (int j = 0; j < tg.n_pass; ++j) {
@@ -154,8 +196,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(double *pair, int 
             const uint32_t bz = 1u << lz, bx = 1u << lx;
             DevPass p{};
             p.n_ops = tg.n_ops[j];
-            p.first = tg.first[j];
-            const int n_rot = count_rot(p, ops);
+            p.first = s_first[j];
+            const int n_rot = s_nrot[j];
             double part[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) part[r] = 0.0;
@@ -164,23 +206,17 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(double *pair, int 
                 b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1u));
                 double lx_ = tl[b | bx], ly_ = tl[b | bx | bz], lz_ = tl[b | bz];
                 double rx_ = tr[b | bx], ry_ = tr[b | bx | bz], rz_ = tr[b | bz];
-                adjoint_group(p, ops, nullptr, lx_, ly_, lz_, rx_, ry_, rz_, part, n_rot);
+                adjoint_group(p, pops, nullptr, lx_, ly_, lz_, rx_, ry_, rz_, part, n_rot);
                 tl[b | bx] = lx_; tl[b | bx | bz] = ly_; tl[b | bz] = lz_;
                 tr[b | bx] = rx_; tr[b | bx | bz] = ry_; tr[b | bz] = rz_;
             }
-            if (n_rot > 0) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < R; ++r) {
+                if (r < n_rot) {
                     double v = part[r];
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                    if (lane == 0) red[warp * R + r] = v;
+                    if (lane == 0) red[(j * R + r) * W + warp] += v;
                 }
-            }
-            __syncthreads();
-            if (threadIdx.x < n_rot) {
-                double total = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += red[w * R + threadIdx.x];
-                acc[j * R + threadIdx.x] += total;
             }
             __syncthreads();
         }
@@ -190,13 +226,16 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(double *pair, int 
         }
         __syncthreads();
     }
+    const int nw = (int)(blockDim.x >> 5);
     for (int k = threadIdx.x; k < tg.n_pass * R; k += blockDim.x) {
         const int j = k / R, r = k % R;
+        if (r >= s_nrot[j]) continue;
+        double total = 0.0;
+        for (int w = 0; w < nw; ++w) total += red[k * W + w];
         DevPass p{};
         p.n_ops = tg.n_ops[j];
         p.first = tg.first[j];
-        if (r < count_rot(p, ops))
-            partials[(size_t)rot_gate(p, ops, r) * gridDim.x + blockIdx.x] = acc[k];
+        partials[(size_t)rot_gate(p, ops, r) * gridDim.x + blockIdx.x] = total;
     }
 }
 
@@ -242,17 +281,18 @@ cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &
 
 size_t adjoint_tile_smem(int tile_bits) {
     const size_t T = (size_t)1 << tile_bits;
-    return 2 * T * sizeof(double) + (kAdjThreads / 32) * R * sizeof(double) +
-           kTileMaxPasses * R * sizeof(double) + T * sizeof(uint32_t);
+    return 2 * T * sizeof(double) + (size_t)kTileMaxPasses * R * (kAdjThreads / 32) * sizeof(double) +
+           kAdjStagedOps * sizeof(DevOp) + T * sizeof(uint32_t);
 }
 
-cudaError_t launch_adjoint_tile(double *pair, int n, const TileGroup &tg, const DevOp *ops,
-                                double *partials, cudaStream_t st) {
+cudaError_t launch_adjoint_tile(const double *src_pair, double *dst_pair, int n,
+                                const TileGroup &tg, const DevOp *ops, double *partials,
+                                cudaStream_t st) {
     int threads = (int)((1u << tg.tile_bits) / 4);
     if (threads > kAdjThreads) threads = kAdjThreads;
     if (threads < 32) threads = 32;
     k_adjoint_tile<<<adjoint_stream_blocks(n), threads, adjoint_tile_smem(tg.tile_bits), st>>>(
-        pair, n, tg, ops, partials);
+        src_pair, dst_pair, n, tg, ops, partials);
     return cudaGetLastError();
 }
 

@@ -191,6 +191,74 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_cliff(uint64_t *keys, double 
     }
 }
 
+// A long Clifford run as its tableau: the images U X_q U^dagger and
+// U Z_q U^dagger of the 2n single-qubit generators (entry q: X_q, entry n + q:
+// Z_q), each a signed string.  One thread per generator, gate by gate.
+__global__ void k_sp_tableau(const SpGate *gates, const int32_t *run_first,
+                             const int32_t *run_count, int n, SpTab *tabs) {
+    const int r = blockIdx.x, j = threadIdx.x;
+    if (j >= 2 * n) return;
+    uint64_t k = j < n ? (1ull << (n + j)) : (1ull << (j - n));
+    uint32_t neg = 0;
+    const SpGate *g = gates + run_first[r];
+    for (int i = 0; i < run_count[r]; ++i) k = sp_clifford(k, n, g[i], neg);
+    tabs[(size_t)r * 64 + j] = SpTab{k, neg};
+}
+
+// Exponent c (mod 4) of P(a) P(b) = i^c P(a xor b) for Hermitian Pauli strings
+// given by x / z masks: per qubit, with a = Y: z_b - x_b; a = X: z_b (2 x_b - 1);
+// a = Z: x_b (1 - 2 z_b) (the phase function of the stabilizer tableau
+// algorithm of Aaronson and Gottesman), summed with population counts.
+__device__ __forceinline__ uint32_t sp_mul_phase(uint32_t ax, uint32_t az, uint32_t bx,
+                                                 uint32_t bz) {
+    const uint32_t A = ax & az, B = ax & ~az, C = ~ax & az;
+    const uint32_t plus = (A & bz & ~bx) | (B & bz & bx) | (C & bx & ~bz);
+    const uint32_t minus = (A & bx & ~bz) | (B & bz & ~bx) | (C & bx & bz);
+    return (uint32_t)(__popc(plus) - __popc(minus)) & 3u;
+}
+
+// U P U^dagger from the tableau: P(x, z) = i^{|x & z|} prod_q X_q^{x_q} Z_q^{z_q}
+// (Y = i X Z), so its image is i^{|x & z|} times the product of the generator
+// images in that order, each factor adding its phase and sign.
+__global__ void __launch_bounds__(kSpThreads) k_sp_cliff_tab(uint64_t *keys, double *vals,
+                                                              int64_t *counts,
+                                                              const int32_t *flags, int step,
+                                                              int n, const SpTab *tab) {
+    __shared__ uint32_t tx[64], tz[64], ts[64];
+    if (sp_stopped_before(flags, step)) return;
+    if (threadIdx.x < 2 * n) {
+        const SpTab t = tab[threadIdx.x];
+        tx[threadIdx.x] = (uint32_t)(t.key >> n);
+        tz[threadIdx.x] = (uint32_t)(t.key & ((1ull << n) - 1));
+        ts[threadIdx.x] = t.neg ? 2u : 0u;
+    }
+    __syncthreads();
+    const int64_t count = counts[step];
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[step + 1] = count;
+    const uint64_t zmask = (1ull << n) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        const uint32_t x = (uint32_t)(k >> n), z = (uint32_t)(k & zmask);
+        uint32_t rx = 0, rz = 0, e = (uint32_t)__popc(x & z);
+        for (int q = 0; q < n; ++q) {
+            if ((x >> q) & 1u) {
+                e += sp_mul_phase(rx, rz, tx[q], tz[q]) + ts[q];
+                rx ^= tx[q];
+                rz ^= tz[q];
+            }
+            if ((z >> q) & 1u) {
+                e += sp_mul_phase(rx, rz, tx[n + q], tz[n + q]) + ts[n + q];
+                rx ^= tx[n + q];
+                rz ^= tz[n + q];
+            }
+        }
+        // a Hermitian image: e is 0 or 2 (mod 4)
+        keys[i] = ((uint64_t)rx << n) | rz;
+        if (e & 2u) vals[i] = -vals[i];
+    }
+}
+
 __global__ void __launch_bounds__(kSpThreads) k_sp_insert(const uint64_t *keys,
                                                            const int64_t *counts,
                                                            const int32_t *flags, int step, int n,
@@ -368,11 +436,15 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_xfree(const uint64_t *keys,
     }
 }
 
+// One warp: lane l sums a contiguous slice of the partials, then a fixed
+// shuffle tree; the order depends only on nblk.
 __global__ void k_sp_sum_partials(const double *partial, int nblk, double *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int lane = threadIdx.x;
+    const int per = (nblk + 31) / 32;
     double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += partial[b];
-    *out = t;
+    for (int b = lane * per; b < nblk && b < (lane + 1) * per; ++b) t += partial[b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) *out = t;
 }
 
 __global__ void k_sp_to_terms(const uint64_t *keys, const double *vals, const int64_t *counts,
@@ -397,6 +469,22 @@ cudaError_t launch_sp_cliff(uint64_t *keys, double *vals, int64_t *counts, const
                             cudaStream_t st) {
     k_sp_cliff<<<sp_grid(bound), kSpThreads, 0, st>>>(keys, vals, counts, flags, step, n, gates,
                                                         n_gates);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_tableau(const SpGate *gates, const int32_t *run_first,
+                              const int32_t *run_count, int n_runs, int n, SpTab *tabs,
+                              cudaStream_t st) {
+    if (n_runs == 0) return cudaSuccess;
+    k_sp_tableau<<<n_runs, 64, 0, st>>>(gates, run_first, run_count, n, tabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_cliff_tab(uint64_t *keys, double *vals, int64_t *counts,
+                                const int32_t *flags, int step, int n, const SpTab *tab,
+                                int64_t bound, cudaStream_t st) {
+    k_sp_cliff_tab<<<sp_grid(bound), kSpThreads, 0, st>>>(keys, vals, counts, flags, step, n,
+                                                           tab);
     return cudaGetLastError();
 }
 

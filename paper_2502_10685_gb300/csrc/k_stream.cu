@@ -182,8 +182,9 @@ __device__ __forceinline__ uint64_t deposit_runs(uint64_t v, const BitRuns &r) {
     return out;
 }
 
-__global__ void __launch_bounds__(kThreads) k_stream_tile(double *vec, int n, int n_vec,
-                                                          TileGroup tg, const DevOp *ops,
+__global__ void __launch_bounds__(kThreads) k_stream_tile(const double *src, double *dst, int n,
+                                                          int n_vec, TileGroup tg,
+                                                          const DevOp *ops,
                                                           const DevMap3 *maps) {
     extern __shared__ double tile[];
     const uint32_t T = 1u << tg.tile_bits;
@@ -196,8 +197,19 @@ __global__ void __launch_bounds__(kThreads) k_stream_tile(double *vec, int n, in
     const uint64_t tiles = (uint64_t)n_vec << tg.rest_bits;
     for (uint64_t tb = blockIdx.x; tb < tiles; tb += gridDim.x) {
         const uint64_t v = tb >> tg.rest_bits, t = tb & ((1ull << tg.rest_bits) - 1ull);
-        double *V = vec + v * E + deposit_runs(t, tg.rest_runs);
-        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) tile[e] = V[offs[e]];
+        const uint64_t base = deposit_runs(t, tg.rest_runs);
+        const double *S = src + v * E;
+        double *V = dst + v * E + base;
+        if (tg.pull_n == 0) {
+            for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) tile[e] = S[base + offs[e]];
+        } else {
+            for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+                uint32_t neg = 0;
+                const uint64_t j = pull_pass(base + offs[e], n, ops + tg.pull_first, tg.pull_n,
+                                             tg.pull_inverse, neg);
+                tile[e] = flip(S[j], neg);
+            }
+        }
         __syncthreads();
         for (int j = 0; j < tg.n_pass; ++j) {
             const int lz = tg.lz[j], lx = tg.lx[j];
@@ -305,8 +317,9 @@ cudaError_t launch_stream_cliff(const double *src, double *dst, int n, int n_vec
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream_tile(double *vec, int n, int n_vec, const TileGroup &tg,
-                               const DevOp *ops, const DevMap3 *maps, cudaStream_t st) {
+cudaError_t launch_stream_tile(const double *src, double *dst, int n, int n_vec,
+                               const TileGroup &tg, const DevOp *ops, const DevMap3 *maps,
+                               cudaStream_t st) {
     const uint32_t T = 1u << tg.tile_bits;
     const uint64_t tiles = (uint64_t)n_vec << tg.rest_bits;
     int threads = (int)(T / 4);
@@ -321,7 +334,7 @@ cudaError_t launch_stream_tile(double *vec, int n, int n_vec, const TileGroup &t
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_stream_tile<<<(int)grid, threads, smem, st>>>(vec, n, n_vec, tg, ops, maps);
+    k_stream_tile<<<(int)grid, threads, smem, st>>>(src, dst, n, n_vec, tg, ops, maps);
     return cudaGetLastError();
 }
 

@@ -118,7 +118,7 @@ cudaError_t launch_xfree_sum(const double *vec, int n, int n_vec, double *out, c
 // streamed launch: each CTA loads a tile (all 4^|Q| slots of the wires Q times
 // some of the lowest other index bits) into shared memory, applies the passes
 // in order and writes it back.
-constexpr int kTileWires = 3;
+constexpr int kTileWires = 4;
 constexpr int kTileMaxPasses = 8;
 constexpr int kTileMaxBits = 12;        // 4096 doubles = 32 KiB of shared memory
 
@@ -137,10 +137,18 @@ struct TileGroup {
     uint32_t first[kTileMaxPasses];
     BitRuns tile_runs;                  // local entry -> global index bits
     BitRuns rest_runs;                  // tile id -> global index bits
+    // A Clifford gather folded into the tile loads (a P_CLIFF pass that
+    // precedes the group): entry i is read from pull(i) of the source, signed.
+    int32_t pull_n;                     // ops of that pass (0: plain load)
+    uint32_t pull_first;
+    int32_t pull_inverse;
 };
 
-cudaError_t launch_stream_tile(double *vec, int n, int n_vec, const TileGroup &tg,
-                               const DevOp *ops, const DevMap3 *maps, cudaStream_t st);
+// src == dst unless the group carries a folded Clifford gather (then the
+// result goes to dst, a different buffer).
+cudaError_t launch_stream_tile(const double *src, double *dst, int n, int n_vec,
+                               const TileGroup &tg, const DevOp *ops, const DevMap3 *maps,
+                               cudaStream_t st);
 
 // Adjoint gradient, shared-memory resident (n <= kMaxResidentAdjoint).
 cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_t st);
@@ -157,8 +165,9 @@ cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &
 constexpr int kAdjTileMaxN = 8;
 constexpr int kAdjTileBits = 9;
 size_t adjoint_tile_smem(int tile_bits);
-cudaError_t launch_adjoint_tile(double *pair, int n, const TileGroup &tg, const DevOp *ops,
-                                double *partials, cudaStream_t st);
+cudaError_t launch_adjoint_tile(const double *src_pair, double *dst_pair, int n,
+                                const TileGroup &tg, const DevOp *ops, double *partials,
+                                cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, int n_rot, int n_blocks,
                                    double *grad_rot, cudaStream_t st);
 cudaError_t launch_gather_grads(const double *grad_rot, const int32_t *param_ptr,
@@ -171,6 +180,12 @@ constexpr int kSpMaxBlocks = 608;        // 4 CTAs per SM on 152 SMs
 
 struct SpGate {                          // one Clifford gate of a run, already inverted for
     uint8_t op, q0, q1, pad;             // backward runs (S <-> S^dagger)
+};
+
+struct SpTab {                           // tableau entry: image of X_q or Z_q, its sign
+    uint64_t key;
+    uint32_t neg;
+    uint32_t pad;
 };
 
 struct SpRotArgs {
@@ -199,6 +214,13 @@ cudaError_t launch_sp_cliff(uint64_t *keys, double *vals, int64_t *counts, const
                             int step, int n, const SpGate *gates, int n_gates, int64_t bound,
                             cudaStream_t st);
 cudaError_t launch_sp_rotation(const SpRotArgs &a, cudaStream_t st);
+// tabs: 64 entries per run (2n used); runs [r] = gates [run_first[r], + run_count[r])
+cudaError_t launch_sp_tableau(const SpGate *gates, const int32_t *run_first,
+                              const int32_t *run_count, int n_runs, int n, SpTab *tabs,
+                              cudaStream_t st);
+cudaError_t launch_sp_cliff_tab(uint64_t *keys, double *vals, int64_t *counts,
+                                const int32_t *flags, int step, int n, const SpTab *tab,
+                                int64_t bound, cudaStream_t st);
 cudaError_t launch_sp_xfree(const uint64_t *keys, const double *vals, const int64_t *counts,
                             int step, int n, double *partial, double *out, cudaStream_t st);
 cudaError_t launch_sp_to_terms(const uint64_t *keys, const double *vals, const int64_t *counts,

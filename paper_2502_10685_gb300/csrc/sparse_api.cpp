@@ -58,13 +58,19 @@ struct SpStep {
     int kind;
     int q, axis, param;       // rotation
     int first, count;         // Clifford run: gates [first, first + count) of the run array
+    int tab;                  // Clifford run applied through its tableau (index), or -1
     int64_t gate_lo, gate_hi; // circuit gates [gate_lo, gate_hi) the step covers
 };
 
 struct SpPlan {
     std::vector<SpStep> steps;
     std::vector<SpGate> gates;
+    std::vector<int32_t> tab_first, tab_count;   // runs that get a tableau
 };
+
+// A run of at least this many gates is applied through its tableau (about
+// 2n phase products per term) instead of gate by gate.
+int tableau_min_gates(int n) { return 2 * n + 8; }
 
 // The outcome of one propagation.
 struct SpRun {
@@ -115,6 +121,18 @@ void build_sp_plan(const std::vector<stab_gate> &gates, bool backward, SpPlan *P
     }
 }
 
+void assign_tableaus(int n, SpPlan *P) {
+    P->tab_first.clear();
+    P->tab_count.clear();
+    for (SpStep &s : P->steps) {
+        s.tab = -1;
+        if (s.kind != SP_CLIFF || s.count < tableau_min_gates(n)) continue;
+        s.tab = (int)P->tab_first.size();
+        P->tab_first.push_back(s.first);
+        P->tab_count.push_back(s.count);
+    }
+}
+
 }  // namespace
 
 struct stab_sparse {
@@ -130,7 +148,7 @@ struct stab_sparse {
     int64_t n_params = 0;
     SpPlan fwd, bwd;
     SpBuf thetas, g_fwd, g_bwd, keys[2], vals[2], hpos, hkey, slot_of, partner, blk, counts,
-        flags, partial, scal, dterms;
+        flags, partial, scal, dterms, t_fwd, t_bwd, runs;
     int log_h = 0;
     void *pinned = nullptr;
     size_t pinned_bytes = 0;
@@ -216,7 +234,7 @@ struct stab_sparse {
         if (st) cudaStreamSynchronize(st);
         for (SpBuf *b : {&thetas, &g_fwd, &g_bwd, &keys[0], &keys[1], &vals[0], &vals[1], &hpos,
                          &hkey, &slot_of, &partner, &blk, &counts, &flags, &partial, &scal,
-                         &dterms})
+                         &dterms, &t_fwd, &t_bwd, &runs})
             dfree(*b);
         if (pinned) cudaFreeHost(pinned);
         if (dense) stab_destroy(dense);
@@ -227,7 +245,8 @@ struct stab_sparse {
 namespace {
 
 // Uploads the initial list to buffer 0 and runs the plan.
-int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, bool backward,
+int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, const SpBuf &tabs,
+           bool backward,
            const std::vector<uint64_t> &k0, const std::vector<double> &v0, SpRun *R,
            int64_t *order_max) {
     const int64_t S = (int64_t)P.steps.size();
@@ -269,7 +288,13 @@ int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, bool backwar
             const SpStep &st = P.steps[e];
             if (st.kind == SP_ROT && 2 * bound > lim && e >= p + kSpMinSegment) break;
             const int cur = buf_before[e];
-            if (st.kind == SP_CLIFF) {
+            if (st.kind == SP_CLIFF && st.tab >= 0) {
+                SCK(launch_sp_cliff_tab((uint64_t *)s->keys[cur].p, (double *)s->vals[cur].p,
+                                        counts, flags, (int)e, s->n,
+                                        (const SpTab *)tabs.p + (size_t)st.tab * 64, bound,
+                                        s->st));
+                buf_before[e + 1] = cur;
+            } else if (st.kind == SP_CLIFF) {
                 SCK(launch_sp_cliff((uint64_t *)s->keys[cur].p, (double *)s->vals[cur].p,
                                     counts, flags, (int)e, s->n, gates + st.first, st.count,
                                     bound, s->st));
@@ -463,20 +488,38 @@ int stab_sparse_load_circuit(stab_sparse *s, const stab_gate *gates, int64_t m,
     s->n_params = n_params;
     build_sp_plan(s->gates, false, &s->fwd);
     build_sp_plan(s->gates, true, &s->bwd);
+    assign_tableaus(s->n, &s->fwd);
+    assign_tableaus(s->n, &s->bwd);
     const size_t bt = (size_t)std::max<int64_t>(n_params, 1) * 8;
     const size_t bf = std::max<size_t>(s->fwd.gates.size(), 1) * sizeof(SpGate);
     const size_t bb = std::max<size_t>(s->bwd.gates.size(), 1) * sizeof(SpGate);
+    const size_t nrf = s->fwd.tab_first.size(), nrb = s->bwd.tab_first.size();
+    const size_t br = std::max<size_t>(2 * (nrf + nrb), 1) * 4;
     SRC(s->dalloc(s->thetas, bt));
     SRC(s->dalloc(s->g_fwd, bf));
     SRC(s->dalloc(s->g_bwd, bb));
-    SRC(s->stage(bt + bf + bb));
+    SRC(s->dalloc(s->runs, br));
+    SRC(s->dalloc(s->t_fwd, std::max<size_t>(nrf, 1) * 64 * sizeof(SpTab)));
+    SRC(s->dalloc(s->t_bwd, std::max<size_t>(nrb, 1) * 64 * sizeof(SpTab)));
+    SRC(s->stage(bt + bf + bb + br));
     char *h = (char *)s->pinned;
     std::memcpy(h, s->thetas_h.data(), (size_t)n_params * 8);
     std::memcpy(h + bt, s->fwd.gates.data(), s->fwd.gates.size() * sizeof(SpGate));
     std::memcpy(h + bt + bf, s->bwd.gates.data(), s->bwd.gates.size() * sizeof(SpGate));
+    int32_t *hr = (int32_t *)(h + bt + bf + bb);
+    std::copy(s->fwd.tab_first.begin(), s->fwd.tab_first.end(), hr);
+    std::copy(s->fwd.tab_count.begin(), s->fwd.tab_count.end(), hr + nrf);
+    std::copy(s->bwd.tab_first.begin(), s->bwd.tab_first.end(), hr + 2 * nrf);
+    std::copy(s->bwd.tab_count.begin(), s->bwd.tab_count.end(), hr + 2 * nrf + nrb);
     SCK(cudaMemcpyAsync(s->thetas.p, h, bt, cudaMemcpyHostToDevice, s->st));
     SCK(cudaMemcpyAsync(s->g_fwd.p, h + bt, bf, cudaMemcpyHostToDevice, s->st));
     SCK(cudaMemcpyAsync(s->g_bwd.p, h + bt + bf, bb, cudaMemcpyHostToDevice, s->st));
+    SCK(cudaMemcpyAsync(s->runs.p, hr, br, cudaMemcpyHostToDevice, s->st));
+    const int32_t *dr = (const int32_t *)s->runs.p;
+    SCK(launch_sp_tableau((const SpGate *)s->g_fwd.p, dr, dr + nrf, (int)nrf, s->n,
+                          (SpTab *)s->t_fwd.p, s->st));
+    SCK(launch_sp_tableau((const SpGate *)s->g_bwd.p, dr + 2 * nrf, dr + 2 * nrf + nrb, (int)nrb,
+                          s->n, (SpTab *)s->t_bwd.p, s->st));
     SCK(cudaStreamSynchronize(s->st));
     s->loaded = true;
     return STAB_OK;
@@ -505,7 +548,7 @@ int stab_sparse_expect(stab_sparse *s, const stab_term *O, int64_t n_terms, doub
         fill_info(s, R, 0, -1, info);
         return STAB_OK;
     }
-    SRC(sp_run(s, s->bwd, s->g_bwd, true, k0, v0, &R, &order_max));
+    SRC(sp_run(s, s->bwd, s->g_bwd, s->t_bwd, true, k0, v0, &R, &order_max));
     int64_t dense_gates = -1;
     if (R.stopped) {
         // the rest of the circuit (backward: gates [0, g)) on the dense vector
@@ -543,7 +586,7 @@ int stab_sparse_generator(stab_sparse *s, int k, int64_t max_out, stab_term *out
     s->threshold = 0;   // generators stay on the list
     SpRun R;
     int64_t order_max = 0;
-    const int r = sp_run(s, s->fwd, s->g_fwd, false, k0, v0, &R, &order_max);
+    const int r = sp_run(s, s->fwd, s->g_fwd, s->t_fwd, false, k0, v0, &R, &order_max);
     s->threshold = keep;
     SRC(r);
     if (R.stopped) return STAB_E_RANGE;

@@ -406,15 +406,35 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
                             ((uint64_t)n_vec << (2 * c->n)) <= (1ull << 17);
     std::vector<const DevPass *> group;
     std::vector<int> wires;
+    // with tiles, a Clifford gather is folded into the loads of the next group
+    const DevPass *pending = nullptr;
+    auto gather_now = [&]() -> int {
+        CK(launch_stream_cliff(*cur, *alt, c->n, n_vec, *pending, P.prog.ops, inverse, s));
+        std::swap(*cur, *alt);
+        c->launches++;
+        pending = nullptr;
+        return STAB_OK;
+    };
     auto flush = [&]() -> int {
         if (group.empty()) return STAB_OK;
-        if (group.size() == 1) {
+        if (group.size() == 1 && !pending) {
             CK(launch_stream_wire(*cur, c->n, n_vec, *group[0], P.prog.ops, P.prog.maps, inverse,
                                   s));
         } else {
             TileGroup tg;
             make_tile_group(c->n, n_vec, group, inverse, &tg);
-            CK(launch_stream_tile(*cur, c->n, n_vec, tg, P.prog.ops, P.prog.maps, s));
+            double *dst = *cur;
+            if (pending) {
+                tg.pull_n = pending->n_ops;
+                tg.pull_first = pending->first;
+                tg.pull_inverse = inverse;
+                dst = *alt;
+            }
+            CK(launch_stream_tile(*cur, dst, c->n, n_vec, tg, P.prog.ops, P.prog.maps, s));
+            if (pending) {
+                std::swap(*cur, *alt);
+                pending = nullptr;
+            }
         }
         c->launches++;
         group.clear();
@@ -435,13 +455,13 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
             continue;
         }
         RC(flush());
-        CK(launch_stream_cliff(*cur, *alt, c->n, n_vec, p, P.prog.ops, inverse, s));
-        double *t = *cur;
-        *cur = *alt;
-        *alt = t;
-        c->launches++;
+        if (pending) RC(gather_now());
+        pending = &p;
+        if (!fuse_tiles) RC(gather_now());
     }
-    return flush();
+    RC(flush());
+    if (pending) RC(gather_now());
+    return STAB_OK;
 }
 
 // Replays the launch sequence `body` (queued on s) from a graph cached under
@@ -871,6 +891,15 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
             const auto &passes = c->grad.host.passes;
             std::vector<const DevPass *> group;
             std::vector<int> wires;
+            // with tiles, a Clifford gather is folded into the loads of the next group
+            const DevPass *pending = nullptr;
+            auto gather_now = [&]() -> int {
+                CK(launch_stream_cliff(pair, alt, n, 2, *pending, c->grad.prog.ops, 1, gs));
+                c->launches++;
+                std::swap(pair, alt);
+                pending = nullptr;
+                return STAB_OK;
+            };
             auto flush = [&]() -> int {
                 if (group.empty()) return STAB_OK;
                 if (!tiles) {
@@ -882,9 +911,20 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                 } else {
                     TileGroup tg;
                     make_tile_group(n, 1, group, 1, &tg, nb, std::min(kAdjTileBits, 2 * n));
-                    CK(launch_adjoint_tile(pair, n, tg, c->grad.prog.ops, (double *)c->partials.p,
-                                           gs));
+                    double *dst = pair;
+                    if (pending) {
+                        tg.pull_n = pending->n_ops;
+                        tg.pull_first = pending->first;
+                        tg.pull_inverse = 1;
+                        dst = alt;
+                    }
+                    CK(launch_adjoint_tile(pair, dst, n, tg, c->grad.prog.ops,
+                                           (double *)c->partials.p, gs));
                     c->launches++;
+                    if (pending) {
+                        std::swap(pair, alt);
+                        pending = nullptr;
+                    }
                 }
                 group.clear();
                 wires.clear();
@@ -903,11 +943,12 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                     continue;
                 }
                 RC(flush());
-                CK(launch_stream_cliff(pair, alt, n, 2, p, c->grad.prog.ops, 1, gs));
-                c->launches++;
-                std::swap(pair, alt);
+                if (pending) RC(gather_now());
+                pending = &p;
+                if (!tiles) RC(gather_now());
             }
             RC(flush());
+            if (pending) RC(gather_now());
             CK(launch_reduce_partials((const double *)c->partials.p, n_rot, nb,
                                       (double *)c->grad_rot.p, gs));
             CK(launch_xfree_sum(pair, n, 1, res, gs));
