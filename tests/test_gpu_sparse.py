@@ -207,3 +207,43 @@ def test_degenerate_inputs(S):
     sp.load_circuit(c.gates, c.thetas)
     assert sp.expect([(1.0, "I" * n)])[0] == 1.0
     sp.close()
+
+
+def _runs_and_rotations(n, run, blocks, seed):
+    """`blocks` Clifford runs of `run` gates, each followed by one rotation."""
+    rng = np.random.default_rng(seed)
+    parts, thetas = [], []
+    for b in range(blocks):
+        c = W.clifford_plus_rotations(n, run, 0, seed=int(rng.integers(1 << 30)))
+        parts.append(c.gates)
+        r = np.zeros(1, dtype=W.GATE_DTYPE)
+        r[0] = (W.OPS[("RX", "RY", "RZ")[b % 3]], int(rng.integers(n)), 0, 0, len(thetas))
+        thetas.append(float(rng.uniform(0, 2 * math.pi)))
+        parts.append(r)
+    return np.concatenate(parts), np.array(thetas)
+
+
+@pytest.mark.parametrize("n,run", [(8, 23), (8, 24), (8, 300), (32, 71), (32, 72), (32, 500)])
+def test_clifford_runs_gate_by_gate_and_tableau(S, n, run):
+    """Runs of at least 2n + 8 gates go through the composed tableau, shorter
+    runs gate by gate; both against the oracles."""
+    gates, th = _runs_and_rotations(n, run, 8, seed=n * 1000 + run)
+    sp = S.Sparse(n, max_terms=1 << 16)
+    sp.load_circuit(gates, th)
+    obs = W.obs_chain(n) + [(0.25, "Y" * n)]
+    got, _ = sp.expect(obs)
+    if n <= 10:
+        want = oracle.expect(n, gates, th, obs)
+        G = oracle.generators(n, gates, th)
+    else:
+        want = oracle.sparse_expect(n, gates, th, obs)
+    assert abs(got - want) <= 1e-12 * l1(obs)
+    for k in (0, n - 1):
+        terms, _ = sp.generator(k)
+        if n <= 10:
+            nz = np.nonzero(G[k])[0]
+            assert_terms_match(n, terms, nz, G[k][nz], 1e-12)
+        else:
+            wk, wv = oracle.sparse_generator(n, gates, th, k)
+            assert_terms_match(n, terms, wk, wv, 1e-12)
+    sp.close()
