@@ -151,10 +151,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
         for (int j = 0; j < tg.n_pass; ++j) {
             s_first[j] = s_staged ? at : (int)tg.first[j];
             at += tg.n_ops[j];
-            DevPass p{};
-            p.n_ops = tg.n_ops[j];
-            p.first = tg.first[j];
-            s_nrot[j] = count_rot(p, ops);
+            s_nrot[j] = tg.n_rot[j];
         }
     }
     __syncthreads();
@@ -234,8 +231,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
         for (int w = 0; w < nw; ++w) total += red[k * W + w];
         DevPass p{};
         p.n_ops = tg.n_ops[j];
-        p.first = tg.first[j];
-        partials[(size_t)rot_gate(p, ops, r) * gridDim.x + blockIdx.x] = total;
+        p.first = s_first[j];
+        partials[(size_t)rot_gate(p, pops, r) * gridDim.x + blockIdx.x] = total;
     }
 }
 

@@ -188,8 +188,21 @@ __global__ void __launch_bounds__(kThreads) k_stream_tile(const double *src, dou
                                                           const DevMap3 *maps) {
     extern __shared__ double tile[];
     const uint32_t T = 1u << tg.tile_bits;
-    // tile-local entry -> offset from the tile's base, the same for every tile
-    uint32_t *offs = reinterpret_cast<uint32_t *>(tile + T);
+    // the group's ops, staged once (when they fit), then the tile-local entry
+    // -> offset table, the same for every tile
+    DevOp *sops = reinterpret_cast<DevOp *>(tile + T);
+    uint32_t *offs = reinterpret_cast<uint32_t *>(sops + kTileStagedOps);
+    int total_ops = 0;
+    for (int j = 0; j < tg.n_pass; ++j) total_ops += tg.n_ops[j];
+    const bool staged = total_ops <= kTileStagedOps;
+    if (staged) {
+        int at = 0;
+        for (int j = 0; j < tg.n_pass; ++j) {
+            for (int k = threadIdx.x; k < (int)tg.n_ops[j]; k += blockDim.x)
+                sops[at + k] = ops[tg.first[j] + k];
+            at += tg.n_ops[j];
+        }
+    }
     for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
         offs[e] = (uint32_t)deposit_runs(e, tg.tile_runs);
     __syncthreads();
@@ -211,17 +224,20 @@ __global__ void __launch_bounds__(kThreads) k_stream_tile(const double *src, dou
             }
         }
         __syncthreads();
+        int at = 0;
         for (int j = 0; j < tg.n_pass; ++j) {
             const int lz = tg.lz[j], lx = tg.lx[j];
             const int lo = lz < lx ? lz : lx, hi = lz < lx ? lx : lz;
             const uint32_t bz = 1u << lz, bx = 1u << lx;
             const int n_ops = tg.n_ops[j];
+            const DevOp *pops = staged ? sops + at : ops + tg.first[j];
+            at += n_ops;
             for (uint32_t g = threadIdx.x; g < T / 4; g += blockDim.x) {
                 uint32_t b = ((g >> lo) << (lo + 1)) | (g & ((1u << lo) - 1u));
                 b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1u));
                 double x = tile[b | bx], y = tile[b | bx | bz], z = tile[b | bz];
                 for (int k = 0; k < n_ops; ++k) {
-                    const DevOp op = ops[tg.first[j] + (tg.inverse ? n_ops - 1 - k : k)];
+                    const DevOp op = pops[tg.inverse ? n_ops - 1 - k : k];
                     apply_op1(x, y, z, op, maps, tg.inverse);
                 }
                 tile[b | bx] = x;
@@ -327,7 +343,7 @@ cudaError_t launch_stream_tile(const double *src, double *dst, int n, int n_vec,
     if (threads < 32) threads = 32;
     uint64_t grid = tiles;
     if (grid > 152ull * 8ull) grid = 152ull * 8ull;
-    const size_t smem = T * (sizeof(double) + sizeof(uint32_t));
+    const size_t smem = T * (sizeof(double) + sizeof(uint32_t)) + kTileStagedOps * sizeof(DevOp);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_stream_tile,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -121,6 +121,7 @@ cudaError_t launch_xfree_sum(const double *vec, int n, int n_vec, double *out, c
 constexpr int kTileWires = 4;
 constexpr int kTileMaxPasses = 8;
 constexpr int kTileMaxBits = 12;        // 4096 doubles = 32 KiB of shared memory
+constexpr int kTileStagedOps = 96;      // ops of a group staged in shared memory (3 KiB)
 
 struct BitRuns {                        // deposit of a packed integer into index bits
     uint8_t n;
@@ -134,6 +135,7 @@ struct TileGroup {
     int32_t inverse;
     uint8_t lz[kTileMaxPasses], lx[kTileMaxPasses];   // tile-local bits of each pass's wire
     uint16_t n_ops[kTileMaxPasses];
+    uint8_t n_rot[kTileMaxPasses];      // rotations of each pass (adjoint groups)
     uint32_t first[kTileMaxPasses];
     BitRuns tile_runs;                  // local entry -> global index bits
     BitRuns rest_runs;                  // tile id -> global index bits

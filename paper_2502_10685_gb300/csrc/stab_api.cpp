@@ -911,6 +911,13 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                 } else {
                     TileGroup tg;
                     make_tile_group(n, 1, group, 1, &tg, nb, std::min(kAdjTileBits, 2 * n));
+                    const auto &hops = c->grad.host.ops;
+                    for (size_t j = 0; j < group.size(); ++j) {
+                        int nr = 0;
+                        for (int k = 0; k < group[j]->n_ops; ++k)
+                            nr += hops[(size_t)group[j]->first + k].kind == K_ROT;
+                        tg.n_rot[j] = (uint8_t)nr;
+                    }
                     double *dst = pair;
                     if (pending) {
                         tg.pull_n = pending->n_ops;
