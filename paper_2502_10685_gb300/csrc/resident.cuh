@@ -160,10 +160,84 @@ __device__ double *run_stream_quads(Stager &st, int c0, int c1, double *cur, dou
     return cur;
 }
 
+// n = 4, LPG = 4, with the vector held in registers between passes: each of
+// the 256 lanes keeps one entry.  In layout A a warp's 32 lanes span the
+// (z, x) bits of wires 0 and 1 (plus z_2), in layout B those of wires 2 and 3
+// (plus z_0); the warp index holds the other three bits.  A pass on a wire
+// of the current layout gathers its group from the quad's lanes by shuffles
+// and needs no shared memory and no barrier; a pass that pulls through a
+// Clifford run, or whose wire is in the other layout, first goes through
+// shared memory (write, one barrier, pulled read in the wanted layout).  The
+// two buffers alternate, so a write never meets a read still in flight.
+__device__ __forceinline__ uint32_t reg4_index(uint32_t t, int layout) {
+    // index bits: z_q = bit q, x_q = bit 4 + q.  Lane/warp bit k -> index bit.
+    const uint32_t pa[8] = {0, 4, 1, 5, 2, 6, 3, 7};
+    const uint32_t pb[8] = {2, 6, 3, 7, 0, 4, 1, 5};
+    uint32_t i = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) i |= ((t >> k) & 1u) << (layout ? pb[k] : pa[k]);
+    return i;
+}
+
+inline __device__ double *run_stream_reg4(Stager &st, int c0, int c1, double *cur, double *nxt,
+                                   int32_t *status) {
+    const uint32_t t = threadIdx.x;
+    const uint32_t lane = t & 31u;
+    const uint32_t iA = reg4_index(t, 0), iB = reg4_index(t, 1);
+    int layout = 0;
+    double v = cur[iA];
+    double *rd = cur, *wr = nxt;   // last buffer read; the one the next write goes to
+    for (int c = c0; c < c1; ++c) {
+        if (!st.wait(c, status)) return nullptr;
+        const Rec *Rr = st.chunk(c);
+        int r = 0;
+        Rec h = Rr[0];
+        while (h.kind == R_PASS) {
+            const int q = h.q, n_pull = h.param;
+            const int r_next = r + 1 + n_pull + h.gate;
+            const int want = q < 2 ? 0 : 1;
+            if (n_pull > 0 || want != layout) {
+                wr[layout ? iB : iA] = v;
+                __syncthreads();
+                uint32_t neg = 0;
+                const uint32_t j = pull_recs(want ? iB : iA, 4, Rr + r + 1, n_pull, neg);
+                v = flip(wr[j], neg);
+                double *tmp = rd;
+                rd = wr;
+                wr = tmp;
+                layout = want;
+            }
+            if (h.gate != 0) {
+                const int sh = 2 * (q & 1);                // the wire's lane-bit pair
+                const uint32_t zb = (lane >> sh) & 1u, xb = (lane >> (sh + 1)) & 1u;
+                const uint32_t base = lane & ~(3u << sh);
+                const double x = __shfl_sync(0xffffffffu, v, base | (2u << sh));
+                const double y = __shfl_sync(0xffffffffu, v, base | (3u << sh));
+                const double z = __shfl_sync(0xffffffffu, v, base | (1u << sh));
+                if (xb | zb) {
+                    // slot 1 = X (x), 2 = Y (x, z), 3 = Z (z): row slot - 1 of the map
+                    const uint32_t slot = xb ? (zb ? 2u : 1u) : 3u;
+                    const double *m =
+                        reinterpret_cast<const double *>(Rr + r + 2 + n_pull) + 3 * (slot - 1u);
+                    v = fma(m[2], z, fma(m[1], y, m[0] * x));
+                }
+            }
+            r = r_next;
+            h = Rr[r];
+        }
+        st.release(c);
+    }
+    wr[layout ? iB : iA] = v;
+    __syncthreads();
+    return wr;
+}
+
 // The block must have at least 4^n threads for LPG = 4.
 template <int N, int LPG, int T = SCfg<N, LPG>::T>
 __device__ double *run_stream(Stager &st, int c0, int c1, double *cur, double *nxt,
                               int32_t *status) {
+    if constexpr (LPG == 4 && N == 4 && T == 256)
+        return run_stream_reg4(st, c0, c1, cur, nxt, status);
     if constexpr (LPG == 4) return run_stream_quads<N>(st, c0, c1, cur, nxt, status);
     for (int c = c0; c < c1; ++c) {
         if (!st.wait(c, status)) return nullptr;
