@@ -312,7 +312,7 @@ def run_ours(args):
     # DRAM bytes per launch from one ncu capture of k_resident_stream<4,4> on the
     # 2,000-gate case (125,440 B read, 0 B written: the staged instruction stream),
     # scaled by gates (the stream grows in proportion); see profiles/.
-    traffic = 125440.0 * c.m / 2000.0 if c.n == 4 else None
+    traffic = 121344.0 * c.m / 2000.0 if c.n == 4 else None
     active_sms = c.n + 1
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
