@@ -367,7 +367,7 @@ typedef struct stab_sparse_info {
 /* Creates a sparse context for n qubits (1 <= n <= STAB_SPARSE_MAX_QUBITS)
  * holding up to max_terms terms (1 <= max_terms <= 2^30); the buffers start
  * small and grow by 8x when a step would overflow them (the step is then
- * re-run), up to max_terms.  Device memory is about 64 bytes per term of
+ * re-run), up to max_terms.  Device memory is about 72 bytes per term of
  * capacity.  opts as for stab_create (kernel and fuse apply to the dense
  * path it switches to).
  * Errors: STAB_E_RANGE (n, max_terms), STAB_E_INVAL, STAB_E_CUDA, STAB_E_NOMEM. */

@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_cliff_tab(uint64_t *keys, dou
 __global__ void __launch_bounds__(kSpThreads) k_sp_insert(const uint64_t *keys,
                                                            const int64_t *counts,
                                                            const int32_t *flags, int step, int n,
-                                                           int q, int axis, int32_t *hpos,
-                                                           uint64_t *hkey, int log_h,
+                                                           int q, int axis, SpSlot *table,
+                                                           int log_h,
                                                            int32_t *slot_of, int32_t *err) {
     if (sp_stopped_before(flags, step)) return;
     const int64_t count = counts[step];
@@ -280,8 +280,8 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_insert(const uint64_t *keys,
         // bound only guards against a corrupted table
         bool ok = false;
         for (uint32_t probe = 0; probe <= mask; ++probe) {
-            if (atomicCAS(&hpos[s], -1, (int32_t)i) == -1) {
-                hkey[s] = k;
+            if (atomicCAS(&table[s].pos, -1, (int32_t)i) == -1) {
+                table[s].key = k;
                 slot_of[i] = (int32_t)s;
                 ok = true;
                 break;
@@ -295,14 +295,15 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_insert(const uint64_t *keys,
     }
 }
 
-__device__ __forceinline__ int32_t sp_lookup(uint64_t k, const int32_t *hpos,
-                                             const uint64_t *hkey, int log_h) {
+__device__ __forceinline__ int32_t sp_lookup(uint64_t k, const SpSlot *table, int log_h) {
     const uint32_t mask = (1u << log_h) - 1u;
     uint32_t s = sp_hash(k, log_h);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const int32_t p = hpos[s];
+        // one 16-byte load: key and position of the slot
+        const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(table + s);
+        const int32_t p = (int32_t)(uint32_t)e.y;
         if (p < 0) return -1;
-        if (hkey[s] == k) return p;
+        if (e.x == k) return p;
         s = (s + 1u) & mask;
     }
     return -1;
@@ -314,8 +315,7 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_count(const uint64_t *keys,
                                                           const int32_t *flags, int step, int n,
                                                           int q, int axis, const double *thetas,
                                                           int param, int inverse,
-                                                          const int32_t *hpos,
-                                                          const uint64_t *hkey, int log_h,
+                                                          const SpSlot *table, int log_h,
                                                           int32_t *partner, int64_t *blk) {
     __shared__ int64_t sh[32];
     if (sp_stopped_before(flags, step)) return;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_count(const uint64_t *keys,
         const uint32_t L = sp_letter(k, n, q);
         int32_t p = -1;
         if (L == u || L == v) {
-            p = sp_lookup(sp_with_letter(k, n, q, L == u ? v : u), hpos, hkey, log_h);
+            p = sp_lookup(sp_with_letter(k, n, q, L == u ? v : u), table, log_h);
             partner[i] = p;
         }
         uint64_t k0, k1;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(1024) k_sp_scan(int64_t *blk, int nblk, int64_
 __global__ void __launch_bounds__(kSpThreads) k_sp_write(
     const uint64_t *keys, const double *vals, const int64_t *counts, const int32_t *flags,
     int step, int n, int q, int axis, const double *thetas, int param, int inverse,
-    int32_t *hpos, const int32_t *slot_of, const int32_t *partner, const int64_t *blk,
+    SpSlot *table, const int32_t *slot_of, const int32_t *partner, const int64_t *blk,
     uint64_t *keys_out, double *vals_out) {
     __shared__ int64_t sh[32];
     if (sp_stopped_before(flags, step)) return;
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_write(
             if (L == u || L == v) {
                 p = partner[i];
                 const int32_t slot = slot_of[i];
-                if (slot >= 0) hpos[slot] = -1;
+                if (slot >= 0) table[slot].pos = -1;
             }
             e = sp_images(k, vals[i], p, vals, n, q, axis, c, s, k0, v0, k1, v1);
         }
@@ -491,14 +491,14 @@ cudaError_t launch_sp_cliff_tab(uint64_t *keys, double *vals, int64_t *counts,
 cudaError_t launch_sp_rotation(const SpRotArgs &a, cudaStream_t st) {
     const int grid = sp_grid(a.bound);
     k_sp_insert<<<grid, kSpThreads, 0, st>>>(a.keys, a.counts, a.flags, a.step, a.n, a.q,
-                                              a.axis, a.hpos, a.hkey, a.log_h, a.slot_of,
+                                              a.axis, a.table, a.log_h, a.slot_of,
                                               a.err);
     k_sp_count<<<grid, kSpThreads, 0, st>>>(a.keys, a.vals, a.counts, a.flags, a.step, a.n, a.q,
-                                             a.axis, a.thetas, a.param, a.inverse, a.hpos,
-                                             a.hkey, a.log_h, a.partner, a.blk);
+                                             a.axis, a.thetas, a.param, a.inverse, a.table,
+                                             a.log_h, a.partner, a.blk);
     k_sp_scan<<<1, 1024, 0, st>>>(a.blk, grid, a.counts, a.flags, a.step, a.cap, a.threshold);
     k_sp_write<<<grid, kSpThreads, 0, st>>>(a.keys, a.vals, a.counts, a.flags, a.step, a.n, a.q,
-                                             a.axis, a.thetas, a.param, a.inverse, a.hpos,
+                                             a.axis, a.thetas, a.param, a.inverse, a.table,
                                              a.slot_of, a.partner, a.blk, a.keys_out,
                                              a.vals_out);
     return cudaGetLastError();

@@ -190,6 +190,12 @@ struct SpTab {                           // tableau entry: image of X_q or Z_q, 
     uint32_t pad;
 };
 
+struct SpSlot {                          // a table slot: key and list position (-1 free)
+    uint64_t key;
+    int32_t pos;
+    int32_t pad;
+};
+
 struct SpRotArgs {
     const uint64_t *keys;                // input list (keys z | x << n, coefficients)
     const double *vals;
@@ -200,8 +206,7 @@ struct SpRotArgs {
     int32_t step, n, q, axis;            // axis 0/1/2 = R_x/R_y/R_z
     const double *thetas;
     int32_t param, inverse;
-    int32_t *hpos;                       // table: position of the term in a slot, -1 free
-    uint64_t *hkey;                      // table: key in a slot
+    SpSlot *table;                       // open-addressing table (one 16-byte slot per probe)
     int32_t log_h;
     int32_t *slot_of;                    // per term: its table slot
     int32_t *partner;                    // per term: position of its partner, -1 absent

@@ -147,7 +147,7 @@ struct stab_sparse {
     std::vector<double> thetas_h;
     int64_t n_params = 0;
     SpPlan fwd, bwd;
-    SpBuf thetas, g_fwd, g_bwd, keys[2], vals[2], hpos, hkey, slot_of, partner, blk, counts,
+    SpBuf thetas, g_fwd, g_bwd, keys[2], vals[2], table, slot_of, partner, blk, counts,
         flags, partial, scal, dterms, t_fwd, t_bwd, runs;
     int log_h = 0;
     void *pinned = nullptr;
@@ -221,9 +221,8 @@ struct stab_sparse {
             SRC(dalloc(partner, (size_t)c * 4));
             int lh = 1;
             while ((1ll << lh) < 2 * c) ++lh;
-            SRC(dalloc(hpos, ((size_t)1 << lh) * 4));
-            SRC(dalloc(hkey, ((size_t)1 << lh) * 8));
-            SCK(cudaMemsetAsync(hpos.p, 0xff, ((size_t)1 << lh) * 4, st));
+            SRC(dalloc(table, ((size_t)1 << lh) * sizeof(SpSlot)));
+            SCK(cudaMemsetAsync(table.p, 0xff, ((size_t)1 << lh) * sizeof(SpSlot), st));
             log_h = lh;
             cap = c;
         }
@@ -232,8 +231,8 @@ struct stab_sparse {
 
     ~stab_sparse() {
         if (st) cudaStreamSynchronize(st);
-        for (SpBuf *b : {&thetas, &g_fwd, &g_bwd, &keys[0], &keys[1], &vals[0], &vals[1], &hpos,
-                         &hkey, &slot_of, &partner, &blk, &counts, &flags, &partial, &scal,
+        for (SpBuf *b : {&thetas, &g_fwd, &g_bwd, &keys[0], &keys[1], &vals[0], &vals[1], &table,
+                         &slot_of, &partner, &blk, &counts, &flags, &partial, &scal,
                          &dterms, &t_fwd, &t_bwd, &runs})
             dfree(*b);
         if (pinned) cudaFreeHost(pinned);
@@ -256,7 +255,7 @@ int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, const SpBuf 
     SRC(s->reserve(std::min(s->max_terms, std::max(kSpMinCap, 4 * n0)), 0, 0));
     if (n0 > s->cap) return STAB_E_RANGE;
     if (s->table_dirty) {
-        SCK(cudaMemsetAsync(s->hpos.p, 0xff, ((size_t)1 << s->log_h) * 4, s->st));
+        SCK(cudaMemsetAsync(s->table.p, 0xff, ((size_t)1 << s->log_h) * sizeof(SpSlot), s->st));
         s->table_dirty = false;
     }
     SRC(s->dalloc(s->counts, (size_t)(S + 1) * 8));
@@ -314,8 +313,7 @@ int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, const SpBuf 
                 a.thetas = (const double *)s->thetas.p;
                 a.param = st.param;
                 a.inverse = backward ? 1 : 0;
-                a.hpos = (int32_t *)s->hpos.p;
-                a.hkey = (uint64_t *)s->hkey.p;
+                a.table = (SpSlot *)s->table.p;
                 a.log_h = s->log_h;
                 a.slot_of = (int32_t *)s->slot_of.p;
                 a.partner = (int32_t *)s->partner.p;
