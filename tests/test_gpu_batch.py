@@ -92,3 +92,37 @@ def test_batch_rejects_too_many_qubits(stab):
     c = W.layered_ansatz(9, 20, seed=1)
     with pytest.raises(StabError):
         stab.Batch([W.BatchItem(c, "generators")])
+
+
+def test_batch_c3_full_size_sampled(stab):
+    """The 4,096-circuit uneven batch exactly as the bench times it (one
+    persistent launch, autotuned grid): a seeded sample of its items across
+    every n present, those whose single vector the oracle propagates quickly
+    (4^n m small), against the oracle -- one generator per generator item;
+    every expectation is finite."""
+    items = W.uneven_batch(4096, seed=1003)
+    b = stab.Batch(items)
+    b.run()
+    ex = b.expectations()
+    rng = np.random.default_rng(5)
+    by_n = {}
+    for k in rng.permutation(len(items)):
+        c = items[k].circuit
+        if 4 ** c.n * c.m <= 6e7 and len(by_n.setdefault(c.n, [])) < 2:
+            by_n[c.n].append(int(k))
+    assert len(by_n) >= 6, sorted(by_n)
+    for n, ks in sorted(by_n.items()):
+        for k in ks:
+            it = items[k]
+            c = it.circuit
+            if it.kind == "expect":
+                ref = oracle.expect(c.n, c.gates, c.thetas, it.observable)
+                assert abs(ex[k] - ref) <= 1e-10 * l1(it.observable), (k, n)
+            else:
+                g = int(rng.integers(c.n))
+                ref = oracle.forward(c.n, c.gates, c.thetas, oracle.generator(c.n, g))
+                got = layout.lib_to_paper(c.n, b.generators(k)[g])
+                assert np.abs(got - ref).max() <= 1e-10, (k, n, g)
+    kinds = np.array([it.kind == "expect" for it in items])
+    assert np.all(np.isfinite(ex[kinds]))
+    b.close()

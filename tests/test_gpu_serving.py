@@ -106,3 +106,34 @@ def test_oversized_and_malformed_requests_fail_alone(stab):
     assert r_good["status"] == 0
     g_ref = oracle.psr_grad(4, good.gates, good.thetas, W.obs_chain(4))
     assert np.abs(r_good["grads"] - g_ref).max() <= 1e-12 * l1(W.obs_chain(4))
+
+
+def test_serving_trace_c5_sampled(stab):
+    """The serving workload's own trace (Poisson 2,000/s, n 4..12, depth
+    log-uniform 100..60,000, seed 1005): its first 48 requests through the
+    server as the bench submits them; those the oracle checks quickly
+    (4^n m small) against the oracle -- <O>, and for gradient requests
+    sampled slots by the parameter shift."""
+    trace = W.serving_trace(48, seed=1005)
+    srv = stab.Server(max_active=64)
+    ids = [srv.submit(r.circuit, r.kind, r.observable) for r in trace]
+    res = [srv.wait(i, timeout_s=600) for i in ids]
+    srv.close()
+    rng = np.random.default_rng(9)
+    checked = 0
+    for r, out in zip(trace, res):
+        assert out["status"] == 0
+        assert np.isfinite(out["expect"])
+        c, obs = r.circuit, r.observable
+        if 4 ** c.n * c.m > 3e7:
+            continue
+        assert abs(out["expect"] - oracle.expect(c.n, c.gates, c.thetas, obs)) <= 1e-10 * l1(obs)
+        if r.kind == "grad" and c.n_params:
+            rot = [i for i, g in enumerate(c.gates) if int(g["op"]) in W.ROTATIONS]
+            for gi in rng.choice(rot, size=min(3, len(rot)), replace=False):
+                slot = int(c.gates[gi]["param"])
+                # each slot is read by one gate in this ansatz: PSR of that gate
+                want = oracle.psr_grad_gate(c.n, c.gates, c.thetas, obs, int(gi))
+                assert abs(out["grads"][slot] - want) <= 1e-10 * l1(obs)
+        checked += 1
+    assert checked >= 6
