@@ -247,3 +247,27 @@ def test_clifford_runs_gate_by_gate_and_tableau(S, n, run):
             wk, wv = oracle.sparse_generator(n, gates, th, k)
             assert_terms_match(n, terms, wk, wv, 1e-12)
     sp.close()
+
+
+def test_bench_config_n32(S):
+    """The bench's term-list workload (n = 32, 20,000 gates, 28 rotations): the
+    call succeeds with the order in the millions, repeats bit for bit, and its
+    order history is bounded by doubling per rotation; the same circuit family
+    with 12 rotations against the sparse oracle."""
+    n, m = 32, 20000
+    obs = W.obs_chain(n)
+    c = W.clifford_plus_rotations(n, m, 28, seed=1006)
+    sp = S.Sparse(n, max_terms=1 << 26)
+    sp.load_circuit(c.gates, c.thetas)
+    v1, info = sp.expect(obs)
+    v2, _ = sp.expect(obs)
+    assert np.isfinite(v1) and v1 == v2
+    assert info["order_max"] > 1_000_000
+    h = sp.order_history()
+    assert len(h) == info["steps"] and h.max() == info["order_max"]
+    assert h.max() <= len(obs) * 2 ** 28
+    c12 = W.clifford_plus_rotations(n, m, 12, seed=1006)
+    sp.load_circuit(c12.gates, c12.thetas)
+    v12, _ = sp.expect(obs)
+    assert abs(v12 - oracle.sparse_expect(n, c12.gates, c12.thetas, obs)) <= 1e-12 * l1(obs)
+    sp.close()
