@@ -748,6 +748,33 @@ def run_sparse(args):
         "clocks": clk,
     }
     sp.close()
+    # where both representations apply (n = 12): term list (switching to the
+    # dense vector past its threshold) against the dense path, same circuits
+    cmp = []
+    for n_rot in (8, 16, 24):
+        c12 = W.clifford_plus_rotations(12, 4000, n_rot, seed=1016)
+        o12 = W.obs_chain(12)
+        sp12 = stab.Sparse(12, max_terms=1 << 22)
+        sp12.load_circuit(c12.gates, c12.thetas)
+        d12 = stab.Stab(12)
+        d12.load_circuit(c12.gates, c12.thetas)
+        for _ in range(3):
+            vs, inf12 = sp12.expect(o12)
+            vd = d12.expect(o12)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            vs, inf12 = sp12.expect(o12)
+        ts = (time.perf_counter() - t0) / 5
+        t0 = time.perf_counter()
+        for _ in range(5):
+            vd = d12.expect(o12)
+        td = (time.perf_counter() - t0) / 5
+        cmp.append({"n": 12, "gates": 4000, "rotations": n_rot, "sparse_ms": ts * 1e3,
+                    "dense_ms": td * 1e3, "order_max": inf12["order_max"],
+                    "dense_gates": inf12["dense_gates"], "abs_diff": abs(vs - vd)})
+        sp12.close()
+        d12.close()
+    line["sparse_vs_dense_n12"] = cmp
     if not args.no_cpu_baseline:
         # oracle on the same circuit with fewer rotations (a bounded sample)
         k = 16
