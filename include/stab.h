@@ -273,8 +273,14 @@ typedef struct stab_server_opts {
     int32_t max_active;    /* requests admitted at once (0 = 64) */
     int64_t hbm_budget;    /* bytes of request state admitted at once (0 = 32 GiB) */
     int32_t planners;      /* host threads that plan and launch requests (0 = 4) */
-    int32_t reserved;
+    int32_t policy;        /* stab_serve_policy: which queued request is admitted next */
 } stab_server_opts;
+
+/* Admission order.  FIFO: the oldest queued request.  SHORTEST: the queued
+ * request with the least estimated work (gates x 4^n, three times that for a
+ * gradient), oldest first among equals; small requests then wait less, large
+ * ones may wait until the queue drains. */
+enum stab_serve_policy { STAB_SERVE_FIFO = 0, STAB_SERVE_SHORTEST = 1 };
 
 enum stab_request_kind { STAB_REQ_EXPECT = 0, STAB_REQ_GRAD = 1 };
 

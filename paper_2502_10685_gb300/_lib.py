@@ -57,7 +57,7 @@ class StabBatchItem(ctypes.Structure):
 class StabServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("planners", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("policy", ctypes.c_int32)]
 
 
 class StabRequest(ctypes.Structure):

@@ -1,8 +1,9 @@
 // server.cpp -- stab_server_*: continuous batching of expectation and gradient
 // requests.
 //
-// Submitted requests wait in a FIFO queue.  Planner threads admit the head of
-// the queue whenever a slot and enough HBM budget are free, plan and upload
+// Submitted requests wait in a queue.  Planner threads admit the next one
+// (the oldest, or with STAB_SERVE_SHORTEST the one with the least estimated
+// work) whenever a slot and enough HBM budget are free, plan and upload
 // it on a pooled context (each context has its own streams and keeps its
 // device vectors between requests) and queue its kernels asynchronously;
 // requests therefore join while others are running and their kernels overlap
@@ -44,6 +45,7 @@ struct Req {
     std::vector<double> thetas;
     std::vector<stab_term> terms;
     int64_t footprint = 0;
+    double work = 0.0;          // estimated work: gates x 4^n (x3 for a gradient)
     stab_result res{};
     std::vector<double> grads;
     bool done = false;
@@ -164,14 +166,25 @@ int launch_request(Req *r) {
     return STAB_OK;
 }
 
+// Position in the queue of the request to admit next (caller holds s->mu).
+size_t next_request_locked(const stab_server *s) {
+    if (s->opts.policy != STAB_SERVE_SHORTEST) return 0;
+    size_t best = 0;
+    for (size_t i = 1; i < s->queue.size(); ++i)
+        if (s->queue[i]->work < s->queue[best]->work) best = i;
+    return best;
+}
+
 void planner_main(stab_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
+        size_t pick = 0;
         s->cv_queue.wait(lk, [&] {
             if (s->stop && s->queue.empty()) return true;
             if (s->queue.empty()) return false;
-            Req *h = s->queue.front();
+            pick = next_request_locked(s);
+            Req *h = s->queue[pick];
             if (h->footprint > s->opts.hbm_budget) return true;   // never fits
             return s->n_active < s->opts.max_active &&
                    s->bytes_in_use + h->footprint <= s->opts.hbm_budget;
@@ -180,8 +193,8 @@ void planner_main(stab_server *s) {
             if (s->stop) break;
             continue;
         }
-        Req *r = s->queue.front();
-        s->queue.pop_front();
+        Req *r = s->queue[pick];
+        s->queue.erase(s->queue.begin() + (std::ptrdiff_t)pick);
         if (r->footprint > s->opts.hbm_budget) {
             complete_locked(s, r, STAB_E_NOMEM);
             s->cv_done.notify_all();
@@ -281,6 +294,10 @@ int stab_server_create(const stab_server_opts *opts, stab_server **out) {
     if (s->opts.max_active <= 0) s->opts.max_active = 64;
     if (s->opts.hbm_budget <= 0) s->opts.hbm_budget = (int64_t)32 << 30;
     if (s->opts.planners <= 0) s->opts.planners = 4;
+    if (s->opts.policy != STAB_SERVE_FIFO && s->opts.policy != STAB_SERVE_SHORTEST) {
+        delete s;
+        return STAB_E_INVAL;
+    }
     int dev = s->opts.device;
     cudaError_t e = cudaSuccess;
     if (dev < 0) e = cudaGetDevice(&dev);
@@ -310,6 +327,9 @@ int stab_server_submit(stab_server *s, const stab_request *req, int64_t *id) {
     r->hdr.thetas = r->thetas.empty() ? nullptr : r->thetas.data();
     r->hdr.obs = r->terms.empty() ? nullptr : r->terms.data();
     r->footprint = stab_request_footprint(req);
+    if (req->n >= 1 && req->n <= STAB_MAX_QUBITS)
+        r->work = (double)(req->m > 0 ? req->m : 1) * (double)(1ull << (2 * req->n)) *
+                  (req->kind == STAB_REQ_GRAD ? 3.0 : 1.0);
     r->res.n_params = (int32_t)req->n_params;
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;

@@ -496,13 +496,16 @@ class Server:
     ``done_s``.
     """
 
+    POLICIES = {"fifo": 0, "shortest": 1}
+
     def __init__(self, device: int = 0, max_active: int = 0, hbm_budget: int = 0,
-                 planners: int = 0):
+                 planners: int = 0, policy: str = "fifo"):
         o = StabServerOpts()
         o.device = device
         o.max_active = max_active
         o.hbm_budget = hbm_budget
         o.planners = planners
+        o.policy = self.POLICIES[policy]
         h = ctypes.c_void_p()
         check(_lib.load().stab_server_create(ctypes.byref(o), ctypes.byref(h)),
               "stab_server_create")

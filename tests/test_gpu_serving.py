@@ -137,3 +137,28 @@ def test_serving_trace_c5_sampled(stab):
                 assert abs(out["grads"][slot] - want) <= 1e-10 * l1(obs)
         checked += 1
     assert checked >= 6
+
+
+@pytest.mark.parametrize("policy", ["fifo", "shortest"])
+def test_admission_order(stab, policy):
+    """One slot: while a blocker runs, a large request and six small ones
+    queue.  FIFO admits the large one first; shortest-work-first admits the
+    small ones first.  Results are the same under either order."""
+    blocker = W.layered_ansatz(9, 1500, seed=1)
+    large = W.layered_ansatz(8, 3000, seed=2)
+    small = [W.layered_ansatz(3, 40 + k, seed=10 + k) for k in range(6)]
+    srv = stab.Server(max_active=1, policy=policy)
+    ib = srv.submit(blocker, "expect", W.obs_chain(9))
+    il = srv.submit(large, "expect", W.obs_chain(8))
+    isml = [srv.submit(c, "expect", W.obs_chain(3)) for c in small]
+    rb = srv.wait(ib, timeout_s=300)
+    rl = srv.wait(il, timeout_s=300)
+    rs = [srv.wait(i, timeout_s=300) for i in isml]
+    srv.close()
+    assert rb["status"] == 0 and rl["status"] == 0 and all(r["status"] == 0 for r in rs)
+    if policy == "fifo":
+        assert all(rl["done_s"] <= r["admit_s"] for r in rs)
+    else:
+        assert all(r["done_s"] <= rl["admit_s"] for r in rs)
+    for c, r in zip(small, rs):
+        assert abs(r["expect"] - oracle.expect(3, c.gates, c.thetas, W.obs_chain(3))) <= 1e-12 * l1(W.obs_chain(3))
