@@ -175,6 +175,59 @@ __global__ void __launch_bounds__(kThreads) k_stream_cliff(const double *__restr
     }
 }
 
+// Exponent c (mod 4) of P(a) P(b) = i^c P(a xor b) for Hermitian Pauli strings
+// given by x / z masks: per qubit, with a = Y: z_b - x_b; a = X: z_b (2 x_b - 1);
+// a = Z: x_b (1 - 2 z_b) (the phase function of Aaronson and Gottesman's
+// tableau algorithm), summed with population counts.
+__device__ __forceinline__ uint32_t tab_mul_phase(uint32_t ax, uint32_t az, uint32_t bx,
+                                                  uint32_t bz) {
+    const uint32_t A = ax & az, B = ax & ~az, C = ~ax & az;
+    const uint32_t plus = (A & bz & ~bx) | (B & bz & bx) | (C & bx & ~bz);
+    const uint32_t minus = (A & bx & ~bz) | (B & bz & ~bx) | (C & bx & bz);
+    return (uint32_t)(__popc(plus) - __popc(minus)) & 3u;
+}
+
+// A Clifford run as one signed gather: dst[i] = sign * src[j] with
+// V P_i V^dagger = sign P_j for the map V whose tableau is given (the run's
+// inverse for a forward application).  V P(x, z) V^dagger is i^{|x & z|} times
+// the product of the generator images (X_q images for x, Z_q images for z, q
+// ascending, Y = i X Z), each factor adding its phase and sign.
+__global__ void __launch_bounds__(kThreads) k_stream_tab(const double *__restrict__ src,
+                                                         double *__restrict__ dst, int n,
+                                                         int n_vec, const DevTab *tab) {
+    __shared__ uint32_t tx[24], tz[24], ts[24];
+    if (threadIdx.x < 2 * n) {
+        tx[threadIdx.x] = tab->x[threadIdx.x];
+        tz[threadIdx.x] = tab->z[threadIdx.x];
+        ts[threadIdx.x] = ((tab->neg >> threadIdx.x) & 1u) ? 2u : 0u;
+    }
+    __syncthreads();
+    const uint64_t E = 1ull << (2 * n);
+    const uint64_t total = E * (uint64_t)n_vec;
+    const uint32_t zmask = (1u << n) - 1u;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = t >> (2 * n);
+        const uint32_t i = (uint32_t)(t & (E - 1));
+        const uint32_t x = i >> n, z = i & zmask;
+        uint32_t rx = 0, rz = 0, e = (uint32_t)__popc(x & z);
+        for (int q = 0; q < n; ++q) {
+            if ((x >> q) & 1u) {
+                e += tab_mul_phase(rx, rz, tx[q], tz[q]) + ts[q];
+                rx ^= tx[q];
+                rz ^= tz[q];
+            }
+            if ((z >> q) & 1u) {
+                e += tab_mul_phase(rx, rz, tx[n + q], tz[n + q]) + ts[n + q];
+                rx ^= tx[n + q];
+                rz ^= tz[n + q];
+            }
+        }
+        const double val = src[v * E + (((uint64_t)rx << n) | rz)];
+        dst[t] = (e & 2u) ? -val : val;
+    }
+}
+
 __device__ __forceinline__ uint64_t deposit_runs(uint64_t v, const BitRuns &r) {
     uint64_t out = 0;
     for (int k = 0; k < r.n; ++k)
@@ -322,6 +375,13 @@ cudaError_t launch_stream_wire(double *vec, int n, int n_vec, const DevPass &p, 
     const uint64_t total = (1ull << (2 * n - 2)) * (uint64_t)n_vec;
     k_stream_wire<<<grid_for(total, kThreads), kThreads, 0, st>>>(vec, n, n_vec, p, ops, maps,
                                                                    inverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_tab(const double *src, double *dst, int n, int n_vec,
+                              const DevTab *tab, cudaStream_t st) {
+    const uint64_t total = (1ull << (2 * n)) * (uint64_t)n_vec;
+    k_stream_tab<<<grid_for(total, kThreads), kThreads, 0, st>>>(src, dst, n, n_vec, tab);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include "launch.h"
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <map>
 
@@ -188,8 +189,63 @@ struct Emitter {
 
 }  // namespace
 
+// Forward conjugation g P g^dagger of one Clifford gate on a string (x, z
+// masks), flipping `neg` with the sign: H swaps x and z on the wire (Y -> -Y),
+// S: z ^= x (Y -> -X), S^dagger: z ^= x (X -> -Y), X: sign z, Y: sign x ^ z,
+// Z: sign x; CX(c, t): x_t ^= x_c, z_c ^= z_t, minus iff x_c z_t (x_t == z_c);
+// CZ(a, b): z_a ^= x_b, z_b ^= x_a, minus iff x_a x_b (z_a != z_b).
+static void conj_clifford(uint32_t &x, uint32_t &z, uint32_t &neg, uint8_t op, int a, int b) {
+    const uint32_t xa = (x >> a) & 1u, za = (z >> a) & 1u;
+    const uint32_t ma = 1u << a;
+    switch (op) {
+    case STAB_H:
+        neg ^= xa & za;
+        x = (x & ~ma) | (za << a);
+        z = (z & ~ma) | (xa << a);
+        break;
+    case STAB_S: neg ^= xa & za; z ^= xa << a; break;
+    case STAB_SDG: neg ^= xa & (za ^ 1u); z ^= xa << a; break;
+    case STAB_X: neg ^= za; break;
+    case STAB_Y: neg ^= xa ^ za; break;
+    case STAB_Z: neg ^= xa; break;
+    case STAB_CX: {
+        const uint32_t xt = (x >> b) & 1u, zt = (z >> b) & 1u;
+        neg ^= xa & zt & ((xt ^ za) ^ 1u);
+        x ^= xa << b;
+        z ^= zt << a;
+        break;
+    }
+    case STAB_CZ: {
+        const uint32_t xb = (x >> b) & 1u, zb = (z >> b) & 1u;
+        neg ^= xa & xb & (za ^ zb);
+        z ^= xb << a;
+        z ^= xa << b;
+        break;
+    }
+    default: break;
+    }
+}
+
+void clifford_tableau(int n, const stab_gate *gates, int64_t i0, int64_t i1, bool inverse,
+                      DevTab *out) {
+    std::memset(out, 0, sizeof(*out));
+    for (int j = 0; j < 2 * n; ++j) {
+        uint32_t x = j < n ? (1u << j) : 0u, z = j < n ? 0u : (1u << (j - n)), neg = 0;
+        for (int64_t k = 0; k < i1 - i0; ++k) {
+            const stab_gate &g = gates[inverse ? i1 - 1 - k : i0 + k];
+            uint8_t op = g.op;
+            if (inverse && op == STAB_S) op = STAB_SDG;
+            else if (inverse && op == STAB_SDG) op = STAB_S;
+            conj_clifford(x, z, neg, op, g.q0, g.q1);
+        }
+        out->x[j] = x;
+        out->z[j] = z;
+        out->neg |= (neg & 1u) << j;
+    }
+}
+
 void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
-                HostPlan *out) {
+                HostPlan *out, bool tableaus) {
     HostPlan &P = *out;
     P = HostPlan();
     P.n_params = n_params;
@@ -224,36 +280,86 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
 
     P.passes.reserve((size_t)m + 1);
     P.ops.reserve((size_t)m + 1);
-    Emitter em{&P, mode, &rot_ordinal};
-    int64_t i = 0;
     std::vector<std::vector<int64_t>> runs((size_t)n);
-    while (i < m) {
-        int64_t j = i;
-        if (is_two_qubit(gates[i].op)) {
-            while (j < m && is_two_qubit(gates[j].op)) ++j;
-            if (mode == PLAN_PLAIN || mode == PLAN_PLAIN_ROWS) {
-                for (int64_t k = i; k < j; ++k) em.emit_cliff(gates, k, k + 1);
+    // Gates [i0, i1) as U_k / V_k passes (Sec. III-A dividing) into `em`.
+    auto emit_range = [&](Emitter &em, int64_t i0, int64_t i1) {
+        int64_t i = i0;
+        while (i < i1) {
+            int64_t j = i;
+            if (is_two_qubit(gates[i].op)) {
+                while (j < i1 && is_two_qubit(gates[j].op)) ++j;
+                if (mode == PLAN_PLAIN || mode == PLAN_PLAIN_ROWS) {
+                    for (int64_t k = i; k < j; ++k) em.emit_cliff(gates, k, k + 1);
+                } else {
+                    // a P_CLIFF pass holds at most 65535 ops
+                    for (int64_t k = i; k < j; k += 65535)
+                        em.emit_cliff(gates, k, std::min(j, k + 65535));
+                }
             } else {
-                // a P_CLIFF pass holds at most 65535 ops
-                for (int64_t k = i; k < j; k += 65535) em.emit_cliff(gates, k, std::min(j, k + 65535));
-            }
-        } else {
-            while (j < m && !is_two_qubit(gates[j].op)) ++j;
-            if (mode == PLAN_PLAIN || mode == PLAN_PLAIN_ROWS) {
-                for (int64_t k = i; k < j; ++k) em.emit_wire(gates, gates[k].q0, &k, 1);
-            } else {
-                for (auto &r : runs) r.clear();
-                for (int64_t k = i; k < j; ++k) runs[gates[k].q0].push_back(k);
-                for (int q = 0; q < n; ++q) {
-                    if (runs[q].empty()) continue;
-                    // a P_WIRE pass holds at most 65535 ops; cut longer unfused runs
-                    const auto &r = runs[q];
-                    for (size_t k = 0; k < r.size(); k += 16384)
-                        em.emit_wire(gates, q, r.data() + k, std::min(r.size() - k, (size_t)16384));
+                while (j < i1 && !is_two_qubit(gates[j].op)) ++j;
+                if (mode == PLAN_PLAIN || mode == PLAN_PLAIN_ROWS) {
+                    for (int64_t k = i; k < j; ++k) em.emit_wire(gates, gates[k].q0, &k, 1);
+                } else {
+                    for (auto &r : runs) r.clear();
+                    for (int64_t k = i; k < j; ++k) runs[gates[k].q0].push_back(k);
+                    for (int q = 0; q < n; ++q) {
+                        if (runs[q].empty()) continue;
+                        // a P_WIRE pass holds at most 65535 ops; cut longer unfused runs
+                        const auto &r = runs[q];
+                        for (size_t k = 0; k < r.size(); k += 16384)
+                            em.emit_wire(gates, q, r.data() + k,
+                                         std::min(r.size() - k, (size_t)16384));
+                    }
                 }
             }
+            i = j;
         }
-        i = j;
+    };
+    Emitter em{&P, mode, &rot_ordinal};
+    const bool tabs = tableaus && n <= 12 && mode != PLAN_PLAIN && mode != PLAN_PLAIN_ROWS;
+    if (!tabs) {
+        emit_range(em, 0, m);
+        return;
+    }
+    // A run of Clifford gates that would take kTabMinPasses or more passes
+    // becomes one P_TAB pass: a signed gather through the run's tableau.
+    constexpr size_t kTabMinPasses = 4;
+    HostPlan scratch;
+    scratch.mode = mode;
+    int64_t i = 0;
+    while (i < m) {
+        int64_t j = i;
+        while (j < m && !is_rotation(gates[j].op)) ++j;   // Clifford run [i, j)
+        if (j - i >= 8) {
+            scratch.passes.clear();
+            scratch.ops.clear();
+            Emitter probe{&scratch, mode, &rot_ordinal};
+            emit_range(probe, i, j);
+            if (scratch.passes.size() >= kTabMinPasses) {
+                DevPass p{};
+                p.type = P_TAB;
+                p.first = (uint32_t)(P.tabs.size() / 2);
+                p.n_ops = 0;
+                P.tabs.resize(P.tabs.size() + 2);
+                clifford_tableau(n, gates, i, j, true, &P.tabs[P.tabs.size() - 2]);
+                clifford_tableau(n, gates, i, j, false, &P.tabs[P.tabs.size() - 1]);
+                P.passes.push_back(p);
+                i = j;
+                continue;
+            }
+        }
+        // the Clifford run (short) and the rotation after it, as usual
+        const int64_t e = j < m ? j + 1 : m;
+        int64_t k = e;
+        // extend over further short runs so ordinary passes still group
+        while (k < m) {
+            int64_t r = k;
+            while (r < m && !is_rotation(gates[r].op)) ++r;
+            if (r - k >= 8) break;
+            k = r < m ? r + 1 : m;
+        }
+        emit_range(em, i, k);
+        i = k;
     }
 }
 

@@ -39,6 +39,7 @@ struct HostPlan {
     int32_t n_rot = 0;
     int64_t n_params = 0;
     PlanMode mode = PLAN_FUSED;
+    std::vector<DevTab> tabs;            // P_TAB passes (two per pass)
 };
 
 // Returns STAB_OK or an error code; msg receives a description on error.
@@ -46,8 +47,15 @@ int validate_gates(int n, const stab_gate *gates, int64_t m, int64_t n_params, s
 int validate_thetas(const double *thetas, int64_t n_params);
 
 // Builds the pass list.  gates must be valid.
+// tableaus: long Clifford runs become P_TAB passes (streamed plans; the
+// resident instruction streams and the batch kernel do not read them).
 void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
-                HostPlan *out);
+                HostPlan *out, bool tableaus = false);
+
+// Tableau of the Clifford gates [i0, i1) applied in order (inverse: the
+// inverse map, the inverse gates in reverse order).
+void clifford_tableau(int n, const stab_gate *gates, int64_t i0, int64_t i1, bool inverse,
+                      DevTab *out);
 
 // Instruction stream of a plan for the resident kernels (see stab_internal.h):
 // forward (backward = false) or for the inverse circuit (backward = true).

@@ -199,12 +199,13 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     const size_t b_raw = align256(H.raw.size() * sizeof(RawGate));
     const size_t b_pptr = align256(H.param_ptr.size() * sizeof(int32_t));
     const size_t b_prot = align256(H.param_rot.size() * sizeof(int32_t));
+    const size_t b_tabs = align256(H.tabs.size() * sizeof(DevTab));
     const size_t b_sf = align256(P.sf.host.size() * sizeof(Rec));
     const size_t b_sfe = align256(P.sf.enc.size() * sizeof(int32_t));
     const size_t b_sb = align256(P.sb.host.size() * sizeof(Rec));
     const size_t b_sbe = align256(P.sb.enc.size() * sizeof(int32_t));
-    const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot + b_sf +
-                         b_sfe + b_sb + b_sbe;
+    const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot + b_tabs +
+                         b_sf + b_sfe + b_sb + b_sbe;
     RC(c->dalloc(P.buf, total, c->st));
     CK(cudaEventSynchronize(c->ev_stage));
     RC(c->host_stage(c->stage, c->stage_bytes, total));
@@ -224,6 +225,7 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     P.raw = (const RawGate *)put(H.raw.data(), H.raw.size() * sizeof(RawGate), b_raw);
     P.param_ptr = (const int32_t *)put(H.param_ptr.data(), H.param_ptr.size() * 4, b_pptr);
     P.param_rot = (const int32_t *)put(H.param_rot.data(), H.param_rot.size() * 4, b_prot);
+    P.prog.tabs = (const DevTab *)put(H.tabs.data(), H.tabs.size() * sizeof(DevTab), b_tabs);
     P.sf.dev = (Rec *)put(P.sf.host.data(), P.sf.host.size() * sizeof(Rec), b_sf);
     P.sf.enc_dev = (const int32_t *)put(P.sf.enc.data(), P.sf.enc.size() * 4, b_sfe);
     P.sb.dev = (Rec *)put(P.sb.host.data(), P.sb.host.size() * sizeof(Rec), b_sb);
@@ -456,6 +458,14 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
         }
         RC(flush());
         if (pending) RC(gather_now());
+        if (p.type == P_TAB) {
+            // a long Clifford run: one gather through its tableau
+            CK(launch_stream_tab(*cur, *alt, c->n, n_vec, P.prog.tabs + 2 * p.first + (inverse ? 1 : 0),
+                                 s));
+            std::swap(*cur, *alt);
+            c->launches++;
+            continue;
+        }
         pending = &p;
         if (!fuse_tiles) RC(gather_now());
     }
@@ -507,7 +517,7 @@ void reset_graphs(stab_ctx *c) {
 int ensure_grad_plan(stab_ctx *c) {
     if (!c->grad.built) {
         build_plan(c->n, c->gates.data(), (int64_t)c->gates.size(), c->n_params, PLAN_GRAD,
-                   &c->grad.host);
+                   &c->grad.host, !c->use_resident_adjoint());
         if (c->use_resident_adjoint()) make_streams(c->grad);
         else no_streams(c->grad);
         c->g_grad.reset();
@@ -663,7 +673,7 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
     c->grad.built = false;
     c->grad.encoded = false;
     reset_graphs(c);
-    build_plan(c->n, gates, m, n_params, c->fwd_mode(), &c->fwd.host);
+    build_plan(c->n, gates, m, n_params, c->fwd_mode(), &c->fwd.host, !c->use_resident());
     if (c->use_resident()) make_streams(c->fwd);
     else no_streams(c->fwd);
     RC(upload_thetas_host(c, thetas));
@@ -951,6 +961,14 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                 }
                 RC(flush());
                 if (pending) RC(gather_now());
+                if (p.type == P_TAB) {
+                    // the Clifford run backward: gather through the run's own tableau
+                    CK(launch_stream_tab(pair, alt, n, 2, c->grad.prog.tabs + 2 * p.first + 1,
+                                         gs));
+                    c->launches++;
+                    std::swap(pair, alt);
+                    continue;
+                }
                 pending = &p;
                 if (!tiles) RC(gather_now());
             }

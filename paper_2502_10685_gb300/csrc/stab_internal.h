@@ -20,7 +20,9 @@ enum OpKind : uint8_t {
     K_CZ = 4,    // CZ(q, q1)
 };
 
-enum PassType : uint8_t { P_WIRE = 0, P_CLIFF = 1 };
+// P_TAB: a long run of Clifford gates of any kind (streamed plans only),
+// applied as one signed gather through the run's tableau (DevTab).
+enum PassType : uint8_t { P_WIRE = 0, P_CLIFF = 1, P_TAB = 2 };
 
 // Rotation axes.  Within the 4-slot group (I, X, Y, Z) of one wire a rotation
 // about axis a mixes the pair (u, v) below as u' = c u - s v, v' = s u + c v
@@ -70,10 +72,24 @@ enum InitMode : int32_t {
     INIT_LOAD = 3,       // copy from a device vector
 };
 
+// Tableau of a Clifford map V on n <= 12 qubits: the images V X_q V^dagger
+// (entry q) and V Z_q V^dagger (entry n + q), each a signed string with x / z
+// masks; sign bit j of `neg` is entry j's sign.  A P_TAB pass (first = k)
+// refers to tabs[2k] = the run's inverse U^dagger (forward gathers) and
+// tabs[2k + 1] = the run U (inverse gathers).
+struct DevTab {         // 200 bytes
+    uint32_t x[24];
+    uint32_t z[24];
+    uint32_t neg;
+    uint32_t pad;
+};
+static_assert(sizeof(DevTab) == 200, "DevTab layout");
+
 struct Program {
     const DevPass *passes;
     const DevOp *ops;
     const DevMap3 *maps;
+    const DevTab *tabs;
     int32_t n_passes;
     int32_t n_ops;
 };

@@ -314,3 +314,39 @@ def test_density_matrix_against_oracle(stab, n):
     ref = oracle.density_matrix(n, c.gates, c.thetas)
     assert np.abs(got - ref).max() <= 1e-12
     assert abs(np.trace(rho) - 1) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [7, 8])
+def test_long_clifford_runs_through_tableaus(stab, n):
+    """Streamed plans apply long runs of Clifford gates as one gather through
+    the run's tableau: generators, <O> and the gradient against the oracle
+    (the gradient on sampled slots by the parameter shift)."""
+    c = W.clifford_plus_rotations(n, 900, 10, seed=50 + n)
+    s = stab.Stab(n)
+    s.apply_circuit(c.gates, c.thetas)
+    _, n_passes, _ = s.plan_info()
+    assert n_passes < 200          # the Clifford runs did not become gate-by-gate passes
+    got = layout.lib_to_paper(n, s.generators())
+    ref = oracle.generators(n, c.gates, c.thetas)
+    assert np.abs(got - ref).max() <= 1e-12
+    obs = W.obs_chain(n) + [(0.3, "Y" * n)]
+    e = s.expect(obs)
+    assert abs(e - oracle.expect(n, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
+    e2, g = s.grad(obs)
+    assert abs(e2 - e) <= 1e-12 * obs_l1(obs)
+    rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+    for gi in rot[:4]:
+        want = oracle.psr_grad_gate(n, c.gates, c.thetas, obs, gi)
+        assert abs(g[int(c.gates[gi]["param"])] - want) <= 1e-12 * obs_l1(obs)
+    s.close()
+
+
+@pytest.mark.parametrize("n", [10, 12])
+def test_long_clifford_runs_large_n_vs_sparse_oracle(stab, n):
+    c = W.clifford_plus_rotations(n, 1500, 8, seed=60 + n)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    obs = W.obs_chain(n)
+    e = s.expect(obs)
+    assert abs(e - oracle.sparse_expect(n, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
+    s.close()
