@@ -9,9 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/stab.h"
@@ -138,9 +140,10 @@ BatchArgs make_args(stab_batch *b, int n_units) {
 }
 
 // Picks CTAs per SM by timing the persistent launch on a prefix of the unit
-// table (the longest units) for each candidate residency.
+// table (the longest units, one per CTA of the widest candidate) for each
+// candidate residency; one untimed launch first.
 int autotune(stab_batch *b, int sms, int max_occ) {
-    const int sample = std::min(b->n_units, 2 * sms * max_occ);
+    const int sample = std::min(b->n_units, sms * max_occ);
     float best = 1e30f;
     int best_occ = max_occ;
     cudaEvent_t e0, e1;
@@ -150,9 +153,9 @@ int autotune(stab_batch *b, int sms, int max_occ) {
     for (int occ : {1, 2, 4, max_occ})
         if (occ <= max_occ && std::find(cands.begin(), cands.end(), occ) == cands.end())
             cands.push_back(occ);
+    BRC(launch_graph_or_direct(b, make_args(b, sample), sms * cands.back(), false));   // warm-up
     for (int occ : cands) {
         const BatchArgs a = make_args(b, sample);
-        BRC(launch_graph_or_direct(b, a, sms * occ, false));   // warm-up
         BCK(cudaEventRecord(e0, b->st));
         BRC(launch_graph_or_direct(b, a, sms * occ, false));
         BCK(cudaEventRecord(e1, b->st));
@@ -192,18 +195,48 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
         const stab_batch_item &I = items[it];
         if (I.n < 1 || I.n > STAB_BATCH_MAX_QUBITS) return STAB_E_RANGE;
         if (I.kind != STAB_ITEM_GENERATORS && I.kind != STAB_ITEM_EXPECT) return STAB_E_INVAL;
-        BRC(validate_gates(I.n, I.gates, I.m, I.n_params, nullptr));
-        BRC(validate_thetas(I.thetas, I.n_params));
+    }
+    // Plans and instruction streams of the items, built on host threads (each
+    // item is independent); then concatenated in item order below.
+    struct ItemPlan {
+        HostPlan P;
+        std::vector<Rec> S;
         std::vector<DevTerm> t;
-        if (I.kind == STAB_ITEM_EXPECT) BRC(encode_terms(I.n, I.obs, I.n_terms, &t));
+        int rc = STAB_OK;
+    };
+    std::vector<ItemPlan> plans((size_t)count);
+    {
+        std::atomic<int64_t> next{0};
+        auto worker = [&]() {
+            for (int64_t it = next++; it < count; it = next++) {
+                const stab_batch_item &I = items[it];
+                ItemPlan &ip = plans[(size_t)it];
+                ip.rc = validate_gates(I.n, I.gates, I.m, I.n_params, nullptr);
+                if (ip.rc == STAB_OK) ip.rc = validate_thetas(I.thetas, I.n_params);
+                if (ip.rc == STAB_OK && I.kind == STAB_ITEM_EXPECT)
+                    ip.rc = encode_terms(I.n, I.obs, I.n_terms, &ip.t);
+                if (ip.rc != STAB_OK) continue;
+                build_plan(I.n, I.gates, I.m, I.n_params, I.n <= 4 ? PLAN_ROWS : PLAN_FUSED,
+                           &ip.P);
+                build_stream(ip.P, I.kind == STAB_ITEM_EXPECT, &ip.S);
+            }
+        };
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int n_threads = (int)std::max(1u, std::min(hw ? hw : 1u, 16u));
+        std::vector<std::thread> pool;
+        for (int k = 1; k < n_threads && k < count; ++k) pool.emplace_back(worker);
+        worker();
+        for (auto &t : pool) t.join();
+    }
+    for (int64_t it = 0; it < count; ++it) BRC(plans[(size_t)it].rc);
+    for (int64_t it = 0; it < count; ++it) {
+        const stab_batch_item &I = items[it];
         b->item_n[it] = I.n;
         b->item_kind[it] = I.kind;
         b->max_n = std::max(b->max_n, (int)I.n);
-
-        HostPlan P;
-        build_plan(I.n, I.gates, I.m, I.n_params, I.n <= 4 ? PLAN_ROWS : PLAN_FUSED, &P);
-        std::vector<Rec> S;
-        build_stream(P, I.kind == STAB_ITEM_EXPECT, &S);
+        HostPlan &P = plans[(size_t)it].P;
+        const std::vector<Rec> &S = plans[(size_t)it].S;
+        const std::vector<DevTerm> &t = plans[(size_t)it].t;
         const int64_t th_off = (int64_t)thetas.size(), raw_off = (int64_t)raw.size();
         const int64_t map_off = (int64_t)maps.size(), midx_off = (int64_t)midx.size();
         const int64_t rec_off = (int64_t)recs.size();
@@ -246,6 +279,7 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
                            cost});
         }
         if (recs.size() > (size_t)INT32_MAX / 2) return STAB_E_RANGE;
+        plans[(size_t)it] = ItemPlan{};   // release the item's host plan
     }
     std::stable_sort(ups.begin(), ups.end(),
                      [](const UnitPlan &x, const UnitPlan &y) { return x.cost > y.cost; });
