@@ -191,29 +191,36 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
             const int lz = tg.lz[j], lx = tg.lx[j];
             const int lo = lz < lx ? lz : lx, hi = lz < lx ? lx : lz;
             const uint32_t bz = 1u << lz, bx = 1u << lx;
-            DevPass p{};
-            p.n_ops = tg.n_ops[j];
-            p.first = s_first[j];
+            const int n_ops = tg.n_ops[j];
+            const DevOp *po = pops + s_first[j];
             const int n_rot = s_nrot[j];
-            double part[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) part[r] = 0.0;
-            for (uint32_t g = threadIdx.x; g < T / 4; g += blockDim.x) {
-                uint32_t b = ((g >> lo) << (lo + 1)) | (g & ((1u << lo) - 1u));
-                b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1u));
-                double lx_ = tl[b | bx], ly_ = tl[b | bx | bz], lz_ = tl[b | bz];
-                double rx_ = tr[b | bx], ry_ = tr[b | bx | bz], rz_ = tr[b | bz];
-                adjoint_group(p, pops, nullptr, lx_, ly_, lz_, rx_, ry_, rz_, part, n_rot);
+            // one group per thread (the launch has T / 4 threads): each
+            // rotation's dot is reduced over the warp right away, so no
+            // per-slot accumulator array is carried through the op loop
+            const uint32_t g = threadIdx.x;
+            const bool live = g < T / 4;
+            uint32_t b = ((g >> lo) << (lo + 1)) | (g & ((1u << lo) - 1u));
+            b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1u));
+            double lx_ = 0.0, ly_ = 0.0, lz_ = 0.0, rx_ = 0.0, ry_ = 0.0, rz_ = 0.0;
+            if (live) {
+                lx_ = tl[b | bx]; ly_ = tl[b | bx | bz]; lz_ = tl[b | bz];
+                rx_ = tr[b | bx]; ry_ = tr[b | bx | bz]; rz_ = tr[b | bz];
+            }
+            int slot = n_rot - 1;
+            for (int k = n_ops - 1; k >= 0; --k) {
+                const DevOp op = po[k];
+                if (op.kind == K_ROT) {
+                    double d = pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+                    if (lane == 0) red[(j * R + slot) * W + warp] += d;
+                    --slot;
+                }
+                apply_op1(lx_, ly_, lz_, op, nullptr, 1);
+                apply_op1(rx_, ry_, rz_, op, nullptr, 1);
+            }
+            if (live) {
                 tl[b | bx] = lx_; tl[b | bx | bz] = ly_; tl[b | bz] = lz_;
                 tr[b | bx] = rx_; tr[b | bx | bz] = ry_; tr[b | bz] = rz_;
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (r < n_rot) {
-                    double v = part[r];
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                    if (lane == 0) red[(j * R + r) * W + warp] += v;
-                }
             }
             __syncthreads();
         }
