@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, doubl
     }
 }
 
-// Tile-fused reverse sweep: up to kTileMaxPasses wire passes on at most
-// kTileWires wires, applied backward to the pair (lambda, rho) held as two
-// shared-memory tiles (pair[0 .. 4^n) = lambda, pair[4^n ..) = rho).  The
+// Tile-fused adjoint sweep: up to kTileMaxPasses wire passes on at most
+// kTileWires wires, applied backward (tg.inverse = 1; forward with 0) to the
+// pair (lambda, rho) held as two shared-memory tiles (pair[0 .. 4^n) =
+// lambda, pair[4^n ..) = rho).  The
 // group's ops are staged in shared memory once per launch.  Every rotation's
 // gradient dot is reduced within each warp per pass (lane 0 adds it to its
 // warp's slot, tile after tile), and over the warps in a fixed order at the
@@ -206,17 +207,35 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
                 lx_ = tl[b | bx]; ly_ = tl[b | bx | bz]; lz_ = tl[b | bz];
                 rx_ = tr[b | bx]; ry_ = tr[b | bx | bz]; rz_ = tr[b | bz];
             }
-            int slot = n_rot - 1;
-            for (int k = n_ops - 1; k >= 0; --k) {
-                const DevOp op = po[k];
-                if (op.kind == K_ROT) {
-                    double d = pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
-                    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-                    if (lane == 0) red[(j * R + slot) * W + warp] += d;
-                    --slot;
+            if (tg.inverse) {
+                // reverse sweep: the dot at the post-gate pair, then the inverse gate
+                int slot = n_rot - 1;
+                for (int k = n_ops - 1; k >= 0; --k) {
+                    const DevOp op = po[k];
+                    if (op.kind == K_ROT) {
+                        double d = pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
+                        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+                        if (lane == 0) red[(j * R + slot) * W + warp] += d;
+                        --slot;
+                    }
+                    apply_op1(lx_, ly_, lz_, op, nullptr, 1);
+                    apply_op1(rx_, ry_, rz_, op, nullptr, 1);
                 }
-                apply_op1(lx_, ly_, lz_, op, nullptr, 1);
-                apply_op1(rx_, ry_, rz_, op, nullptr, 1);
+            } else {
+                // forward sweep (both vectors carried forward, the maps being
+                // orthogonal): the gate, then the dot at the post-gate pair
+                int slot = 0;
+                for (int k = 0; k < n_ops; ++k) {
+                    const DevOp op = po[k];
+                    apply_op1(lx_, ly_, lz_, op, nullptr, 0);
+                    apply_op1(rx_, ry_, rz_, op, nullptr, 0);
+                    if (op.kind == K_ROT) {
+                        double d = pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
+                        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+                        if (lane == 0) red[(j * R + slot) * W + warp] += d;
+                        ++slot;
+                    }
+                }
             }
             if (live) {
                 tl[b | bx] = lx_; tl[b | bx | bz] = ly_; tl[b | bz] = lz_;

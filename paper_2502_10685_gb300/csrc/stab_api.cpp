@@ -99,6 +99,8 @@ struct stab_ctx {
     int fuse = 1;
     cudaStream_t st = nullptr;
     cudaStream_t aux = nullptr;
+    cudaStream_t aux2 = nullptr;       // second branch of the split adjoint
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool own_st = false;
     cudaEvent_t ev_ready = nullptr;    // plan uploaded and encoded (on st)
     cudaEvent_t ev_aux = nullptr;      // aux work done
@@ -115,6 +117,7 @@ struct stab_ctx {
     DevPlan fwd, grad;
     DevBuf thetas, gens, gens_tmp, lam, rho, tmp, tmp2, terms, scal, grad_rot, partials, grads;
     DevBuf gbuf;                     // gradients written inside captured graphs
+    DevBuf lam2, tmp3;               // pair buffers of the split adjoint's forward half
     DevBuf status;                   // int32 set by kernels whose bounded waits gave up
     GraphCache g_gens, g_expect, g_grad; // streamed launch sequences (n > resident sizes)
     int64_t plan_gen = 0;            // bumped whenever a plan is rebuilt
@@ -153,6 +156,7 @@ struct stab_ctx {
         // a buffer may be in use on either stream of the context
         if (st) cudaStreamSynchronize(st);
         if (aux) cudaStreamSynchronize(aux);
+        if (aux2) cudaStreamSynchronize(aux2);
         if (free) free(b.p, b.bytes, (void *)s, user);
         else cudaFreeAsync(b.p, s);
         b.p = nullptr;
@@ -399,9 +403,10 @@ void make_tile_group(int n, int n_vec, const std::vector<const DevPass *> &group
 // most kTileWires wires run as one tile-fused launch (fused plans only; the
 // gate-by-gate forms keep one launch per gate).
 int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int n_vec,
-                 int inverse, cudaStream_t s) {
+                 int inverse, cudaStream_t s, int k0 = 0, int k1 = -1) {
     const auto &passes = P.host.passes;
-    const int np = (int)passes.size();
+    if (k1 < 0) k1 = (int)passes.size();
+    const int np = k1 - k0;   // passes [k0, k1), walked backward when inverse
     // tiles pay where a launch is small (launch-bound: few vectors, n <= 8); larger
     // launches are FP64-bound and run faster one wire per launch
     const bool fuse_tiles = P.host.mode != PLAN_PLAIN && P.host.mode != PLAN_PLAIN_ROWS &&
@@ -444,7 +449,7 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
         return STAB_OK;
     };
     for (int k = 0; k < np; ++k) {
-        const DevPass &p = passes[inverse ? np - 1 - k : k];
+        const DevPass &p = passes[inverse ? k1 - 1 - k : k0 + k];
         if (p.type == P_WIRE) {
             const bool known = std::find(wires.begin(), wires.end(), (int)p.q) != wires.end();
             if (!fuse_tiles || (int)group.size() == kTileMaxPasses ||
@@ -612,6 +617,9 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
         }
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming);
@@ -638,12 +646,13 @@ int stab_destroy(stab_ctx *c) {
     cudaSetDevice(c->device);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->aux) cudaStreamSynchronize(c->aux);
+    if (c->aux2) cudaStreamSynchronize(c->aux2);
     c->g_gens.reset();
     c->g_expect.reset();
     c->g_grad.reset();
     DevBuf *bufs[] = {&c->fwd.buf, &c->grad.buf, &c->thetas, &c->gens, &c->gens_tmp, &c->lam,
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
-                      &c->partials, &c->grads, &c->status, &c->gbuf};
+                      &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -652,6 +661,9 @@ int stab_destroy(stab_ctx *c) {
     if (c->ev_aux) cudaEventDestroy(c->ev_aux);
     if (c->ev_stage) cudaEventDestroy(c->ev_stage);
     if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->aux2) cudaStreamDestroy(c->aux2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_st && c->st) cudaStreamDestroy(c->st);
     delete c;
     return STAB_OK;
@@ -886,9 +898,142 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         RC(c->dalloc(c->partials, (size_t)(n_rot ? n_rot : 1) * nb * sizeof(double), s));
         double *res = (double *)c->scal.p + 3;
         const bool tiles = n <= kAdjTileMaxN;
+        if (tiles) {
+            RC(c->dalloc(c->lam2, 2 * vb, s));
+            RC(c->dalloc(c->tmp3, 2 * vb, s));
+        }
         const std::vector<const void *> key = {
-            (const void *)c->plan_gen, c->lam.p, c->tmp.p, c->partials.p, c->grad_rot.p,
-            c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
+            (const void *)c->plan_gen, c->lam.p, c->tmp.p, c->lam2.p, c->tmp3.p, c->partials.p,
+            c->grad_rot.p, c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
+        if (tiles) {
+            // Split sweep.  The circuit's passes are cut in two halves at
+            // `mid`.  Phase 1, two branches at once: r forward through the
+            // first half, lambda backward through the second; both meet at
+            // `mid`.  Phase 2, two branches at once: the pair (lambda, r)
+            // backward through the first half and forward through the second
+            // (every map is orthogonal, so lambda moves forward as r does),
+            // each rotation's dot taken at its post-gate pair.  Half the
+            // sequential depth of forward-then-reverse, and two chains of
+            // small launches share the GPU.
+            RC(run_graph(c, c->g_grad, key, s, [&](cudaStream_t gs, void **) {
+                const auto &passes = c->grad.host.passes;
+                const int np = (int)passes.size(), mid = np / 2;
+                const DevOp *ops = c->grad.prog.ops;
+                const auto &hops = c->grad.host.ops;
+                double *A = (double *)c->lam.p, *B = (double *)c->tmp.p;
+                double *Cb = (double *)c->lam2.p, *D = (double *)c->tmp3.p;
+                auto fork = [&](cudaStream_t from, cudaStream_t to) -> int {
+                    CK(cudaEventRecord(c->ev_fork, from));
+                    CK(cudaStreamWaitEvent(to, c->ev_fork, 0));
+                    return STAB_OK;
+                };
+                auto join = [&](cudaStream_t from, cudaStream_t to) -> int {
+                    CK(cudaEventRecord(c->ev_join, from));
+                    CK(cudaStreamWaitEvent(to, c->ev_join, 0));
+                    return STAB_OK;
+                };
+                // the adjoint sweep of passes [k0, k1) on a pair, one way
+                auto sweep = [&](double *&pr, double *&al, int k0, int k1, bool forward,
+                                 cudaStream_t st) -> int {
+                    std::vector<const DevPass *> group;
+                    std::vector<int> wires;
+                    const DevPass *pending = nullptr;
+                    auto gather_now = [&]() -> int {
+                        CK(launch_stream_cliff(pr, al, n, 2, *pending, ops, forward ? 0 : 1, st));
+                        c->launches++;
+                        std::swap(pr, al);
+                        pending = nullptr;
+                        return STAB_OK;
+                    };
+                    auto flush = [&]() -> int {
+                        if (group.empty()) return STAB_OK;
+                        TileGroup tg;
+                        make_tile_group(n, 1, group, forward ? 0 : 1, &tg, nb,
+                                        std::min(kAdjTileBits, 2 * n));
+                        for (size_t j = 0; j < group.size(); ++j) {
+                            int nr = 0;
+                            for (int k = 0; k < group[j]->n_ops; ++k)
+                                nr += hops[(size_t)group[j]->first + k].kind == K_ROT;
+                            tg.n_rot[j] = (uint8_t)nr;
+                        }
+                        double *dst = pr;
+                        if (pending) {
+                            tg.pull_n = pending->n_ops;
+                            tg.pull_first = pending->first;
+                            tg.pull_inverse = forward ? 0 : 1;
+                            dst = al;
+                        }
+                        CK(launch_adjoint_tile(pr, dst, n, tg, ops, (double *)c->partials.p, st));
+                        c->launches++;
+                        if (pending) {
+                            std::swap(pr, al);
+                            pending = nullptr;
+                        }
+                        group.clear();
+                        wires.clear();
+                        return STAB_OK;
+                    };
+                    for (int t = 0; t < k1 - k0; ++t) {
+                        const DevPass &p = passes[forward ? k0 + t : k1 - 1 - t];
+                        if (p.type == P_WIRE) {
+                            const bool known =
+                                std::find(wires.begin(), wires.end(), (int)p.q) != wires.end();
+                            if ((int)group.size() == kTileMaxPasses ||
+                                (!known && (int)wires.size() == kTileWires))
+                                RC(flush());
+                            group.push_back(&p);
+                            if (!known) wires.push_back(p.q);
+                            continue;
+                        }
+                        RC(flush());
+                        if (pending) RC(gather_now());
+                        if (p.type == P_TAB) {
+                            CK(launch_stream_tab(pr, al, n, 2,
+                                                 c->grad.prog.tabs + 2 * p.first + (forward ? 0 : 1),
+                                                 st));
+                            c->launches++;
+                            std::swap(pr, al);
+                            continue;
+                        }
+                        pending = &p;
+                    }
+                    RC(flush());
+                    if (pending) RC(gather_now());
+                    return STAB_OK;
+                };
+                // phase 1
+                RC(fork(gs, c->aux2));
+                double *rho = A + E, *rho_alt = B + E;
+                CK(launch_fill(rho, n, 1, INIT_RHO0, nullptr, 0, gs));
+                RC(run_streamed(c, c->grad, &rho, &rho_alt, 1, 0, gs, 0, mid));
+                double *lam = Cb, *lam_alt = D;
+                CK(launch_fill(lam, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, c->aux2));
+                RC(run_streamed(c, c->grad, &lam, &lam_alt, 1, 1, c->aux2, mid, np));
+                c->launches += nt ? 3 : 2;
+                RC(join(c->aux2, gs));
+                // the meeting pair, once in each branch's buffers
+                double *X = rho - E, *Xalt = X == A ? B : A;
+                double *Y = lam, *Yalt = Y == Cb ? D : Cb;
+                CK(cudaMemcpyAsync(X, lam, vb, cudaMemcpyDeviceToDevice, gs));
+                CK(cudaMemcpyAsync(Y + E, rho, vb, cudaMemcpyDeviceToDevice, gs));
+                // phase 2
+                RC(fork(gs, c->aux2));
+                RC(sweep(X, Xalt, 0, mid, false, gs));
+                RC(sweep(Y, Yalt, mid, np, true, c->aux2));
+                RC(join(c->aux2, gs));
+                CK(launch_reduce_partials((const double *)c->partials.p, n_rot, nb,
+                                          (double *)c->grad_rot.p, gs));
+                CK(launch_xfree_sum(X, n, 1, res, gs));   // <O> = <lambda_0, rho_0>
+                c->launches += 2;
+                if (c->n_params > 0) {
+                    CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
+                                           c->grad.param_rot, (int)c->n_params,
+                                           (double *)c->gbuf.p, gs));
+                    c->launches++;
+                }
+                return STAB_OK;
+            }));
+        } else
         RC(run_graph(c, c->g_grad, key, s, [&](cudaStream_t gs, void **) {
             double *pa = (double *)c->lam.p, *pb = (double *)c->tmp.p;
             double *rho = pa + E, *rho_alt = pb + E;
