@@ -322,6 +322,38 @@ __global__ void __launch_bounds__(kThreads) k_xfree_sum(const double *vec, int n
     }
 }
 
+// Inner product <a, b> of two coefficient vectors in a fixed order: block b
+// sums a contiguous slice (strided by the block's threads, then a shuffle
+// tree), the last kernel the kDotBlocks partials in order.
+constexpr int kDotBlocks = 256;
+
+__global__ void __launch_bounds__(kThreads) k_dot_partial(const double *a, const double *b,
+                                                          int n, double *partial) {
+    __shared__ double red[kThreads / 32];
+    const uint64_t E = 1ull << (2 * n);
+    const uint64_t per = (E + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = blockIdx.x * per, hi = lo + per < E ? lo + per : E;
+    double acc = 0.0;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc = fma(a[i], b[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double total = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) total += red[w];
+        partial[blockIdx.x] = total;
+    }
+}
+
+__global__ void k_dot_final(const double *partial, int nblk, double *out) {
+    const int lane = threadIdx.x;
+    const int per = (nblk + 31) / 32;
+    double t = 0.0;
+    for (int k = lane * per; k < nblk && k < (lane + 1) * per; ++k) t += partial[k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) *out = t;
+}
+
 // Waits on a barrier nothing completes, with a poll bound; records a timeout.
 __global__ void k_bounded_wait(int64_t polls, int32_t *status) {
     __shared__ uint64_t bar;
@@ -411,6 +443,13 @@ cudaError_t launch_stream_tile(const double *src, double *dst, int n, int n_vec,
         if (e != cudaSuccess) return e;
     }
     k_stream_tile<<<(int)grid, threads, smem, st>>>(src, dst, n, n_vec, tg, ops, maps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double *a, const double *b, int n, double *partial, double *out,
+                       cudaStream_t st) {
+    k_dot_partial<<<kDotBlocks, kThreads, 0, st>>>(a, b, n, partial);
+    k_dot_final<<<1, 32, 0, st>>>(partial, kDotBlocks, out);
     return cudaGetLastError();
 }
 

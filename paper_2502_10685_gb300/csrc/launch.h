@@ -113,6 +113,9 @@ cudaError_t launch_stream_wire(double *vec, int n, int n_vec, const DevPass &p, 
 cudaError_t launch_stream_cliff(const double *src, double *dst, int n, int n_vec,
                                 const DevPass &p, const DevOp *ops, int inverse, cudaStream_t st);
 cudaError_t launch_xfree_sum(const double *vec, int n, int n_vec, double *out, cudaStream_t st);
+// *out = <a, b> over the 4^n entries, fixed order; partial: 256 doubles of scratch.
+cudaError_t launch_dot(const double *a, const double *b, int n, double *partial, double *out,
+                       cudaStream_t st);
 // P_TAB: dst = the Clifford map whose tableau is *tab applied as a signed gather (n <= 12).
 cudaError_t launch_stream_tab(const double *src, double *dst, int n, int n_vec,
                               const DevTab *tab, cudaStream_t st);

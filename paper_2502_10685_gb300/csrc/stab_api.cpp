@@ -117,7 +117,8 @@ struct stab_ctx {
     DevPlan fwd, grad;
     DevBuf thetas, gens, gens_tmp, lam, rho, tmp, tmp2, terms, scal, grad_rot, partials, grads;
     DevBuf gbuf;                     // gradients written inside captured graphs
-    DevBuf lam2, tmp3;               // pair buffers of the split adjoint's forward half
+    DevBuf lam2, tmp3;               // second-branch buffers of the split sweeps
+    DevBuf dotbuf;                   // partial sums of the split expectation's inner product
     DevBuf status;                   // int32 set by kernels whose bounded waits gave up
     GraphCache g_gens, g_expect, g_grad; // streamed launch sequences (n > resident sizes)
     int64_t plan_gen = 0;            // bumped whenever a plan is rebuilt
@@ -652,7 +653,8 @@ int stab_destroy(stab_ctx *c) {
     c->g_grad.reset();
     DevBuf *bufs[] = {&c->fwd.buf, &c->grad.buf, &c->thetas, &c->gens, &c->gens_tmp, &c->lam,
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
-                      &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3};
+                      &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3,
+                      &c->dotbuf};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -814,19 +816,48 @@ int stab_expect_async(stab_ctx *c, double *out_dev) {
         CK(launch_resident_stream(c->n, a, s));
         c->launches++;
     } else {
-        RC(c->dalloc(c->lam, c->vec_bytes(), s));
-        RC(c->dalloc(c->tmp, c->vec_bytes(), s));
+        const size_t vb = c->vec_bytes();
+        RC(c->dalloc(c->lam, vb, s));
+        RC(c->dalloc(c->tmp, vb, s));
         RC(c->dalloc(c->scal, 64 * sizeof(double), s));
+        // small vectors (the tile regime): O backward through the second half
+        // of the circuit and rho_0 forward through the first half, at once on
+        // two streams; <O> = <lambda_mid, r_mid> (orthogonal maps keep inner
+        // products), half the sequential depth
+        const bool split = c->fwd.host.mode != PLAN_PLAIN && c->fwd.host.mode != PLAN_PLAIN_ROWS &&
+                           (1ull << (2 * c->n)) <= (1ull << 17) && c->fwd.host.passes.size() >= 8;
+        if (split) {
+            RC(c->dalloc(c->lam2, vb, s));
+            RC(c->dalloc(c->tmp3, vb, s));
+            RC(c->dalloc(c->dotbuf, 256 * sizeof(double), s));
+        }
         double *res = (double *)c->scal.p + 2;
         const std::vector<const void *> key = {(const void *)c->plan_gen, c->lam.p, c->tmp.p,
-                                               c->terms.p, (const void *)(intptr_t)nt, res};
+                                               c->lam2.p, c->tmp3.p, c->dotbuf.p,
+                                               c->terms.p, (const void *)(intptr_t)nt, res,
+                                               (const void *)(intptr_t)split};
         RC(run_graph(c, c->g_expect, key, s, [&](cudaStream_t gs, void **) {
             double *cur = (double *)c->lam.p, *alt = (double *)c->tmp.p;
+            if (!split) {
+                CK(launch_fill(cur, c->n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, gs));
+                c->launches += nt ? 2 : 1;
+                RC(run_streamed(c, c->fwd, &cur, &alt, 1, 1, gs));
+                CK(launch_xfree_sum(cur, c->n, 1, res, gs));
+                c->launches++;
+                return STAB_OK;
+            }
+            const int np = (int)c->fwd.host.passes.size(), mid = np / 2;
+            CK(cudaEventRecord(c->ev_fork, gs));
+            CK(cudaStreamWaitEvent(c->aux2, c->ev_fork, 0));
             CK(launch_fill(cur, c->n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, gs));
-            c->launches += nt ? 2 : 1;
-            RC(run_streamed(c, c->fwd, &cur, &alt, 1, 1, gs));
-            CK(launch_xfree_sum(cur, c->n, 1, res, gs));
-            c->launches++;
+            RC(run_streamed(c, c->fwd, &cur, &alt, 1, 1, gs, mid, np));
+            double *rc = (double *)c->lam2.p, *ra = (double *)c->tmp3.p;
+            CK(launch_fill(rc, c->n, 1, INIT_RHO0, nullptr, 0, c->aux2));
+            RC(run_streamed(c, c->fwd, &rc, &ra, 1, 0, c->aux2, 0, mid));
+            CK(cudaEventRecord(c->ev_join, c->aux2));
+            CK(cudaStreamWaitEvent(gs, c->ev_join, 0));
+            CK(launch_dot(cur, rc, c->n, (double *)c->dotbuf.p, res, gs));
+            c->launches += (nt ? 2 : 1) + 1 + 2;
             return STAB_OK;
         }));
         CK(cudaMemcpyAsync(out_dev, res, sizeof(double), cudaMemcpyDeviceToDevice, s));
