@@ -825,7 +825,7 @@ int stab_expect_async(stab_ctx *c, double *out_dev) {
         // two streams; <O> = <lambda_mid, r_mid> (orthogonal maps keep inner
         // products), half the sequential depth
         const bool split = c->fwd.host.mode != PLAN_PLAIN && c->fwd.host.mode != PLAN_PLAIN_ROWS &&
-                           (1ull << (2 * c->n)) <= (1ull << 17) && c->fwd.host.passes.size() >= 8;
+                           (1ull << (2 * c->n)) <= (1ull << 20) && c->fwd.host.passes.size() >= 8;
         if (split) {
             RC(c->dalloc(c->lam2, vb, s));
             RC(c->dalloc(c->tmp3, vb, s));
