@@ -470,7 +470,7 @@ def run_batch(args):
         dist.destroy_process_group()
     if rank != 0:
         return 0
-    print(json.dumps({
+    line = {
         "metric": "circuits/s", "value": len(items) * world / (ms / 1e3), "unit": "circuits/s",
         "n_gpus": world, "scaling": "weak", "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms,
@@ -478,7 +478,30 @@ def run_batch(args):
         "config": {"workload": args.workload, "circuits": len(items), "units": info["units"],
                    "grid": info["grid"], "ctas_per_sm": info["ctas_per_sm"],
                    "l2": "flushed between steps"},
-        "updates_per_s": upd * world / (ms / 1e3), "create_s": create_s, "vs_forms": forms}))
+        "updates_per_s": upd * world / (ms / 1e3), "create_s": create_s, "vs_forms": forms}
+    if world == 1 and not args.no_cpu_baseline and len(items) >= 12:
+        # the oracle on a seeded sample of small items, scaled by updates
+        import oracle
+        oracle.build()
+        cand = [it for it in items if 4 ** it.circuit.n * it.circuit.m <= 2e7]
+        pick = [cand[i] for i in np.random.default_rng(2).choice(len(cand),
+                                                                  size=min(12, len(cand)),
+                                                                  replace=False)]
+        p_upd = sum((it.circuit.n if it.kind == "generators" else 1) * it.circuit.m *
+                    4 ** it.circuit.n for it in pick)
+        t0 = time.perf_counter()
+        for it in pick:
+            c = it.circuit
+            if it.kind == "expect":
+                oracle.expect(c.n, c.gates, c.thetas, it.observable)
+            else:
+                oracle.generators(c.n, c.gates, c.thetas)
+        cpu_s = (time.perf_counter() - t0) * upd / p_upd
+        line["cpu_baseline"] = {"value": len(items) / cpu_s, "unit": "circuits/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "12 seeded items with 4^n m <= 2e7, one core, scaled "
+                                          "to the batch by coefficient updates"}
+    print(json.dumps(line))
     return 0
 
 
@@ -537,13 +560,27 @@ def run_grad(args):
     assert err <= 1e-10 * l1, err
     psr_all_ms = psr_ms * c.n_params / len(js)
     s.close()
-    print(json.dumps({
+    line = {
         "metric": "gradient time", "value": adj_ms, "unit": "ms", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": adj_ms,
         "higher_is_better": False, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "grad-c4", "n": 8, "gates": c.m, "params": c.n_params},
         "psr_batched_ms_all_params": psr_all_ms, "adjoint_speedup": psr_all_ms / adj_ms,
-        "max_abs_diff_vs_psr_sample": err}))
+        "max_abs_diff_vs_psr_sample": err}
+    if not args.no_cpu_baseline:
+        # the oracle's parameter shift of one slot (two full propagations),
+        # scaled to every slot: the CPU way to these gradients
+        import oracle
+        oracle.build()
+        gi = int(np.nonzero([int(g["op"]) in W.ROTATIONS for g in c.gates])[0][0])
+        t0 = time.perf_counter()
+        oracle.psr_grad_gate(c.n, c.gates, c.thetas, obs, gi)
+        one = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": one * 1e3 * c.n_params, "unit": "ms", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "parameter shift of one slot (2 propagations of the "
+                                          "full circuit), scaled to all %d slots" % c.n_params}
+    print(json.dumps(line))
     return 0
 
 
