@@ -584,6 +584,44 @@ def run_grad(args):
     return 0
 
 
+def run_grad_n(args):
+    """All gradients by the adjoint on the layered ansatz with n, m from the
+    workload name grad-n<N>-<M> (O = the ZZ chain + 0.5 X field); device time of
+    grad_async with CUDA events, L2 flushed between steps."""
+    import torch
+    from paper_2502_10685_gb300 import stab, workloads as W
+    n, m = (int(v) for v in args.workload[len("grad-n"):].split("-"))
+    torch.cuda.set_stream(torch.cuda.Stream())
+    st = torch.cuda.current_stream()
+    c = W.layered_ansatz(n, m, seed=1000 + n)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    s.set_observable(W.obs_chain(n))
+    g = torch.zeros(max(1, c.n_params), dtype=torch.float64, device="cuda")
+    e = torch.zeros(8, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        s.grad_async(e, g)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = _events()
+        e0.record(st)
+        s.grad_async(e, g)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    s.close()
+    ms = sum(times) / len(times)
+    print(json.dumps({
+        "metric": "gradient time", "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "n": n, "gates": m,
+                                        "params": c.n_params, "l2": "flushed between steps"}}))
+    return 0
+
+
 def run_serve(args):
     """Poisson trace (2,000 req/s), n ~ U{4..12}, depth log-uniform [100, 60000],
     50/50 <O> / gradient requests, submitted at their arrival times to the
@@ -867,6 +905,8 @@ def main():
         return run_batch(args)
     if args.workload == "grad-c4":
         return run_grad(args)
+    if args.workload.startswith("grad-n"):
+        return run_grad_n(args)
     if args.workload == "serve-c5":
         return run_serve(args)
     if args.workload.startswith("expect-n"):

@@ -61,6 +61,23 @@ __device__ __forceinline__ void adjoint_group(const DevPass &p, const DevOp *ops
     }
 }
 
+// The same pass forward: each gate on both vectors, then (rotations) the dot
+// at the post-gate pair; slots in op order.
+__device__ __forceinline__ void adjoint_group_fwd(const DevPass &p, const DevOp *ops,
+                                                  double &lx, double &ly, double &lz, double &rx,
+                                                  double &ry, double &rz, double (&part)[R]) {
+    int slot = 0;
+    for (int j = 0; j < p.n_ops; ++j) {
+        const DevOp op = ops[p.first + j];
+        apply_op1(lx, ly, lz, op, nullptr, 0);
+        apply_op1(rx, ry, rz, op, nullptr, 0);
+        if (op.kind == K_ROT) {
+            add_slot(part, slot, pair_dot(op.axis, lx, ly, lz, rx, ry, rz));
+            ++slot;
+        }
+    }
+}
+
 __device__ __forceinline__ int count_rot(const DevPass &p, const DevOp *ops) {
     int c = 0;
     for (int j = 0; j < p.n_ops; ++j) c += ops[p.first + j].kind == K_ROT;
@@ -85,7 +102,7 @@ constexpr int kAdjStagedOps = 96;   // ops of a tile group staged in shared memo
 
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, double *rho, int n,
                                                               DevPass p, const DevOp *ops,
-                                                              double *partials) {
+                                                              double *partials, int forward) {
     __shared__ double red[(kAdjThreads / 32) * R];
     const int q = p.q;
     const uint64_t G = 1ull << (2 * n - 2);
@@ -100,7 +117,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, doubl
         double *L = lam + b, *Rh = rho + b;
         double lx = L[bx], ly = L[bx | bz], lz = L[bz];
         double rx = Rh[bx], ry = Rh[bx | bz], rz = Rh[bz];
-        adjoint_group(p, ops, nullptr, lx, ly, lz, rx, ry, rz, part, n_rot);
+        if (forward) adjoint_group_fwd(p, ops, lx, ly, lz, rx, ry, rz, part);
+        else adjoint_group(p, ops, nullptr, lx, ly, lz, rx, ry, rz, part, n_rot);
         L[bx] = lx; L[bx | bz] = ly; L[bz] = lz;
         Rh[bx] = rx; Rh[bx | bz] = ry; Rh[bz] = rz;
     }
@@ -295,10 +313,10 @@ int adjoint_stream_blocks(int n) {
 }
 
 cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &p,
-                                const DevOp *ops, double *partials, int, int,
+                                const DevOp *ops, double *partials, int forward,
                                 cudaStream_t st) {
     k_adjoint_wire<<<adjoint_stream_blocks(n), kAdjThreads, 0, st>>>(lam, rho, n, p, ops,
-                                                                      partials);
+                                                                      partials, forward);
     return cudaGetLastError();
 }
 

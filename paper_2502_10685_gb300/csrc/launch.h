@@ -163,8 +163,11 @@ cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_
 
 // Streamed adjoint pieces.
 int adjoint_stream_blocks(int n);
+// One wire pass of the adjoint on (lambda, rho): backward (forward = 0: the
+// dot at the post-gate pair, then the inverse gate) or forward (the gate, then
+// the dot); partials[gate][block], adjoint_stream_blocks(n) blocks.
 cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &p,
-                                const DevOp *ops, double *partials, int rot_base, int n_rot_total,
+                                const DevOp *ops, double *partials, int forward,
                                 cudaStream_t st);
 // Tile-fused reverse sweep on the contiguous pair (lambda, rho) for n <=
 // kAdjTileMaxN: tiles of 2^kAdjTileBits entries, one per CTA and one group per

@@ -929,14 +929,15 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         RC(c->dalloc(c->partials, (size_t)(n_rot ? n_rot : 1) * nb * sizeof(double), s));
         double *res = (double *)c->scal.p + 3;
         const bool tiles = n <= kAdjTileMaxN;
-        if (tiles) {
+        const bool split = n <= 10;   // beyond, one pass fills the GPU
+        if (split) {
             RC(c->dalloc(c->lam2, 2 * vb, s));
             RC(c->dalloc(c->tmp3, 2 * vb, s));
         }
         const std::vector<const void *> key = {
             (const void *)c->plan_gen, c->lam.p, c->tmp.p, c->lam2.p, c->tmp3.p, c->partials.p,
             c->grad_rot.p, c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
-        if (tiles) {
+        if (split) {
             // Split sweep.  The circuit's passes are cut in two halves at
             // `mid`.  Phase 1, two branches at once: r forward through the
             // first half, lambda backward through the second; both meet at
@@ -978,6 +979,17 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                     };
                     auto flush = [&]() -> int {
                         if (group.empty()) return STAB_OK;
+                        if (!tiles) {
+                            for (const DevPass *gp : group) {
+                                CK(launch_adjoint_wire(pr, pr + E, n, *gp, ops,
+                                                       (double *)c->partials.p, forward ? 1 : 0,
+                                                       st));
+                                c->launches++;
+                            }
+                            group.clear();
+                            wires.clear();
+                            return STAB_OK;
+                        }
                         TileGroup tg;
                         make_tile_group(n, 1, group, forward ? 0 : 1, &tg, nb,
                                         std::min(kAdjTileBits, 2 * n));
@@ -1027,6 +1039,7 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                             continue;
                         }
                         pending = &p;
+                        if (!tiles) RC(gather_now());
                     }
                     RC(flush());
                     if (pending) RC(gather_now());
@@ -1091,7 +1104,7 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                 if (!tiles) {
                     for (const DevPass *p : group) {
                         CK(launch_adjoint_wire(pair, pair + E, n, *p, c->grad.prog.ops,
-                                               (double *)c->partials.p, 0, n_rot, gs));
+                                               (double *)c->partials.p, 0, gs));
                         c->launches++;
                     }
                 } else {

@@ -350,3 +350,22 @@ def test_long_clifford_runs_large_n_vs_sparse_oracle(stab, n):
     e = s.expect(obs)
     assert abs(e - oracle.sparse_expect(n, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
     s.close()
+
+
+@pytest.mark.parametrize("n,m", [(9, 300), (10, 150)])
+def test_gradient_split_wire_path(stab, n, m):
+    """n = 9, 10: the split adjoint with one launch per wire pass (r forward and
+    lambda backward meet mid-circuit, then both halves at once): <O> against
+    the oracle and sampled slots against the oracle's parameter shift."""
+    c = W.layered_ansatz(n, m, seed=70 + n)
+    obs = W.obs_chain(n)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    e, g = s.grad(obs)
+    s.close()
+    assert abs(e - oracle.expect(n, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
+    rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+    rng = np.random.default_rng(n)
+    for gi in [rot[0], rot[-1]] + list(rng.choice(rot, size=2, replace=False)):
+        want = oracle.psr_grad_gate(n, c.gates, c.thetas, obs, int(gi))
+        assert abs(g[int(c.gates[gi]["param"])] - want) <= 1e-12 * obs_l1(obs)
