@@ -304,8 +304,9 @@ typedef struct stab_result {
     double done_s;           /* results on the host */
 } stab_result;
 
-/* Admission footprint of a request: max(n 4^n 8, 4^n 8 x (2 for <O>, 4 for a
- * gradient)) bytes plus 64 bytes per gate. */
+/* Admission footprint of a request: max(n 4^n 8, 4^n 8 x (4 for <O>, 8 for a
+ * gradient: the vectors of the split sweeps)) bytes plus 64 bytes per gate,
+ * plus the streamed adjoint's per-CTA partial sums above n = 6. */
 int64_t stab_request_footprint(const stab_request *req);
 
 int stab_server_create(const stab_server_opts *opts, stab_server **out);

@@ -275,7 +275,8 @@ int64_t stab_request_footprint(const stab_request *q) {
     if (!q || q->n < 1 || q->n > STAB_MAX_QUBITS) return 0;
     const int64_t vec = (int64_t)8 << (2 * q->n);
     int64_t fp = (int64_t)q->n * vec;
-    const int64_t work = vec * (q->kind == STAB_REQ_GRAD ? 4 : 2);
+    // expectation: two vector pairs of the split sweep; gradient: four (lambda, rho) pairs
+    const int64_t work = vec * (q->kind == STAB_REQ_GRAD ? 8 : 4);
     if (work > fp) fp = work;
     fp += 64 * (q->m > 0 ? q->m : 0);
     if (q->kind == STAB_REQ_GRAD && q->n > stab::kMaxResidentAdjoint) {

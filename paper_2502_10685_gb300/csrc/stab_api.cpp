@@ -825,7 +825,7 @@ int stab_expect_async(stab_ctx *c, double *out_dev) {
         // two streams; <O> = <lambda_mid, r_mid> (orthogonal maps keep inner
         // products), half the sequential depth
         const bool split = c->fwd.host.mode != PLAN_PLAIN && c->fwd.host.mode != PLAN_PLAIN_ROWS &&
-                           (1ull << (2 * c->n)) <= (1ull << 20) && c->fwd.host.passes.size() >= 8;
+                           c->fwd.host.passes.size() >= 8;
         if (split) {
             RC(c->dalloc(c->lam2, vb, s));
             RC(c->dalloc(c->tmp3, vb, s));
@@ -929,15 +929,12 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         RC(c->dalloc(c->partials, (size_t)(n_rot ? n_rot : 1) * nb * sizeof(double), s));
         double *res = (double *)c->scal.p + 3;
         const bool tiles = n <= kAdjTileMaxN;
-        const bool split = n <= 10;   // beyond, one pass fills the GPU
-        if (split) {
-            RC(c->dalloc(c->lam2, 2 * vb, s));
-            RC(c->dalloc(c->tmp3, 2 * vb, s));
-        }
+        RC(c->dalloc(c->lam2, 2 * vb, s));
+        RC(c->dalloc(c->tmp3, 2 * vb, s));
         const std::vector<const void *> key = {
             (const void *)c->plan_gen, c->lam.p, c->tmp.p, c->lam2.p, c->tmp3.p, c->partials.p,
             c->grad_rot.p, c->gbuf.p, c->terms.p, (const void *)(intptr_t)nt, res};
-        if (split) {
+        {
             // Split sweep.  The circuit's passes are cut in two halves at
             // `mid`.  Phase 1, two branches at once: r forward through the
             // first half, lambda backward through the second; both meet at
@@ -946,7 +943,8 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
             // (every map is orthogonal, so lambda moves forward as r does),
             // each rotation's dot taken at its post-gate pair.  Half the
             // sequential depth of forward-then-reverse, and two chains of
-            // small launches share the GPU.
+            // launches share the GPU (measured faster at every n: 1.6x at
+            // n = 8, 1.1-1.3x at n = 9..12).
             RC(run_graph(c, c->g_grad, key, s, [&](cudaStream_t gs, void **) {
                 const auto &passes = c->grad.host.passes;
                 const int np = (int)passes.size(), mid = np / 2;
@@ -1077,104 +1075,7 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
                 }
                 return STAB_OK;
             }));
-        } else
-        RC(run_graph(c, c->g_grad, key, s, [&](cudaStream_t gs, void **) {
-            double *pa = (double *)c->lam.p, *pb = (double *)c->tmp.p;
-            double *rho = pa + E, *rho_alt = pb + E;
-            CK(launch_fill(rho, n, 1, INIT_RHO0, nullptr, 0, gs));
-            c->launches++;
-            RC(run_streamed(c, c->grad, &rho, &rho_alt, 1, 0, gs));
-            double *pair = rho - E, *alt = (pair == pa) ? pb : pa;
-            CK(launch_fill(pair, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, gs));
-            c->launches += nt ? 2 : 1;
-            const auto &passes = c->grad.host.passes;
-            std::vector<const DevPass *> group;
-            std::vector<int> wires;
-            // with tiles, a Clifford gather is folded into the loads of the next group
-            const DevPass *pending = nullptr;
-            auto gather_now = [&]() -> int {
-                CK(launch_stream_cliff(pair, alt, n, 2, *pending, c->grad.prog.ops, 1, gs));
-                c->launches++;
-                std::swap(pair, alt);
-                pending = nullptr;
-                return STAB_OK;
-            };
-            auto flush = [&]() -> int {
-                if (group.empty()) return STAB_OK;
-                if (!tiles) {
-                    for (const DevPass *p : group) {
-                        CK(launch_adjoint_wire(pair, pair + E, n, *p, c->grad.prog.ops,
-                                               (double *)c->partials.p, 0, gs));
-                        c->launches++;
-                    }
-                } else {
-                    TileGroup tg;
-                    make_tile_group(n, 1, group, 1, &tg, nb, std::min(kAdjTileBits, 2 * n));
-                    const auto &hops = c->grad.host.ops;
-                    for (size_t j = 0; j < group.size(); ++j) {
-                        int nr = 0;
-                        for (int k = 0; k < group[j]->n_ops; ++k)
-                            nr += hops[(size_t)group[j]->first + k].kind == K_ROT;
-                        tg.n_rot[j] = (uint8_t)nr;
-                    }
-                    double *dst = pair;
-                    if (pending) {
-                        tg.pull_n = pending->n_ops;
-                        tg.pull_first = pending->first;
-                        tg.pull_inverse = 1;
-                        dst = alt;
-                    }
-                    CK(launch_adjoint_tile(pair, dst, n, tg, c->grad.prog.ops,
-                                           (double *)c->partials.p, gs));
-                    c->launches++;
-                    if (pending) {
-                        std::swap(pair, alt);
-                        pending = nullptr;
-                    }
-                }
-                group.clear();
-                wires.clear();
-                return STAB_OK;
-            };
-            for (int k = (int)passes.size() - 1; k >= 0; --k) {
-                const DevPass &p = passes[k];
-                if (p.type == P_WIRE) {
-                    const bool known =
-                        std::find(wires.begin(), wires.end(), (int)p.q) != wires.end();
-                    if ((int)group.size() == kTileMaxPasses ||
-                        (!known && (int)wires.size() == kTileWires))
-                        RC(flush());
-                    group.push_back(&p);
-                    if (!known) wires.push_back(p.q);
-                    continue;
-                }
-                RC(flush());
-                if (pending) RC(gather_now());
-                if (p.type == P_TAB) {
-                    // the Clifford run backward: gather through the run's own tableau
-                    CK(launch_stream_tab(pair, alt, n, 2, c->grad.prog.tabs + 2 * p.first + 1,
-                                         gs));
-                    c->launches++;
-                    std::swap(pair, alt);
-                    continue;
-                }
-                pending = &p;
-                if (!tiles) RC(gather_now());
-            }
-            RC(flush());
-            if (pending) RC(gather_now());
-            CK(launch_reduce_partials((const double *)c->partials.p, n_rot, nb,
-                                      (double *)c->grad_rot.p, gs));
-            CK(launch_xfree_sum(pair, n, 1, res, gs));
-            c->launches += 2;
-            if (c->n_params > 0) {
-                CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
-                                       c->grad.param_rot, (int)c->n_params, (double *)c->gbuf.p,
-                                       gs));
-                c->launches++;
-            }
-            return STAB_OK;
-        }));
+        }
         CK(cudaMemcpyAsync(e_out, res, sizeof(double), cudaMemcpyDeviceToDevice, s));
         if (c->n_params > 0)
             CK(cudaMemcpyAsync(grads_dev, c->gbuf.p, (size_t)c->n_params * sizeof(double),
