@@ -309,18 +309,35 @@ def run_ours(args):
     peak = SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     gen_avg_s = statistics.mean(gen_ms) / 1e3
     achieved = algorithmic_flops_generators(c) / gen_avg_s / 1e12
-    # DRAM bytes per launch from one ncu capture of k_resident_stream<4,4> on the
-    # 2,000-gate case (125,440 B read, 0 B written: the staged instruction stream),
-    # scaled by gates (the stream grows in proportion); see profiles/.
-    traffic = 121344.0 * c.m / 2000.0 if c.n == 4 else None
-    active_sms = c.n + 1
+    cut, gen_units, _ = s.split_info()
+    n_passes = s.plan_info()[1]
+    if gen_units:
+        # the generators' persistent launch: n vectors through passes [0, cut)
+        # and the 4^n - 1 transfer-matrix columns through [cut, P), then one
+        # product; FP64 work executed per algorithmic flop, counted in passes
+        kernel = "k_batch (split: %d units) + k_apply_transfer" % gen_units
+        executed = (c.n * cut + (4 ** c.n - 1) * (n_passes - cut)) / (c.n * n_passes)
+        active_sms = min(SMS, gen_units)
+        note = ("one circuit: the generators split at pass %d of %d; the n first-part "
+                "vectors and the 4^n-1 basis columns run at once, one CTA each; passes "
+                "are sequential within a unit" % (cut, n_passes))
+    else:
+        kernel = "k_resident_stream (generators)"
+        executed = 1.0
+        active_sms = c.n
+        note = "one circuit: n independent vectors, one CTA each; passes are sequential"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_resident_stream<4,4> (generators)", "launch_ms": gen_avg_s * 1e3,
+                "frac": achieved / peak,
+                # DRAM bytes of the generators' k_batch launch from one ncu capture
+                # of this workload (3,198,208 B read: the two staged half-streams;
+                # 0 B written); see profiles/
+                "traffic": 3198208.0 if (gen_units and c.n == 4 and c.m == 60200) else None,
+                "kernel": kernel, "launch_ms": gen_avg_s * 1e3,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock",
                 "active_sms": active_sms,
-                "frac_of_active_sms": achieved / (peak * active_sms / SMS),
-                "note": "one circuit: 5 independent vectors, one CTA each; passes are sequential"}
+                "executed_per_algorithmic": executed,
+                "executed_frac": achieved * executed / peak,
+                "note": note}
 
     # the plain GPU form: one launch per gate, no fusion, same step
     plain = None

@@ -416,6 +416,17 @@ int stab_sparse_order_history(stab_sparse *s, int64_t *orders, int64_t max, int6
 /* Number of qubits, loaded gates and fused passes of the current plan. */
 int stab_plan_info(stab_ctx *ctx, int64_t *n_gates, int64_t *n_passes, int32_t *kernel);
 
+/* The cut of the split resident sweeps of the current plan (n <= 6, AUTO
+ * kernel, fused).  <O> = <lambda, r> for any cut of the circuit, since every
+ * gate's map is orthogonal (Sec. II): r = rho_0 through passes [0, cut) and
+ * lambda = O backward through [cut, n_passes) run at once; for n <= 4 the
+ * generators are T a_k, a_k = Z_k through [0, cut) and T the transfer matrix
+ * of [cut, n_passes).  Writes *cut (-1: no split; the plan runs as one
+ * sweep), *gen_units (vectors of the generators' persistent launch, 0 when
+ * not split) and *expect_units (of the expectation's, 0 when not split).
+ * Any output pointer may be NULL.  Errors: STAB_E_INVAL (ctx NULL). */
+int stab_split_info(stab_ctx *ctx, int64_t *cut, int32_t *gen_units, int32_t *expect_units);
+
 /* Number of kernels this context launched since creation (all entry points). */
 int64_t stab_launch_count(stab_ctx *ctx);
 

@@ -132,6 +132,8 @@ def load(build_if_missing: bool = True):
             "stab_synchronize": (i32, [vp]),
             "stab_plan_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_int32)]),
+            "stab_split_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
             "stab_launch_count": (i64, [vp]),
             "stab_error_string": (ctypes.c_char_p, [i32]),
             "stab_last_cuda_error": (i32, []),

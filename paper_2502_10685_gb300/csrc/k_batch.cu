@@ -104,8 +104,8 @@ size_t batch_smem_bytes(int max_n_in_smem) {
 int batch_threads() { return kBatchThreads; }
 
 cudaError_t batch_occupancy(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    static SmemLimit lim;
+    cudaError_t e = raise_smem_limit(k_batch, smem, lim);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_batch, kBatchThreads,
                                                          smem);

@@ -55,12 +55,9 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode_rho(const double *__r
 
 cudaError_t launch_decode_rho(const double *r, int n, double *rho, cudaStream_t st) {
     const size_t smem = 2 * (sizeof(double) << n);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_decode_rho,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    static SmemLimit lim;
+    cudaError_t e = raise_smem_limit(k_decode_rho, smem, lim);
+    if (e != cudaSuccess) return e;
     k_decode_rho<<<1u << n, kDecodeThreads, smem, st>>>(r, n, rho);
     return cudaGetLastError();
 }

@@ -72,6 +72,33 @@ __global__ void __launch_bounds__(SCfg<N, LPG>::T) k_resident_stream(StreamArgs 
     }
 }
 
+// Generators through a transfer matrix: out[k] = T a[k] for k < n_vec, with
+// column j of T (T + j E) the image of the basis string j.  One CTA per vector,
+// one output entry per thread, the sum over j in order.
+// out_k = T a_k.  One CTA per 32 consecutive outputs i of one vector k: lane
+// = output (each row j of T is read coalesced), warp w sums the rows j = w,
+// w + 8, ...; the eight partial sums are added in a fixed order.
+__global__ void __launch_bounds__(256) k_apply_transfer(const double *T, const double *a,
+                                                        double *out, int E) {
+    __shared__ double sa[256];
+    __shared__ double part[8][32];
+    const int k = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double *ak = a + (size_t)k * E;
+    for (int j = threadIdx.x; j < E; j += blockDim.x) sa[j] = ak[j];
+    __syncthreads();
+    const int i = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (i < E)
+        for (int j = w; j < E; j += 8) acc = fma(T[(size_t)j * E + i], sa[j], acc);
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && i < E) {
+        double t = part[0][lane];
+        for (int r = 1; r < 8; ++r) t += part[r][lane];
+        out[(size_t)k * E + i] = t;
+    }
+}
+
 // ---------------------------------------------------------------- adjoint
 
 __device__ __forceinline__ double pair_dot(int axis, double lx, double ly, double lz, double rx,
@@ -194,25 +221,12 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
     if (threadIdx.x == 0 && a.expect_out) *a.expect_out = total;
 }
 
-template <typename K>
-cudaError_t set_smem(K kernel, size_t smem, bool *configured) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) configured[dev] = true;
-    }
-    return cudaSuccess;
-}
-
 template <int N, int LPG>
 cudaError_t launch_stream_n(const StreamArgs &a, cudaStream_t s) {
     using C = SCfg<N, LPG>;
     const size_t smem = kSmemHeader + 2 * (size_t)C::E * sizeof(double);
-    static bool configured[64] = {};
-    cudaError_t e = set_smem(k_resident_stream<N, LPG>, smem, configured);
+    static SmemLimit lim;
+    cudaError_t e = raise_smem_limit(k_resident_stream<N, LPG>, smem, lim);
     if (e != cudaSuccess) return e;
     k_resident_stream<N, LPG><<<a.n_vec, C::T, smem, s>>>(a);
     return cudaGetLastError();
@@ -222,8 +236,8 @@ template <int N>
 cudaError_t launch_adjoint_stream_n(const AdjointStreamArgs &a, cudaStream_t s) {
     using C = SCfg<N, 1>;
     const size_t smem = kSmemHeader + 4 * (size_t)C::E * sizeof(double);
-    static bool configured[64] = {};
-    cudaError_t e = set_smem(k_adjoint_stream<N>, smem, configured);
+    static SmemLimit lim;
+    cudaError_t e = raise_smem_limit(k_adjoint_stream<N>, smem, lim);
     if (e != cudaSuccess) return e;
     k_adjoint_stream<N><<<1, C::T, smem, s>>>(a);
     return cudaGetLastError();
@@ -255,6 +269,15 @@ cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_
     case 6: return launch_adjoint_stream_n<6>(a, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_apply_transfer(const double *T, const double *a, double *out, int n_vec,
+                                  int n, cudaStream_t st) {
+    const int E = 1 << (2 * n);
+    if (E > 256) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((E + 31) / 32), (unsigned)n_vec);
+    k_apply_transfer<<<grid, 256, 0, st>>>(T, a, out, E);
+    return cudaGetLastError();
 }
 
 }  // namespace stab

@@ -436,12 +436,9 @@ cudaError_t launch_stream_tile(const double *src, double *dst, int n, int n_vec,
     uint64_t grid = tiles;
     if (grid > 152ull * 8ull) grid = 152ull * 8ull;
     const size_t smem = T * (sizeof(double) + sizeof(uint32_t)) + kTileStagedOps * sizeof(DevOp);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_stream_tile,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    static SmemLimit lim;
+    cudaError_t e = raise_smem_limit(k_stream_tile, smem, lim);
+    if (e != cudaSuccess) return e;
     k_stream_tile<<<(int)grid, threads, smem, st>>>(src, dst, n, n_vec, tg, ops, maps);
     return cudaGetLastError();
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -12,6 +13,29 @@ namespace stab {
 constexpr int kMaxResidentQubits = 6;   // two buffers of 4^6 doubles = 64 KiB of shared memory
 constexpr int kMaxResidentAdjoint = 6;  // four buffers of 4^6 doubles = 128 KiB
 constexpr int kRotPerGradPass = 8;      // rotations per P_WIRE pass in gradient plans
+
+// A kernel's dynamic shared-memory limit belongs to the function, not to a
+// launch: every thread and context of the process sees the same value.  It is
+// only ever raised here, under a lock, so that one thread lowering it cannot
+// fail another thread's larger launch.  One SmemLimit per kernel.
+struct SmemLimit {
+    std::mutex mu;
+    size_t set[64] = {};   // per device: the limit set so far
+};
+
+template <typename K>
+cudaError_t raise_smem_limit(K kernel, size_t smem, SmemLimit &lim) {
+    if (smem <= 48 * 1024) return cudaSuccess;   // the default limit
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(lim.mu);
+    const bool tracked = dev >= 0 && dev < 64;
+    if (tracked && lim.set[dev] >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && tracked) lim.set[dev] = smem;
+    return e;
+}
 
 struct StreamArgs {
     const Rec *stream;       // instruction stream (device), n_chunks x kChunkRecs records
@@ -103,6 +127,9 @@ cudaError_t launch_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const
 
 // Shared-memory-resident propagation, one CTA per vector (n <= kMaxResidentQubits).
 cudaError_t launch_resident_stream(int n, const StreamArgs &a, cudaStream_t st);
+// out[k] = T a[k] (k < n_vec) for 4^n x 4^n T stored by columns; n <= 4.
+cudaError_t launch_apply_transfer(const double *T, const double *a, double *out, int n_vec,
+                                  int n, cudaStream_t st);
 int resident_lanes_per_group(int n);
 
 // Streamed passes over n_vec vectors of 4^n doubles in global memory.

@@ -408,7 +408,7 @@ Rec pull_rec(const DevOp &op) {
 
 }  // namespace
 
-void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out) {
+void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out, int k0, int k1) {
     out->clear();
     StreamWriter w{out};
     // two-qubit Clifford gates waiting to be pulled, in application order
@@ -428,9 +428,10 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out) {
         w.pass(q, seg, pass_ops);
         applied.clear();
     };
-    const int np = (int)P.passes.size();
+    if (k1 < 0) k1 = (int)P.passes.size();
+    const int np = k1 - k0;
     for (int k = 0; k < np; ++k) {
-        const DevPass &p = P.passes[backward ? np - 1 - k : k];
+        const DevPass &p = P.passes[backward ? k1 - 1 - k : k0 + k];
         if (p.type == P_CLIFF) {
             for (int j = 0; j < p.n_ops; ++j) {
                 const int jj = backward ? p.n_ops - 1 - j : j;

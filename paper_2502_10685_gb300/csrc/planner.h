@@ -59,7 +59,10 @@ void clifford_tableau(int n, const stab_gate *gates, int64_t i0, int64_t i1, boo
 
 // Instruction stream of a plan for the resident kernels (see stab_internal.h):
 // forward (backward = false) or for the inverse circuit (backward = true).
-void build_stream(const HostPlan &plan, bool backward, std::vector<Rec> *out);
+// With k1 >= 0 only passes [k0, k1) of the plan (walked backward when
+// backward is set).
+void build_stream(const HostPlan &plan, bool backward, std::vector<Rec> *out, int k0 = 0,
+                  int k1 = -1);
 
 // Signed permutation codes of the single-qubit Clifford opcodes on (X, Y, Z).
 uint32_t clifford_perm_code(int op);

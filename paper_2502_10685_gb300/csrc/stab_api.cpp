@@ -48,6 +48,9 @@ struct DevBuf {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Resident plans with at least this many passes also get split streams.
+constexpr int kSplitMinPasses = 64;
+
 // Instruction stream of a plan for the resident kernels, with the indices of
 // the records the encode kernel fills (rotations and maps).
 struct DevStreamBuf {
@@ -65,6 +68,10 @@ struct DevPlan {
     HostPlan host;
     bool streams = false;
     DevStreamBuf sf, sb;
+    // split resident streams (see split_resident): forward passes [0, split)
+    // and [split, P), backward passes [split, P); split < 0: none
+    DevStreamBuf h1, h2, h2b;
+    int split = -1;
     DevBuf buf;
     Program prog{};
     const int32_t *map_gate_idx = nullptr;
@@ -119,6 +126,13 @@ struct stab_ctx {
     DevBuf gbuf;                     // gradients written inside captured graphs
     DevBuf lam2, tmp3;               // second-branch buffers of the split sweeps
     DevBuf dotbuf;                   // partial sums of the split expectation's inner product
+    // split resident sweeps (n <= 6; see split_units): transfer matrix of the
+    // second part (n <= 4), first-part generators, meeting vectors, basis
+    // terms, batch units (generators; expectation), unit counters
+    DevBuf tmat, avec, rmid, lmid, bterms, units_g, units_e, cnt;
+    std::vector<const void *> key_g, key_e;
+    int n_units_g = 0;
+    size_t split_smem = 0;
     DevBuf status;                   // int32 set by kernels whose bounded waits gave up
     GraphCache g_gens, g_expect, g_grad; // streamed launch sequences (n > resident sizes)
     int64_t plan_gen = 0;            // bumped whenever a plan is rebuilt
@@ -209,8 +223,11 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     const size_t b_sfe = align256(P.sf.enc.size() * sizeof(int32_t));
     const size_t b_sb = align256(P.sb.host.size() * sizeof(Rec));
     const size_t b_sbe = align256(P.sb.enc.size() * sizeof(int32_t));
+    size_t b_split = 0;
+    for (const DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b})
+        b_split += align256(S->host.size() * sizeof(Rec)) + align256(S->enc.size() * 4);
     const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot + b_tabs +
-                         b_sf + b_sfe + b_sb + b_sbe;
+                         b_sf + b_sfe + b_sb + b_sbe + b_split;
     RC(c->dalloc(P.buf, total, c->st));
     CK(cudaEventSynchronize(c->ev_stage));
     RC(c->host_stage(c->stage, c->stage_bytes, total));
@@ -235,6 +252,12 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     P.sf.enc_dev = (const int32_t *)put(P.sf.enc.data(), P.sf.enc.size() * 4, b_sfe);
     P.sb.dev = (Rec *)put(P.sb.host.data(), P.sb.host.size() * sizeof(Rec), b_sb);
     P.sb.enc_dev = (const int32_t *)put(P.sb.enc.data(), P.sb.enc.size() * 4, b_sbe);
+    for (DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b}) {
+        S->dev = (Rec *)put(S->host.data(), S->host.size() * sizeof(Rec),
+                            align256(S->host.size() * sizeof(Rec)));
+        S->enc_dev = (const int32_t *)put(S->enc.data(), S->enc.size() * 4,
+                                          align256(S->enc.size() * 4));
+    }
     P.prog.n_passes = (int32_t)n_pass;
     P.prog.n_ops = (int32_t)n_ops;
     CK(cudaMemcpyAsync(P.buf.p, h, total, cudaMemcpyHostToDevice, c->st));
@@ -249,7 +272,7 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
     const double *th = (const double *)c->thetas.p;
     if (P.streams) {
         // resident plans: only the instruction streams are read by kernels
-        for (DevStreamBuf *S : {&P.sf, &P.sb}) {
+        for (DevStreamBuf *S : {&P.sf, &P.sb, &P.h1, &P.h2, &P.h2b}) {
             if (S->enc.empty()) continue;
             CK(launch_encode_stream(S->dev, S->enc_dev, (int)S->enc.size(), P.prog.maps,
                                     P.map_gate_idx, P.raw, th, c->st));
@@ -270,6 +293,17 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
     return STAB_OK;
 }
 
+void make_stream_range(const DevPlan &P, DevStreamBuf &S, bool backward, int k0, int k1) {
+    build_stream(P.host, backward, &S.host, k0, k1);
+    S.enc.clear();
+    for (size_t i = 0; i < S.host.size(); ++i) {
+        const uint8_t k = S.host[i].kind;
+        if (k == R_ROT || k == R_MAP3) S.enc.push_back((int32_t)i);
+        if (k == R_MAP3) i += 3;   // its data records are not kinds
+    }
+    S.n_chunks = (int)(S.host.size() / kChunkRecs);
+}
+
 void make_stream(DevPlan &P, bool backward) {
     DevStreamBuf &S = backward ? P.sb : P.sf;
     build_stream(P.host, backward, &S.host);
@@ -282,18 +316,34 @@ void make_stream(DevPlan &P, bool backward) {
     S.n_chunks = (int)(S.host.size() / kChunkRecs);
 }
 
-// Forward and backward streams, built concurrently on two host threads.
-void make_streams(DevPlan &P) {
+// Forward and backward streams, built concurrently on two host threads; with
+// split_frac > 0 (and enough passes) also the split streams cut at that
+// fraction of the passes.
+void make_streams(DevPlan &P, double split_frac = 0.0) {
     P.streams = true;
+    const int np = (int)P.host.passes.size();
+    P.split = (split_frac > 0.0 && np >= kSplitMinPasses) ? (int)(np * split_frac) : -1;
     std::thread bwd([&P] { make_stream(P, true); });
+    std::thread halves([&P, np] {
+        if (P.split < 0) {
+            P.h1 = P.h2 = P.h2b = DevStreamBuf();
+            return;
+        }
+        make_stream_range(P, P.h1, false, 0, P.split);
+        make_stream_range(P, P.h2, false, P.split, np);
+        make_stream_range(P, P.h2b, true, P.split, np);
+    });
     make_stream(P, false);
     bwd.join();
+    halves.join();
 }
 
 void no_streams(DevPlan &P) {
     P.streams = false;
     P.sf = DevStreamBuf();
     P.sb = DevStreamBuf();
+    P.h1 = P.h2 = P.h2b = DevStreamBuf();
+    P.split = -1;
 }
 
 // Reads and clears the kernels' status word (synchronizes the context).
@@ -397,6 +447,114 @@ void make_tile_group(int n, int n_vec, const std::vector<const DevPass *> &group
     }
     bit_runs(tile, &tg->tile_runs);
     bit_runs(rest, &tg->rest_runs);
+}
+
+// ---------------------------------------------------------------- split resident sweeps
+//
+// A resident vector walks the circuit's passes one after another on one SM.
+// With the passes cut at `split` (DevPlan h1 = [0, split), h2 = [split, P)):
+//   generators (n <= 4): U Z_k U^dagger = T a_k with a_k = Z_k through h1 and
+//     T the transfer matrix of h2, whose 4^n - 1 nontrivial columns are the
+//     basis strings through h2 -- 4^n - 1 + n independent vectors, one batch
+//     launch, then one product;
+//   <O> = <lambda, r> with r = rho_0 through h1 and lambda = O backward through
+//     h2 -- two vectors at once, then one inner product.
+// Every part runs on its own CTA of the persistent batch kernel.
+
+bool split_gens_ok(const stab_ctx *c) { return c->fwd.split >= 0 && c->n <= 4; }
+bool split_expect_ok(const stab_ctx *c) { return c->fwd.split >= 0; }
+
+int split_setup(stab_ctx *c, cudaStream_t s) {
+    if (c->split_smem == 0) {
+        c->split_smem = batch_smem_bytes(c->n);
+        int occ = 0;
+        CK(batch_occupancy(c->split_smem, &occ));
+    }
+    const int E = 1 << (2 * c->n);
+    RC(c->dalloc(c->cnt, 256, s));
+    RC(c->dalloc(c->rmid, (size_t)E * 8, s));
+    RC(c->dalloc(c->lmid, (size_t)E * 8, s));
+    RC(c->dalloc(c->dotbuf, 256 * sizeof(double), s));
+    return STAB_OK;
+}
+
+// Units of the generators' split sweep (rebuilt when the plan changes).
+int split_units_g(stab_ctx *c) {
+    const int n = c->n, E = 1 << (2 * n);
+    RC(split_setup(c, c->st));
+    RC(c->dalloc(c->tmat, (size_t)E * E * 8, c->st));
+    RC(c->dalloc(c->avec, (size_t)n * E * 8, c->st));
+    RC(c->dalloc(c->bterms, (size_t)E * sizeof(DevTerm), c->st));
+    RC(c->dalloc(c->units_g, (size_t)(E - 1 + n) * sizeof(BatchUnit), c->st));
+    const std::vector<const void *> key = {(const void *)c->plan_gen, c->fwd.h1.dev,
+                                           c->fwd.h2.dev, c->tmat.p, c->avec.p, c->bterms.p,
+                                           c->units_g.p};
+    if (key == c->key_g) return STAB_OK;
+    std::vector<BatchUnit> U;
+    for (int k = 0; k < n; ++k) {
+        BatchUnit u{};
+        u.stream = c->fwd.h1.dev;
+        u.n_chunks = c->fwd.h1.n_chunks;
+        u.n = (int8_t)n;
+        u.init = INIT_GENERATOR;
+        u.gen = (int16_t)k;
+        u.out = (double *)c->avec.p + (size_t)k * E;
+        U.push_back(u);
+    }
+    std::vector<DevTerm> basis((size_t)E);
+    for (int j = 1; j < E; ++j) {
+        basis[(size_t)j] = DevTerm{1.0, (uint64_t)j};
+        BatchUnit u{};
+        u.stream = c->fwd.h2.dev;
+        u.n_chunks = c->fwd.h2.n_chunks;
+        u.n = (int8_t)n;
+        u.init = INIT_TERMS;
+        u.terms = (const DevTerm *)c->bterms.p + j;
+        u.n_terms = 1;
+        u.out = (double *)c->tmat.p + (size_t)j * E;
+        U.push_back(u);
+    }
+    // column 0 of T: the identity string stays itself
+    CK(cudaMemsetAsync(c->tmat.p, 0, (size_t)E * 8, c->st));
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(c->tmat.p, &one, 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->bterms.p, basis.data(), basis.size() * sizeof(DevTerm),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->units_g.p, U.data(), U.size() * sizeof(BatchUnit),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));   // the host vectors above are temporaries
+    c->n_units_g = (int)U.size();
+    c->key_g = key;
+    return STAB_OK;
+}
+
+// Units of the expectation's split sweep on stream s (rebuilt when the plan
+// or the observable's device terms change).
+int split_units_e(stab_ctx *c, cudaStream_t s) {
+    RC(split_setup(c, s));
+    RC(c->dalloc(c->units_e, 2 * sizeof(BatchUnit), s));
+    const int32_t nt = c->n_obs_terms;
+    const std::vector<const void *> key = {(const void *)c->plan_gen, c->fwd.h1.dev,
+                                           c->fwd.h2b.dev, c->terms.p, (const void *)(intptr_t)nt,
+                                           c->rmid.p, c->lmid.p, c->units_e.p};
+    if (key == c->key_e) return STAB_OK;
+    BatchUnit U[2] = {};
+    U[0].stream = c->fwd.h1.dev;
+    U[0].n_chunks = c->fwd.h1.n_chunks;
+    U[0].n = (int8_t)c->n;
+    U[0].init = INIT_RHO0;
+    U[0].out = (double *)c->rmid.p;
+    U[1].stream = c->fwd.h2b.dev;
+    U[1].n_chunks = c->fwd.h2b.n_chunks;
+    U[1].n = (int8_t)c->n;
+    U[1].init = INIT_TERMS;
+    U[1].terms = (const DevTerm *)c->terms.p;
+    U[1].n_terms = nt;
+    U[1].out = (double *)c->lmid.p;
+    CK(cudaMemcpyAsync(c->units_e.p, U, sizeof(U), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    c->key_e = key;
+    return STAB_OK;
 }
 
 // Streamed propagation of n_vec vectors through a plan; *cur / *alt are the
@@ -654,7 +812,8 @@ int stab_destroy(stab_ctx *c) {
     DevBuf *bufs[] = {&c->fwd.buf, &c->grad.buf, &c->thetas, &c->gens, &c->gens_tmp, &c->lam,
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
                       &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3,
-                      &c->dotbuf};
+                      &c->dotbuf, &c->tmat, &c->avec, &c->rmid, &c->lmid, &c->bterms,
+                      &c->units_g, &c->units_e, &c->cnt};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -688,7 +847,15 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
     c->grad.encoded = false;
     reset_graphs(c);
     build_plan(c->n, gates, m, n_params, c->fwd_mode(), &c->fwd.host, !c->use_resident());
-    if (c->use_resident()) make_streams(c->fwd);
+    if (c->use_resident()) {
+        // split streams for the resident sweeps: generators through the
+        // transfer matrix of the second part (n <= 4), expectations meeting in
+        // the middle.  Cut at half the passes: a pass is latency-bound, so the
+        // 4^n - 1 transfer-matrix units run as fast as the n first-part units
+        // even where two of them share an SM.
+        const bool split = c->kernel == STAB_KERNEL_AUTO && c->fuse;
+        make_streams(c->fwd, split ? 0.5 : 0.0);
+    }
     else no_streams(c->fwd);
     RC(upload_thetas_host(c, thetas));
     RC(upload_plan(c, c->fwd));
@@ -726,7 +893,20 @@ int stab_run_generators(stab_ctx *c) {
     const int n = c->n;
     const size_t bytes = c->vec_bytes() * (size_t)n;
     RC(c->dalloc(c->gens, bytes, c->st));
-    if (c->use_resident()) {
+    if (c->use_resident() && split_gens_ok(c)) {
+        RC(split_units_g(c));
+        BatchArgs a{};
+        a.units = (const BatchUnit *)c->units_g.p;
+        a.n_units = c->n_units_g;
+        a.counter = (int32_t *)c->cnt.p;
+        a.status = (int32_t *)c->status.p;
+        CK(cudaMemsetAsync(c->cnt.p, 0, 4, c->st));
+        CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
+        CK(launch_apply_transfer((const double *)c->tmat.p, (const double *)c->avec.p,
+                                 (double *)c->gens.p, n, n, c->st));
+        c->launches += 2;
+        c->gens_cur = (double *)c->gens.p;
+    } else if (c->use_resident()) {
         StreamArgs a{};
         a.stream = c->fwd.sf.dev;
         a.n_chunks = c->fwd.sf.n_chunks;
@@ -803,7 +983,19 @@ int stab_expect_async(stab_ctx *c, double *out_dev) {
     cudaStream_t s = c->aux;
     CK(cudaStreamWaitEvent(s, c->ev_ready, 0));
     const int32_t nt = c->n_obs_terms;
-    if (c->use_resident()) {
+    if (c->use_resident() && split_expect_ok(c)) {
+        RC(split_units_e(c, s));
+        BatchArgs a{};
+        a.units = (const BatchUnit *)c->units_e.p;
+        a.n_units = 2;
+        a.counter = (int32_t *)c->cnt.p + 16;
+        a.status = (int32_t *)c->status.p;
+        CK(cudaMemsetAsync((int32_t *)c->cnt.p + 16, 0, 4, s));
+        CK(launch_batch(a, 2, c->split_smem, s));
+        CK(launch_dot((const double *)c->lmid.p, (const double *)c->rmid.p, c->n,
+                      (double *)c->dotbuf.p, out_dev, s));
+        c->launches += 3;
+    } else if (c->use_resident()) {
         StreamArgs a{};
         a.stream = c->fwd.sb.dev;
         a.n_chunks = c->fwd.sb.n_chunks;
@@ -1163,6 +1355,16 @@ int stab_plan_info(stab_ctx *c, int64_t *n_gates, int64_t *n_passes, int32_t *ke
     if (n_gates) *n_gates = (int64_t)c->gates.size();
     if (n_passes) *n_passes = (int64_t)c->fwd.host.passes.size();
     if (kernel) *kernel = c->use_resident() ? STAB_KERNEL_RESIDENT : STAB_KERNEL_STREAMED;
+    return STAB_OK;
+}
+
+int stab_split_info(stab_ctx *c, int64_t *cut, int32_t *gen_units, int32_t *expect_units) {
+    if (!c) return STAB_E_INVAL;
+    const bool on = c->loaded && c->use_resident() && c->fwd.split >= 0;
+    const int E = 1 << (2 * c->n);
+    if (cut) *cut = on ? c->fwd.split : -1;
+    if (gen_units) *gen_units = on && split_gens_ok(c) ? c->n + E - 1 : 0;
+    if (expect_units) *expect_units = on && split_expect_ok(c) ? 2 : 0;
     return STAB_OK;
 }
 

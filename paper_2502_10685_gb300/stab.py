@@ -172,6 +172,14 @@ def stab_plan_info(h) -> Tuple[int, int, int]:
     return a.value, b.value, k.value
 
 
+def stab_split_info(h) -> Tuple[int, int, int]:
+    """(cut, generator units, expectation units) of the split sweeps; cut -1: none."""
+    a, g, e = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    check(_lib.load().stab_split_info(h, ctypes.byref(a), ctypes.byref(g), ctypes.byref(e)),
+          "stab_split_info")
+    return a.value, g.value, e.value
+
+
 def stab_launch_count(h) -> int:
     return int(_lib.load().stab_launch_count(h))
 
@@ -291,6 +299,9 @@ class Stab:
 
     def plan_info(self):
         return stab_plan_info(self.h)
+
+    def split_info(self):
+        return stab_split_info(self.h)
 
     def launch_count(self) -> int:
         return stab_launch_count(self.h)

@@ -132,3 +132,25 @@ def test_server_small_and_large_requests_mixed(stab):
         ref = oracle.expect(c.n, c.gates, c.thetas, obs) if c.n <= 6 else None
         if ref is not None:
             assert abs(r["expect"] - ref) <= 1e-12 * sum(abs(a) for a, _ in obs)
+
+
+def test_contexts_of_different_sizes_interleaved(stab):
+    # The persistent batch kernel serves contexts of every n <= 6 with a
+    # shared-memory size of its own; a small context set up after a large one
+    # must not shrink the large one's launch limit.
+    ctxs = []
+    for n in (6, 2, 5, 3):
+        c = W.layered_ansatz(n, 400, seed=40 + n)
+        s = stab.Stab(n)
+        s.load_circuit(c.gates, c.thetas)
+        ctxs.append((s, c))
+    for _ in range(2):
+        for s, c in ctxs:
+            obs = W.obs_chain(c.n)
+            ref = oracle.expect(c.n, c.gates, c.thetas, obs)
+            assert abs(s.expect(obs) - ref) <= 1e-12 * sum(abs(a) for a, _ in obs)
+            s.apply_circuit(c.gates, c.thetas)
+            g = layout.lib_to_paper(c.n, s.generators())
+            assert np.abs(g - oracle.generators(c.n, c.gates, c.thetas)).max() <= 1e-12
+    for s, _ in ctxs:
+        s.close()
