@@ -315,12 +315,18 @@ def run_ours(args):
         # the generators' persistent launch: n vectors through passes [0, cut)
         # and the 4^n - 1 transfer-matrix columns through [cut, P), then one
         # product; FP64 work executed per algorithmic flop, counted in passes
-        kernel = "k_batch (split: %d units) + k_apply_transfer" % gen_units
+        if c.n == 4:
+            kernel = ("k_transfer_cols (255 columns, 2 per CTA) + k_batch (%d first-part "
+                      "units) + k_apply_transfer" % c.n)
+        else:
+            kernel = "k_batch (split: %d units) + k_apply_transfer" % gen_units
         executed = (c.n * cut + (4 ** c.n - 1) * (n_passes - cut)) / (c.n * n_passes)
-        active_sms = min(SMS, gen_units)
+        active_sms = min(SMS, c.n + 128 if c.n == 4 else gen_units)
         note = ("one circuit: the generators split at pass %d of %d; the n first-part "
-                "vectors and the 4^n-1 basis columns run at once, one CTA each; passes "
-                "are sequential within a unit" % (cut, n_passes))
+                "vectors and the 4^n-1 basis columns run at once (%s); passes are "
+                "sequential within a vector" % (cut, n_passes,
+                                                 "two columns per CTA" if c.n == 4
+                                                 else "one CTA each"))
     else:
         kernel = "k_resident_stream (generators)"
         executed = 1.0
@@ -328,10 +334,10 @@ def run_ours(args):
         note = "one circuit: n independent vectors, one CTA each; passes are sequential"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                # DRAM bytes of the generators' k_batch launch from one ncu capture
-                # of this workload (3,198,208 B read: the two staged half-streams;
-                # 0 B written); see profiles/
-                "traffic": 3198208.0 if (gen_units and c.n == 4 and c.m == 60200) else None,
+                # DRAM bytes of the generator phase's two launches from one ncu
+                # capture of this workload (k_batch 1,795,840 + k_transfer_cols
+                # 1,592,832 B read, the staged half-streams; 0 B written)
+                "traffic": 3388672.0 if (c.n == 4 and c.m == 60200) else None,
                 "kernel": kernel, "launch_ms": gen_avg_s * 1e3,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock",
                 "active_sms": active_sms,

@@ -64,7 +64,9 @@ __device__ void batch_unit(const BatchUnit &U, Stager &st, unsigned char *smem, 
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a) {
+// At least four CTAs per SM: with the thread bound alone ptxas settled on 48
+// registers and spilled inside the pass loop; 4 gives 62 and no spills.
+__global__ void __launch_bounds__(kBatchThreads, 4) k_batch(BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_unit;
     Stager st;

@@ -99,6 +99,100 @@ __global__ void __launch_bounds__(256) k_apply_transfer(const double *T, const d
     }
 }
 
+// ---------------------------------------------------------------- transfer columns
+//
+// Columns of the transfer matrix T of a stream at n = 4: column j is the
+// basis string j carried through the stream's passes.  One CTA of 16 warps
+// carries two columns; each half (8 warps) owns one column, its own copy of
+// the staged stream and a named barrier, so the halves run independently and
+// one's loads and barriers overlap the other's FP64 work, as two CTAs on an
+// SM would.  For a pass on wire q the warp index holds the wire's (x_q, z_q)
+// bits and the lane plus warp bit 0 the other six index bits, so the two warps
+// of the I slot do no FP64 work (those entries do not change) and the other
+// six compute one output row each from the group's X, Y, Z entries.  The
+// halves use mirrored slot maps: warp w = 8v + 4 b2 + 2 b1 + b0 runs on SMSP
+// w % 4 and holds slot (x, z) = (b1 ^ v, b2), so each SMSP has three working
+// warps -- nine warp-wide FP64 instructions per pass for both columns, where
+// two CTAs of the lane-per-entry form issue twelve.
+constexpr int kColThreads = 512;
+constexpr int kColN = 4;
+constexpr int kColE = 1 << (2 * kColN);
+constexpr int kColHalf = (kOffRed + 127) / 128 * 128;   // one half's chunks + barriers
+
+__global__ void __launch_bounds__(kColThreads, 1) k_transfer_cols(const Rec *stream,
+                                                                   int n_chunks, double *tmat,
+                                                                   int32_t *status) {
+    constexpr int N = kColN, E = kColE;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int w = threadIdx.x >> 5;
+    const int v = w >> 3;                             // this half's column
+    const int col = 1 + 2 * (int)blockIdx.x + v;
+    if (col >= E) return;                             // odd column count: the last half idles
+    const uint32_t tid = threadIdx.x & 255u;
+    const uint32_t bar = 1u + (uint32_t)v;
+    Stager st;
+    stager_setup(st, smem + v * kColHalf);
+    st.lead = (uint32_t)v * 256u;
+    st.bar_id = bar;
+    st.bar_n = 256;
+    st.s0 = stream;
+    st.s1 = nullptr;
+    st.n0 = n_chunks;
+    st.n_total = n_chunks;
+    double *cur = reinterpret_cast<double *>(smem + 2 * kColHalf) + v * 2 * E;
+    double *nxt = cur + E;
+    for (uint32_t i = tid; i < (uint32_t)E; i += 256u) cur[i] = (i == (uint32_t)col) ? 1.0 : 0.0;
+    st.start();   // barrier of the half inside
+    const uint32_t sx = (uint32_t)(((w >> 1) & 1) ^ v), sz = (uint32_t)((w >> 2) & 1);
+    const uint32_t g = (threadIdx.x & 31u) | ((uint32_t)(w & 1) << 5);
+    const bool work = (sx | sz) != 0u;
+    // slot 1 = X, 2 = Y, 3 = Z: row slot - 1 of the composed map
+    const uint32_t slot = sx ? (sz ? 2u : 1u) : 3u;
+    for (int c = 0; c < n_chunks; ++c) {
+        if (!st.wait(c, status)) return;
+        const Rec *Rr = st.chunk(c);
+        int r = 0;
+        Rec h = Rr[0];
+        while (h.kind == R_PASS) {
+            const int q = h.q, n_pull = h.param;
+            const uint32_t base = group_base32(g, N, q);
+            const uint32_t i = base | (sz << q) | (sx << (N + q));
+            if (n_pull > 0) {
+                // the pass's reads go through the preceding Clifford run
+                uint32_t neg = 0;
+                const uint32_t j = pull_recs(i, N, Rr + r + 1, n_pull, neg);
+                nxt[i] = flip(cur[j], neg);
+                double *t = cur;
+                cur = nxt;
+                nxt = t;
+                named_sync(bar, 256);
+            }
+            if (h.gate != 0) {
+                double out;
+                if (work) {
+                    const double x = cur[base | (1u << (N + q))];
+                    const double y = cur[base | (1u << q) | (1u << (N + q))];
+                    const double z = cur[base | (1u << q)];
+                    const double *m =
+                        reinterpret_cast<const double *>(Rr + r + 2 + n_pull) + 3 * (slot - 1u);
+                    out = fma(m[2], z, fma(m[1], y, m[0] * x));
+                } else {
+                    out = cur[i];
+                }
+                nxt[i] = out;
+                double *t = cur;
+                cur = nxt;
+                nxt = t;
+                named_sync(bar, 256);
+            }
+            r += 1 + n_pull + h.gate;
+            h = Rr[r];
+        }
+        st.release(c);
+    }
+    for (uint32_t i = tid; i < (uint32_t)E; i += 256u) tmat[(size_t)col * E + i] = cur[i];
+}
+
 // ---------------------------------------------------------------- adjoint
 
 __device__ __forceinline__ double pair_dot(int axis, double lx, double ly, double lz, double rx,
@@ -269,6 +363,22 @@ cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_
     case 6: return launch_adjoint_stream_n<6>(a, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+int transfer_cols_ctas(int n) { return n == kColN ? kColE / 2 : 0; }
+
+cudaError_t launch_transfer_cols(const Rec *stream, int n_chunks, double *tmat, int n,
+                                 int32_t *status, cudaStream_t st) {
+    if (n != kColN) return cudaErrorInvalidValue;
+    // more than half an SM's shared memory, so two of these CTAs never share
+    // an SM (the kernel needs two halves' chunks and barriers + 8 KiB)
+    const size_t smem = 116 * 1024;
+    static_assert(2 * kColHalf + 4 * kColE * sizeof(double) <= 116 * 1024, "column buffers");
+    static SmemLimit lim;
+    cudaError_t e = raise_smem_limit(k_transfer_cols, smem, lim);
+    if (e != cudaSuccess) return e;
+    k_transfer_cols<<<kColE / 2, kColThreads, smem, st>>>(stream, n_chunks, tmat, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_apply_transfer(const double *T, const double *a, double *out, int n_vec,

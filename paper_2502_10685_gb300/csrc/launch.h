@@ -128,6 +128,12 @@ cudaError_t launch_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const
 // Shared-memory-resident propagation, one CTA per vector (n <= kMaxResidentQubits).
 cudaError_t launch_resident_stream(int n, const StreamArgs &a, cudaStream_t st);
 // out[k] = T a[k] (k < n_vec) for 4^n x 4^n T stored by columns; n <= 4.
+// Columns 1 .. 4^n - 1 of the transfer matrix of a stream (column j = basis
+// string j through its passes) into tmat (column j at tmat + j * 4^n), two
+// columns per CTA; n = 4 only.  transfer_cols_ctas(n): its grid (0: n unsupported).
+int transfer_cols_ctas(int n);
+cudaError_t launch_transfer_cols(const Rec *stream, int n_chunks, double *tmat, int n,
+                                 int32_t *status, cudaStream_t st);
 cudaError_t launch_apply_transfer(const double *T, const double *a, double *out, int n_vec,
                                   int n, cudaStream_t st);
 int resident_lanes_per_group(int n);

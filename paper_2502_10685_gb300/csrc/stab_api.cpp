@@ -459,7 +459,9 @@ void make_tile_group(int n, int n_vec, const std::vector<const DevPass *> &group
 //     launch, then one product;
 //   <O> = <lambda, r> with r = rho_0 through h1 and lambda = O backward through
 //     h2 -- two vectors at once, then one inner product.
-// Every part runs on its own CTA of the persistent batch kernel.
+// Every part runs on its own CTA of the persistent batch kernel, except the
+// columns of T at n = 4 (255 of them, more than the SMs): k_transfer_cols
+// carries them two to a CTA.
 
 bool split_gens_ok(const stab_ctx *c) { return c->fwd.split >= 0 && c->n <= 4; }
 bool split_expect_ok(const stab_ctx *c) { return c->fwd.split >= 0; }
@@ -501,8 +503,11 @@ int split_units_g(stab_ctx *c) {
         u.out = (double *)c->avec.p + (size_t)k * E;
         U.push_back(u);
     }
+    // the columns of T: units of the same launch, or (n = 4, where they would
+    // outnumber the SMs) the two-column CTAs of k_transfer_cols
+    const int n_basis = transfer_cols_ctas(n) > 0 ? 1 : E;
     std::vector<DevTerm> basis((size_t)E);
-    for (int j = 1; j < E; ++j) {
+    for (int j = 1; j < n_basis; ++j) {
         basis[(size_t)j] = DevTerm{1.0, (uint64_t)j};
         BatchUnit u{};
         u.stream = c->fwd.h2.dev;
@@ -850,11 +855,13 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
     if (c->use_resident()) {
         // split streams for the resident sweeps: generators through the
         // transfer matrix of the second part (n <= 4), expectations meeting in
-        // the middle.  Cut at half the passes: a pass is latency-bound, so the
-        // 4^n - 1 transfer-matrix units run as fast as the n first-part units
-        // even where two of them share an SM.
+        // the middle.  The cut balances the two parts' pass times: at half the
+        // passes for n <= 3 (every unit has an SM to itself); at n = 4, where
+        // k_transfer_cols takes ~780 cycles per pass against ~610 for a
+        // first-part unit alone on its SM, at 0.56 (measured optimum).
         const bool split = c->kernel == STAB_KERNEL_AUTO && c->fuse;
-        make_streams(c->fwd, split ? 0.5 : 0.0);
+        const double cut = transfer_cols_ctas(c->n) > 0 ? 0.56 : 0.5;
+        make_streams(c->fwd, split ? cut : 0.0);
     }
     else no_streams(c->fwd);
     RC(upload_thetas_host(c, thetas));
@@ -901,7 +908,19 @@ int stab_run_generators(stab_ctx *c) {
         a.counter = (int32_t *)c->cnt.p;
         a.status = (int32_t *)c->status.p;
         CK(cudaMemsetAsync(c->cnt.p, 0, 4, c->st));
-        CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
+        if (transfer_cols_ctas(n) > 0) {
+            // the n first-part units and the columns of T at once, on two streams
+            CK(cudaEventRecord(c->ev_fork, c->st));
+            CK(cudaStreamWaitEvent(c->aux2, c->ev_fork, 0));
+            CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
+            CK(launch_transfer_cols(c->fwd.h2.dev, c->fwd.h2.n_chunks, (double *)c->tmat.p, n,
+                                    (int32_t *)c->status.p, c->aux2));
+            CK(cudaEventRecord(c->ev_join, c->aux2));
+            CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
+            c->launches++;
+        } else {
+            CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
+        }
         CK(launch_apply_transfer((const double *)c->tmat.p, (const double *)c->avec.p,
                                  (double *)c->gens.p, n, n, c->st));
         c->launches += 2;

@@ -66,9 +66,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Named barrier over `count` threads (ids 1 .. 15; 0 is __syncthreads).
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // Two-buffer stager of a sequence of instruction chunks taken from up to two
-// streams (chunk c < n0 from s0, else from s1).  Thread 0 issues the copies
-// and waits; the others learn the outcome through `flag` after a barrier.
+// streams (chunk c < n0 from s0, else from s1).  The lead thread issues the
+// copies and waits; the others learn the outcome through `flag` after a
+// barrier.  By default the stager serves the whole CTA (thread 0, CTA
+// barrier); a part of a CTA that runs on its own sets lead / bar_id / bar_n
+// (its first thread, a named barrier over its threads).
 struct Stager {
     const Rec *s0, *s1;
     int n0, n_total;
@@ -76,6 +84,13 @@ struct Stager {
     uint64_t *bar;     // 2 mbarriers in shared memory
     int *flag;         // shared flag: 1 = chunk ready, 0 = gave up
     uint32_t ph0 = 0, ph1 = 0;   // phases each barrier completed before this sequence
+    uint32_t lead = 0, bar_id = 0, bar_n = 0;
+
+    __device__ bool is_lead() const { return threadIdx.x == lead; }
+    __device__ void sync() const {
+        if (bar_n) named_sync(bar_id, bar_n);
+        else __syncthreads();
+    }
 
     __device__ uint32_t parity(int c) const {
         return ((c & 1 ? ph1 : ph0) + (uint32_t)(c >> 1)) & 1u;
@@ -88,11 +103,11 @@ struct Stager {
     // Later sequences on the same barriers (persistent kernels): issue the
     // first chunks without re-initialising the barriers.
     __device__ void restart() {
-        if (threadIdx.x == 0) {
+        if (is_lead()) {
             if (n_total > 0) issue(0);
             if (n_total > 1) issue(1);
         }
-        __syncthreads();
+        sync();
     }
 
     __device__ const Rec *src(int c) const {
@@ -105,19 +120,19 @@ struct Stager {
     }
     // Called by all threads once, before any wait.
     __device__ void start() {
-        if (threadIdx.x == 0) {
+        if (is_lead()) {
             mbar_init(bar, 1);
             mbar_init(bar + 1, 1);
             mbar_fence_init();
             if (n_total > 0) issue(0);
             if (n_total > 1) issue(1);
         }
-        __syncthreads();
+        sync();
     }
     // All threads: wait until chunk c is in buf[c & 1].  Returns false (for
     // every thread) when the bounded wait gave up; *status is then set.
     __device__ bool wait(int c, int32_t *status) {
-        if (threadIdx.x == 0) {
+        if (is_lead()) {
             bool ok = mbar_wait_bounded(bar + (c & 1), parity(c));
             *flag = ok ? 1 : 0;
             if (!ok) {
@@ -127,13 +142,13 @@ struct Stager {
                 if (c + 1 < n_total) mbar_wait_bounded(bar + ((c + 1) & 1), parity(c + 1));
             }
         }
-        __syncthreads();
+        sync();
         return *flag != 0;
     }
     // All threads, after their last read of buf[c & 1]: refill it with c + 2.
     __device__ void release(int c) {
-        __syncthreads();
-        if (threadIdx.x == 0 && c + 2 < n_total) {
+        sync();
+        if (is_lead() && c + 2 < n_total) {
             fence_proxy_async_smem();
             issue(c + 2);
         }
