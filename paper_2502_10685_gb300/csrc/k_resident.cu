@@ -204,38 +204,25 @@ __device__ __forceinline__ double pair_dot(int axis, double lx, double ly, doubl
     return fma(ly, rx, -lx * ry);
 }
 
+// The pair (lambda, rho) through chunks [c0, c1) of a gradient stream, with
+// each rotation's dot <lambda_j, G_j rho_j> taken at its post-gate pair (G_j
+// the generator of the rotation on its pairs) and written to grad_rot at the
+// rotation's ordinal.  fwd = false: a backward stream -- the pair holds the
+// post-gate values when an inverse op comes up, so dot, then apply; fwd =
+// true: a forward stream (lambda_j = M_j lambda_{j-1} because every map is
+// orthogonal) -- apply, then dot.  On return lam / rho point at the results;
+// false when a staging wait gave up.
 template <int N>
-__global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamArgs a) {
+__device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double *&lam,
+                                              double *&lam_n, double *&rho, double *&rho_n,
+                                              double *grad_rot, int32_t *status,
+                                              unsigned char *smem, const bool fwd) {
     using C = SCfg<N, 1>;
-    extern __shared__ __align__(128) unsigned char smem[];
-    Stager st;
-    st.s0 = a.fwd;
-    st.s1 = a.bwd;
-    st.n0 = a.n_fwd_chunks;
-    st.n_total = a.n_fwd_chunks + a.n_bwd_chunks;
-    stager_setup(st, smem);
     int *gslot = reinterpret_cast<int *>(smem + kOffSlot);
     double *red = reinterpret_cast<double *>(smem + kOffRed);
-    double *rA = reinterpret_cast<double *>(smem + kSmemHeader);
-    double *rB = rA + C::E, *lA = rB + C::E, *lB = lA + C::E;
-    st.start();
-    for (int i = threadIdx.x; i < C::E; i += C::T) {
-        rA[i] = i < (1 << N) ? 1.0 : 0.0;
-        lA[i] = 0.0;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < a.n_terms; k += C::T) lA[a.terms[k].idx] = a.terms[k].coeff;
-    __syncthreads();
-
-    // forward: r_m = M_m ... M_1 rho_0
-    double *rho = run_stream<N, 1>(st, 0, a.n_fwd_chunks, rA, rB, a.status);
-    if (rho == nullptr) return;
-    double *rho_n = rho == rA ? rB : rA;
-    double *lam = lA, *lam_n = lB;
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int c = a.n_fwd_chunks; c < st.n_total; ++c) {
-        if (!st.wait(c, a.status)) return;
+    for (int c = c0; c < c1; ++c) {
+        if (!st.wait(c, status)) return false;
         const Rec *Rr = st.chunk(c);
         int r = 0;
         while (true) {
@@ -263,6 +250,10 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
                     double rz = pulled<N>(rho, iz, pulls, n_pull);
                     int slot = 0;
                     for (int j = 0; j < n_ops; ++j) {
+                        if (fwd) {
+                            apply_recs(lx, ly, lz, ops + j, 1);
+                            apply_recs(rx, ry, rz, ops + j, 1);
+                        }
                         if (ops[j].kind == R_ROT) {
                             const double d = pair_dot(ops[j].axis, lx, ly, lz, rx, ry, rz);
 #pragma unroll
@@ -270,8 +261,10 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
                                 if (s == slot) part[s] += d;
                             ++slot;
                         }
-                        apply_recs(lx, ly, lz, ops + j, 1);
-                        apply_recs(rx, ry, rz, ops + j, 1);
+                        if (!fwd) {
+                            apply_recs(lx, ly, lz, ops + j, 1);
+                            apply_recs(rx, ry, rz, ops + j, 1);
+                        }
                     }
                     lam_n[ii] = li; lam_n[ix] = lx; lam_n[iy] = ly; lam_n[iz] = lz;
                     rho_n[ii] = ri; rho_n[ix] = rx; rho_n[iy] = ry; rho_n[iz] = rz;
@@ -296,7 +289,7 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
             if (threadIdx.x < n_rot) {
                 double total = 0.0;
                 for (int w = 0; w < C::W; ++w) total += red[w * R + threadIdx.x];
-                a.grad_rot[gslot[threadIdx.x]] = total;
+                grad_rot[gslot[threadIdx.x]] = total;
             }
             double *t = lam;
             lam = lam_n;
@@ -309,6 +302,90 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
         }
         st.release(c);
     }
+    return true;
+}
+
+template <int N>
+__global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamArgs a) {
+    using C = SCfg<N, 1>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    Stager st;
+    st.s0 = a.fwd;
+    st.s1 = a.bwd;
+    st.n0 = a.n_fwd_chunks;
+    st.n_total = a.n_fwd_chunks + a.n_bwd_chunks;
+    stager_setup(st, smem);
+    double *red = reinterpret_cast<double *>(smem + kOffRed);
+    double *rA = reinterpret_cast<double *>(smem + kSmemHeader);
+    double *rB = rA + C::E, *lA = rB + C::E, *lB = lA + C::E;
+    st.start();
+    for (int i = threadIdx.x; i < C::E; i += C::T) {
+        rA[i] = i < (1 << N) ? 1.0 : 0.0;
+        lA[i] = 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.n_terms; k += C::T) lA[a.terms[k].idx] = a.terms[k].coeff;
+    __syncthreads();
+
+    // forward: r_m = M_m ... M_1 rho_0
+    double *rho = run_stream<N, 1>(st, 0, a.n_fwd_chunks, rA, rB, a.status);
+    if (rho == nullptr) return;
+    double *rho_n = rho == rA ? rB : rA;
+    double *lam = lA, *lam_n = lB;
+    if (!adjoint_sweep<N>(st, a.n_fwd_chunks, st.n_total, lam, lam_n, rho, rho_n, a.grad_rot,
+                          a.status, smem, false))
+        return;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
+    const double total = block_sum<C::T>(acc, red);
+    if (threadIdx.x == 0 && a.expect_out) *a.expect_out = total;
+}
+
+// Split adjoint, two CTAs, two launches (phase 0, then phase 1):
+//   phase 0: CTA 0 carries rho_0 forward through the first part (stream 0)
+//     into rmid, CTA 1 carries O backward through the second part (stream 1)
+//     into lmid;
+//   phase 1: both CTAs start from the pair (lmid, rmid) at the cut: CTA 0
+//     sweeps it backward through the first part (stream 0) and also writes
+//     <O> (x-free sum of lambda_0), CTA 1 forward through the second part
+//     (stream 1); each rotation's dot lands in the part that holds it.
+template <int N>
+__global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_split(AdjointSplitArgs a) {
+    using C = SCfg<N, 1>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int b = blockIdx.x;
+    Stager st;
+    st.s0 = b == 0 ? a.stream[0] : a.stream[1];
+    st.s1 = nullptr;
+    st.n0 = b == 0 ? a.n_chunks[0] : a.n_chunks[1];
+    st.n_total = st.n0;
+    stager_setup(st, smem);
+    double *red = reinterpret_cast<double *>(smem + kOffRed);
+    double *rA = reinterpret_cast<double *>(smem + kSmemHeader);
+    double *rB = rA + C::E, *lA = rB + C::E, *lB = lA + C::E;
+    st.start();
+    if (a.phase == 0) {
+        for (int i = threadIdx.x; i < C::E; i += C::T)
+            rA[i] = (b == 0 && i < (1 << N)) ? 1.0 : 0.0;
+        __syncthreads();
+        if (b == 1)
+            for (int k = threadIdx.x; k < a.n_terms; k += C::T) rA[a.terms[k].idx] = a.terms[k].coeff;
+        __syncthreads();
+        const double *v = run_stream<N, 1>(st, 0, st.n_total, rA, rB, a.status);
+        if (v == nullptr) return;
+        double *out = b == 0 ? a.rmid : a.lmid;
+        for (int i = threadIdx.x; i < C::E; i += C::T) out[i] = v[i];
+        return;
+    }
+    for (int i = threadIdx.x; i < C::E; i += C::T) {
+        rA[i] = a.rmid[i];
+        lA[i] = a.lmid[i];
+    }
+    __syncthreads();
+    double *rho = rA, *rho_n = rB, *lam = lA, *lam_n = lB;
+    const bool ok = adjoint_sweep<N>(st, 0, st.n_total, lam, lam_n, rho, rho_n, a.grad_rot,
+                                     a.status, smem, b == 1);
+    if (!ok || b != 0) return;
     double acc = 0.0;
     for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
     const double total = block_sum<C::T>(acc, red);
@@ -323,6 +400,17 @@ cudaError_t launch_stream_n(const StreamArgs &a, cudaStream_t s) {
     cudaError_t e = raise_smem_limit(k_resident_stream<N, LPG>, smem, lim);
     if (e != cudaSuccess) return e;
     k_resident_stream<N, LPG><<<a.n_vec, C::T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_adjoint_split_n(const AdjointSplitArgs &a, cudaStream_t s) {
+    using C = SCfg<N, 1>;
+    const size_t smem = kSmemHeader + 4 * (size_t)C::E * sizeof(double);
+    static SmemLimit lim;
+    cudaError_t e = raise_smem_limit(k_adjoint_split<N>, smem, lim);
+    if (e != cudaSuccess) return e;
+    k_adjoint_split<N><<<2, C::T, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -361,6 +449,18 @@ cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_
     case 4: return launch_adjoint_stream_n<4>(a, s);
     case 5: return launch_adjoint_stream_n<5>(a, s);
     case 6: return launch_adjoint_stream_n<6>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_adjoint_split(int n, const AdjointSplitArgs &a, cudaStream_t s) {
+    switch (n) {
+    case 1: return launch_adjoint_split_n<1>(a, s);
+    case 2: return launch_adjoint_split_n<2>(a, s);
+    case 3: return launch_adjoint_split_n<3>(a, s);
+    case 4: return launch_adjoint_split_n<4>(a, s);
+    case 5: return launch_adjoint_split_n<5>(a, s);
+    case 6: return launch_adjoint_split_n<6>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -50,6 +50,20 @@ struct StreamArgs {
     int32_t *status;         // set to a nonzero code when a bounded wait gives up
 };
 
+// Split resident adjoint (two CTAs, two launches; see k_adjoint_split).
+struct AdjointSplitArgs {
+    const Rec *stream[2];    // phase 0: forward [0, cut), backward [cut, P); phase 1: backward
+                             // [0, cut), forward [cut, P) -- all of the gradient plan
+    int32_t n_chunks[2];
+    int32_t phase;           // 0 or 1
+    const DevTerm *terms;    // phase 0, CTA 1: O
+    int32_t n_terms;
+    double *rmid, *lmid;     // rho and lambda at the cut: phase 0 writes, phase 1 reads
+    double *grad_rot;        // phase 1: one entry per rotation ordinal
+    double *expect_out;      // phase 1: <O>
+    int32_t *status;
+};
+
 struct AdjointStreamArgs {
     const Rec *fwd;          // forward stream of the gradient plan
     const Rec *bwd;          // backward stream of the gradient plan
@@ -192,6 +206,7 @@ cudaError_t launch_stream_tile(const double *src, double *dst, int n, int n_vec,
                                cudaStream_t st);
 
 // Adjoint gradient, shared-memory resident (n <= kMaxResidentAdjoint).
+cudaError_t launch_adjoint_split(int n, const AdjointSplitArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint_stream(int n, const AdjointStreamArgs &a, cudaStream_t st);
 
 // Streamed adjoint pieces.

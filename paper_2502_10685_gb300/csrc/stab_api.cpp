@@ -69,8 +69,9 @@ struct DevPlan {
     bool streams = false;
     DevStreamBuf sf, sb;
     // split resident streams (see split_resident): forward passes [0, split)
-    // and [split, P), backward passes [split, P); split < 0: none
-    DevStreamBuf h1, h2, h2b;
+    // and [split, P), backward passes [split, P) and (gradient plans) [0, split);
+    // split < 0: none
+    DevStreamBuf h1, h2, h2b, h1b;
     int split = -1;
     DevBuf buf;
     Program prog{};
@@ -126,6 +127,7 @@ struct stab_ctx {
     DevBuf gbuf;                     // gradients written inside captured graphs
     DevBuf lam2, tmp3;               // second-branch buffers of the split sweeps
     DevBuf dotbuf;                   // partial sums of the split expectation's inner product
+    DevBuf gmid;                     // split resident adjoint: rho, then lambda, at the cut
     // split resident sweeps (n <= 6; see split_units): transfer matrix of the
     // second part (n <= 4), first-part generators, meeting vectors, basis
     // terms, batch units (generators; expectation), unit counters
@@ -224,7 +226,7 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     const size_t b_sb = align256(P.sb.host.size() * sizeof(Rec));
     const size_t b_sbe = align256(P.sb.enc.size() * sizeof(int32_t));
     size_t b_split = 0;
-    for (const DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b})
+    for (const DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b, &P.h1b})
         b_split += align256(S->host.size() * sizeof(Rec)) + align256(S->enc.size() * 4);
     const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot + b_tabs +
                          b_sf + b_sfe + b_sb + b_sbe + b_split;
@@ -252,7 +254,7 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     P.sf.enc_dev = (const int32_t *)put(P.sf.enc.data(), P.sf.enc.size() * 4, b_sfe);
     P.sb.dev = (Rec *)put(P.sb.host.data(), P.sb.host.size() * sizeof(Rec), b_sb);
     P.sb.enc_dev = (const int32_t *)put(P.sb.enc.data(), P.sb.enc.size() * 4, b_sbe);
-    for (DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b}) {
+    for (DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b, &P.h1b}) {
         S->dev = (Rec *)put(S->host.data(), S->host.size() * sizeof(Rec),
                             align256(S->host.size() * sizeof(Rec)));
         S->enc_dev = (const int32_t *)put(S->enc.data(), S->enc.size() * 4,
@@ -272,7 +274,7 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
     const double *th = (const double *)c->thetas.p;
     if (P.streams) {
         // resident plans: only the instruction streams are read by kernels
-        for (DevStreamBuf *S : {&P.sf, &P.sb, &P.h1, &P.h2, &P.h2b}) {
+        for (DevStreamBuf *S : {&P.sf, &P.sb, &P.h1, &P.h2, &P.h2b, &P.h1b}) {
             if (S->enc.empty()) continue;
             CK(launch_encode_stream(S->dev, S->enc_dev, (int)S->enc.size(), P.prog.maps,
                                     P.map_gate_idx, P.raw, th, c->st));
@@ -316,19 +318,29 @@ void make_stream(DevPlan &P, bool backward) {
     S.n_chunks = (int)(S.host.size() / kChunkRecs);
 }
 
-// Forward and backward streams, built concurrently on two host threads; with
+// Forward and backward streams, built concurrently on host threads; with
 // split_frac > 0 (and enough passes) also the split streams cut at that
-// fraction of the passes.
-void make_streams(DevPlan &P, double split_frac = 0.0) {
+// fraction of the passes.  A split gradient plan (grad) needs only the four
+// half streams, not the whole-circuit ones.
+void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false) {
     P.streams = true;
     const int np = (int)P.host.passes.size();
     P.split = (split_frac > 0.0 && np >= kSplitMinPasses) ? (int)(np * split_frac) : -1;
+    P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
+    if (grad && P.split >= 0) {
+        P.sf = P.sb = DevStreamBuf();
+        std::thread t1([&P] { make_stream_range(P, P.h1, false, 0, P.split); });
+        std::thread t2([&P, np] { make_stream_range(P, P.h2, false, P.split, np); });
+        std::thread t3([&P, np] { make_stream_range(P, P.h2b, true, P.split, np); });
+        make_stream_range(P, P.h1b, true, 0, P.split);
+        t1.join();
+        t2.join();
+        t3.join();
+        return;
+    }
     std::thread bwd([&P] { make_stream(P, true); });
     std::thread halves([&P, np] {
-        if (P.split < 0) {
-            P.h1 = P.h2 = P.h2b = DevStreamBuf();
-            return;
-        }
+        if (P.split < 0) return;
         make_stream_range(P, P.h1, false, 0, P.split);
         make_stream_range(P, P.h2, false, P.split, np);
         make_stream_range(P, P.h2b, true, P.split, np);
@@ -342,7 +354,7 @@ void no_streams(DevPlan &P) {
     P.streams = false;
     P.sf = DevStreamBuf();
     P.sb = DevStreamBuf();
-    P.h1 = P.h2 = P.h2b = DevStreamBuf();
+    P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
     P.split = -1;
 }
 
@@ -687,7 +699,10 @@ int ensure_grad_plan(stab_ctx *c) {
     if (!c->grad.built) {
         build_plan(c->n, c->gates.data(), (int64_t)c->gates.size(), c->n_params, PLAN_GRAD,
                    &c->grad.host, !c->use_resident_adjoint());
-        if (c->use_resident_adjoint()) make_streams(c->grad);
+        // resident adjoint: split at half the passes (the AUTO kernel; the
+        // RESIDENT choice keeps the single-CTA forward-then-reverse sweep)
+        if (c->use_resident_adjoint())
+            make_streams(c->grad, c->kernel == STAB_KERNEL_AUTO ? 0.5 : 0.0, true);
         else no_streams(c->grad);
         c->g_grad.reset();
         c->plan_gen++;
@@ -818,7 +833,7 @@ int stab_destroy(stab_ctx *c) {
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
                       &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3,
                       &c->dotbuf, &c->tmat, &c->avec, &c->rmid, &c->lmid, &c->bterms,
-                      &c->units_g, &c->units_e, &c->cnt};
+                      &c->units_g, &c->units_e, &c->cnt, &c->gmid};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -1110,7 +1125,39 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
     RC(c->dalloc(c->scal, 64 * sizeof(double), s));
     RC(c->dalloc(c->grad_rot, (size_t)(n_rot ? n_rot : 1) * sizeof(double), s));
     double *e_out = expect_dev ? expect_dev : (double *)c->scal.p + 1;
-    if (c->use_resident_adjoint()) {
+    if (c->use_resident_adjoint() && c->grad.split >= 0) {
+        // meet in the middle: rho_0 forward through the first part and O
+        // backward through the second, then the pair at the cut backward
+        // through the first part and forward through the second
+        const size_t E = (size_t)1 << (2 * n);
+        RC(c->dalloc(c->gmid, 2 * E * sizeof(double), s));
+        AdjointSplitArgs a{};
+        a.stream[0] = c->grad.h1.dev;
+        a.n_chunks[0] = c->grad.h1.n_chunks;
+        a.stream[1] = c->grad.h2b.dev;
+        a.n_chunks[1] = c->grad.h2b.n_chunks;
+        a.phase = 0;
+        a.terms = (const DevTerm *)c->terms.p;
+        a.n_terms = nt;
+        a.rmid = (double *)c->gmid.p;
+        a.lmid = (double *)c->gmid.p + E;
+        a.grad_rot = (double *)c->grad_rot.p;
+        a.expect_out = e_out;
+        a.status = (int32_t *)c->status.p;
+        CK(launch_adjoint_split(n, a, s));
+        a.stream[0] = c->grad.h1b.dev;
+        a.n_chunks[0] = c->grad.h1b.n_chunks;
+        a.stream[1] = c->grad.h2.dev;
+        a.n_chunks[1] = c->grad.h2.n_chunks;
+        a.phase = 1;
+        CK(launch_adjoint_split(n, a, s));
+        c->launches += 2;
+        if (c->n_params > 0) {
+            CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
+                                   c->grad.param_rot, (int)c->n_params, grads_dev, s));
+            c->launches++;
+        }
+    } else if (c->use_resident_adjoint()) {
         AdjointStreamArgs a{};
         a.fwd = c->grad.sf.dev;
         a.bwd = c->grad.sb.dev;

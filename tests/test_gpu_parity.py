@@ -136,6 +136,26 @@ def test_gradient_shared_parameters(stab):
     assert np.abs(g - gref).max() <= 1e-12 * obs_l1(obs)
 
 
+@pytest.mark.parametrize("n", [2, 4, 5, 6])
+def test_gradient_split_resident(stab, n):
+    # long enough for the meet-in-the-middle adjoint (rho_0 and O meet at the
+    # cut, then the pair sweeps both parts); shared slots put gates of one
+    # parameter on both sides of the cut
+    c = W.random_circuit(n, 400, seed=4100 + n, shared_params=7)
+    obs = W.random_observable(n, 5, seed=41 + n)
+    gref = oracle.psr_grad(n, c.gates, c.thetas, obs)
+    eref = oracle.expect(n, c.gates, c.thetas, obs)
+    out = {}
+    for kernel in ("auto", "resident"):
+        s = stab.Stab(n, kernel=kernel)
+        s.load_circuit(c.gates, c.thetas)
+        out[kernel] = s.grad(obs)
+        s.close()
+    for kernel, (e, g) in out.items():
+        assert abs(e - eref) <= 1e-12 * obs_l1(obs), kernel
+        assert np.abs(g - gref).max() <= 1e-12 * obs_l1(obs), kernel
+
+
 def test_gradient_n8_sampled_psr_and_fd(stab):
     """n=8 layered ansatz, chain observable: adjoint vs oracle PSR on sampled
     gates, and vs central finite differences (h = 1e-6) of the GPU <O>."""
