@@ -320,7 +320,7 @@ def run_ours(args):
                       "units) + k_apply_transfer" % c.n)
         else:
             kernel = "k_batch (split: %d units) + k_apply_transfer" % gen_units
-        executed = (c.n * cut + (4 ** c.n - 1) * (n_passes - cut)) / (c.n * n_passes)
+        executed = ((c.n + 1) * cut + (4 ** c.n - 1) * (n_passes - cut)) / (c.n * n_passes)
         active_sms = min(SMS, c.n + 128 if c.n == 4 else gen_units)
         note = ("one circuit: the generators split at pass %d of %d; the n first-part "
                 "vectors and the 4^n-1 basis columns run at once (%s); passes are "

@@ -422,8 +422,10 @@ int stab_plan_info(stab_ctx *ctx, int64_t *n_gates, int64_t *n_passes, int32_t *
  * lambda = O backward through [cut, n_passes) run at once; for n <= 4 the
  * generators are T a_k, a_k = Z_k through [0, cut) and T the transfer matrix
  * of [cut, n_passes).  Writes *cut (-1: no split; the plan runs as one
- * sweep), *gen_units (vectors of the generators' persistent launch, 0 when
- * not split) and *expect_units (of the expectation's, 0 when not split).
+ * sweep), *gen_units (vectors of the generators' split sweep -- the n
+ * generators and rho_0 through [0, cut), the 4^n - 1 columns of T; 0 when not
+ * split; stab_density_matrix uses the same sweep, r = T r_1) and
+ * *expect_units (of the expectation's, 0 when not split).
  * Any output pointer may be NULL.  Errors: STAB_E_INVAL (ctx NULL). */
 int stab_split_info(stab_ctx *ctx, int64_t *cut, int32_t *gen_units, int32_t *expect_units);
 

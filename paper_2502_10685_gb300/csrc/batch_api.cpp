@@ -335,10 +335,14 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
     put(o_terms, terms.data(), terms.size() * sizeof(DevTerm));
     put(o_units, units.data(), units.size() * sizeof(BatchUnit));
     cudaError_t e = cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = launch_compose_maps((DevMap3 *)(d + o_maps), (int)maps.size(),
+                                max_map_count(maps.data(), maps.size()),
+                                (const int32_t *)(d + o_midx), (const RawGate *)(d + o_raw),
+                                (const double *)(d + o_th), b->st);
     if (e == cudaSuccess && !enc.empty())
         e = launch_encode_stream((Rec *)(d + o_recs), (const int32_t *)(d + o_enc), (int)enc.size(),
-                                 (const DevMap3 *)(d + o_maps), (const int32_t *)(d + o_midx),
-                                 (const RawGate *)(d + o_raw), (const double *)(d + o_th), b->st);
+                                 (const DevMap3 *)(d + o_maps), (const double *)(d + o_th), b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     cudaFreeHost(h);
     BCK(e);

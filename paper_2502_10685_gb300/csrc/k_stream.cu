@@ -69,21 +69,75 @@ __device__ void shear_coeffs(double theta, double &t, double &s, uint16_t &neg) 
     s = sin(phi);
 }
 
-__device__ void compose_map(const DevMap3 &mp, const int32_t *map_gate_idx, const RawGate *gates,
-                            const double *thetas, double M[9]) {
-    for (int k = 0; k < 9; ++k) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
+// 3x3 product C = A B (row-major).
+__device__ __forceinline__ void mul3(const double A[9], const double B[9], double C[9]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = fma(A[3 * r + 2], B[6 + c], fma(A[3 * r + 1], B[3 + c], A[3 * r] * B[c]));
+}
+
+// Composed map of every run, one warp per map: lane l composes a contiguous
+// chunk of the run's gates in order (the lanes evaluate their gates' sin/cos
+// at once), then the 32 partial products are multiplied in order by a
+// shuffle tree (later chunk times earlier chunk), log2(32) steps instead of a
+// sequential walk over the whole run.
+__global__ void k_compose_maps(DevMap3 *maps, int n_maps, const int32_t *map_gate_idx,
+                               const RawGate *gates, const double *thetas) {
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = (int)(threadIdx.x & 31u);
+    if (w >= n_maps) return;   // whole warps
+    const DevMap3 mp = maps[w];
+    const int per = (mp.count + 31) / 32;
+    const int k0 = min(lane * per, mp.count), k1 = min(k0 + per, mp.count);
+    double M[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
+    for (int k = k0; k < k1; ++k) {
+        double G[9], R[9];
+        gate_matrix3(gates[map_gate_idx[mp.first + k]], thetas, G);
+        mul3(G, M, R);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) M[j] = R[j];
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        double O[9], R[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) O[j] = __shfl_down_sync(0xffffffffu, M[j], d);
+        if ((lane & (2 * d - 1)) == 0) {
+            mul3(O, M, R);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) M[j] = R[j];
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 9; ++j) maps[w].m[j] = M[j];
+}
+
+// Composed map of every run, one thread per map walking its gates in order:
+// the form for plans of short runs (a warp per map would idle most lanes).
+__global__ void k_compose_maps_seq(DevMap3 *maps, int n_maps, const int32_t *map_gate_idx,
+                                   const RawGate *gates, const double *thetas) {
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= n_maps) return;
+    const DevMap3 mp = maps[i];
+    double M[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
     for (int k = 0; k < mp.count; ++k) {
         double G[9], R[9];
         gate_matrix3(gates[map_gate_idx[mp.first + k]], thetas, G);
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c)
-                R[3 * r + c] = G[3 * r] * M[c] + G[3 * r + 1] * M[3 + c] + G[3 * r + 2] * M[6 + c];
-        for (int k2 = 0; k2 < 9; ++k2) M[k2] = R[k2];
+        mul3(G, M, R);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) M[j] = R[j];
     }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) maps[i].m[j] = M[j];
 }
 
+// Angles -> stream records: shear coefficients of rotations, and the composed
+// maps (from k_compose_maps) copied into the R_MAP3 data records, transposed
+// (the inverse) in backward streams.
 __global__ void k_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const DevMap3 *maps,
-                                const int32_t *map_gate_idx, const RawGate *gates,
                                 const double *thetas) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_enc) return;
@@ -96,16 +150,14 @@ __global__ void k_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const 
         r.s = r.inv ? -s : s;
         r.code = neg;
     } else if (r.kind == R_MAP3) {
-        double M[9];
-        compose_map(maps[r.param], map_gate_idx, gates, thetas, M);
+        const double *M = maps[r.param].m;
         double *dst = reinterpret_cast<double *>(&r + 1);
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) dst[3 * i + j] = r.inv ? M[3 * j + i] : M[3 * i + j];
     }
 }
 
-__global__ void k_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
-                         const int32_t *map_gate_idx, const RawGate *gates, const double *thetas) {
+__global__ void k_encode(DevOp *ops, int n_ops, const double *thetas) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_ops && ops[i].kind == K_ROT) {
         double t, s;
@@ -115,7 +167,6 @@ __global__ void k_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
         ops[i].s = s;
         ops[i].perm = neg;
     }
-    if (i < n_maps) compose_map(maps[i], map_gate_idx, gates, thetas, maps[i].m);
 }
 
 __global__ void k_fill(double *vec, int n, int n_vec, int init) {
@@ -373,22 +424,38 @@ cudaError_t launch_bounded_wait(int64_t polls, int32_t *status, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
+int max_map_count(const DevMap3 *maps, size_t n_maps) {
+    int m = 0;
+    for (size_t i = 0; i < n_maps; ++i) m = maps[i].count > m ? maps[i].count : m;
+    return m;
+}
+
+cudaError_t launch_compose_maps(DevMap3 *maps, int n_maps, int max_count,
+                                const int32_t *map_gate_idx, const RawGate *gates,
+                                const double *thetas, cudaStream_t st) {
+    if (n_maps == 0) return cudaSuccess;
+    if (max_count <= kSeqMapGates)
+        k_compose_maps_seq<<<(n_maps + 127) / 128, 128, 0, st>>>(maps, n_maps, map_gate_idx, gates,
+                                                                 thetas);
+    else
+        k_compose_maps<<<(n_maps + 3) / 4, 128, 0, st>>>(maps, n_maps, map_gate_idx, gates,
+                                                         thetas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps, int max_count,
                           const int32_t *map_gate_idx, const RawGate *gates, const double *thetas,
                           cudaStream_t st) {
-    const int work = n_ops > n_maps ? n_ops : n_maps;
-    if (work == 0) return cudaSuccess;
-    k_encode<<<(work + 127) / 128, 128, 0, st>>>(ops, n_ops, maps, n_maps, map_gate_idx, gates,
-                                                 thetas);
+    cudaError_t e = launch_compose_maps(maps, n_maps, max_count, map_gate_idx, gates, thetas, st);
+    if (e != cudaSuccess || n_ops == 0) return e;
+    k_encode<<<(n_ops + 127) / 128, 128, 0, st>>>(ops, n_ops, thetas);
     return cudaGetLastError();
 }
 
 cudaError_t launch_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const DevMap3 *maps,
-                                 const int32_t *map_gate_idx, const RawGate *gates,
                                  const double *thetas, cudaStream_t st) {
     if (n_enc == 0) return cudaSuccess;
-    k_encode_stream<<<(n_enc + 127) / 128, 128, 0, st>>>(recs, enc, n_enc, maps, map_gate_idx,
-                                                         gates, thetas);
+    k_encode_stream<<<(n_enc + 127) / 128, 128, 0, st>>>(recs, enc, n_enc, maps, thetas);
     return cudaGetLastError();
 }
 

@@ -127,16 +127,24 @@ cudaError_t launch_bounded_wait(int64_t polls, int32_t *status, cudaStream_t st)
 // Records the CUDA error behind a STAB_E_CUDA status (stab_last_cuda_error).
 void record_cuda_error(cudaError_t e);
 
-// Encode kernel: lifting coefficients of every rotation op and composed 3x3
-// maps, from the angle array on the device.
-cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps,
+// Composed 3x3 map of every run (maps[i].m), from the angle array on the
+// device: one thread per map when no run is longer than kSeqMapGates gates
+// (max_count, the longest run), else one warp per map.
+constexpr int kSeqMapGates = 32;
+cudaError_t launch_compose_maps(DevMap3 *maps, int n_maps, int max_count,
+                                const int32_t *map_gate_idx, const RawGate *gates,
+                                const double *thetas, cudaStream_t st);
+int max_map_count(const DevMap3 *maps, size_t n_maps);   // host: the longest run
+
+// Encode: the composed maps, then the lifting coefficients of every rotation op.
+cudaError_t launch_encode(DevOp *ops, int n_ops, DevMap3 *maps, int n_maps, int max_count,
                           const int32_t *map_gate_idx, const RawGate *gates, const double *thetas,
                           cudaStream_t st);
 
-// Stream encode: shear coefficients of the R_ROT records and matrices of the
-// R_MAP3 records listed in enc (indices into recs).
+// Stream encode: shear coefficients of the R_ROT records and the matrices of
+// the R_MAP3 records listed in enc (indices into recs), copied from maps
+// (composed before by launch_compose_maps).
 cudaError_t launch_encode_stream(Rec *recs, const int32_t *enc, int n_enc, const DevMap3 *maps,
-                                 const int32_t *map_gate_idx, const RawGate *gates,
                                  const double *thetas, cudaStream_t st);
 
 // Shared-memory-resident propagation, one CTA per vector (n <= kMaxResidentQubits).

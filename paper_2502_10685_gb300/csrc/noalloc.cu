@@ -128,8 +128,8 @@ extern "C" int stab_expect_static(int n, const stab_gate *gates, int64_t m, cons
     if (e == cudaSuccess) e = h2d(d_th, thetas, (size_t)n_params * sizeof(double));
     if (e == cudaSuccess) e = h2d(d_terms, terms.data(), terms.size() * sizeof(DevTerm));
     if (e == cudaSuccess && (!P.ops.empty() || !P.maps.empty()))
-        e = launch_encode(d_ops, (int)P.ops.size(), d_maps, (int)P.maps.size(), d_midx, d_raw,
-                          d_th, s);
+        e = launch_encode(d_ops, (int)P.ops.size(), d_maps, (int)P.maps.size(),
+                          max_map_count(P.maps.data(), P.maps.size()), d_midx, d_raw, d_th, s);
     // every entry of the working vector is written here, so nothing left by
     // an earlier call survives
     if (e == cudaSuccess)

@@ -273,11 +273,19 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
 int encode_plan(stab_ctx *c, DevPlan &P) {
     const double *th = (const double *)c->thetas.p;
     if (P.streams) {
-        // resident plans: only the instruction streams are read by kernels
+        // resident plans: only the instruction streams are read by kernels;
+        // each run's map is composed once and copied into every stream
+        const int n_maps = (int)P.host.maps.size();
+        if (n_maps > 0) {
+            CK(launch_compose_maps(const_cast<DevMap3 *>(P.prog.maps), n_maps,
+                                   max_map_count(P.host.maps.data(), P.host.maps.size()),
+                                   P.map_gate_idx, P.raw, th, c->st));
+            c->launches++;
+        }
         for (DevStreamBuf *S : {&P.sf, &P.sb, &P.h1, &P.h2, &P.h2b, &P.h1b}) {
             if (S->enc.empty()) continue;
-            CK(launch_encode_stream(S->dev, S->enc_dev, (int)S->enc.size(), P.prog.maps,
-                                    P.map_gate_idx, P.raw, th, c->st));
+            CK(launch_encode_stream(S->dev, S->enc_dev, (int)S->enc.size(), P.prog.maps, th,
+                                    c->st));
             c->launches++;
         }
         P.encoded = true;
@@ -289,8 +297,9 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
         return STAB_OK;
     }
     CK(launch_encode(const_cast<DevOp *>(P.prog.ops), n_ops, const_cast<DevMap3 *>(P.prog.maps),
-                     n_maps, P.map_gate_idx, P.raw, th, c->st));
-    c->launches++;
+                     n_maps, max_map_count(P.host.maps.data(), P.host.maps.size()),
+                     P.map_gate_idx, P.raw, th, c->st));
+    c->launches += (n_maps > 0) + (n_ops > 0);
     P.encoded = true;
     return STAB_OK;
 }
@@ -492,14 +501,16 @@ int split_setup(stab_ctx *c, cudaStream_t s) {
     return STAB_OK;
 }
 
-// Units of the generators' split sweep (rebuilt when the plan changes).
+// Units of the generators' split sweep (rebuilt when the plan changes):
+// the first part carries Z_0 .. Z_{n-1} and rho_0 into avec, the second part
+// the basis strings into the columns of T.
 int split_units_g(stab_ctx *c) {
     const int n = c->n, E = 1 << (2 * n);
     RC(split_setup(c, c->st));
     RC(c->dalloc(c->tmat, (size_t)E * E * 8, c->st));
-    RC(c->dalloc(c->avec, (size_t)n * E * 8, c->st));
+    RC(c->dalloc(c->avec, (size_t)(n + 1) * E * 8, c->st));
     RC(c->dalloc(c->bterms, (size_t)E * sizeof(DevTerm), c->st));
-    RC(c->dalloc(c->units_g, (size_t)(E - 1 + n) * sizeof(BatchUnit), c->st));
+    RC(c->dalloc(c->units_g, (size_t)(E + n) * sizeof(BatchUnit), c->st));
     const std::vector<const void *> key = {(const void *)c->plan_gen, c->fwd.h1.dev,
                                            c->fwd.h2.dev, c->tmat.p, c->avec.p, c->bterms.p,
                                            c->units_g.p};
@@ -513,6 +524,16 @@ int split_units_g(stab_ctx *c) {
         u.init = INIT_GENERATOR;
         u.gen = (int16_t)k;
         u.out = (double *)c->avec.p + (size_t)k * E;
+        U.push_back(u);
+    }
+    {
+        // rho_0 through the first part, for the density matrix (r = T r_1)
+        BatchUnit u{};
+        u.stream = c->fwd.h1.dev;
+        u.n_chunks = c->fwd.h1.n_chunks;
+        u.n = (int8_t)n;
+        u.init = INIT_RHO0;
+        u.out = (double *)c->avec.p + (size_t)n * E;
         U.push_back(u);
     }
     // the columns of T: units of the same launch, or (n = 4, where they would
@@ -542,6 +563,33 @@ int split_units_g(stab_ctx *c) {
     CK(cudaStreamSynchronize(c->st));   // the host vectors above are temporaries
     c->n_units_g = (int)U.size();
     c->key_g = key;
+    return STAB_OK;
+}
+
+// The generators' split sweep on the context stream: the first-part vectors
+// into avec and the columns of T into tmat (the caller applies T).
+int split_run_g(stab_ctx *c) {
+    RC(split_units_g(c));
+    BatchArgs a{};
+    a.units = (const BatchUnit *)c->units_g.p;
+    a.n_units = c->n_units_g;
+    a.counter = (int32_t *)c->cnt.p;
+    a.status = (int32_t *)c->status.p;
+    CK(cudaMemsetAsync(c->cnt.p, 0, 4, c->st));
+    if (transfer_cols_ctas(c->n) > 0) {
+        // the first-part units and the columns of T at once, on two streams
+        CK(cudaEventRecord(c->ev_fork, c->st));
+        CK(cudaStreamWaitEvent(c->aux2, c->ev_fork, 0));
+        CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
+        CK(launch_transfer_cols(c->fwd.h2.dev, c->fwd.h2.n_chunks, (double *)c->tmat.p, c->n,
+                                (int32_t *)c->status.p, c->aux2));
+        CK(cudaEventRecord(c->ev_join, c->aux2));
+        CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
+        c->launches++;
+    } else {
+        CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
+    }
+    c->launches++;
     return STAB_OK;
 }
 
@@ -916,29 +964,10 @@ int stab_run_generators(stab_ctx *c) {
     const size_t bytes = c->vec_bytes() * (size_t)n;
     RC(c->dalloc(c->gens, bytes, c->st));
     if (c->use_resident() && split_gens_ok(c)) {
-        RC(split_units_g(c));
-        BatchArgs a{};
-        a.units = (const BatchUnit *)c->units_g.p;
-        a.n_units = c->n_units_g;
-        a.counter = (int32_t *)c->cnt.p;
-        a.status = (int32_t *)c->status.p;
-        CK(cudaMemsetAsync(c->cnt.p, 0, 4, c->st));
-        if (transfer_cols_ctas(n) > 0) {
-            // the n first-part units and the columns of T at once, on two streams
-            CK(cudaEventRecord(c->ev_fork, c->st));
-            CK(cudaStreamWaitEvent(c->aux2, c->ev_fork, 0));
-            CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
-            CK(launch_transfer_cols(c->fwd.h2.dev, c->fwd.h2.n_chunks, (double *)c->tmat.p, n,
-                                    (int32_t *)c->status.p, c->aux2));
-            CK(cudaEventRecord(c->ev_join, c->aux2));
-            CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
-            c->launches++;
-        } else {
-            CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
-        }
+        RC(split_run_g(c));
         CK(launch_apply_transfer((const double *)c->tmat.p, (const double *)c->avec.p,
                                  (double *)c->gens.p, n, n, c->st));
-        c->launches += 2;
+        c->launches++;
         c->gens_cur = (double *)c->gens.p;
     } else if (c->use_resident()) {
         StreamArgs a{};
@@ -1375,7 +1404,15 @@ int stab_density_matrix(stab_ctx *c, double *out, int out_is_device) {
     const size_t vb = c->vec_bytes();
     RC(c->dalloc(c->rho, vb, c->st));
     double *r = (double *)c->rho.p;
-    if (c->use_resident()) {
+    if (c->use_resident() && split_gens_ok(c)) {
+        // r = T r_1: rho_0 through the first part, then the second part's
+        // transfer matrix (built alongside, as for the generators)
+        RC(split_run_g(c));
+        const size_t E = (size_t)1 << (2 * n);
+        CK(launch_apply_transfer((const double *)c->tmat.p, (const double *)c->avec.p + n * E, r,
+                                 1, n, c->st));
+        c->launches++;
+    } else if (c->use_resident()) {
         StreamArgs a{};
         a.stream = c->fwd.sf.dev;
         a.n_chunks = c->fwd.sf.n_chunks;
@@ -1429,7 +1466,7 @@ int stab_split_info(stab_ctx *c, int64_t *cut, int32_t *gen_units, int32_t *expe
     const bool on = c->loaded && c->use_resident() && c->fwd.split >= 0;
     const int E = 1 << (2 * c->n);
     if (cut) *cut = on ? c->fwd.split : -1;
-    if (gen_units) *gen_units = on && split_gens_ok(c) ? c->n + E - 1 : 0;
+    if (gen_units) *gen_units = on && split_gens_ok(c) ? c->n + E : 0;
     if (expect_units) *expect_units = on && split_expect_ok(c) ? 2 : 0;
     return STAB_OK;
 }

@@ -101,6 +101,22 @@ def test_config_paper_scale_n4_60200(stab):
     s.close()
 
 
+@pytest.mark.parametrize("n,layers,repeats", [(3, 40, 40), (4, 30, 100), (7, 6, 40)])
+def test_paper_shaped_long_runs(stab, n, layers, repeats):
+    """Runs of 120-300 rotations per wire: each run's map is composed by a
+    warp (chunks per lane, ordered product tree) -- through the split sweeps
+    at n = 3, 4 and the streamed encode at n = 7."""
+    c = W.paper_shaped_ansatz(n, layers, repeats, seed=70 + n)
+    ref = oracle.generators(n, c.gates, c.thetas)
+    obs = W.obs_chain(n)
+    s = stab.Stab(n)
+    s.apply_circuit(c.gates, c.thetas)
+    got = layout.lib_to_paper(n, s.generators())
+    assert np.abs(got - ref).max() <= 1e-12
+    assert abs(s.expect(obs) - oracle.expect(n, c.gates, c.thetas, obs)) <= 1e-12 * obs_l1(obs)
+    s.close()
+
+
 def test_paper_shaped_ansatz_fused_maps(stab):
     """W_chain + ZXZ with many repeats: wire runs compose into 3x3 maps."""
     c = W.paper_shaped_ansatz(4, 5, 20, seed=7)
@@ -333,6 +349,22 @@ def test_density_matrix_against_oracle(stab, n):
     got = rho[np.ix_(perm, perm)]
     ref = oracle.density_matrix(n, c.gates, c.thetas)
     assert np.abs(got - ref).max() <= 1e-12
+    assert abs(np.trace(rho) - 1) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_density_matrix_split_sweep(stab, n):
+    """Long circuits: rho_0 through the first part, then the second part's
+    transfer matrix (the split sweep of the generators), decoded."""
+    c = W.layered_ansatz(n, 2000, seed=610 + n)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    assert s.split_info()[0] > 0
+    rho = s.density_matrix()
+    s.close()
+    perm = _bitrev_perm(n)
+    ref = oracle.density_matrix(n, c.gates, c.thetas)
+    assert np.abs(rho[np.ix_(perm, perm)] - ref).max() <= 1e-12
     assert abs(np.trace(rho) - 1) <= 1e-12
 
 
