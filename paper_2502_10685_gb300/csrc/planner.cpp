@@ -247,7 +247,15 @@ void clifford_tableau(int n, const stab_gate *gates, int64_t i0, int64_t i1, boo
 void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
                 HostPlan *out, bool tableaus) {
     HostPlan &P = *out;
-    P = HostPlan();
+    // cleared, not replaced: a context reloading circuits keeps the capacity
+    P.passes.clear();
+    P.ops.clear();
+    P.maps.clear();
+    P.map_gate_idx.clear();
+    P.param_ptr.clear();
+    P.param_rot.clear();
+    P.tabs.clear();
+    P.n_rot = 0;
     P.n_params = n_params;
     P.mode = mode;
     P.raw.resize((size_t)m);

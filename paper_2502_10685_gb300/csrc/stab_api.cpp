@@ -66,6 +66,7 @@ struct DevStreamBuf {
 // backward instruction streams.
 struct DevPlan {
     HostPlan host;
+    int host_n = 0;                  // qubits of the plan
     bool streams = false;
     DevStreamBuf sf, sb;
     // split resident streams (see split_resident): forward passes [0, split)
@@ -335,7 +336,9 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false) {
     P.streams = true;
     const int np = (int)P.host.passes.size();
     P.split = (split_frac > 0.0 && np >= kSplitMinPasses) ? (int)(np * split_frac) : -1;
-    P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
+    // streams that are rebuilt keep their capacity; the others are released
+    if (P.split < 0) P.h1 = P.h2 = P.h2b = DevStreamBuf();
+    if (!(grad && P.split >= 0)) P.h1b = DevStreamBuf();
     if (grad && P.split >= 0) {
         P.sf = P.sb = DevStreamBuf();
         std::thread t1([&P] { make_stream_range(P, P.h1, false, 0, P.split); });
@@ -347,16 +350,26 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false) {
         t3.join();
         return;
     }
-    std::thread bwd([&P] { make_stream(P, true); });
-    std::thread halves([&P, np] {
-        if (P.split < 0) return;
-        make_stream_range(P, P.h1, false, 0, P.split);
-        make_stream_range(P, P.h2, false, P.split, np);
-        make_stream_range(P, P.h2b, true, P.split, np);
-    });
-    make_stream(P, false);
-    bwd.join();
-    halves.join();
+    if (P.split < 0) {
+        std::thread bwd([&P] { make_stream(P, true); });
+        make_stream(P, false);
+        bwd.join();
+        return;
+    }
+    // A split plan reads the halves: the generators (n <= 4) and the density
+    // matrix through h1 and h2, <O> through h1 and h2b.  Only n = 5, 6 still
+    // read the whole forward stream (their generators and density matrix are
+    // not split); nothing reads the whole backward stream.
+    P.sb = DevStreamBuf();
+    const bool whole_fwd = P.host_n > 4;
+    if (!whole_fwd) P.sf = DevStreamBuf();
+    std::thread t1([&P] { make_stream_range(P, P.h1, false, 0, P.split); });
+    std::thread t2([&P, np] { make_stream_range(P, P.h2, false, P.split, np); });
+    std::thread t3([&P, np] { make_stream_range(P, P.h2b, true, P.split, np); });
+    if (whole_fwd) make_stream(P, false);
+    t1.join();
+    t2.join();
+    t3.join();
 }
 
 void no_streams(DevPlan &P) {
@@ -825,6 +838,7 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
     stab_ctx *c = new (std::nothrow) stab_ctx();
     if (!c) return STAB_E_NOMEM;
     c->n = n;
+    c->fwd.host_n = c->grad.host_n = n;
     c->kernel = o.kernel;
     c->fuse = o.fuse;
     c->alloc = o.alloc;
