@@ -111,7 +111,8 @@ struct stab_ctx {
     cudaStream_t aux2 = nullptr;       // second branch of the split adjoint
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool own_st = false;
-    cudaEvent_t ev_ready = nullptr;    // plan uploaded and encoded (on st)
+    cudaEvent_t ev_ready = nullptr;    // plan uploaded and encoded (on st); the aux work waits
+                                       // on it (the observable's terms are uploaded on aux)
     cudaEvent_t ev_aux = nullptr;      // aux work done
     cudaEvent_t ev_stage = nullptr;    // staging buffer free
     stab_alloc_fn alloc = nullptr;
@@ -414,16 +415,17 @@ int upload_terms(stab_ctx *c, const stab_term *O, int64_t n_terms) {
     std::vector<DevTerm> t;
     RC(encode_terms(c->n, O, n_terms, &t));
     const size_t bytes = (t.size() ? t.size() : 1) * sizeof(DevTerm);
-    // the aux stream may still read the previous terms
+    // The terms are read on the aux stream (expectations, gradients), so they
+    // are uploaded there, from the aux staging buffer: the upload does not
+    // queue behind generator work on the main stream.  The aux stream may
+    // still read the previous terms and its staging buffer.
     CK(cudaStreamSynchronize(c->aux));
-    RC(c->dalloc(c->terms, bytes, c->st));
+    RC(c->dalloc(c->terms, bytes, c->aux));
     if (!t.empty()) {
-        CK(cudaEventSynchronize(c->ev_stage));
-        RC(c->host_stage(c->stage, c->stage_bytes, bytes));
-        std::memcpy(c->stage, t.data(), t.size() * sizeof(DevTerm));
-        CK(cudaMemcpyAsync(c->terms.p, c->stage, t.size() * sizeof(DevTerm),
-                           cudaMemcpyHostToDevice, c->st));
-        CK(cudaEventRecord(c->ev_stage, c->st));
+        RC(c->host_stage(c->aux_stage, c->aux_stage_bytes, bytes));
+        std::memcpy(c->aux_stage, t.data(), t.size() * sizeof(DevTerm));
+        CK(cudaMemcpyAsync(c->terms.p, c->aux_stage, t.size() * sizeof(DevTerm),
+                           cudaMemcpyHostToDevice, c->aux));
         c->h2d_bytes += (int64_t)(t.size() * sizeof(DevTerm));
     }
     c->n_obs_terms = (int32_t)t.size();
@@ -1048,7 +1050,6 @@ int stab_set_observable(stab_ctx *c, const stab_term *O, int64_t n_terms) {
     CK(cudaSetDevice(c->device));
     c->obs_loaded = false;
     RC(upload_terms(c, O, n_terms));
-    CK(cudaEventRecord(c->ev_ready, c->st));
     c->obs_loaded = true;
     return STAB_OK;
 }
