@@ -408,12 +408,6 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def shard(items, rank, world):
-    """Units of a batch for one rank: every world-th item, starting at rank
-    (items are independent, so ranks need no collective on the data path)."""
-    return items[rank::world]
-
-
 def run_batch(args):
     """Uneven batch: 4,096 circuits (n ~ U{2..8}, depth ~ U[100, 20000]) including
     the 2m parameter-shift copies of a 6-qubit 2,000-gate circuit, one
@@ -422,7 +416,7 @@ def run_batch(args):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2502_10685_gb300 import stab, workloads as W
+    from paper_2502_10685_gb300 import stab, units, workloads as W
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -437,7 +431,11 @@ def run_batch(args):
                                    psr_base=None)
     else:
         all_items = W.uneven_batch(4096 * world, seed=1003)   # weak scaling: 4,096 per GPU
-    items = shard(all_items, rank, world)
+    # units to ranks by longest processing time first on their coefficient updates
+    costs = [units.unit_cost(it.circuit.n, it.circuit.m,
+                             it.circuit.n if it.kind == "generators" else 1) for it in all_items]
+    mine = units.lpt_partition(costs, world)[rank]
+    items = [all_items[i] for i in mine]
     t0 = time.perf_counter()
     b = stab.Batch(items, device=local)
     create_s = time.perf_counter() - t0
@@ -488,20 +486,27 @@ def run_batch(args):
         forms["fused_per_circuit" if kernel == "auto" else "plain_per_gate"] = {
             "extrapolated_ms": est, "batch_speedup": est / ms, "sample_circuits": len(sample)}
     info = b.info()
+    # every item's <O> (NaN for generator items) back on rank 0, in item order
+    full = units.gather_to_root(mine, [float(x) for x in b.expectations()], len(all_items),
+                                dist if world > 1 else None)
     b.close()
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
         return 0
+    total_upd = sum(costs)
     line = {
-        "metric": "circuits/s", "value": len(items) * world / (ms / 1e3), "unit": "circuits/s",
+        "metric": "circuits/s", "value": len(all_items) / (ms / 1e3), "unit": "circuits/s",
         "n_gpus": world, "scaling": "weak", "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms,
         "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "circuits": len(items), "units": info["units"],
+        "config": {"workload": args.workload, "circuits": len(all_items),
+                   "circuits_rank0": len(items), "units": info["units"],
                    "grid": info["grid"], "ctas_per_sm": info["ctas_per_sm"],
+                   "partition": "longest processing time first on coefficient updates",
                    "l2": "flushed between steps"},
-        "updates_per_s": upd * world / (ms / 1e3), "create_s": create_s, "vs_forms": forms}
+        "updates_per_s": total_upd / (ms / 1e3), "create_s": create_s, "vs_forms": forms,
+        "results_gathered": sum(1 for x in full if x is not None)}
     if world == 1 and not args.no_cpu_baseline and len(items) >= 12:
         # the oracle on a seeded sample of small items, scaled by updates
         import oracle
@@ -650,16 +655,34 @@ def run_serve(args):
     50/50 <O> / gradient requests, submitted at their arrival times to the
     continuous-batching server; latency = completion - arrival.  The line's
     value uses shortest-estimated-work-first admission; the same trace in FIFO
-    order is reported beside it."""
+    order is reported beside it.  With several ranks each request is routed,
+    in arrival order, to the rank with the least work assigned so far (the
+    same routing on every rank, no exchange), every rank serves its share on
+    its GPU, and the per-request results are gathered to rank 0 (the trace is
+    fixed: strong scaling)."""
     import numpy as np
-    from paper_2502_10685_gb300 import stab, workloads as W
+    import torch
+    import torch.distributed as dist
+    from paper_2502_10685_gb300 import stab, units, workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     reqs = W.serving_trace(args.requests, seed=1005)
+    # a gradient sweeps about three vectors where <O> sweeps one
+    costs = [units.unit_cost(r.circuit.n, r.circuit.m, 1 if r.kind == "expect" else 3)
+             for r in reqs]
+    route = units.route_in_arrival_order(costs, world)
+    mine = [i for i, r in enumerate(route) if r == rank]
 
     def serve(policy):
-        srv = stab.Server(max_active=args.max_active, policy=policy)
+        srv = stab.Server(max_active=args.max_active, policy=policy, device=local)
         t0 = time.perf_counter()
         ids = []
-        for r in reqs:
+        for i in mine:
+            r = reqs[i]
             delay = r.arrival_s - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
@@ -667,21 +690,32 @@ def run_serve(args):
         res = [srv.wait(i) for i in ids]
         srv.close()
         assert all(x["status"] == 0 for x in res)
-        lat = np.array([x["done_s"] - x["submit_s"] for x in res])
-        span = max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)
-        return lat, span, res
+        span = (max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)) if res else 0.0
+        out = [(x["done_s"] - x["submit_s"], x["expect"]) for x in res]
+        full = units.gather_to_root(mine, out, len(reqs), dist if world > 1 else None)
+        spans = [span] * world
+        if world > 1:
+            dist.all_gather_object(spans, span)
+        return full, max(spans)
 
-    lat, span, res = serve("shortest")
-    lat2, span2, res2 = serve("fifo")
+    full, span = serve("shortest")
+    full2, span2 = serve("fifo")
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    lat = np.array([x[0] for x in full])
+    lat2 = np.array([x[0] for x in full2])
     # the same request gives the same numbers under either order
-    worst = max(abs(a["expect"] - b["expect"]) for a, b in zip(res, res2))
+    worst = max(abs(a[1] - b[1]) for a, b in zip(full, full2))
     upd = sum((1 if r.kind == "expect" else 2) * r.circuit.m * 4 ** r.circuit.n for r in reqs)
     print(json.dumps({
         "metric": "p50/p99 latency", "value": float(np.percentile(lat, 50)), "unit": "s",
-        "p99_s": float(np.percentile(lat, 99)), "n_gpus": 1, "higher_is_better": False,
-        "dtype": "f64", "data": "synthetic",
+        "p99_s": float(np.percentile(lat, 99)), "n_gpus": world, "higher_is_better": False,
+        "scaling": "strong", "dtype": "f64", "data": "synthetic",
         "config": {"workload": "serve-c5", "requests": len(reqs), "rate_per_s": 2000,
-                   "max_active": args.max_active, "policy": "shortest estimated work first"},
+                   "max_active": args.max_active, "policy": "shortest estimated work first",
+                   "routing": "arrival order, least assigned work"},
         "circuits_per_s": len(reqs) / span, "updates_per_s": upd / span, "makespan_s": span,
         "fifo": {"p50_s": float(np.percentile(lat2, 50)), "p99_s": float(np.percentile(lat2, 99)),
                  "makespan_s": span2, "circuits_per_s": len(reqs) / span2},

@@ -52,9 +52,80 @@ def test_combine_ranks_single():
     assert total_ms == 50.0 and abs(value - 200.0) < 1e-12
 
 
-def test_batch_shards_cover_every_item_once():
-    import bench
-    items = list(range(4096 * 3))
-    shards = [bench.shard(items, r, 3) for r in range(3)]
-    assert sorted(x for sh in shards for x in sh) == items
-    assert max(len(sh) for sh in shards) - min(len(sh) for sh in shards) <= 1
+def _costs(count, seed):
+    from paper_2502_10685_gb300 import units, workloads as W
+    items = W.uneven_batch(count, seed=seed)
+    return [units.unit_cost(it.circuit.n, it.circuit.m,
+                            it.circuit.n if it.kind == "generators" else 1) for it in items]
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_lpt_partition_covers_every_item_once_and_balances(world):
+    from paper_2502_10685_gb300 import units
+    costs = _costs(600, seed=1003)
+    parts = units.lpt_partition(costs, world)
+    assert sorted(i for p in parts for i in p) == list(range(len(costs)))
+    loads = [sum(costs[i] for i in p) for p in parts]
+    # the list-scheduling bound of LPT: no rank above the mean plus one item
+    assert max(loads) <= sum(costs) / world + max(costs)
+    assert parts == units.lpt_partition(costs, world)          # deterministic
+
+
+def test_lpt_partition_small_cases():
+    from paper_2502_10685_gb300 import units
+    assert units.lpt_partition([], 2) == [[], []]
+    assert units.lpt_partition([5, 5, 5, 5], 2) == [[0, 2], [1, 3]]
+    # LPT on {7, 6, 5, 4, 3, 3} over 2 ranks: 7+4+3 = 14 and 6+5+3 = 14
+    parts = units.lpt_partition([7, 6, 5, 4, 3, 3], 2)
+    assert sorted(sum([7, 6, 5, 4, 3, 3][i] for i in p) for p in parts) == [14, 14]
+    with pytest.raises(ValueError):
+        units.lpt_partition([1], 0)
+
+
+def test_route_in_arrival_order():
+    from paper_2502_10685_gb300 import units
+    # least assigned work first, ties to the lower rank
+    assert units.route_in_arrival_order([4, 1, 1, 1, 2], 2) == [0, 1, 1, 1, 1]
+    assert units.route_in_arrival_order([1, 1, 1], 1) == [0, 0, 0]
+
+
+def _gather_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2502_10685_gb300 import units
+    costs = _costs(200, seed=7)
+    mine = units.lpt_partition(costs, world)[rank]
+    # each rank "runs" its units: the result of item i is a value only i gives
+    results = [{"item": i, "value": i * 0.5} for i in mine]
+    got = units.gather_to_root(mine, results, len(costs), dist)
+    q.put((rank, got))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gather_to_root_gloo(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert all(out[r] is None for r in range(1, world))
+    full = out[0]
+    assert [x["item"] for x in full] == list(range(len(full)))
+    assert all(x["value"] == x["item"] * 0.5 for x in full)
+
+
+def test_gather_to_root_rejects_duplicates_and_gaps():
+    from paper_2502_10685_gb300 import units
+    assert units.gather_to_root([1, 0], ["b", "a"], 2) == ["a", "b"]
+    with pytest.raises(ValueError):
+        units.gather_to_root([0, 0], ["a", "b"], 2)
+    with pytest.raises(ValueError):
+        units.gather_to_root([0], ["a"], 2)
