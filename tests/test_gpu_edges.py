@@ -154,3 +154,39 @@ def test_contexts_of_different_sizes_interleaved(stab):
             assert np.abs(g - oracle.generators(c.n, c.gates, c.thetas)).max() <= 1e-12
     for s, _ in ctxs:
         s.close()
+
+
+@pytest.mark.parametrize("n", [3, 4, 6, 8])
+def test_interleaved_async_calls(stab, n):
+    # Generators on the context stream while observables are swapped and
+    # expectations and gradients queued on the other stream: each result
+    # must be that of its own observable and of the circuit loaded last.
+    import torch
+    c1 = W.layered_ansatz(n, 600 if n <= 6 else 200, seed=900 + n)
+    c2 = W.layered_ansatz(n, 600 if n <= 6 else 200, seed=950 + n)
+    obs = [W.obs_chain(n), W.obs_z(n, 0), W.random_observable(n, 4, seed=9 + n)]
+    s = stab.Stab(n)
+    out = torch.zeros(len(obs), dtype=torch.float64, device="cuda")
+    got = {}
+    for c in (c1, c2):
+        s.load_circuit(c.gates, c.thetas)
+        s.run_generators()
+        for k, o in enumerate(obs):
+            s.set_observable(o)
+            s.expect_async(out[k:k + 1])
+        g = torch.zeros(max(c.n_params, 1), dtype=torch.float64, device="cuda")
+        e = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.grad_async(e, g)
+        s.synchronize()
+        got[id(c)] = (out.cpu().numpy().copy(), s.generators(), float(e[0]))
+    s.close()
+    for c in (c1, c2):
+        ex, gens, e_grad = got[id(c)]
+        for k, o in enumerate(obs):
+            ref = oracle.expect(n, c.gates, c.thetas, o)
+            assert abs(ex[k] - ref) <= 1e-12 * sum(abs(a) for a, _ in o)
+        ref_last = oracle.expect(n, c.gates, c.thetas, obs[-1])
+        assert abs(e_grad - ref_last) <= 1e-12 * sum(abs(a) for a, _ in obs[-1])
+        if n <= 6:
+            ref_g = oracle.generators(n, c.gates, c.thetas)
+            assert np.abs(layout.lib_to_paper(n, gens) - ref_g).max() <= 1e-12
