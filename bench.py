@@ -345,7 +345,7 @@ def run_ours(args):
                 "executed_frac": achieved * executed / peak,
                 "note": note}
 
-    # the plain GPU form: one launch per gate, no fusion, same step
+    # the plain GPU form: one launch per circuit, one pass per gate, no fusion, same step
     plain = None
     if not args.no_plain:
         sp = stab.Stab(c.n, kernel="plain", device=local)
@@ -370,7 +370,7 @@ def run_ours(args):
         assert abs(float(out_p[0].item()) - got) <= 1e-10
         plain = {"value": units_per_step(c) / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
                  "speedup": pms / (total_ms / args.steps),
-                 "form": "one launch per gate, no fusion (STAB_KERNEL_PLAIN)"}
+                 "form": "one launch per circuit, one pass per gate, no fusion (STAB_KERNEL_PLAIN)"}
         sp.close()
 
     line = {
@@ -412,7 +412,8 @@ def run_batch(args):
     """Uneven batch: 4,096 circuits (n ~ U{2..8}, depth ~ U[100, 20000]) including
     the 2m parameter-shift copies of a 6-qubit 2,000-gate circuit, one
     persistent launch per step; compared with one fused launch per circuit and
-    one launch per gate (both timed on a seeded sample, scaled by updates)."""
+    the plain form, one pass per gate (both timed on a seeded sample, scaled by
+    updates)."""
     import numpy as np
     import torch
     import torch.distributed as dist

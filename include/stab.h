@@ -83,10 +83,18 @@ typedef struct stab_term {
 
 /* ---------------------------------------------------------------- options */
 enum stab_kernel {
-    STAB_KERNEL_AUTO = 0,      /* autotuner choice per n */
-    STAB_KERNEL_RESIDENT = 1,  /* one CTA per vector, vector resident in shared memory (n <= 7) */
-    STAB_KERNEL_STREAMED = 2,  /* vector in HBM, one fused pass per launch (any n) */
-    STAB_KERNEL_PLAIN = 3      /* one launch per gate, no fusion: the comparison form */
+    /* The library's choice.  n <= 6: vectors resident in shared memory; plans of
+     * 64 or more passes are cut in two and both parts run at once (the
+     * generators at n <= 4 through the second part's transfer matrix, <O> and
+     * gradients meeting at the cut).  n >= 7: vectors in HBM, passes grouped
+     * into shared-memory tiles where the vectors are small, else one fused pass
+     * per launch (gradients again meet at the cut).  Batches pick their CTAs
+     * per SM by timing a sample of their units. */
+    STAB_KERNEL_AUTO = 0,
+    STAB_KERNEL_RESIDENT = 1,  /* n <= 6: one CTA per vector through the whole circuit, never cut */
+    STAB_KERNEL_STREAMED = 2,  /* vector in HBM, fused passes (any n) */
+    STAB_KERNEL_PLAIN = 3      /* the comparison form: one pass per gate, no fusion, no cut; one
+                                  resident launch per circuit at n <= 6, one launch per gate above */
 };
 
 /* Device allocator hooks.  With alloc == NULL the library uses cudaMallocAsync
