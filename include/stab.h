@@ -433,7 +433,11 @@ int stab_plan_info(stab_ctx *ctx, int64_t *n_gates, int64_t *n_passes, int32_t *
  * sweep), *gen_units (vectors of the generators' split sweep -- the n
  * generators and rho_0 through [0, cut), the 4^n - 1 columns of T; 0 when not
  * split; stab_density_matrix uses the same sweep, r = T r_1) and
- * *expect_units (of the expectation's, 0 when not split).
+ * *expect_units (of the expectation's own launch, 0 when not split).  At
+ * n <= 3 a long plan is cut into K >= 3 parts of equal pass counts (cut = the
+ * first cut): the sweep carries the K - 1 later parts' transfer matrices,
+ * the generators are T_K ... T_2 a_k, and <O> = sum_P o_P (T_K ... T_2 r_1)_P
+ * reuses the sweep made for the same angles (*expect_units = 0).
  * Any output pointer may be NULL.  Errors: STAB_E_INVAL (ctx NULL). */
 int stab_split_info(stab_ctx *ctx, int64_t *cut, int32_t *gen_units, int32_t *expect_units);
 

@@ -99,6 +99,44 @@ __global__ void __launch_bounds__(256) k_apply_transfer(const double *T, const d
     }
 }
 
+// v_k <- T_{S-1} ... T_1 T_0 v_k for small vectors (E = 4^n <= 64): one CTA
+// per vector, the vector in shared memory.  For each matrix, thread t sums
+// the columns j = t / E, t / E + 256 / E, ... of output row i = t % E, and the
+// 256 / E shares of a row are added in a fixed order.  With terms (one
+// vector), dot_out receives sum_k coeff_k v[idx_k], summed in term order.
+__global__ void __launch_bounds__(256) k_apply_chain(const double *T, int n_mats,
+                                                     const double *in, double *out, int E,
+                                                     const DevTerm *terms, int n_terms,
+                                                     double *dot_out) {
+    __shared__ double v[64];
+    __shared__ double part[256];
+    const int t = threadIdx.x;
+    const int groups = 256 / E;
+    const int i = t % E, p = t / E;
+    const size_t at = (size_t)blockIdx.x * E;
+    if (t < E) v[t] = in[at + t];
+    __syncthreads();
+    for (int s = 0; s < n_mats; ++s) {
+        const double *M = T + (size_t)s * E * E;
+        double acc = 0.0;
+        for (int j = p; j < E; j += groups) acc = fma(M[(size_t)j * E + i], v[j], acc);
+        part[t] = acc;
+        __syncthreads();
+        if (t < E) {
+            double tot = 0.0;
+            for (int g = 0; g < groups; ++g) tot += part[g * E + t];
+            v[t] = tot;
+        }
+        __syncthreads();
+    }
+    if (out && t < E) out[at + t] = v[t];
+    if (dot_out && t == 0) {
+        double acc = 0.0;
+        for (int k = 0; k < n_terms; ++k) acc = fma(terms[k].coeff, v[terms[k].idx], acc);
+        *dot_out = acc;
+    }
+}
+
 // ---------------------------------------------------------------- transfer columns
 //
 // Columns of the transfer matrix T of a stream at n = 4: column j is the
@@ -463,6 +501,15 @@ cudaError_t launch_adjoint_split(int n, const AdjointSplitArgs &a, cudaStream_t 
     case 6: return launch_adjoint_split_n<6>(a, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_apply_chain(const double *T, int n_mats, const double *in, double *out,
+                               int n_vec, int n, const DevTerm *terms, int n_terms,
+                               double *dot_out, cudaStream_t st) {
+    const int E = 1 << (2 * n);
+    if (n < 1 || n > 3 || n_vec < 1 || (dot_out && n_vec != 1)) return cudaErrorInvalidValue;
+    k_apply_chain<<<n_vec, 256, 0, st>>>(T, n_mats, in, out, E, terms, n_terms, dot_out);
+    return cudaGetLastError();
 }
 
 int transfer_cols_ctas(int n) { return n == kColN ? kColE / 2 : 0; }

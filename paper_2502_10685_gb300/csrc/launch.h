@@ -154,6 +154,12 @@ cudaError_t launch_resident_stream(int n, const StreamArgs &a, cudaStream_t st);
 // string j through its passes) into tmat (column j at tmat + j * 4^n), two
 // columns per CTA; n = 4 only.  transfer_cols_ctas(n): its grid (0: n unsupported).
 int transfer_cols_ctas(int n);
+// out_k = T_{n_mats-1} ... T_0 in_k for n <= 3 (matrices of 4^n x 4^n, column
+// j of matrix s at T + s 16^n + j 4^n); with dot_out (n_vec = 1) also
+// <O> = sum of terms' coeff x out[idx].  out may be null.
+cudaError_t launch_apply_chain(const double *T, int n_mats, const double *in, double *out,
+                               int n_vec, int n, const DevTerm *terms, int n_terms,
+                               double *dot_out, cudaStream_t st);
 cudaError_t launch_transfer_cols(const Rec *stream, int n_chunks, double *tmat, int n,
                                  int32_t *status, cudaStream_t st);
 cudaError_t launch_apply_transfer(const double *T, const double *a, double *out, int n_vec,

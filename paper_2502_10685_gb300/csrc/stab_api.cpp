@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <thread>
@@ -50,6 +51,9 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Resident plans with at least this many passes also get split streams.
 constexpr int kSplitMinPasses = 64;
+// Plans of at least this many passes build their instruction streams on
+// several host threads.
+constexpr int kThreadedStreamPasses = 2048;
 
 // Instruction stream of a plan for the resident kernels, with the indices of
 // the records the encode kernel fills (rotations and maps).
@@ -74,6 +78,16 @@ struct DevPlan {
     // split < 0: none
     DevStreamBuf h1, h2, h2b, h1b;
     int split = -1;
+    // n <= 3, long plans: K >= 3 forward parts, part k = passes [cuts[k], cuts[k+1])
+    // (the generators, rho_0 and <O> through the chain of the parts' transfer
+    // matrices); empty otherwise
+    std::vector<DevStreamBuf> parts;
+    std::vector<int> cuts;
+    std::vector<DevStreamBuf *> all_streams() {
+        std::vector<DevStreamBuf *> v = {&sf, &sb, &h1, &h2, &h2b, &h1b};
+        for (DevStreamBuf &p : parts) v.push_back(&p);
+        return v;
+    }
     DevBuf buf;
     Program prog{};
     const int32_t *map_gate_idx = nullptr;
@@ -137,6 +151,11 @@ struct stab_ctx {
     std::vector<const void *> key_g, key_e;
     int n_units_g = 0;
     size_t split_smem = 0;
+    int sms = 0;                     // SMs of the device
+    // the split sweep's launch (first-part vectors, columns of T) was made for
+    // these angles when tx_gen == param_gen; ev_tx marks its end on st
+    int64_t param_gen = 0, tx_gen = -1;
+    cudaEvent_t ev_tx = nullptr;
     DevBuf status;                   // int32 set by kernels whose bounded waits gave up
     GraphCache g_gens, g_expect, g_grad; // streamed launch sequences (n > resident sizes)
     int64_t plan_gen = 0;            // bumped whenever a plan is rebuilt
@@ -223,15 +242,12 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     const size_t b_pptr = align256(H.param_ptr.size() * sizeof(int32_t));
     const size_t b_prot = align256(H.param_rot.size() * sizeof(int32_t));
     const size_t b_tabs = align256(H.tabs.size() * sizeof(DevTab));
-    const size_t b_sf = align256(P.sf.host.size() * sizeof(Rec));
-    const size_t b_sfe = align256(P.sf.enc.size() * sizeof(int32_t));
-    const size_t b_sb = align256(P.sb.host.size() * sizeof(Rec));
-    const size_t b_sbe = align256(P.sb.enc.size() * sizeof(int32_t));
-    size_t b_split = 0;
-    for (const DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b, &P.h1b})
-        b_split += align256(S->host.size() * sizeof(Rec)) + align256(S->enc.size() * 4);
+    const std::vector<DevStreamBuf *> streams = P.all_streams();
+    size_t b_streams = 0;
+    for (const DevStreamBuf *S : streams)
+        b_streams += align256(S->host.size() * sizeof(Rec)) + align256(S->enc.size() * 4);
     const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot + b_tabs +
-                         b_sf + b_sfe + b_sb + b_sbe + b_split;
+                         b_streams;
     RC(c->dalloc(P.buf, total, c->st));
     CK(cudaEventSynchronize(c->ev_stage));
     RC(c->host_stage(c->stage, c->stage_bytes, total));
@@ -252,11 +268,7 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     P.param_ptr = (const int32_t *)put(H.param_ptr.data(), H.param_ptr.size() * 4, b_pptr);
     P.param_rot = (const int32_t *)put(H.param_rot.data(), H.param_rot.size() * 4, b_prot);
     P.prog.tabs = (const DevTab *)put(H.tabs.data(), H.tabs.size() * sizeof(DevTab), b_tabs);
-    P.sf.dev = (Rec *)put(P.sf.host.data(), P.sf.host.size() * sizeof(Rec), b_sf);
-    P.sf.enc_dev = (const int32_t *)put(P.sf.enc.data(), P.sf.enc.size() * 4, b_sfe);
-    P.sb.dev = (Rec *)put(P.sb.host.data(), P.sb.host.size() * sizeof(Rec), b_sb);
-    P.sb.enc_dev = (const int32_t *)put(P.sb.enc.data(), P.sb.enc.size() * 4, b_sbe);
-    for (DevStreamBuf *S : {&P.h1, &P.h2, &P.h2b, &P.h1b}) {
+    for (DevStreamBuf *S : streams) {
         S->dev = (Rec *)put(S->host.data(), S->host.size() * sizeof(Rec),
                             align256(S->host.size() * sizeof(Rec)));
         S->enc_dev = (const int32_t *)put(S->enc.data(), S->enc.size() * 4,
@@ -284,7 +296,7 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
                                    P.map_gate_idx, P.raw, th, c->st));
             c->launches++;
         }
-        for (DevStreamBuf *S : {&P.sf, &P.sb, &P.h1, &P.h2, &P.h2b, &P.h1b}) {
+        for (DevStreamBuf *S : P.all_streams()) {
             if (S->enc.empty()) continue;
             CK(launch_encode_stream(S->dev, S->enc_dev, (int)S->enc.size(), P.prog.maps, th,
                                     c->st));
@@ -333,28 +345,56 @@ void make_stream(DevPlan &P, bool backward) {
 // split_frac > 0 (and enough passes) also the split streams cut at that
 // fraction of the passes.  A split gradient plan (grad) needs only the four
 // half streams, not the whole-circuit ones.
-void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false) {
+void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_parts = 2) {
     P.streams = true;
     const int np = (int)P.host.passes.size();
+    if (!grad && n_parts >= 3) {
+        // K forward parts of equal pass counts (on up to four threads when long)
+        P.sf = P.sb = P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
+        P.parts.resize((size_t)n_parts);
+        P.cuts.assign((size_t)n_parts + 1, 0);
+        for (int k = 0; k <= n_parts; ++k) P.cuts[k] = (int)((int64_t)np * k / n_parts);
+        P.split = P.cuts[1];
+        const int n_thr = np < kThreadedStreamPasses ? 1 : std::min(n_parts, 4);
+        auto work = [&P, n_parts](int t, int n_t) {
+            for (int k = t; k < n_parts; k += n_t)
+                make_stream_range(P, P.parts[k], false, P.cuts[k], P.cuts[k + 1]);
+        };
+        std::vector<std::thread> thr;
+        for (int t = 1; t < n_thr; ++t) thr.emplace_back(work, t, n_thr);
+        work(0, n_thr);
+        for (std::thread &x : thr) x.join();
+        return;
+    }
+    P.parts.clear();
+    P.cuts.clear();
     P.split = (split_frac > 0.0 && np >= kSplitMinPasses) ? (int)(np * split_frac) : -1;
     // streams that are rebuilt keep their capacity; the others are released
     if (P.split < 0) P.h1 = P.h2 = P.h2b = DevStreamBuf();
     if (!(grad && P.split >= 0)) P.h1b = DevStreamBuf();
+    // below kThreadedStreamPasses passes the streams are built on the calling
+    // thread: starting threads would cost more than the work
+    const bool threads = np >= kThreadedStreamPasses;
+    auto run_all = [threads](std::vector<std::function<void()>> jobs) {
+        if (!threads) {
+            for (auto &j : jobs) j();
+            return;
+        }
+        std::vector<std::thread> thr;
+        for (size_t k = 1; k < jobs.size(); ++k) thr.emplace_back(jobs[k]);
+        jobs[0]();
+        for (std::thread &x : thr) x.join();
+    };
     if (grad && P.split >= 0) {
         P.sf = P.sb = DevStreamBuf();
-        std::thread t1([&P] { make_stream_range(P, P.h1, false, 0, P.split); });
-        std::thread t2([&P, np] { make_stream_range(P, P.h2, false, P.split, np); });
-        std::thread t3([&P, np] { make_stream_range(P, P.h2b, true, P.split, np); });
-        make_stream_range(P, P.h1b, true, 0, P.split);
-        t1.join();
-        t2.join();
-        t3.join();
+        run_all({[&P] { make_stream_range(P, P.h1b, true, 0, P.split); },
+                 [&P] { make_stream_range(P, P.h1, false, 0, P.split); },
+                 [&P, np] { make_stream_range(P, P.h2, false, P.split, np); },
+                 [&P, np] { make_stream_range(P, P.h2b, true, P.split, np); }});
         return;
     }
     if (P.split < 0) {
-        std::thread bwd([&P] { make_stream(P, true); });
-        make_stream(P, false);
-        bwd.join();
+        run_all({[&P] { make_stream(P, false); }, [&P] { make_stream(P, true); }});
         return;
     }
     // A split plan reads the halves: the generators (n <= 4) and the density
@@ -364,13 +404,12 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false) {
     P.sb = DevStreamBuf();
     const bool whole_fwd = P.host_n > 4;
     if (!whole_fwd) P.sf = DevStreamBuf();
-    std::thread t1([&P] { make_stream_range(P, P.h1, false, 0, P.split); });
-    std::thread t2([&P, np] { make_stream_range(P, P.h2, false, P.split, np); });
-    std::thread t3([&P, np] { make_stream_range(P, P.h2b, true, P.split, np); });
-    if (whole_fwd) make_stream(P, false);
-    t1.join();
-    t2.join();
-    t3.join();
+    std::vector<std::function<void()>> jobs = {
+        [&P] { make_stream_range(P, P.h1, false, 0, P.split); },
+        [&P, np] { make_stream_range(P, P.h2, false, P.split, np); },
+        [&P, np] { make_stream_range(P, P.h2b, true, P.split, np); }};
+    if (whole_fwd) jobs.push_back([&P] { make_stream(P, false); });
+    run_all(std::move(jobs));
 }
 
 void no_streams(DevPlan &P) {
@@ -378,6 +417,8 @@ void no_streams(DevPlan &P) {
     P.sf = DevStreamBuf();
     P.sb = DevStreamBuf();
     P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
+    P.parts.clear();
+    P.cuts.clear();
     P.split = -1;
 }
 
@@ -500,6 +541,23 @@ void make_tile_group(int n, int n_vec, const std::vector<const DevPass *> &group
 // carries them two to a CTA.
 
 bool split_gens_ok(const stab_ctx *c) { return c->fwd.split >= 0 && c->n <= 4; }
+
+// n <= 3: parts of a long plan for the chain of transfer matrices -- as many
+// as the SMs hold one unit each (n generators and rho_0 through the first
+// part, 4^n - 1 columns per further part, two CTAs left for other work),
+// each part at least kChainMinPasses passes; < 3 means the two-part split.
+constexpr int kChainMinPasses = 32;
+int chain_parts(const stab_ctx *c) {
+    if (c->n > 3) return 2;
+    const int E = 1 << (2 * c->n);
+    const int np = (int)c->fwd.host.passes.size();
+    const int by_sms = 1 + (c->sms - (c->n + 1) - 2) / (E - 1);
+    const int by_len = np / kChainMinPasses;
+    const int k = std::min(by_sms, by_len);
+    return k >= 3 ? k : 2;
+}
+
+bool chain_mode(const stab_ctx *c) { return !c->fwd.parts.empty(); }
 bool split_expect_ok(const stab_ctx *c) { return c->fwd.split >= 0; }
 
 int split_setup(stab_ctx *c, cudaStream_t s) {
@@ -521,20 +579,23 @@ int split_setup(stab_ctx *c, cudaStream_t s) {
 // the basis strings into the columns of T.
 int split_units_g(stab_ctx *c) {
     const int n = c->n, E = 1 << (2 * n);
+    // one transfer matrix per part after the first
+    const int n_mats = chain_mode(c) ? (int)c->fwd.parts.size() - 1 : 1;
     RC(split_setup(c, c->st));
-    RC(c->dalloc(c->tmat, (size_t)E * E * 8, c->st));
+    RC(c->dalloc(c->tmat, (size_t)n_mats * E * E * 8, c->st));
     RC(c->dalloc(c->avec, (size_t)(n + 1) * E * 8, c->st));
     RC(c->dalloc(c->bterms, (size_t)E * sizeof(DevTerm), c->st));
-    RC(c->dalloc(c->units_g, (size_t)(E + n) * sizeof(BatchUnit), c->st));
-    const std::vector<const void *> key = {(const void *)c->plan_gen, c->fwd.h1.dev,
+    RC(c->dalloc(c->units_g, (size_t)(n_mats * (E - 1) + n + 1) * sizeof(BatchUnit), c->st));
+    const DevStreamBuf &first = chain_mode(c) ? c->fwd.parts[0] : c->fwd.h1;
+    const std::vector<const void *> key = {(const void *)c->plan_gen, first.dev,
                                            c->fwd.h2.dev, c->tmat.p, c->avec.p, c->bterms.p,
-                                           c->units_g.p};
+                                           c->units_g.p, (const void *)(intptr_t)n_mats};
     if (key == c->key_g) return STAB_OK;
     std::vector<BatchUnit> U;
     for (int k = 0; k < n; ++k) {
         BatchUnit u{};
-        u.stream = c->fwd.h1.dev;
-        u.n_chunks = c->fwd.h1.n_chunks;
+        u.stream = first.dev;
+        u.n_chunks = first.n_chunks;
         u.n = (int8_t)n;
         u.init = INIT_GENERATOR;
         u.gen = (int16_t)k;
@@ -544,8 +605,8 @@ int split_units_g(stab_ctx *c) {
     {
         // rho_0 through the first part, for the density matrix (r = T r_1)
         BatchUnit u{};
-        u.stream = c->fwd.h1.dev;
-        u.n_chunks = c->fwd.h1.n_chunks;
+        u.stream = first.dev;
+        u.n_chunks = first.n_chunks;
         u.n = (int8_t)n;
         u.init = INIT_RHO0;
         u.out = (double *)c->avec.p + (size_t)n * E;
@@ -555,22 +616,27 @@ int split_units_g(stab_ctx *c) {
     // outnumber the SMs) the two-column CTAs of k_transfer_cols
     const int n_basis = transfer_cols_ctas(n) > 0 ? 1 : E;
     std::vector<DevTerm> basis((size_t)E);
-    for (int j = 1; j < n_basis; ++j) {
-        basis[(size_t)j] = DevTerm{1.0, (uint64_t)j};
-        BatchUnit u{};
-        u.stream = c->fwd.h2.dev;
-        u.n_chunks = c->fwd.h2.n_chunks;
-        u.n = (int8_t)n;
-        u.init = INIT_TERMS;
-        u.terms = (const DevTerm *)c->bterms.p + j;
-        u.n_terms = 1;
-        u.out = (double *)c->tmat.p + (size_t)j * E;
-        U.push_back(u);
+    for (int j = 1; j < E; ++j) basis[(size_t)j] = DevTerm{1.0, (uint64_t)j};
+    for (int mtx = 0; mtx < n_mats; ++mtx) {
+        const DevStreamBuf &part = chain_mode(c) ? c->fwd.parts[(size_t)mtx + 1] : c->fwd.h2;
+        for (int j = 1; j < n_basis; ++j) {
+            BatchUnit u{};
+            u.stream = part.dev;
+            u.n_chunks = part.n_chunks;
+            u.n = (int8_t)n;
+            u.init = INIT_TERMS;
+            u.terms = (const DevTerm *)c->bterms.p + j;
+            u.n_terms = 1;
+            u.out = (double *)c->tmat.p + (size_t)mtx * E * E + (size_t)j * E;
+            U.push_back(u);
+        }
     }
-    // column 0 of T: the identity string stays itself
-    CK(cudaMemsetAsync(c->tmat.p, 0, (size_t)E * 8, c->st));
-    const double one = 1.0;
-    CK(cudaMemcpyAsync(c->tmat.p, &one, 8, cudaMemcpyHostToDevice, c->st));
+    // column 0 of every T: the identity string stays itself
+    std::vector<double> col0((size_t)E, 0.0);
+    col0[0] = 1.0;
+    for (int mtx = 0; mtx < n_mats; ++mtx)
+        CK(cudaMemcpyAsync((double *)c->tmat.p + (size_t)mtx * E * E, col0.data(), (size_t)E * 8,
+                           cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->bterms.p, basis.data(), basis.size() * sizeof(DevTerm),
                        cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->units_g.p, U.data(), U.size() * sizeof(BatchUnit),
@@ -603,6 +669,24 @@ int split_run_g(stab_ctx *c) {
         c->launches++;
     } else {
         CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
+    }
+    c->launches++;
+    CK(cudaEventRecord(c->ev_tx, c->st));
+    c->tx_gen = c->param_gen;
+    return STAB_OK;
+}
+
+// Applies the chain of the parts' transfer matrices (chain mode) or the one
+// transfer matrix to n_vec first-part vectors of avec starting at `first`.
+int split_apply(stab_ctx *c, int first, int n_vec, double *out, const DevTerm *terms, int n_terms,
+                double *dot_out, cudaStream_t s) {
+    const size_t E = (size_t)1 << (2 * c->n);
+    const double *in = (const double *)c->avec.p + (size_t)first * E;
+    if (chain_mode(c)) {
+        CK(launch_apply_chain((const double *)c->tmat.p, (int)c->fwd.parts.size() - 1, in, out,
+                              n_vec, c->n, terms, n_terms, dot_out, s));
+    } else {
+        CK(launch_apply_transfer((const double *)c->tmat.p, in, out, n_vec, c->n, s));
     }
     c->launches++;
     return STAB_OK;
@@ -850,6 +934,7 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
     cudaError_t e = cudaSuccess;
     if (dev < 0) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
         c->device = dev;
         if (o.stream || o.stream_given) {
@@ -864,6 +949,7 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_tx, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_stage, c->st);
@@ -903,6 +989,7 @@ int stab_destroy(stab_ctx *c) {
     if (c->stage) cudaFreeHost(c->stage);
     if (c->aux_stage) cudaFreeHost(c->aux_stage);
     if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+    if (c->ev_tx) cudaEventDestroy(c->ev_tx);
     if (c->ev_aux) cudaEventDestroy(c->ev_aux);
     if (c->ev_stage) cudaEventDestroy(c->ev_stage);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -940,13 +1027,14 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
         // first-part unit alone on its SM, at 0.56 (measured optimum).
         const bool split = c->kernel == STAB_KERNEL_AUTO && c->fuse;
         const double cut = transfer_cols_ctas(c->n) > 0 ? 0.56 : 0.5;
-        make_streams(c->fwd, split ? cut : 0.0);
+        make_streams(c->fwd, split ? cut : 0.0, false, split ? chain_parts(c) : 2);
     }
     else no_streams(c->fwd);
     RC(upload_thetas_host(c, thetas));
     RC(upload_plan(c, c->fwd));
     RC(encode_plan(c, c->fwd));
     CK(cudaEventRecord(c->ev_ready, c->st));
+    c->param_gen++;
     c->loaded = true;
     return STAB_OK;
 }
@@ -968,6 +1056,7 @@ int stab_set_params(stab_ctx *c, const double *thetas, int is_device) {
     RC(encode_plan(c, c->fwd));
     c->grad.encoded = false;
     c->gens_valid = false;
+    c->param_gen++;
     CK(cudaEventRecord(c->ev_ready, c->st));
     return STAB_OK;
 }
@@ -981,9 +1070,7 @@ int stab_run_generators(stab_ctx *c) {
     RC(c->dalloc(c->gens, bytes, c->st));
     if (c->use_resident() && split_gens_ok(c)) {
         RC(split_run_g(c));
-        CK(launch_apply_transfer((const double *)c->tmat.p, (const double *)c->avec.p,
-                                 (double *)c->gens.p, n, n, c->st));
-        c->launches++;
+        RC(split_apply(c, 0, n, (double *)c->gens.p, nullptr, 0, nullptr, c->st));
         c->gens_cur = (double *)c->gens.p;
     } else if (c->use_resident()) {
         StreamArgs a{};
@@ -1061,7 +1148,15 @@ int stab_expect_async(stab_ctx *c, double *out_dev) {
     cudaStream_t s = c->aux;
     CK(cudaStreamWaitEvent(s, c->ev_ready, 0));
     const int32_t nt = c->n_obs_terms;
-    if (c->use_resident() && split_expect_ok(c)) {
+    if (c->use_resident() && chain_mode(c)) {
+        // <O> = sum_P o_P r_P with r = T_K ... T_2 r_1 (Schroedinger picture;
+        // the orthogonal maps make it equal to the x-free sum of U^dagger O U):
+        // the generators' launch made for these angles carries rho_0 and the
+        // parts' transfer matrices; else it runs here first
+        if (c->tx_gen != c->param_gen) RC(split_run_g(c));
+        CK(cudaStreamWaitEvent(s, c->ev_tx, 0));
+        RC(split_apply(c, c->n, 1, nullptr, (const DevTerm *)c->terms.p, nt, out_dev, s));
+    } else if (c->use_resident() && split_expect_ok(c)) {
         RC(split_units_e(c, s));
         BatchArgs a{};
         a.units = (const BatchUnit *)c->units_e.p;
@@ -1423,10 +1518,7 @@ int stab_density_matrix(stab_ctx *c, double *out, int out_is_device) {
         // r = T r_1: rho_0 through the first part, then the second part's
         // transfer matrix (built alongside, as for the generators)
         RC(split_run_g(c));
-        const size_t E = (size_t)1 << (2 * n);
-        CK(launch_apply_transfer((const double *)c->tmat.p, (const double *)c->avec.p + n * E, r,
-                                 1, n, c->st));
-        c->launches++;
+        RC(split_apply(c, n, 1, r, nullptr, 0, nullptr, c->st));
     } else if (c->use_resident()) {
         StreamArgs a{};
         a.stream = c->fwd.sf.dev;
@@ -1481,8 +1573,9 @@ int stab_split_info(stab_ctx *c, int64_t *cut, int32_t *gen_units, int32_t *expe
     const bool on = c->loaded && c->use_resident() && c->fwd.split >= 0;
     const int E = 1 << (2 * c->n);
     if (cut) *cut = on ? c->fwd.split : -1;
-    if (gen_units) *gen_units = on && split_gens_ok(c) ? c->n + E : 0;
-    if (expect_units) *expect_units = on && split_expect_ok(c) ? 2 : 0;
+    const int n_mats = chain_mode(c) ? (int)c->fwd.parts.size() - 1 : 1;
+    if (gen_units) *gen_units = on && split_gens_ok(c) ? c->n + 1 + n_mats * (E - 1) : 0;
+    if (expect_units) *expect_units = on && !chain_mode(c) && split_expect_ok(c) ? 2 : 0;
     return STAB_OK;
 }
 

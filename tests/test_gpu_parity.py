@@ -368,6 +368,39 @@ def test_density_matrix_split_sweep(stab, n):
     assert abs(np.trace(rho) - 1) <= 1e-12
 
 
+@pytest.mark.parametrize("n,m", [(2, 4000), (3, 6000)])
+def test_chain_of_transfer_matrices(stab, n, m):
+    """n <= 3, long circuits: cut into K >= 3 parts; the generators, rho and
+    <O> go through the chain of the later parts' transfer matrices.  <O> alone
+    runs the sweep itself; after the generators it reuses theirs; new angles
+    must not reuse a sweep made for the old ones."""
+    c = W.layered_ansatz(n, m, seed=620 + n)
+    obs = W.random_observable(n, 5, seed=62 + n)
+    l1 = sum(abs(a) for a, _ in obs)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    cut, vectors, expect_units = s.split_info()
+    assert cut > 0 and expect_units == 0
+    assert vectors >= n + 1 + 2 * (4 ** n - 1)          # at least two transfer matrices
+    assert abs(s.expect(obs) - oracle.expect(n, c.gates, c.thetas, obs)) <= 1e-12 * l1
+    s.run_generators()
+    assert abs(s.expect(W.obs_chain(n)) - oracle.expect(n, c.gates, c.thetas, W.obs_chain(n))) \
+        <= 1e-12 * sum(abs(a) for a, _ in W.obs_chain(n))
+    got = layout.lib_to_paper(n, s.generators())
+    assert np.abs(got - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12
+    rho = s.density_matrix()
+    perm = _bitrev_perm(n)
+    assert np.abs(rho[np.ix_(perm, perm)] - oracle.density_matrix(n, c.gates, c.thetas)).max() \
+        <= 1e-12
+    th2 = np.random.default_rng(5).uniform(0, 2 * np.pi, c.n_params)
+    s.set_params(th2)
+    assert abs(s.expect(obs) - oracle.expect(n, c.gates, th2, obs)) <= 1e-12 * l1
+    s.run_generators()
+    got = layout.lib_to_paper(n, s.generators())
+    assert np.abs(got - oracle.generators(n, c.gates, th2)).max() <= 1e-12
+    s.close()
+
+
 @pytest.mark.parametrize("n", [7, 8])
 def test_long_clifford_runs_through_tableaus(stab, n):
     """Streamed plans apply long runs of Clifford gates as one gather through
