@@ -190,3 +190,29 @@ def test_interleaved_async_calls(stab, n):
         if n <= 6:
             ref_g = oracle.generators(n, c.gates, c.thetas)
             assert np.abs(layout.lib_to_paper(n, gens) - ref_g).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n,m", [(2, 8 * 32), (2, 8 * 40), (3, 12 * 25)])
+def test_chain_edges(stab, n, m):
+    # the shortest plans that still cut into K >= 3 parts, an observable with
+    # an identity term and a repeated string, and a Clifford-only stretch
+    base = W.layered_ansatz(n, m, seed=700 + m)
+    cliff = W.random_circuit(n, 200, seed=701 + m, clifford_only=True)
+    g = np.concatenate([base.gates, cliff.gates, base.gates])
+    th = np.concatenate([base.thetas, base.thetas + 0.25])
+    g = g.copy()
+    off = len(base.gates) + len(cliff.gates)
+    rot = np.isin(g["op"][off:], [W.OPS[r] for r in ("RX", "RY", "RZ")])
+    g["param"][off:][rot] += base.n_params
+    c = W.Circuit(n, g, th)
+    obs = [(0.5, "I" * n), (1.0, "Z" + "I" * (n - 1)), (0.25, "Z" + "I" * (n - 1)),
+           (-0.75, "X" * n)]
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    cut, vectors, eu = s.split_info()
+    ref = oracle.expect(n, c.gates, c.thetas, obs)
+    assert abs(s.expect(obs) - ref) <= 1e-12 * sum(abs(a) for a, _ in obs)
+    s.run_generators()
+    got = layout.lib_to_paper(n, s.generators())
+    assert np.abs(got - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12
+    s.close()
