@@ -217,21 +217,44 @@ __device__ __forceinline__ uint32_t sp_mul_phase(uint32_t ax, uint32_t az, uint3
     return (uint32_t)(__popc(plus) - __popc(minus)) & 3u;
 }
 
+// The tableau regrouped by chunks of kSpChunkQubits qubits: entry
+// (chunk c, subset t) is the ordered product prod_{q in c} (U X_q U^dagger)^{x_q}
+// (U Z_q U^dagger)^{z_q} of the generator images the subset selects (bit j of
+// t: x of qubit 4c + j, bit 4 + j: its z), as a Hermitian string and a phase
+// i^e.  One block per (run, chunk), one thread per subset.
+__global__ void k_sp_tab_chunks(const SpTab *tabs, int n, SpChunk *chunks) {
+    const int r = blockIdx.x / kSpChunks, c = blockIdx.x % kSpChunks, t = threadIdx.x;
+    const uint64_t zmask = (1ull << n) - 1;
+    uint32_t rx = 0, rz = 0, e = 0;
+    for (int j = 0; j < kSpChunkQubits; ++j) {
+        const int q = kSpChunkQubits * c + j;
+        if (q >= n) break;
+        for (int part = 0; part < 2; ++part) {   // X_q, then Z_q
+            if (!((t >> (part * kSpChunkQubits + j)) & 1)) continue;
+            const SpTab g = tabs[(size_t)r * 64 + (part ? n + q : q)];
+            const uint32_t gx = (uint32_t)(g.key >> n), gz = (uint32_t)(g.key & zmask);
+            e += sp_mul_phase(rx, rz, gx, gz) + (g.neg ? 2u : 0u);
+            rx ^= gx;
+            rz ^= gz;
+        }
+    }
+    chunks[(size_t)blockIdx.x * 256 + t] = SpChunk{rx, rz, e & 3u, 0u};
+}
+
 // U P U^dagger from the tableau: P(x, z) = i^{|x & z|} prod_q X_q^{x_q} Z_q^{z_q}
 // (Y = i X Z), so its image is i^{|x & z|} times the product of the generator
-// images in that order, each factor adding its phase and sign.
+// images in that order, each factor adding its phase and sign.  The product
+// is taken chunk by chunk from the run's chunk table (staged in shared
+// memory): ceil(n / 4) lookups and string products per term instead of one
+// product per set bit.
 __global__ void __launch_bounds__(kSpThreads) k_sp_cliff_tab(uint64_t *keys, double *vals,
                                                               int64_t *counts,
                                                               const int32_t *flags, int step,
-                                                              int n, const SpTab *tab) {
-    __shared__ uint32_t tx[64], tz[64], ts[64];
+                                                              int n, const SpChunk *chunks) {
+    __shared__ SpChunk sc[kSpChunks * 256];
     if (sp_stopped_before(flags, step)) return;
-    if (threadIdx.x < 2 * n) {
-        const SpTab t = tab[threadIdx.x];
-        tx[threadIdx.x] = (uint32_t)(t.key >> n);
-        tz[threadIdx.x] = (uint32_t)(t.key & ((1ull << n) - 1));
-        ts[threadIdx.x] = t.neg ? 2u : 0u;
-    }
+    const int n_ch = (n + kSpChunkQubits - 1) / kSpChunkQubits;
+    for (int k = threadIdx.x; k < n_ch * 256; k += blockDim.x) sc[k] = chunks[k];
     __syncthreads();
     const int64_t count = counts[step];
     if (blockIdx.x == 0 && threadIdx.x == 0) counts[step + 1] = count;
@@ -241,17 +264,12 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_cliff_tab(uint64_t *keys, dou
         const uint64_t k = keys[i];
         const uint32_t x = (uint32_t)(k >> n), z = (uint32_t)(k & zmask);
         uint32_t rx = 0, rz = 0, e = (uint32_t)__popc(x & z);
-        for (int q = 0; q < n; ++q) {
-            if ((x >> q) & 1u) {
-                e += sp_mul_phase(rx, rz, tx[q], tz[q]) + ts[q];
-                rx ^= tx[q];
-                rz ^= tz[q];
-            }
-            if ((z >> q) & 1u) {
-                e += sp_mul_phase(rx, rz, tx[n + q], tz[n + q]) + ts[n + q];
-                rx ^= tx[n + q];
-                rz ^= tz[n + q];
-            }
+        for (int c = 0; c < n_ch; ++c) {
+            const uint32_t sh = (uint32_t)(kSpChunkQubits * c);
+            const SpChunk g = sc[c * 256 + (((x >> sh) & 15u) | (((z >> sh) & 15u) << 4))];
+            e += g.e + sp_mul_phase(rx, rz, g.x, g.z);
+            rx ^= g.x;
+            rz ^= g.z;
         }
         // a Hermitian image: e is 0 or 2 (mod 4)
         keys[i] = ((uint64_t)rx << n) | rz;
@@ -474,17 +492,20 @@ cudaError_t launch_sp_cliff(uint64_t *keys, double *vals, int64_t *counts, const
 
 cudaError_t launch_sp_tableau(const SpGate *gates, const int32_t *run_first,
                               const int32_t *run_count, int n_runs, int n, SpTab *tabs,
-                              cudaStream_t st) {
+                              SpChunk *chunks, cudaStream_t st) {
     if (n_runs == 0) return cudaSuccess;
     k_sp_tableau<<<n_runs, 64, 0, st>>>(gates, run_first, run_count, n, tabs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sp_tab_chunks<<<n_runs * kSpChunks, 256, 0, st>>>(tabs, n, chunks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sp_cliff_tab(uint64_t *keys, double *vals, int64_t *counts,
-                                const int32_t *flags, int step, int n, const SpTab *tab,
+                                const int32_t *flags, int step, int n, const SpChunk *chunks,
                                 int64_t bound, cudaStream_t st) {
     k_sp_cliff_tab<<<sp_grid(bound), kSpThreads, 0, st>>>(keys, vals, counts, flags, step, n,
-                                                           tab);
+                                                           chunks);
     return cudaGetLastError();
 }
 

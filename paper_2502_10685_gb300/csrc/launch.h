@@ -261,6 +261,15 @@ struct SpTab {                           // tableau entry: image of X_q or Z_q, 
     uint32_t pad;
 };
 
+// A run's tableau regrouped by chunks of 4 qubits (8 generators): per chunk
+// the ordered products of all 256 subsets of its generator images.
+constexpr int kSpChunkQubits = 4;
+constexpr int kSpChunks = 8;             // 32 qubits
+constexpr int kSpChunkEntries = kSpChunks * 256;
+struct SpChunk {                         // x, z of the product string, phase exponent (mod 4)
+    uint32_t x, z, e, pad;
+};
+
 struct SpSlot {                          // a table slot: key and list position (-1 free)
     uint64_t key;
     int32_t pos;
@@ -292,12 +301,14 @@ cudaError_t launch_sp_cliff(uint64_t *keys, double *vals, int64_t *counts, const
                             int step, int n, const SpGate *gates, int n_gates, int64_t bound,
                             cudaStream_t st);
 cudaError_t launch_sp_rotation(const SpRotArgs &a, cudaStream_t st);
-// tabs: 64 entries per run (2n used); runs [r] = gates [run_first[r], + run_count[r])
+// tabs: 64 entries per run (2n used); runs [r] = gates [run_first[r], + run_count[r]);
+// chunks: kSpChunkEntries per run, built from tabs
 cudaError_t launch_sp_tableau(const SpGate *gates, const int32_t *run_first,
                               const int32_t *run_count, int n_runs, int n, SpTab *tabs,
-                              cudaStream_t st);
+                              SpChunk *chunks, cudaStream_t st);
+// chunks: the run's kSpChunkEntries entries
 cudaError_t launch_sp_cliff_tab(uint64_t *keys, double *vals, int64_t *counts,
-                                const int32_t *flags, int step, int n, const SpTab *tab,
+                                const int32_t *flags, int step, int n, const SpChunk *chunks,
                                 int64_t bound, cudaStream_t st);
 cudaError_t launch_sp_xfree(const uint64_t *keys, const double *vals, const int64_t *counts,
                             int step, int n, double *partial, double *out, cudaStream_t st);

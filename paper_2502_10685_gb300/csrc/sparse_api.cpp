@@ -148,7 +148,7 @@ struct stab_sparse {
     int64_t n_params = 0;
     SpPlan fwd, bwd;
     SpBuf thetas, g_fwd, g_bwd, keys[2], vals[2], table, slot_of, partner, blk, counts,
-        flags, partial, scal, dterms, t_fwd, t_bwd, runs;
+        flags, partial, scal, dterms, t_fwd, t_bwd, c_fwd, c_bwd, runs;
     int log_h = 0;
     void *pinned = nullptr;
     size_t pinned_bytes = 0;
@@ -233,7 +233,7 @@ struct stab_sparse {
         if (st) cudaStreamSynchronize(st);
         for (SpBuf *b : {&thetas, &g_fwd, &g_bwd, &keys[0], &keys[1], &vals[0], &vals[1], &table,
                          &slot_of, &partner, &blk, &counts, &flags, &partial, &scal,
-                         &dterms, &t_fwd, &t_bwd, &runs})
+                         &dterms, &t_fwd, &t_bwd, &c_fwd, &c_bwd, &runs})
             dfree(*b);
         if (pinned) cudaFreeHost(pinned);
         if (dense) stab_destroy(dense);
@@ -244,7 +244,7 @@ struct stab_sparse {
 namespace {
 
 // Uploads the initial list to buffer 0 and runs the plan.
-int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, const SpBuf &tabs,
+int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, const SpBuf &chunks,
            bool backward,
            const std::vector<uint64_t> &k0, const std::vector<double> &v0, SpRun *R,
            int64_t *order_max) {
@@ -290,8 +290,8 @@ int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, const SpBuf 
             if (st.kind == SP_CLIFF && st.tab >= 0) {
                 SCK(launch_sp_cliff_tab((uint64_t *)s->keys[cur].p, (double *)s->vals[cur].p,
                                         counts, flags, (int)e, s->n,
-                                        (const SpTab *)tabs.p + (size_t)st.tab * 64, bound,
-                                        s->st));
+                                        (const SpChunk *)chunks.p + (size_t)st.tab * kSpChunkEntries,
+                                        bound, s->st));
                 buf_before[e + 1] = cur;
             } else if (st.kind == SP_CLIFF) {
                 SCK(launch_sp_cliff((uint64_t *)s->keys[cur].p, (double *)s->vals[cur].p,
@@ -499,6 +499,8 @@ int stab_sparse_load_circuit(stab_sparse *s, const stab_gate *gates, int64_t m,
     SRC(s->dalloc(s->runs, br));
     SRC(s->dalloc(s->t_fwd, std::max<size_t>(nrf, 1) * 64 * sizeof(SpTab)));
     SRC(s->dalloc(s->t_bwd, std::max<size_t>(nrb, 1) * 64 * sizeof(SpTab)));
+    SRC(s->dalloc(s->c_fwd, std::max<size_t>(nrf, 1) * kSpChunkEntries * sizeof(SpChunk)));
+    SRC(s->dalloc(s->c_bwd, std::max<size_t>(nrb, 1) * kSpChunkEntries * sizeof(SpChunk)));
     SRC(s->stage(bt + bf + bb + br));
     char *h = (char *)s->pinned;
     std::memcpy(h, s->thetas_h.data(), (size_t)n_params * 8);
@@ -515,9 +517,9 @@ int stab_sparse_load_circuit(stab_sparse *s, const stab_gate *gates, int64_t m,
     SCK(cudaMemcpyAsync(s->runs.p, hr, br, cudaMemcpyHostToDevice, s->st));
     const int32_t *dr = (const int32_t *)s->runs.p;
     SCK(launch_sp_tableau((const SpGate *)s->g_fwd.p, dr, dr + nrf, (int)nrf, s->n,
-                          (SpTab *)s->t_fwd.p, s->st));
+                          (SpTab *)s->t_fwd.p, (SpChunk *)s->c_fwd.p, s->st));
     SCK(launch_sp_tableau((const SpGate *)s->g_bwd.p, dr + 2 * nrf, dr + 2 * nrf + nrb, (int)nrb,
-                          s->n, (SpTab *)s->t_bwd.p, s->st));
+                          s->n, (SpTab *)s->t_bwd.p, (SpChunk *)s->c_bwd.p, s->st));
     SCK(cudaStreamSynchronize(s->st));
     s->loaded = true;
     return STAB_OK;
@@ -546,7 +548,7 @@ int stab_sparse_expect(stab_sparse *s, const stab_term *O, int64_t n_terms, doub
         fill_info(s, R, 0, -1, info);
         return STAB_OK;
     }
-    SRC(sp_run(s, s->bwd, s->g_bwd, s->t_bwd, true, k0, v0, &R, &order_max));
+    SRC(sp_run(s, s->bwd, s->g_bwd, s->c_bwd, true, k0, v0, &R, &order_max));
     int64_t dense_gates = -1;
     if (R.stopped) {
         // the rest of the circuit (backward: gates [0, g)) on the dense vector
@@ -584,7 +586,7 @@ int stab_sparse_generator(stab_sparse *s, int k, int64_t max_out, stab_term *out
     s->threshold = 0;   // generators stay on the list
     SpRun R;
     int64_t order_max = 0;
-    const int r = sp_run(s, s->fwd, s->g_fwd, s->t_fwd, false, k0, v0, &R, &order_max);
+    const int r = sp_run(s, s->fwd, s->g_fwd, s->c_fwd, false, k0, v0, &R, &order_max);
     s->threshold = keep;
     SRC(r);
     if (R.stopped) return STAB_E_RANGE;
