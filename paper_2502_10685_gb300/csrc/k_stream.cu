@@ -246,11 +246,32 @@ __device__ __forceinline__ uint32_t tab_mul_phase(uint32_t ax, uint32_t az, uint
 __global__ void __launch_bounds__(kThreads) k_stream_tab(const double *__restrict__ src,
                                                          double *__restrict__ dst, int n,
                                                          int n_vec, const DevTab *tab) {
-    __shared__ uint32_t tx[24], tz[24], ts[24];
-    if (threadIdx.x < 2 * n) {
-        tx[threadIdx.x] = tab->x[threadIdx.x];
-        tz[threadIdx.x] = tab->z[threadIdx.x];
-        ts[threadIdx.x] = ((tab->neg >> threadIdx.x) & 1u) ? 2u : 0u;
+    // The tableau regrouped by chunks of 4 qubits: entry (c, t) is the ordered
+    // product of the generator images that subset t of chunk c selects (bit j:
+    // X of qubit 4c + j, bit 4 + j: its Z), built by every block in shared
+    // memory; an index then takes ceil(n / 4) lookups and string products
+    // instead of one product per set bit.
+    constexpr int kChunkQ = 4;
+    __shared__ uint32_t cx[3 * 256], cz[3 * 256], ce[3 * 256];
+    const int n_ch = (n + kChunkQ - 1) / kChunkQ;
+    for (int k = threadIdx.x; k < n_ch * 256; k += blockDim.x) {
+        const int c = k >> 8, t = k & 255;
+        uint32_t rx = 0, rz = 0, e = 0;
+        for (int j = 0; j < kChunkQ; ++j) {
+            const int q = kChunkQ * c + j;
+            if (q >= n) break;
+            for (int part = 0; part < 2; ++part) {   // X_q, then Z_q
+                if (!((t >> (part * kChunkQ + j)) & 1)) continue;
+                const int g = part ? n + q : q;
+                e += tab_mul_phase(rx, rz, tab->x[g], tab->z[g]) +
+                     (((tab->neg >> g) & 1u) ? 2u : 0u);
+                rx ^= tab->x[g];
+                rz ^= tab->z[g];
+            }
+        }
+        cx[k] = rx;
+        cz[k] = rz;
+        ce[k] = e & 3u;
     }
     __syncthreads();
     const uint64_t E = 1ull << (2 * n);
@@ -262,17 +283,12 @@ __global__ void __launch_bounds__(kThreads) k_stream_tab(const double *__restric
         const uint32_t i = (uint32_t)(t & (E - 1));
         const uint32_t x = i >> n, z = i & zmask;
         uint32_t rx = 0, rz = 0, e = (uint32_t)__popc(x & z);
-        for (int q = 0; q < n; ++q) {
-            if ((x >> q) & 1u) {
-                e += tab_mul_phase(rx, rz, tx[q], tz[q]) + ts[q];
-                rx ^= tx[q];
-                rz ^= tz[q];
-            }
-            if ((z >> q) & 1u) {
-                e += tab_mul_phase(rx, rz, tx[n + q], tz[n + q]) + ts[n + q];
-                rx ^= tx[n + q];
-                rz ^= tz[n + q];
-            }
+        for (int c = 0; c < n_ch; ++c) {
+            const uint32_t sh = (uint32_t)(kChunkQ * c);
+            const int k = (c << 8) | (int)(((x >> sh) & 15u) | (((z >> sh) & 15u) << 4));
+            e += ce[k] + tab_mul_phase(rx, rz, cx[k], cz[k]);
+            rx ^= cx[k];
+            rz ^= cz[k];
         }
         const double val = src[v * E + (((uint64_t)rx << n) | rz)];
         dst[t] = (e & 2u) ? -val : val;
