@@ -13,6 +13,7 @@
 
 #include "../../include/stab.h"
 #include "launch.h"
+#include "host_pool.h"
 #include "planner.h"
 
 using namespace stab;
@@ -254,8 +255,15 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     char *h = (char *)c->stage;
     char *d = (char *)P.buf.p;
     size_t off = 0;
+    // large pieces are copied into the staging buffer by the host pool
+    std::vector<std::function<void()>> copies;
     auto put = [&](const void *src, size_t bytes, size_t span) {
-        if (bytes) std::memcpy(h + off, src, bytes);
+        if (bytes >= ((size_t)1 << 18)) {
+            char *dst = h + off;
+            copies.push_back([dst, src, bytes] { std::memcpy(dst, src, bytes); });
+        } else if (bytes) {
+            std::memcpy(h + off, src, bytes);
+        }
         const size_t at = off;
         off += span;
         return d + at;
@@ -276,6 +284,7 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     }
     P.prog.n_passes = (int32_t)n_pass;
     P.prog.n_ops = (int32_t)n_ops;
+    HostPool::run(copies);
     CK(cudaMemcpyAsync(P.buf.p, h, total, cudaMemcpyHostToDevice, c->st));
     CK(cudaEventRecord(c->ev_stage, c->st));
     c->h2d_bytes += (int64_t)total;
@@ -355,15 +364,16 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_
         P.cuts.assign((size_t)n_parts + 1, 0);
         for (int k = 0; k <= n_parts; ++k) P.cuts[k] = (int)((int64_t)np * k / n_parts);
         P.split = P.cuts[1];
-        const int n_thr = np < kThreadedStreamPasses ? 1 : std::min(n_parts, 4);
-        auto work = [&P, n_parts](int t, int n_t) {
-            for (int k = t; k < n_parts; k += n_t)
+        std::vector<std::function<void()>> jobs;
+        for (int k = 0; k < n_parts; ++k)
+            jobs.push_back([&P, k] {
                 make_stream_range(P, P.parts[k], false, P.cuts[k], P.cuts[k + 1]);
-        };
-        std::vector<std::thread> thr;
-        for (int t = 1; t < n_thr; ++t) thr.emplace_back(work, t, n_thr);
-        work(0, n_thr);
-        for (std::thread &x : thr) x.join();
+            });
+        if (np < kThreadedStreamPasses) {
+            for (auto &j : jobs) j();
+        } else {
+            HostPool::run(jobs);
+        }
         return;
     }
     P.parts.clear();
@@ -373,17 +383,14 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_
     if (P.split < 0) P.h1 = P.h2 = P.h2b = DevStreamBuf();
     if (!(grad && P.split >= 0)) P.h1b = DevStreamBuf();
     // below kThreadedStreamPasses passes the streams are built on the calling
-    // thread: starting threads would cost more than the work
+    // thread: handing them to the pool would cost more than the work
     const bool threads = np >= kThreadedStreamPasses;
     auto run_all = [threads](std::vector<std::function<void()>> jobs) {
         if (!threads) {
             for (auto &j : jobs) j();
             return;
         }
-        std::vector<std::thread> thr;
-        for (size_t k = 1; k < jobs.size(); ++k) thr.emplace_back(jobs[k]);
-        jobs[0]();
-        for (std::thread &x : thr) x.join();
+        HostPool::run(jobs);
     };
     if (grad && P.split >= 0) {
         P.sf = P.sb = DevStreamBuf();
