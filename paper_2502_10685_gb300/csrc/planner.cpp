@@ -1,6 +1,7 @@
 // planner.cpp -- host-side validation, gate encoding and pass planning (see planner.h).
 #include "planner.h"
 
+#include "host_pool.h"
 #include "launch.h"
 
 #include <algorithm>
@@ -9,6 +10,11 @@
 #include <map>
 
 namespace stab {
+
+// Gate lists of at least this many gates are planned in kPlanChunks chunks at
+// once (see build_plan).
+constexpr int64_t kParallelPlanGates = 16384;
+constexpr int kPlanChunks = 4;
 
 namespace {
 
@@ -288,9 +294,10 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
 
     P.passes.reserve((size_t)m + 1);
     P.ops.reserve((size_t)m + 1);
-    std::vector<std::vector<int64_t>> runs((size_t)n);
-    // Gates [i0, i1) as U_k / V_k passes (Sec. III-A dividing) into `em`.
-    auto emit_range = [&](Emitter &em, int64_t i0, int64_t i1) {
+    // Gates [i0, i1) as U_k / V_k passes (Sec. III-A dividing) into `em`;
+    // `runs` is scratch (one per concurrent caller).
+    auto emit_range_with = [&](Emitter &em, int64_t i0, int64_t i1,
+                               std::vector<std::vector<int64_t>> &runs) {
         int64_t i = i0;
         while (i < i1) {
             int64_t j = i;
@@ -323,10 +330,82 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
             i = j;
         }
     };
+    std::vector<std::vector<int64_t>> runs((size_t)n);
+    auto emit_range = [&](Emitter &em, int64_t i0, int64_t i1) {
+        emit_range_with(em, i0, i1, runs);
+    };
     Emitter em{&P, mode, &rot_ordinal};
     const bool tabs = tableaus && n <= 12 && mode != PLAN_PLAIN && mode != PLAN_PLAIN_ROWS;
     if (!tabs) {
-        emit_range(em, 0, m);
+        if (m < kParallelPlanGates) {
+            emit_range(em, 0, m);
+            return;
+        }
+        // Chunks of the gate list cut where a block of two-qubit gates ends and
+        // a block of single-qubit gates begins: the dividing into U_k / V_k is
+        // then the same on both sides, so the chunks are planned at once and
+        // concatenated (op, map and gate-index references offset).
+        std::vector<int64_t> cut = {0};
+        for (int w = 1; w < kPlanChunks; ++w) {
+            int64_t i = std::max(cut.back() + 1, m * w / kPlanChunks);
+            while (i < m && !(is_two_qubit(gates[i - 1].op) && !is_two_qubit(gates[i].op))) ++i;
+            if (i < m) cut.push_back(i);
+        }
+        cut.push_back(m);
+        const size_t nc = cut.size() - 1;
+        if (nc == 1) {
+            emit_range(em, 0, m);
+            return;
+        }
+        std::vector<HostPlan> part(nc);
+        std::vector<std::function<void()>> jobs;
+        for (size_t k = 0; k < nc; ++k)
+            jobs.push_back([&, k] {
+                part[k].mode = mode;
+                std::vector<std::vector<int64_t>> r((size_t)n);
+                Emitter ek{&part[k], mode, &rot_ordinal};
+                emit_range_with(ek, cut[k], cut[k + 1], r);
+            });
+        HostPool::run(jobs);
+        size_t np = 0, no = 0, nm = 0, ni = 0;
+        std::vector<size_t> op_off(nc), map_off(nc), idx_off(nc), pass_off(nc);
+        for (size_t k = 0; k < nc; ++k) {
+            pass_off[k] = np;
+            op_off[k] = no;
+            map_off[k] = nm;
+            idx_off[k] = ni;
+            np += part[k].passes.size();
+            no += part[k].ops.size();
+            nm += part[k].maps.size();
+            ni += part[k].map_gate_idx.size();
+        }
+        P.passes.resize(np);
+        P.ops.resize(no);
+        P.maps.resize(nm);
+        P.map_gate_idx.resize(ni);
+        jobs.clear();
+        for (size_t k = 0; k < nc; ++k)
+            jobs.push_back([&, k] {
+                const HostPlan &Q = part[k];
+                for (size_t i = 0; i < Q.passes.size(); ++i) {
+                    DevPass d = Q.passes[i];
+                    d.first += (uint32_t)op_off[k];
+                    P.passes[pass_off[k] + i] = d;
+                }
+                for (size_t i = 0; i < Q.ops.size(); ++i) {
+                    DevOp o = Q.ops[i];
+                    if (o.kind == K_MAP3) o.param += (int32_t)map_off[k];
+                    P.ops[op_off[k] + i] = o;
+                }
+                for (size_t i = 0; i < Q.maps.size(); ++i) {
+                    DevMap3 mp = Q.maps[i];
+                    mp.first += (int32_t)idx_off[k];
+                    P.maps[map_off[k] + i] = mp;
+                }
+                std::copy(Q.map_gate_idx.begin(), Q.map_gate_idx.end(),
+                          P.map_gate_idx.begin() + (ptrdiff_t)idx_off[k]);
+            });
+        HostPool::run(jobs);
         return;
     }
     // A run of Clifford gates that would take kTabMinPasses or more passes
