@@ -463,6 +463,14 @@ int stab_version(void);
  * Errors: STAB_E_RANGE (polls < 0), STAB_E_CUDA. */
 int stab_selftest_bounded_wait(int64_t polls);
 
+/* Self-test of the host planner (no device work): plans the m gates (host
+ * memory) in plan mode `mode` (0 fused, 1 gradient, 2 one pass per gate,
+ * 3 one map per wire run) both in parallel chunks and sequentially, with
+ * their forward and backward instruction streams, and returns STAB_OK when
+ * every array is byte-identical, STAB_E_STATE when any differs.
+ * Errors: STAB_E_INVAL / STAB_E_RANGE (gates as for stab_load_circuit, mode). */
+int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, int mode);
+
 #ifdef __cplusplus
 }
 #endif

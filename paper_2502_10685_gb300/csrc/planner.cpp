@@ -251,7 +251,7 @@ void clifford_tableau(int n, const stab_gate *gates, int64_t i0, int64_t i1, boo
 }
 
 void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
-                HostPlan *out, bool tableaus) {
+                HostPlan *out, bool tableaus, bool chunked) {
     HostPlan &P = *out;
     // cleared, not replaced: a context reloading circuits keeps the capacity
     P.passes.clear();
@@ -337,7 +337,7 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
     Emitter em{&P, mode, &rot_ordinal};
     const bool tabs = tableaus && n <= 12 && mode != PLAN_PLAIN && mode != PLAN_PLAIN_ROWS;
     if (!tabs) {
-        if (m < kParallelPlanGates) {
+        if (!chunked || m < kParallelPlanGates) {
             emit_range(em, 0, m);
             return;
         }

@@ -49,8 +49,9 @@ int validate_thetas(const double *thetas, int64_t n_params);
 // Builds the pass list.  gates must be valid.
 // tableaus: long Clifford runs become P_TAB passes (streamed plans; the
 // resident instruction streams and the batch kernel do not read them).
+// chunked: long gate lists are planned in parallel chunks (same result).
 void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, PlanMode mode,
-                HostPlan *out, bool tableaus = false);
+                HostPlan *out, bool tableaus = false, bool chunked = true);
 
 // Tableau of the Clifford gates [i0, i1) applied in order (inverse: the
 // inverse map, the inverse gates in reverse order).

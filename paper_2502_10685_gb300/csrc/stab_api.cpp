@@ -883,6 +883,33 @@ void stab_default_opts(stab_opts *o) {
 
 int stab_version(void) { return STAB_VERSION; }
 
+int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, int mode) {
+    if (n < 1 || n > STAB_MAX_QUBITS) return STAB_E_RANGE;
+    if (mode < 0 || mode > 3) return STAB_E_RANGE;
+    std::string msg;
+    RC(validate_gates(n, gates, m, n_params, &msg));
+    const PlanMode pm = mode == 0 ? PLAN_FUSED : mode == 1 ? PLAN_GRAD : mode == 2 ? PLAN_PLAIN
+                                                                               : PLAN_ROWS;
+    HostPlan a, b;
+    build_plan(n, gates, m, n_params, pm, &a, false, true);
+    build_plan(n, gates, m, n_params, pm, &b, false, false);
+    auto same = [](const auto &x, const auto &y) {
+        return x.size() == y.size() &&
+               (x.empty() || std::memcmp(x.data(), y.data(), x.size() * sizeof(x[0])) == 0);
+    };
+    bool ok = same(a.passes, b.passes) && same(a.ops, b.ops) && same(a.maps, b.maps) &&
+              same(a.map_gate_idx, b.map_gate_idx) && same(a.raw, b.raw) &&
+              same(a.param_ptr, b.param_ptr) && same(a.param_rot, b.param_rot) &&
+              a.n_rot == b.n_rot;
+    for (bool backward : {false, true}) {
+        std::vector<Rec> sa, sb;
+        build_stream(a, backward, &sa);
+        build_stream(b, backward, &sb);
+        ok = ok && same(sa, sb);
+    }
+    return ok ? STAB_OK : STAB_E_STATE;
+}
+
 int stab_selftest_bounded_wait(int64_t polls) {
     if (polls < 0) return STAB_E_RANGE;
     cudaStream_t s = nullptr;

@@ -39,3 +39,21 @@ def test_host_only_calls():
     assert L.stab_error_string(-5) == b"non-finite angle or coefficient"
     o = stab.stab_default_opts()
     assert o.device == -1 and o.fuse == 1 and o.kernel == 0
+
+
+def test_chunked_planner_equals_sequential():
+    # host-only: long gate lists are planned in parallel chunks; the plan and
+    # its instruction streams must be byte-identical to the sequential ones
+    import numpy as np
+    from paper_2502_10685_gb300 import _lib, workloads as W
+    L = _lib.load()
+    cases = [W.layered_ansatz(4, 60200, seed=1002), W.layered_ansatz(8, 20000, seed=3),
+             W.random_circuit(5, 30000, seed=11), W.random_circuit(3, 20000, seed=12,
+                                                                     shared_params=9),
+             W.paper_shaped_ansatz(4, 50, 100, seed=13)]
+    for c in cases:
+        g = np.ascontiguousarray(c.gates)
+        for mode in range(4):
+            rc = L.stab_selftest_plan(c.n, g.ctypes.data, len(g), c.n_params, mode)
+            assert rc == 0, (c.n, len(g), mode, rc)
+    assert L.stab_selftest_plan(2, g.ctypes.data, len(g), c.n_params, 7) != 0
