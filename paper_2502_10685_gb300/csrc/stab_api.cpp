@@ -103,12 +103,14 @@ struct DevPlan {
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     std::vector<const void *> key;
+    std::vector<const void *> seen;  // key of the last run made without a graph
     int64_t launches = 0;            // kernels in the graph
     void *result = nullptr;          // buffer that ends up holding the result
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
         key.clear();
+        seen.clear();
         launches = 0;
         result = nullptr;
     }
@@ -816,6 +818,17 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
 template <class F>
 int run_graph(stab_ctx *c, GraphCache &g, const std::vector<const void *> &key, cudaStream_t s,
               F body) {
+    if (!(g.exec && g.key == key) && g.seen != key) {
+        // First run of this sequence: launched directly.  A sequence that is
+        // run once (a served request, a one-off circuit) would only pay for
+        // capturing and instantiating a graph; it is captured when it comes
+        // again.
+        if (g.exec) g.reset();
+        const int rc = body(s, &g.result);
+        if (rc != STAB_OK) return rc;
+        g.seen = key;
+        return STAB_OK;
+    }
     if (!g.exec || g.key != key) {
         g.reset();
         cudaGraph_t graph = nullptr;
