@@ -446,6 +446,8 @@ def run_batch(args):
         b.run()
     torch.cuda.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
     times = []
     for _ in range(args.steps):
         flush.zero_()
@@ -455,6 +457,7 @@ def run_batch(args):
         e1.record(st)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
     ms, _ = combine_ranks(sum(times) / len(times), 0, world, dist if world > 1 else None,
                           torch.device("cuda", local))
     forms = {}
@@ -507,7 +510,7 @@ def run_batch(args):
                    "partition": "longest processing time first on coefficient updates",
                    "l2": "flushed between steps"},
         "updates_per_s": total_upd / (ms / 1e3), "create_s": create_s, "vs_forms": forms,
-        "results_gathered": sum(1 for x in full if x is not None)}
+        "results_gathered": sum(1 for x in full if x is not None), "clocks": clk}
     if world == 1 and not args.no_cpu_baseline and len(items) >= 12:
         # the oracle on a seeded sample of small items, scaled by updates
         import oracle
@@ -553,6 +556,8 @@ def run_grad(args):
     for _ in range(args.warmup):
         s.grad_async(e, g)
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     times = []
     for _ in range(args.steps):
         e0, e1 = _events()
@@ -561,6 +566,7 @@ def run_grad(args):
         e1.record(st)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
     adj_ms = sum(times) / len(times)
     grads = g.cpu().numpy()
     # parameter shift on a sample of slots, batched
@@ -595,7 +601,7 @@ def run_grad(args):
         "higher_is_better": False, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "grad-c4", "n": 8, "gates": c.m, "params": c.n_params},
         "psr_batched_ms_all_params": psr_all_ms, "adjoint_speedup": psr_all_ms / adj_ms,
-        "max_abs_diff_vs_psr_sample": err}
+        "max_abs_diff_vs_psr_sample": err, "clocks": clk}
     if not args.no_cpu_baseline:
         # the oracle's parameter shift of one slot (two full propagations),
         # scaled to every slot: the CPU way to these gradients
