@@ -168,10 +168,20 @@ __device__ T block_exclusive_scan(T x, T &total, T *sh) {
     return warp_before + incl - x;
 }
 
-__device__ __forceinline__ void sp_rot_cs(const double *thetas, int param, int inverse,
-                                          double &c, double &s) {
-    sincos(thetas[param], &s, &c);
+// cos and sin of a slot's angle, from the table k_sp_cos_sin fills once per
+// circuit load (cs[2 p] = cos, cs[2 p + 1] = sin): every thread of every block
+// needs them, and evaluating sincos there cost the FP64 pipe more than the
+// rotation itself on short lists.
+__device__ __forceinline__ void sp_rot_cs(const double *cs, int param, int inverse, double &c,
+                                          double &s) {
+    c = cs[2 * param];
+    s = cs[2 * param + 1];
     if (inverse) s = -s;
+}
+
+__global__ void k_sp_cos_sin(const double *thetas, int64_t n_params, double *cs) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n_params) sincos(thetas[p], &cs[2 * p + 1], &cs[2 * p]);
 }
 
 __global__ void __launch_bounds__(kSpThreads) k_sp_cliff(uint64_t *keys, double *vals,
@@ -331,7 +341,7 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_count(const uint64_t *keys,
                                                           const double *vals,
                                                           const int64_t *counts,
                                                           const int32_t *flags, int step, int n,
-                                                          int q, int axis, const double *thetas,
+                                                          int q, int axis, const double *cs,
                                                           int param, int inverse,
                                                           const SpSlot *table, int log_h,
                                                           int32_t *partner, int64_t *blk) {
@@ -341,7 +351,7 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_count(const uint64_t *keys,
     int64_t lo, hi;
     sp_block_range(count, lo, hi);
     double c, s;
-    sp_rot_cs(thetas, param, inverse, c, s);
+    sp_rot_cs(cs, param, inverse, c, s);
     uint32_t u, v;
     sp_pair(axis, u, v);
     int64_t mine = 0;
@@ -388,7 +398,7 @@ __global__ void __launch_bounds__(1024) k_sp_scan(int64_t *blk, int nblk, int64_
 
 __global__ void __launch_bounds__(kSpThreads) k_sp_write(
     const uint64_t *keys, const double *vals, const int64_t *counts, const int32_t *flags,
-    int step, int n, int q, int axis, const double *thetas, int param, int inverse,
+    int step, int n, int q, int axis, const double *cs, int param, int inverse,
     SpSlot *table, const int32_t *slot_of, const int32_t *partner, const int64_t *blk,
     uint64_t *keys_out, double *vals_out) {
     __shared__ int64_t sh[32];
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(kSpThreads) k_sp_write(
     int64_t lo, hi;
     sp_block_range(count, lo, hi);
     double c, s;
-    sp_rot_cs(thetas, param, inverse, c, s);
+    sp_rot_cs(cs, param, inverse, c, s);
     uint32_t u, v;
     sp_pair(axis, u, v);
     int64_t base = blk[blockIdx.x];
@@ -482,6 +492,13 @@ int sp_grid(int64_t bound) {
 
 }  // namespace
 
+cudaError_t launch_sp_cos_sin(const double *thetas, int64_t n_params, double *cs,
+                              cudaStream_t st) {
+    if (n_params <= 0) return cudaSuccess;
+    k_sp_cos_sin<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(thetas, n_params, cs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sp_cliff(uint64_t *keys, double *vals, int64_t *counts, const int32_t *flags,
                             int step, int n, const SpGate *gates, int n_gates, int64_t bound,
                             cudaStream_t st) {
@@ -515,11 +532,11 @@ cudaError_t launch_sp_rotation(const SpRotArgs &a, cudaStream_t st) {
                                               a.axis, a.table, a.log_h, a.slot_of,
                                               a.err);
     k_sp_count<<<grid, kSpThreads, 0, st>>>(a.keys, a.vals, a.counts, a.flags, a.step, a.n, a.q,
-                                             a.axis, a.thetas, a.param, a.inverse, a.table,
+                                             a.axis, a.cs, a.param, a.inverse, a.table,
                                              a.log_h, a.partner, a.blk);
     k_sp_scan<<<1, 1024, 0, st>>>(a.blk, grid, a.counts, a.flags, a.step, a.cap, a.threshold);
     k_sp_write<<<grid, kSpThreads, 0, st>>>(a.keys, a.vals, a.counts, a.flags, a.step, a.n, a.q,
-                                             a.axis, a.thetas, a.param, a.inverse, a.table,
+                                             a.axis, a.cs, a.param, a.inverse, a.table,
                                              a.slot_of, a.partner, a.blk, a.keys_out,
                                              a.vals_out);
     return cudaGetLastError();

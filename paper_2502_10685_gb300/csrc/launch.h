@@ -284,7 +284,7 @@ struct SpRotArgs {
     int64_t *counts;                     // counts[step] = order before step
     int32_t *flags;                      // [0] stop code (1 overflow, 2 threshold), [1] step
     int32_t step, n, q, axis;            // axis 0/1/2 = R_x/R_y/R_z
-    const double *thetas;
+    const double *cs;
     int32_t param, inverse;
     SpSlot *table;                       // open-addressing table (one 16-byte slot per probe)
     int32_t log_h;
@@ -301,6 +301,9 @@ cudaError_t launch_sp_cliff(uint64_t *keys, double *vals, int64_t *counts, const
                             int step, int n, const SpGate *gates, int n_gates, int64_t bound,
                             cudaStream_t st);
 cudaError_t launch_sp_rotation(const SpRotArgs &a, cudaStream_t st);
+// cs[2 p] = cos(thetas[p]), cs[2 p + 1] = sin(thetas[p]) for every slot
+cudaError_t launch_sp_cos_sin(const double *thetas, int64_t n_params, double *cs,
+                              cudaStream_t st);
 // tabs: 64 entries per run (2n used); runs [r] = gates [run_first[r], + run_count[r]);
 // chunks: kSpChunkEntries per run, built from tabs
 cudaError_t launch_sp_tableau(const SpGate *gates, const int32_t *run_first,

@@ -147,7 +147,7 @@ struct stab_sparse {
     std::vector<double> thetas_h;
     int64_t n_params = 0;
     SpPlan fwd, bwd;
-    SpBuf thetas, g_fwd, g_bwd, keys[2], vals[2], table, slot_of, partner, blk, counts,
+    SpBuf thetas, cs, g_fwd, g_bwd, keys[2], vals[2], table, slot_of, partner, blk, counts,
         flags, partial, scal, dterms, t_fwd, t_bwd, c_fwd, c_bwd, runs;
     int log_h = 0;
     void *pinned = nullptr;
@@ -231,7 +231,7 @@ struct stab_sparse {
 
     ~stab_sparse() {
         if (st) cudaStreamSynchronize(st);
-        for (SpBuf *b : {&thetas, &g_fwd, &g_bwd, &keys[0], &keys[1], &vals[0], &vals[1], &table,
+        for (SpBuf *b : {&thetas, &cs, &g_fwd, &g_bwd, &keys[0], &keys[1], &vals[0], &vals[1], &table,
                          &slot_of, &partner, &blk, &counts, &flags, &partial, &scal,
                          &dterms, &t_fwd, &t_bwd, &c_fwd, &c_bwd, &runs})
             dfree(*b);
@@ -310,7 +310,7 @@ int sp_run(stab_sparse *s, const SpPlan &P, const SpBuf &run_gates, const SpBuf 
                 a.n = s->n;
                 a.q = st.q;
                 a.axis = st.axis;
-                a.thetas = (const double *)s->thetas.p;
+                a.cs = (const double *)s->cs.p;
                 a.param = st.param;
                 a.inverse = backward ? 1 : 0;
                 a.table = (SpSlot *)s->table.p;
@@ -494,6 +494,7 @@ int stab_sparse_load_circuit(stab_sparse *s, const stab_gate *gates, int64_t m,
     const size_t nrf = s->fwd.tab_first.size(), nrb = s->bwd.tab_first.size();
     const size_t br = std::max<size_t>(2 * (nrf + nrb), 1) * 4;
     SRC(s->dalloc(s->thetas, bt));
+    SRC(s->dalloc(s->cs, 2 * bt));
     SRC(s->dalloc(s->g_fwd, bf));
     SRC(s->dalloc(s->g_bwd, bb));
     SRC(s->dalloc(s->runs, br));
@@ -512,6 +513,7 @@ int stab_sparse_load_circuit(stab_sparse *s, const stab_gate *gates, int64_t m,
     std::copy(s->bwd.tab_first.begin(), s->bwd.tab_first.end(), hr + 2 * nrf);
     std::copy(s->bwd.tab_count.begin(), s->bwd.tab_count.end(), hr + 2 * nrf + nrb);
     SCK(cudaMemcpyAsync(s->thetas.p, h, bt, cudaMemcpyHostToDevice, s->st));
+    SCK(launch_sp_cos_sin((const double *)s->thetas.p, n_params, (double *)s->cs.p, s->st));
     SCK(cudaMemcpyAsync(s->g_fwd.p, h + bt, bf, cudaMemcpyHostToDevice, s->st));
     SCK(cudaMemcpyAsync(s->g_bwd.p, h + bt + bf, bb, cudaMemcpyHostToDevice, s->st));
     SCK(cudaMemcpyAsync(s->runs.p, hr, br, cudaMemcpyHostToDevice, s->st));
