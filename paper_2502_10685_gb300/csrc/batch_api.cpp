@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/stab.h"
+#include "host_pool.h"
 #include "launch.h"
 #include "planner.h"
 
@@ -141,7 +142,12 @@ BatchArgs make_args(stab_batch *b, int n_units) {
 
 // Picks CTAs per SM by timing the persistent launch on a prefix of the unit
 // table (the longest units, one per CTA of the widest candidate) for each
-// candidate residency; one untimed launch first.
+// candidate residency; one untimed launch first.  Each sampled unit runs only
+// its first kTuneChunks chunks: the choice rests on the per-pass rate of each
+// residency, and whole streams of the longest circuits made the tuning cost
+// seconds.  (The partial outputs are overwritten by the first real run.)
+constexpr int kTuneChunks = 24;
+
 int autotune(stab_batch *b, int sms, int max_occ) {
     const int sample = std::min(b->n_units, sms * max_occ);
     float best = 1e30f;
@@ -153,9 +159,12 @@ int autotune(stab_batch *b, int sms, int max_occ) {
     for (int occ : {1, 2, 4, max_occ})
         if (occ <= max_occ && std::find(cands.begin(), cands.end(), occ) == cands.end())
             cands.push_back(occ);
-    BRC(launch_graph_or_direct(b, make_args(b, sample), sms * cands.back(), false));   // warm-up
+    BatchArgs warm = make_args(b, sample);
+    warm.max_chunks = kTuneChunks;
+    BRC(launch_graph_or_direct(b, warm, sms * cands.back(), false));   // warm-up
     for (int occ : cands) {
-        const BatchArgs a = make_args(b, sample);
+        BatchArgs a = make_args(b, sample);
+        a.max_chunks = kTuneChunks;
         BCK(cudaEventRecord(e0, b->st));
         BRC(launch_graph_or_direct(b, a, sms * occ, false));
         BCK(cudaEventRecord(e1, b->st));
@@ -202,6 +211,7 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
         HostPlan P;
         std::vector<Rec> S;
         std::vector<DevTerm> t;
+        int64_t n_enc = 0;           // R_ROT and R_MAP3 records of S (filled by the encoder)
         int rc = STAB_OK;
     };
     std::vector<ItemPlan> plans((size_t)count);
@@ -219,6 +229,13 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
                 build_plan(I.n, I.gates, I.m, I.n_params, I.n <= 4 ? PLAN_ROWS : PLAN_FUSED,
                            &ip.P);
                 build_stream(ip.P, I.kind == STAB_ITEM_EXPECT, &ip.S);
+                for (size_t i = 0; i < ip.S.size(); ++i) {
+                    if (ip.S[i].kind == R_ROT) ip.n_enc++;
+                    if (ip.S[i].kind == R_MAP3) {
+                        ip.n_enc++;
+                        i += 3;   // its data records
+                    }
+                }
             }
         };
         const unsigned hw = std::thread::hardware_concurrency();
@@ -229,58 +246,95 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
         for (auto &t : pool) t.join();
     }
     for (int64_t it = 0; it < count; ++it) BRC(plans[(size_t)it].rc);
+    // Concatenation in item order: offsets first, then every item's records,
+    // maps and gate indices copied (references offset) on the host pool.
+    struct Off {
+        int64_t rec, enc, map, midx, raw, th, term;
+    };
+    std::vector<Off> off((size_t)count);
+    Off tot{0, 0, 0, 0, 0, 0, 0};
+    for (int64_t it = 0; it < count; ++it) {
+        const ItemPlan &ip = plans[(size_t)it];
+        off[(size_t)it] = tot;
+        tot.rec += (int64_t)ip.S.size();
+        tot.enc += ip.n_enc;
+        tot.map += (int64_t)ip.P.maps.size();
+        tot.midx += (int64_t)ip.P.map_gate_idx.size();
+        tot.raw += (int64_t)ip.P.raw.size();
+        tot.th += items[it].n_params;
+        tot.term += (int64_t)ip.t.size();
+    }
+    if (tot.rec > (int64_t)INT32_MAX / 2) return STAB_E_RANGE;
+    recs.resize((size_t)tot.rec);
+    enc.resize((size_t)tot.enc);
+    maps.resize((size_t)tot.map);
+    midx.resize((size_t)tot.midx);
+    raw.resize((size_t)tot.raw);
+    thetas.resize((size_t)tot.th);
+    terms.resize((size_t)tot.term);
+    {
+        std::vector<std::function<void()>> jobs;
+        const int64_t per = std::max<int64_t>(1, count / 64);
+        for (int64_t lo = 0; lo < count; lo += per) {
+            const int64_t hi = std::min(count, lo + per);
+            jobs.push_back([&, lo, hi] {
+                for (int64_t it = lo; it < hi; ++it) {
+                    const stab_batch_item &I = items[it];
+                    const ItemPlan &ip = plans[(size_t)it];
+                    const Off &o = off[(size_t)it];
+                    const std::vector<Rec> &S = ip.S;
+                    int64_t e = o.enc;
+                    for (size_t i = 0; i < S.size(); ++i) {
+                        Rec r = S[i];
+                        if (r.kind == R_ROT) {
+                            r.param += (int32_t)o.th;
+                            enc[(size_t)e++] = (int32_t)(o.rec + (int64_t)i);
+                        } else if (r.kind == R_MAP3) {
+                            r.param += (int32_t)o.map;
+                            enc[(size_t)e++] = (int32_t)(o.rec + (int64_t)i);
+                        }
+                        recs[(size_t)o.rec + i] = r;
+                    }
+                    for (size_t i = 0; i < ip.P.maps.size(); ++i) {
+                        DevMap3 mp = ip.P.maps[i];
+                        mp.first += (int32_t)o.midx;
+                        maps[(size_t)o.map + i] = mp;
+                    }
+                    for (size_t i = 0; i < ip.P.map_gate_idx.size(); ++i)
+                        midx[(size_t)o.midx + i] = ip.P.map_gate_idx[i] + (int32_t)o.raw;
+                    for (size_t i = 0; i < ip.P.raw.size(); ++i) {
+                        RawGate g = ip.P.raw[i];
+                        if (g.op >= STAB_RX) g.param += (int32_t)o.th;
+                        raw[(size_t)o.raw + i] = g;
+                    }
+                    std::copy(I.thetas, I.thetas + I.n_params, thetas.begin() + (ptrdiff_t)o.th);
+                    std::copy(ip.t.begin(), ip.t.end(), terms.begin() + (ptrdiff_t)o.term);
+                }
+            });
+        }
+        HostPool::run(jobs);
+    }
     for (int64_t it = 0; it < count; ++it) {
         const stab_batch_item &I = items[it];
         b->item_n[it] = I.n;
         b->item_kind[it] = I.kind;
         b->max_n = std::max(b->max_n, (int)I.n);
-        HostPlan &P = plans[(size_t)it].P;
-        const std::vector<Rec> &S = plans[(size_t)it].S;
-        const std::vector<DevTerm> &t = plans[(size_t)it].t;
-        const int64_t th_off = (int64_t)thetas.size(), raw_off = (int64_t)raw.size();
-        const int64_t map_off = (int64_t)maps.size(), midx_off = (int64_t)midx.size();
-        const int64_t rec_off = (int64_t)recs.size();
-        for (size_t i = 0; i < S.size(); ++i) {
-            Rec r = S[i];
-            if (r.kind == R_ROT) {
-                r.param += (int32_t)th_off;
-                enc.push_back((int32_t)(rec_off + (int64_t)i));
-            } else if (r.kind == R_MAP3) {
-                r.param += (int32_t)map_off;
-                enc.push_back((int32_t)(rec_off + (int64_t)i));
-                recs.push_back(r);
-                for (int k = 1; k <= 3; ++k) recs.push_back(S[i + k]);
-                i += 3;
-                continue;
-            }
-            recs.push_back(r);
-        }
-        for (DevMap3 mp : P.maps) {
-            mp.first += (int32_t)midx_off;
-            maps.push_back(mp);
-        }
-        for (int32_t g : P.map_gate_idx) midx.push_back(g + (int32_t)raw_off);
-        for (RawGate g : P.raw) {
-            if (g.op >= STAB_RX) g.param += (int32_t)th_off;
-            raw.push_back(g);
-        }
-        thetas.insert(thetas.end(), I.thetas, I.thetas + I.n_params);
-        const int64_t n_chunks = (int64_t)S.size() / kChunkRecs;
+        const ItemPlan &ip = plans[(size_t)it];
+        const Off &o = off[(size_t)it];
+        const int64_t n_chunks = (int64_t)ip.S.size() / kChunkRecs;
         const int64_t cost = n_chunks * ((int64_t)1 << (2 * I.n));
         if (I.kind == STAB_ITEM_GENERATORS) {
             b->gen_off[it] = gens_doubles;
             for (int k = 0; k < I.n; ++k)
-                ups.push_back({rec_off, n_chunks, 0, 0, it, I.n, INIT_GENERATOR, k, cost});
+                ups.push_back({o.rec, n_chunks, 0, 0, it, I.n, INIT_GENERATOR, k, cost});
             gens_doubles += (int64_t)I.n << (2 * I.n);
         } else {
-            const int64_t toff = (int64_t)terms.size();
-            terms.insert(terms.end(), t.begin(), t.end());
-            ups.push_back({rec_off, n_chunks, toff, (int64_t)t.size(), it, I.n, INIT_TERMS, 0,
+            ups.push_back({o.rec, n_chunks, o.term, (int64_t)ip.t.size(), it, I.n, INIT_TERMS, 0,
                            cost});
         }
-        if (recs.size() > (size_t)INT32_MAX / 2) return STAB_E_RANGE;
-        plans[(size_t)it] = ItemPlan{};   // release the item's host plan
     }
+    plans.clear();   // the items' host plans
+    plans.shrink_to_fit();
     std::stable_sort(ups.begin(), ups.end(),
                      [](const UnitPlan &x, const UnitPlan &y) { return x.cost > y.cost; });
     b->n_units = (int)ups.size();

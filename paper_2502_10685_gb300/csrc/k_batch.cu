@@ -21,8 +21,8 @@ using namespace resident;
 constexpr int kBatchThreads = 256;
 
 template <int N>
-__device__ void batch_unit(const BatchUnit &U, Stager &st, unsigned char *smem, double *slab,
-                           int32_t *status, bool &ok) {
+__device__ void batch_unit(const BatchUnit &U, int n_chunks, Stager &st, unsigned char *smem,
+                           double *slab, int32_t *status, bool &ok) {
     constexpr int E = 1 << (2 * N);
     constexpr int LPG = N <= 4 ? 4 : 1;
     double *red = reinterpret_cast<double *>(smem + kOffRed);
@@ -30,8 +30,8 @@ __device__ void batch_unit(const BatchUnit &U, Stager &st, unsigned char *smem, 
     double *bufB = bufA + E;
     st.s0 = U.stream;
     st.s1 = nullptr;
-    st.n0 = U.n_chunks;
-    st.n_total = U.n_chunks;
+    st.n0 = n_chunks;
+    st.n_total = n_chunks;
     st.restart();
     for (int i = threadIdx.x; i < E; i += kBatchThreads) {
         double v = 0.0;
@@ -46,7 +46,7 @@ __device__ void batch_unit(const BatchUnit &U, Stager &st, unsigned char *smem, 
             bufA[U.terms[k].idx] = U.terms[k].coeff;
     }
     __syncthreads();
-    double *res = run_stream<N, LPG, kBatchThreads>(st, 0, U.n_chunks, bufA, bufB, status);
+    double *res = run_stream<N, LPG, kBatchThreads>(st, 0, n_chunks, bufA, bufB, status);
     if (res == nullptr) {
         ok = false;
         return;
@@ -82,15 +82,16 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch(BatchArgs a) {
         __syncthreads();
         if (u >= a.n_units) break;
         const BatchUnit U = a.units[u];
+        const int nc = (a.max_chunks > 0 && U.n_chunks > a.max_chunks) ? a.max_chunks : U.n_chunks;
         switch (U.n) {
-        case 1: batch_unit<1>(U, st, smem, slab, a.status, ok); break;
-        case 2: batch_unit<2>(U, st, smem, slab, a.status, ok); break;
-        case 3: batch_unit<3>(U, st, smem, slab, a.status, ok); break;
-        case 4: batch_unit<4>(U, st, smem, slab, a.status, ok); break;
-        case 5: batch_unit<5>(U, st, smem, slab, a.status, ok); break;
-        case 6: batch_unit<6>(U, st, smem, slab, a.status, ok); break;
-        case 7: batch_unit<7>(U, st, smem, slab, a.status, ok); break;
-        case 8: batch_unit<8>(U, st, smem, slab, a.status, ok); break;
+        case 1: batch_unit<1>(U, nc, st, smem, slab, a.status, ok); break;
+        case 2: batch_unit<2>(U, nc, st, smem, slab, a.status, ok); break;
+        case 3: batch_unit<3>(U, nc, st, smem, slab, a.status, ok); break;
+        case 4: batch_unit<4>(U, nc, st, smem, slab, a.status, ok); break;
+        case 5: batch_unit<5>(U, nc, st, smem, slab, a.status, ok); break;
+        case 6: batch_unit<6>(U, nc, st, smem, slab, a.status, ok); break;
+        case 7: batch_unit<7>(U, nc, st, smem, slab, a.status, ok); break;
+        case 8: batch_unit<8>(U, nc, st, smem, slab, a.status, ok); break;
         default: break;
         }
     }

@@ -100,6 +100,8 @@ struct BatchArgs {
     int32_t *status;
     double *slab;              // per-CTA global vectors for n > kMaxResidentQubits (may be null)
     size_t slab_doubles;       // doubles per CTA slab
+    int32_t max_chunks;        // > 0: each unit runs only its first max_chunks chunks (timing
+                               // samples; the outputs are then partial); 0: whole streams
 };
 
 size_t batch_smem_bytes(int max_n_in_smem);
