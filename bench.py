@@ -507,6 +507,7 @@ def run_batch(args):
         "config": {"workload": args.workload, "circuits": len(all_items),
                    "circuits_rank0": len(items), "units": info["units"],
                    "grid": info["grid"], "ctas_per_sm": info["ctas_per_sm"],
+                   "smem_max_n": info["smem_max_n"],
                    "partition": "longest processing time first on coefficient updates",
                    "l2": "flushed between steps"},
         "updates_per_s": total_upd / (ms / 1e3), "create_s": create_s, "vs_forms": forms,

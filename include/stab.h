@@ -240,10 +240,13 @@ typedef struct stab_batch_item {
 typedef struct stab_batch stab_batch;
 
 /* Validates, plans and uploads count items (all host arrays are copied before
- * return).  opts may be NULL; with kernel = STAB_KERNEL_AUTO the number of
- * CTAs per SM is picked by timing candidate launches on a sample of the
- * units.  Errors: as stab_load_circuit / stab_expect, STAB_E_RANGE (n > 8 or
- * count < 1), STAB_E_NOMEM, STAB_E_CUDA. */
+ * return).  opts may be NULL.  opts->kernel sets the residency: AUTO times
+ * candidate launches on a sample of the units (prefixes of their streams) and
+ * picks which vectors stay in shared memory (n <= 4, 5 or 6; larger ones in a
+ * per-CTA global slab) and how many CTAs run per SM; RESIDENT keeps every
+ * n <= 6 vector in shared memory; STREAMED keeps n <= 4 there and the rest in
+ * slabs (both at the largest residency).  Errors: as stab_load_circuit /
+ * stab_expect, STAB_E_RANGE (n > 8 or count < 1), STAB_E_NOMEM, STAB_E_CUDA. */
 int stab_batch_create(const stab_batch_item *items, int64_t count, const stab_opts *opts,
                       stab_batch **out);
 
@@ -260,8 +263,12 @@ int stab_batch_expectations(stab_batch *b, double *out);
 int stab_batch_generators(stab_batch *b, int64_t item, double *out, int out_is_device);
 
 /* units: vectors in the batch; grid: CTAs of the persistent launch;
- * ctas_per_sm: the chosen residency.  Any pointer may be NULL. */
-int stab_batch_info(stab_batch *b, int64_t *units, int32_t *grid, int32_t *ctas_per_sm);
+ * ctas_per_sm and smem_max_n: the chosen residency (vectors of up to
+ * smem_max_n qubits in shared memory, larger ones in a per-CTA global slab;
+ * with STAB_KERNEL_AUTO both are picked by timing candidates at creation).
+ * Any pointer may be NULL. */
+int stab_batch_info(stab_batch *b, int64_t *units, int32_t *grid, int32_t *ctas_per_sm,
+                    int32_t *smem_max_n);
 
 int stab_batch_destroy(stab_batch *b);
 

@@ -118,7 +118,8 @@ def load(build_if_missing: bool = True):
             "stab_batch_expectations": (i32, [vp, dp]),
             "stab_batch_generators": (i32, [vp, i64, dp, i32]),
             "stab_batch_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
-                                      ctypes.POINTER(ctypes.c_int32)]),
+                                     ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32)]),
             "stab_batch_destroy": (i32, [vp]),
             "stab_request_footprint": (i64, [ctypes.POINTER(StabRequest)]),
             "stab_server_create": (i32, [ctypes.POINTER(StabServerOpts), ctypes.POINTER(vp)]),

@@ -52,6 +52,7 @@ struct stab_batch {
     int max_n = 1;
     int grid = 0;
     int ctas_per_sm = 1;
+    int smem_n = kMaxResidentQubits;   // vectors up to this n in shared memory, larger in the slab
     size_t smem = 0;
 
     Buf data, gens, exps, slab, counter;   // counter also holds the status word
@@ -136,49 +137,68 @@ BatchArgs make_args(stab_batch *b, int n_units) {
     a.counter = (int32_t *)b->counter.p;
     a.status = (int32_t *)b->counter.p + 32;
     a.slab = (double *)b->slab.p;
-    a.slab_doubles = b->max_n > kMaxResidentQubits ? (size_t)2 << (2 * b->max_n) : 0;
+    a.slab_doubles = b->max_n > b->smem_n ? (size_t)2 << (2 * b->max_n) : 0;
+    a.smem_n = b->smem_n;
     return a;
 }
 
-// Picks CTAs per SM by timing the persistent launch on a prefix of the unit
-// table (the longest units, one per CTA of the widest candidate) for each
-// candidate residency; one untimed launch first.  Each sampled unit runs only
-// its first kTuneChunks chunks: the choice rests on the per-pass rate of each
-// residency, and whole streams of the longest circuits made the tuning cost
-// seconds.  (The partial outputs are overwritten by the first real run.)
+// Picks the residency -- which vectors live in shared memory (n <= smem_n)
+// rather than in the CTA's slab, and how many CTAs run per SM -- by timing the
+// persistent launch on a prefix of the unit table (the longest units, one per
+// CTA of the widest candidate) for every candidate pair; one untimed launch
+// first.  Each sampled unit runs only its first kTuneChunks chunks: the choice
+// rests on the per-pass rate of each residency, and whole streams of the
+// longest circuits made the tuning cost seconds.  (The partial outputs are
+// overwritten by the first real run.)
 constexpr int kTuneChunks = 24;
 
-int autotune(stab_batch *b, int sms, int max_occ) {
-    const int sample = std::min(b->n_units, sms * max_occ);
+struct Residency {
+    int smem_n;
+    size_t smem;
+    int max_occ;
+};
+
+int autotune(stab_batch *b, int sms, const std::vector<Residency> &res) {
+    int widest = 1;
+    for (const Residency &r : res) widest = std::max(widest, r.max_occ);
+    const int sample = std::min(b->n_units, sms * widest);
     float best = 1e30f;
-    int best_occ = max_occ;
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    std::vector<int> cands;
-    for (int occ : {1, 2, 4, max_occ})
-        if (occ <= max_occ && std::find(cands.begin(), cands.end(), occ) == cands.end())
-            cands.push_back(occ);
-    BatchArgs warm = make_args(b, sample);
-    warm.max_chunks = kTuneChunks;
-    BRC(launch_graph_or_direct(b, warm, sms * cands.back(), false));   // warm-up
-    for (int occ : cands) {
-        BatchArgs a = make_args(b, sample);
-        a.max_chunks = kTuneChunks;
-        BCK(cudaEventRecord(e0, b->st));
-        BRC(launch_graph_or_direct(b, a, sms * occ, false));
-        BCK(cudaEventRecord(e1, b->st));
-        BCK(cudaEventSynchronize(e1));
-        float ms = 0;
-        BCK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_occ = occ;
+    bool warm = false;
+    Residency tuned = res[0];
+    for (const Residency &r : res) {
+        std::vector<int> cands;
+        for (int occ : {1, 2, 4, r.max_occ})
+            if (occ <= r.max_occ && std::find(cands.begin(), cands.end(), occ) == cands.end())
+                cands.push_back(occ);
+        b->smem_n = r.smem_n;
+        b->smem = r.smem;
+        for (int occ : cands) {
+            BatchArgs a = make_args(b, sample);
+            a.max_chunks = kTuneChunks;
+            if (!warm) {
+                BRC(launch_graph_or_direct(b, a, sms * occ, false));
+                warm = true;
+            }
+            BCK(cudaEventRecord(e0, b->st));
+            BRC(launch_graph_or_direct(b, a, sms * occ, false));
+            BCK(cudaEventRecord(e1, b->st));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                b->ctas_per_sm = occ;
+                tuned = r;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->ctas_per_sm = best_occ;
+    b->smem_n = tuned.smem_n;
+    b->smem = tuned.smem;
     return STAB_OK;
 }
 
@@ -402,21 +422,39 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
     BCK(e);
     b->units_dev = (const BatchUnit *)(d + o_units);
 
-    // residency: shared memory for the vectors of n <= 6, a global slab above
-    const int smem_n = std::min(b->max_n, kMaxResidentQubits);
-    b->smem = batch_smem_bytes(smem_n);
-    int max_occ = 1, sms = 0;
+    // residency: shared memory for the vectors of n <= smem_n, a global slab
+    // per CTA above.  Candidates: smem_n = min(max n, 6) and, with AUTO, also
+    // 5 and 4 (less shared memory per CTA, so more CTAs per SM, at the cost of
+    // n = 5, 6 vectors in L2-resident slabs); the autotuner times them.
+    // RESIDENT keeps min(max n, 6); STREAMED takes 4 (every n >= 5 vector in a slab).
+    int sms = 0;
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    BCK(batch_occupancy(b->smem, &max_occ));
-    if (max_occ < 1) return STAB_E_RANGE;
-    max_occ = std::min(max_occ, 8);
-    if (b->max_n > kMaxResidentQubits) {
-        // the slabs of all resident CTAs: 2 x 4^max_n doubles each
-        const size_t per = (size_t)2 << (2 * b->max_n);
-        BRC(b->dalloc(b->slab, per * 8 * (size_t)sms * max_occ));
+    std::vector<Residency> res;
+    const int top = std::min(b->max_n, kMaxResidentQubits);
+    const int lo = kernel == STAB_KERNEL_AUTO ? std::max(4, top - 2)
+                   : kernel == STAB_KERNEL_STREAMED ? std::min(4, top) : top;
+    const int hi = kernel == STAB_KERNEL_STREAMED ? std::min(4, top) : top;
+    for (int sn = hi; sn >= lo; --sn) {
+        Residency r{sn, batch_smem_bytes(sn), 1};
+        BCK(batch_occupancy(r.smem, &r.max_occ));
+        if (r.max_occ < 1) continue;
+        r.max_occ = std::min(r.max_occ, 8);
+        res.push_back(r);
     }
-    b->ctas_per_sm = max_occ;
-    if (kernel == STAB_KERNEL_AUTO && max_occ > 1) BRC(autotune(b, sms, max_occ));
+    if (res.empty()) return STAB_E_RANGE;
+    // the slabs of all resident CTAs of the widest candidate that needs them
+    int slab_ctas = 0;
+    for (const Residency &r : res)
+        if (b->max_n > r.smem_n) slab_ctas = std::max(slab_ctas, sms * r.max_occ);
+    if (slab_ctas > 0) {
+        const size_t per = (size_t)2 << (2 * b->max_n);
+        BRC(b->dalloc(b->slab, per * 8 * (size_t)slab_ctas));
+    }
+    b->smem_n = res[0].smem_n;
+    b->smem = res[0].smem;
+    b->ctas_per_sm = res[0].max_occ;
+    if (kernel == STAB_KERNEL_AUTO && (res.size() > 1 || res[0].max_occ > 1))
+        BRC(autotune(b, sms, res));
     b->grid = sms * b->ctas_per_sm;
     return STAB_OK;
 }
@@ -529,11 +567,13 @@ int stab_batch_generators(stab_batch *b, int64_t item, double *out, int out_is_d
     return batch_status(b);
 }
 
-int stab_batch_info(stab_batch *b, int64_t *units, int32_t *grid, int32_t *ctas_per_sm) {
+int stab_batch_info(stab_batch *b, int64_t *units, int32_t *grid, int32_t *ctas_per_sm,
+                    int32_t *smem_max_n) {
     if (!b) return STAB_E_INVAL;
     if (units) *units = b->n_units;
     if (grid) *grid = b->grid;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (smem_max_n) *smem_max_n = b->smem_n;
     return STAB_OK;
 }
 

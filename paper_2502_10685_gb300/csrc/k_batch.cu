@@ -21,12 +21,16 @@ using namespace resident;
 constexpr int kBatchThreads = 256;
 
 template <int N>
-__device__ void batch_unit(const BatchUnit &U, int n_chunks, Stager &st, unsigned char *smem,
-                           double *slab, int32_t *status, bool &ok) {
+__device__ void batch_unit(const BatchUnit &U, int n_chunks, int smem_n, Stager &st,
+                           unsigned char *smem, double *slab, int32_t *status, bool &ok) {
     constexpr int E = 1 << (2 * N);
     constexpr int LPG = N <= 4 ? 4 : 1;
     double *red = reinterpret_cast<double *>(smem + kOffRed);
-    double *bufA = N <= kMaxResidentQubits ? reinterpret_cast<double *>(smem + kSmemHeader) : slab;
+    // the launch's shared memory holds vectors up to smem_n qubits (chosen by
+    // the batch's autotuner); larger ones live in the CTA's slab
+    double *bufA = (N <= kMaxResidentQubits && N <= smem_n)
+                       ? reinterpret_cast<double *>(smem + kSmemHeader)
+                       : slab;
     double *bufB = bufA + E;
     st.s0 = U.stream;
     st.s1 = nullptr;
@@ -83,15 +87,16 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch(BatchArgs a) {
         if (u >= a.n_units) break;
         const BatchUnit U = a.units[u];
         const int nc = (a.max_chunks > 0 && U.n_chunks > a.max_chunks) ? a.max_chunks : U.n_chunks;
+        const int sn = a.smem_n > 0 ? a.smem_n : kMaxResidentQubits;
         switch (U.n) {
-        case 1: batch_unit<1>(U, nc, st, smem, slab, a.status, ok); break;
-        case 2: batch_unit<2>(U, nc, st, smem, slab, a.status, ok); break;
-        case 3: batch_unit<3>(U, nc, st, smem, slab, a.status, ok); break;
-        case 4: batch_unit<4>(U, nc, st, smem, slab, a.status, ok); break;
-        case 5: batch_unit<5>(U, nc, st, smem, slab, a.status, ok); break;
-        case 6: batch_unit<6>(U, nc, st, smem, slab, a.status, ok); break;
-        case 7: batch_unit<7>(U, nc, st, smem, slab, a.status, ok); break;
-        case 8: batch_unit<8>(U, nc, st, smem, slab, a.status, ok); break;
+        case 1: batch_unit<1>(U, nc, sn, st, smem, slab, a.status, ok); break;
+        case 2: batch_unit<2>(U, nc, sn, st, smem, slab, a.status, ok); break;
+        case 3: batch_unit<3>(U, nc, sn, st, smem, slab, a.status, ok); break;
+        case 4: batch_unit<4>(U, nc, sn, st, smem, slab, a.status, ok); break;
+        case 5: batch_unit<5>(U, nc, sn, st, smem, slab, a.status, ok); break;
+        case 6: batch_unit<6>(U, nc, sn, st, smem, slab, a.status, ok); break;
+        case 7: batch_unit<7>(U, nc, sn, st, smem, slab, a.status, ok); break;
+        case 8: batch_unit<8>(U, nc, sn, st, smem, slab, a.status, ok); break;
         default: break;
         }
     }

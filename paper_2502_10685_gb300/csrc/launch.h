@@ -102,6 +102,8 @@ struct BatchArgs {
     size_t slab_doubles;       // doubles per CTA slab
     int32_t max_chunks;        // > 0: each unit runs only its first max_chunks chunks (timing
                                // samples; the outputs are then partial); 0: whole streams
+    int32_t smem_n;            // units of n <= smem_n keep their vectors in shared memory, the
+                               // others in the slab (0: kMaxResidentQubits)
 };
 
 size_t batch_smem_bytes(int max_n_in_smem);

@@ -389,10 +389,11 @@ class Batch:
         return out
 
     def info(self):
-        u, g, o = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        u, g, o, sn = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         check(_lib.load().stab_batch_info(self.h, ctypes.byref(u), ctypes.byref(g),
-                                          ctypes.byref(o)), "stab_batch_info")
-        return {"units": u.value, "grid": g.value, "ctas_per_sm": o.value}
+                                          ctypes.byref(o), ctypes.byref(sn)), "stab_batch_info")
+        return {"units": u.value, "grid": g.value, "ctas_per_sm": o.value,
+                "smem_max_n": sn.value}
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None:

@@ -87,6 +87,27 @@ def test_batch_parameter_shift_equals_adjoint(stab):
     b.close()
 
 
+def test_batch_residencies_agree(stab):
+    # n = 5, 6 vectors in shared memory (RESIDENT), in per-CTA slabs
+    # (STREAMED), and whatever the autotuner picks (AUTO): the same results
+    items = mixed_items(7)
+    out = {}
+    for kernel in ("resident", "streamed", "auto"):
+        b = stab.Batch(items, kernel=kernel)
+        b.run()
+        out[kernel] = (b.expectations(), [b.generators(i) for i, it in enumerate(items)
+                                          if it.kind == "generators"], b.info())
+        b.close()
+    assert out["resident"][2]["smem_max_n"] >= 5 and out["streamed"][2]["smem_max_n"] == 4
+    for kernel in ("streamed", "auto"):
+        e0, g0 = out["resident"][0], out["resident"][1]
+        e1, g1 = out[kernel][0], out[kernel][1]
+        assert np.array_equal(np.isnan(e0), np.isnan(e1))
+        assert np.nanmax(np.abs(e0 - e1)) <= 1e-12 * 10
+        for a, b in zip(g0, g1):
+            assert np.abs(a - b).max() <= 1e-12
+
+
 def test_batch_rejects_too_many_qubits(stab):
     from paper_2502_10685_gb300._lib import StabError
     c = W.layered_ansatz(9, 20, seed=1)
