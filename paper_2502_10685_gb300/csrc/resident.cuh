@@ -236,36 +236,39 @@ inline __device__ double *run_stream_reg4(Stager &st, int c0, int c1, double *cu
 template <int N, int LPG, int T = SCfg<N, LPG>::T>
 __device__ double *run_stream(Stager &st, int c0, int c1, double *cur, double *nxt,
                               int32_t *status) {
-    if constexpr (LPG == 4 && N == 4 && T == 256)
+    if constexpr (LPG == 4 && N == 4 && T == 256) {
         return run_stream_reg4(st, c0, c1, cur, nxt, status);
-    if constexpr (LPG == 4) return run_stream_quads<N>(st, c0, c1, cur, nxt, status);
-    for (int c = c0; c < c1; ++c) {
-        if (!st.wait(c, status)) return nullptr;
-        const Rec *Rr = st.chunk(c);
-        int r = 0;
-        while (true) {
-            const Rec h = Rr[r];
-            if (h.kind != R_PASS) break;   // R_NEXT or R_END
-            const Rec *pulls = Rr + r + 1;
-            const Rec *ops = pulls + h.param;
-            // Without pulls a thread reads and writes only its own groups, so
-            // the pass runs in place; a pull pass permutes and needs the
-            // second buffer.  (In place keeps one vector hot in L2 when the
-            // buffers are in global memory.)
-            if (h.param == 0) {
-                pass_groups<N, T>(cur, cur, h.q, pulls, 0, ops, h.gate);
-            } else {
-                pass_groups<N, T>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
-                double *t = cur;
-                cur = nxt;
-                nxt = t;
+    } else if constexpr (LPG == 4) {
+        return run_stream_quads<N>(st, c0, c1, cur, nxt, status);
+    } else {
+        for (int c = c0; c < c1; ++c) {
+            if (!st.wait(c, status)) return nullptr;
+            const Rec *Rr = st.chunk(c);
+            int r = 0;
+            while (true) {
+                const Rec h = Rr[r];
+                if (h.kind != R_PASS) break;   // R_NEXT or R_END
+                const Rec *pulls = Rr + r + 1;
+                const Rec *ops = pulls + h.param;
+                // Without pulls a thread reads and writes only its own groups, so
+                // the pass runs in place; a pull pass permutes and needs the
+                // second buffer.  (In place keeps one vector hot in L2 when the
+                // buffers are in global memory.)
+                if (h.param == 0) {
+                    pass_groups<N, T>(cur, cur, h.q, pulls, 0, ops, h.gate);
+                } else {
+                    pass_groups<N, T>(cur, nxt, h.q, pulls, h.param, ops, h.gate);
+                    double *t = cur;
+                    cur = nxt;
+                    nxt = t;
+                }
+                __syncthreads();
+                r += 1 + h.param + h.gate;
             }
-            __syncthreads();
-            r += 1 + h.param + h.gate;
+            st.release(c);
         }
-        st.release(c);
+        return cur;
     }
-    return cur;
 }
 
 }  // namespace resident
