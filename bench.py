@@ -335,9 +335,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 # DRAM bytes of the generator phase's two launches from one ncu
-                # capture of this workload (k_batch 1,795,840 + k_transfer_cols
-                # 1,592,832 B read, the staged half-streams; 0 B written)
-                "traffic": 3388672.0 if (c.n == 4 and c.m == 60200) else None,
+                # capture of this workload (k_batch 1,803,776 + k_transfer_cols
+                # 1,589,248 B read, the staged half-streams; 0 B written)
+                "traffic": 3393024.0 if (c.n == 4 and c.m == 60200) else None,
                 "kernel": kernel, "launch_ms": gen_avg_s * 1e3,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock",
                 "active_sms": active_sms,
