@@ -238,6 +238,7 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
     {
         std::atomic<int64_t> next{0};
         auto worker = [&]() {
+            std::vector<int32_t> enc_pos;   // positions of the encoded records (counted only)
             for (int64_t it = next++; it < count; it = next++) {
                 const stab_batch_item &I = items[it];
                 ItemPlan &ip = plans[(size_t)it];
@@ -248,14 +249,8 @@ int build(stab_batch *b, const stab_batch_item *items, int64_t count, int kernel
                 if (ip.rc != STAB_OK) continue;
                 build_plan(I.n, I.gates, I.m, I.n_params, I.n <= 4 ? PLAN_ROWS : PLAN_FUSED,
                            &ip.P);
-                build_stream(ip.P, I.kind == STAB_ITEM_EXPECT, &ip.S);
-                for (size_t i = 0; i < ip.S.size(); ++i) {
-                    if (ip.S[i].kind == R_ROT) ip.n_enc++;
-                    if (ip.S[i].kind == R_MAP3) {
-                        ip.n_enc++;
-                        i += 3;   // its data records
-                    }
-                }
+                build_stream(ip.P, I.kind == STAB_ITEM_EXPECT, &ip.S, 0, -1, &enc_pos);
+                ip.n_enc = (int64_t)enc_pos.size();
             }
         };
         const unsigned hw = std::thread::hardware_concurrency();

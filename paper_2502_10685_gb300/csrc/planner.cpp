@@ -14,7 +14,7 @@ namespace stab {
 // Gate lists of at least this many gates are planned in kPlanChunks chunks at
 // once (see build_plan).
 constexpr int64_t kParallelPlanGates = 16384;
-constexpr int kPlanChunks = 4;
+constexpr int kPlanChunks = 8;
 
 namespace {
 
@@ -115,13 +115,19 @@ struct Emitter {
 
     // One wire's run (gate indices in order) -> one or more P_WIRE passes.
     void emit_wire(const stab_gate *gates, int q, const int64_t *run, size_t run_len) {
-        int n_rot = 0;
-        for (size_t k = 0; k < run_len; ++k) n_rot += is_rotation(gates[run[k]].op);
-        if ((mode == PLAN_FUSED && n_rot > 3) || mode == PLAN_ROWS || mode == PLAN_PLAIN_ROWS) {
+        bool as_map = mode == PLAN_ROWS || mode == PLAN_PLAIN_ROWS;
+        if (mode == PLAN_FUSED) {
+            int n_rot = 0;
+            for (size_t k = 0; k < run_len && n_rot <= 3; ++k) n_rot += is_rotation(gates[run[k]].op);
+            as_map = n_rot > 3;
+        }
+        if (as_map) {
             DevMap3 mp{};
             mp.first = (int32_t)P->map_gate_idx.size();
             mp.count = (int32_t)run_len;
-            for (size_t k = 0; k < run_len; ++k) P->map_gate_idx.push_back((int32_t)run[k]);
+            const size_t at = P->map_gate_idx.size();
+            P->map_gate_idx.resize(at + run_len);
+            for (size_t k = 0; k < run_len; ++k) P->map_gate_idx[at + k] = (int32_t)run[k];
             DevOp op{};
             op.kind = K_MAP3;
             op.q = (uint8_t)q;
@@ -264,32 +270,32 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
     P.n_rot = 0;
     P.n_params = n_params;
     P.mode = mode;
+    // the gate list (map composition reads it) and the rotation ordinals
+    // (gradient slots, gate order); the slot -> ordinals CSR for gradient plans
     P.raw.resize((size_t)m);
-    for (int64_t i = 0; i < m; ++i) {
-        P.raw[i].op = gates[i].op;
-        P.raw[i].q0 = gates[i].q0;
-        P.raw[i].q1 = gates[i].q1;
-        P.raw[i].flags = 0;
-        P.raw[i].param = gates[i].param;
-    }
-    // rotation ordinals (gradient slots, gate order) and the slot -> ordinals CSR
-    std::vector<int32_t> rot_ordinal((size_t)m, -1);
-    std::vector<int32_t> count((size_t)n_params, 0);
+    std::vector<int32_t> &rot_ordinal = P.rot_ordinal;
+    rot_ordinal.resize((size_t)m);
     int32_t nr = 0;
     for (int64_t i = 0; i < m; ++i) {
-        if (is_rotation(gates[i].op)) {
-            rot_ordinal[i] = nr++;
-            count[gates[i].param]++;
-        }
+        const stab_gate &g = gates[i];
+        RawGate &r = P.raw[i];
+        r.op = g.op;
+        r.q0 = g.q0;
+        r.q1 = g.q1;
+        r.flags = 0;
+        r.param = g.param;
+        rot_ordinal[i] = is_rotation(g.op) ? nr++ : -1;
     }
     P.n_rot = nr;
-    P.param_ptr.assign((size_t)n_params + 1, 0);
-    for (int64_t j = 0; j < n_params; ++j) P.param_ptr[j + 1] = P.param_ptr[j] + count[j];
-    P.param_rot.assign((size_t)nr, 0);
-    {
+    if (mode == PLAN_GRAD) {
+        P.param_ptr.assign((size_t)n_params + 1, 0);
+        for (int64_t i = 0; i < m; ++i)
+            if (rot_ordinal[i] >= 0) P.param_ptr[gates[i].param + 1]++;
+        for (int64_t j = 0; j < n_params; ++j) P.param_ptr[j + 1] += P.param_ptr[j];
+        P.param_rot.assign((size_t)nr, 0);
         std::vector<int32_t> fill(P.param_ptr.begin(), P.param_ptr.end() - 1);
         for (int64_t i = 0; i < m; ++i)
-            if (is_rotation(gates[i].op)) P.param_rot[fill[gates[i].param]++] = rot_ordinal[i];
+            if (rot_ordinal[i] >= 0) P.param_rot[fill[gates[i].param]++] = rot_ordinal[i];
     }
 
     P.passes.reserve((size_t)m + 1);
@@ -454,34 +460,41 @@ namespace {
 
 constexpr int kMaxPullPerPass = 64;
 
+// Appends passes to a stream, packing them into chunks of kChunkRecs records
+// (a pass never straddles a chunk; an R_NEXT record ends a chunk early).
 struct StreamWriter {
     std::vector<Rec> *out;
+    std::vector<int32_t> *enc;
     int fill = 0;   // records used in the current chunk
 
-    void pass(int q, const std::vector<Rec> &pulls, const std::vector<Rec> &ops) {
-        const int need = 1 + (int)pulls.size() + (int)ops.size();
+    // Header of a pass with n_pull pull records and n_op op records; the
+    // caller appends them.
+    void header(int q, int n_pull, int n_op) {
+        const int need = 1 + n_pull + n_op;
         if (fill + need > kChunkRecs - 1) {
             Rec nx{};
             nx.kind = R_NEXT;
             out->push_back(nx);
-            while (out->size() % kChunkRecs) out->push_back(Rec{});
+            out->resize(out->size() + (kChunkRecs - out->size() % kChunkRecs) % kChunkRecs);
             fill = 0;
         }
         Rec h{};
         h.kind = R_PASS;
         h.q = (uint8_t)q;
-        h.param = (int32_t)pulls.size();
-        h.gate = (int32_t)ops.size();
+        h.param = n_pull;
+        h.gate = n_op;
         out->push_back(h);
-        out->insert(out->end(), pulls.begin(), pulls.end());
-        out->insert(out->end(), ops.begin(), ops.end());
         fill += need;
+    }
+    // Pull records [b, e) of the applied two-qubit gates, last applied first.
+    void pulls(const Rec *b, const Rec *e) {
+        while (e != b) out->push_back(*--e);
     }
     void end() {
         Rec e{};
         e.kind = R_END;
         out->push_back(e);
-        while (out->size() % kChunkRecs) out->push_back(Rec{});
+        out->resize(out->size() + (kChunkRecs - out->size() % kChunkRecs) % kChunkRecs);
     }
 };
 
@@ -495,28 +508,39 @@ Rec pull_rec(const DevOp &op) {
 
 }  // namespace
 
-void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out, int k0, int k1) {
+void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out, int k0, int k1,
+                  std::vector<int32_t> *enc) {
     out->clear();
-    StreamWriter w{out};
+    if (enc) enc->clear();
+    StreamWriter w{out, enc};
     // two-qubit Clifford gates waiting to be pulled, in application order
-    std::vector<Rec> applied, seg, none, ops;
-    out->reserve(P.passes.size() * 4 + P.ops.size() * 2 + kChunkRecs);
-    auto emit = [&](int q, const std::vector<Rec> &pass_ops) {
-        // all but the last kMaxPullPerPass-segment go into identity passes
-        size_t k = 0;
-        while (applied.size() - k > (size_t)kMaxPullPerPass) {
-            seg.assign(applied.begin() + k, applied.begin() + k + kMaxPullPerPass);
-            std::reverse(seg.begin(), seg.end());
-            w.pass(0, seg, none);
-            k += kMaxPullPerPass;
-        }
-        seg.assign(applied.begin() + k, applied.end());
-        std::reverse(seg.begin(), seg.end());   // a pull walks the last applied gate first
-        w.pass(q, seg, pass_ops);
-        applied.clear();
-    };
+    std::vector<Rec> applied;
     if (k1 < 0) k1 = (int)P.passes.size();
     const int np = k1 - k0;
+    {
+        const size_t all = P.passes.size() ? P.passes.size() : 1;
+        const size_t share = (size_t)np * (P.ops.size() + P.passes.size()) / all;
+        out->reserve(2 * share + (size_t)np + kChunkRecs);
+    }
+    // The pending pulls: all but the last kMaxPullPerPass-segment go into
+    // identity passes; the last goes with the pass on wire q and its ops.
+    auto flush_pulls = [&](int q, const DevPass *p) {
+        size_t k = 0;
+        while (applied.size() - k > (size_t)kMaxPullPerPass) {
+            w.header(0, kMaxPullPerPass, 0);
+            w.pulls(applied.data() + k, applied.data() + k + kMaxPullPerPass);
+            k += kMaxPullPerPass;
+        }
+        int n_op = 0;
+        if (p)
+            for (int j = 0; j < p->n_ops; ++j) {
+                const int kind = P.ops[p->first + j].kind;
+                n_op += (kind == K_ROT || kind == K_PERM) ? 1 : 4;
+            }
+        w.header(q, (int)(applied.size() - k), n_op);
+        w.pulls(applied.data() + k, applied.data() + applied.size());
+        applied.clear();
+    };
     for (int k = 0; k < np; ++k) {
         const DevPass &p = P.passes[backward ? k1 - 1 - k : k0 + k];
         if (p.type == P_CLIFF) {
@@ -525,10 +549,10 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out, int k
                 applied.push_back(pull_rec(P.ops[p.first + jj]));
             }
             // the gate-by-gate forms keep each two-qubit gate a pass of its own
-            if (P.mode == PLAN_PLAIN || P.mode == PLAN_PLAIN_ROWS) emit(0, none);
+            if (P.mode == PLAN_PLAIN || P.mode == PLAN_PLAIN_ROWS) flush_pulls(0, nullptr);
             continue;
         }
-        ops.clear();
+        flush_pulls(p.q, &p);
         for (int j = 0; j < p.n_ops; ++j) {
             const DevOp &op = P.ops[p.first + (backward ? p.n_ops - 1 - j : j)];
             Rec r{};
@@ -539,25 +563,26 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out, int k
                 r.axis = op.axis;
                 r.param = op.param;
                 r.gate = op.gate;
-                ops.push_back(r);
+                if (enc) enc->push_back((int32_t)out->size());
+                out->push_back(r);
             } else if (op.kind == K_PERM) {
                 r.kind = R_PERM;
                 r.code = backward ? op.perm_inv : op.perm;
-                ops.push_back(r);
+                out->push_back(r);
             } else {
                 r.kind = R_MAP3;
                 r.param = op.param;
-                ops.push_back(r);
+                if (enc) enc->push_back((int32_t)out->size());
+                out->push_back(r);
                 Rec d{};
                 d.kind = R_DATA;
-                ops.push_back(d);
-                ops.push_back(d);
-                ops.push_back(d);
+                out->push_back(d);
+                out->push_back(d);
+                out->push_back(d);
             }
         }
-        emit(p.q, ops);
     }
-    if (!applied.empty()) emit(0, none);
+    if (!applied.empty()) flush_pulls(0, nullptr);
     w.end();
 }
 

@@ -34,8 +34,9 @@ struct HostPlan {
     std::vector<DevMap3> maps;
     std::vector<int32_t> map_gate_idx;
     std::vector<RawGate> raw;            // copy of the gate list (map composition reads it)
-    std::vector<int32_t> param_ptr;      // CSR: angle slot -> rotation ordinals
+    std::vector<int32_t> param_ptr;      // CSR: angle slot -> rotation ordinals (PLAN_GRAD only)
     std::vector<int32_t> param_rot;
+    std::vector<int32_t> rot_ordinal;    // planning scratch: gate -> rotation ordinal, or -1
     int32_t n_rot = 0;
     int64_t n_params = 0;
     PlanMode mode = PLAN_FUSED;
@@ -61,9 +62,10 @@ void clifford_tableau(int n, const stab_gate *gates, int64_t i0, int64_t i1, boo
 // Instruction stream of a plan for the resident kernels (see stab_internal.h):
 // forward (backward = false) or for the inverse circuit (backward = true).
 // With k1 >= 0 only passes [k0, k1) of the plan (walked backward when
-// backward is set).
+// backward is set).  enc, when given, receives the positions of the R_ROT and
+// R_MAP3 records (the records the device encodes from the angles).
 void build_stream(const HostPlan &plan, bool backward, std::vector<Rec> *out, int k0 = 0,
-                  int k1 = -1);
+                  int k1 = -1, std::vector<int32_t> *enc = nullptr);
 
 // Signed permutation codes of the single-qubit Clifford opcodes on (X, Y, Z).
 uint32_t clifford_perm_code(int op);

@@ -330,26 +330,12 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
 }
 
 void make_stream_range(const DevPlan &P, DevStreamBuf &S, bool backward, int k0, int k1) {
-    build_stream(P.host, backward, &S.host, k0, k1);
-    S.enc.clear();
-    for (size_t i = 0; i < S.host.size(); ++i) {
-        const uint8_t k = S.host[i].kind;
-        if (k == R_ROT || k == R_MAP3) S.enc.push_back((int32_t)i);
-        if (k == R_MAP3) i += 3;   // its data records are not kinds
-    }
+    build_stream(P.host, backward, &S.host, k0, k1, &S.enc);
     S.n_chunks = (int)(S.host.size() / kChunkRecs);
 }
 
 void make_stream(DevPlan &P, bool backward) {
-    DevStreamBuf &S = backward ? P.sb : P.sf;
-    build_stream(P.host, backward, &S.host);
-    S.enc.clear();
-    for (size_t i = 0; i < S.host.size(); ++i) {
-        const uint8_t k = S.host[i].kind;
-        if (k == R_ROT || k == R_MAP3) S.enc.push_back((int32_t)i);
-        if (k == R_MAP3) i += 3;   // its data records are not kinds
-    }
-    S.n_chunks = (int)(S.host.size() / kChunkRecs);
+    make_stream_range(P, backward ? P.sb : P.sf, backward, 0, -1);
 }
 
 // Forward and backward streams, built concurrently on host threads; with
