@@ -474,7 +474,9 @@ int stab_selftest_bounded_wait(int64_t polls);
  * memory) in plan mode `mode` (0 fused, 1 gradient, 2 one pass per gate,
  * 3 one map per wire run) both in parallel chunks and sequentially, with
  * their forward and backward instruction streams, and returns STAB_OK when
- * every array is byte-identical, STAB_E_STATE when any differs.
+ * every array is byte-identical and the streams built as two pieces at once
+ * (long streams on the host pool) apply the same pulls and passes in the same
+ * order as the one-piece streams; STAB_E_STATE when any of this fails.
  * Errors: STAB_E_INVAL / STAB_E_RANGE (gates as for stab_load_circuit, mode). */
 int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, int mode);
 

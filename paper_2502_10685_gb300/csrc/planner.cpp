@@ -5,6 +5,7 @@
 #include "launch.h"
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <cmath>
 #include <map>
@@ -60,11 +61,46 @@ uint32_t perm_inverse(uint32_t code) {
     return out;
 }
 
+namespace {
+
+// Gates [i0, i1): STAB_OK, or the error of the first bad gate (its index in *at).
+int check_gates(int n, const stab_gate *gates, int64_t i0, int64_t i1, int64_t n_params,
+                int64_t *at) {
+    for (int64_t i = i0; i < i1; ++i) {
+        const stab_gate &g = gates[i];
+        *at = i;
+        if (g.op > STAB_RZ || g.flags != 0 || g.q0 >= n) return STAB_E_INVAL;
+        if (is_two_qubit(g.op) && (g.q1 >= n || g.q1 == g.q0)) return STAB_E_INVAL;
+        if (is_rotation(g.op) && (g.param < 0 || g.param >= n_params)) return STAB_E_RANGE;
+    }
+    return STAB_OK;
+}
+
+}  // namespace
+
 int validate_gates(int n, const stab_gate *gates, int64_t m, int64_t n_params, std::string *msg) {
     if (m < 0 || n_params < 0) return STAB_E_RANGE;
     if (m > 0 && gates == nullptr) return STAB_E_INVAL;
     if (m > (int64_t)INT32_MAX / 2) return STAB_E_RANGE;
-    for (int64_t i = 0; i < m; ++i) {
+    // long lists are checked in chunks at once; the first bad gate of the
+    // first failing chunk is then described by the walk below
+    int64_t from = 0;
+    if (m >= kParallelPlanGates) {
+        int rc[kPlanChunks];
+        int64_t at[kPlanChunks];
+        std::vector<std::function<void()>> jobs;
+        for (int k = 0; k < kPlanChunks; ++k)
+            jobs.push_back([&, k] {
+                rc[k] = check_gates(n, gates, m * k / kPlanChunks, m * (k + 1) / kPlanChunks,
+                                    n_params, &at[k]);
+            });
+        HostPool::run(jobs);
+        int k = 0;
+        while (k < kPlanChunks && rc[k] == STAB_OK) ++k;
+        if (k == kPlanChunks) return STAB_OK;
+        from = at[k];
+    }
+    for (int64_t i = from; i < m; ++i) {
         const stab_gate &g = gates[i];
         if (g.op > STAB_RZ || g.flags != 0 || g.q0 >= n) {
             if (msg) *msg = "gate " + std::to_string(i) + ": bad opcode, flags or qubit";
@@ -272,20 +308,14 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
     P.mode = mode;
     // the gate list (map composition reads it) and the rotation ordinals
     // (gradient slots, gate order); the slot -> ordinals CSR for gradient plans
+    static_assert(sizeof(RawGate) == sizeof(stab_gate) && offsetof(RawGate, param) ==
+                      offsetof(stab_gate, param), "RawGate mirrors stab_gate");
     P.raw.resize((size_t)m);
+    if (m > 0) std::memcpy(P.raw.data(), gates, (size_t)m * sizeof(RawGate));   // flags are 0
     std::vector<int32_t> &rot_ordinal = P.rot_ordinal;
     rot_ordinal.resize((size_t)m);
     int32_t nr = 0;
-    for (int64_t i = 0; i < m; ++i) {
-        const stab_gate &g = gates[i];
-        RawGate &r = P.raw[i];
-        r.op = g.op;
-        r.q0 = g.q0;
-        r.q1 = g.q1;
-        r.flags = 0;
-        r.param = g.param;
-        rot_ordinal[i] = is_rotation(g.op) ? nr++ : -1;
-    }
+    for (int64_t i = 0; i < m; ++i) rot_ordinal[i] = is_rotation(gates[i].op) ? nr++ : -1;
     P.n_rot = nr;
     if (mode == PLAN_GRAD) {
         P.param_ptr.assign((size_t)n_params + 1, 0);
@@ -490,9 +520,12 @@ struct StreamWriter {
     void pulls(const Rec *b, const Rec *e) {
         while (e != b) out->push_back(*--e);
     }
-    void end() {
+    // R_END (the stream ends) or R_NEXT (another piece follows on the next
+    // chunk; nothing when the piece is empty), then padding to the chunk end.
+    void end(bool last) {
+        if (!last && out->empty()) return;
         Rec e{};
-        e.kind = R_END;
+        e.kind = last ? R_END : R_NEXT;
         out->push_back(e);
         out->resize(out->size() + (kChunkRecs - out->size() % kChunkRecs) % kChunkRecs);
     }
@@ -509,7 +542,7 @@ Rec pull_rec(const DevOp &op) {
 }  // namespace
 
 void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out, int k0, int k1,
-                  std::vector<int32_t> *enc) {
+                  std::vector<int32_t> *enc, bool last) {
     out->clear();
     if (enc) enc->clear();
     StreamWriter w{out, enc};
@@ -583,7 +616,7 @@ void build_stream(const HostPlan &P, bool backward, std::vector<Rec> *out, int k
         }
     }
     if (!applied.empty()) flush_pulls(0, nullptr);
-    w.end();
+    w.end(last);
 }
 
 int encode_terms(int n, const stab_term *O, int64_t n_terms, std::vector<DevTerm> *out) {

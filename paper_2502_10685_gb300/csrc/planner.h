@@ -63,9 +63,12 @@ void clifford_tableau(int n, const stab_gate *gates, int64_t i0, int64_t i1, boo
 // forward (backward = false) or for the inverse circuit (backward = true).
 // With k1 >= 0 only passes [k0, k1) of the plan (walked backward when
 // backward is set).  enc, when given, receives the positions of the R_ROT and
-// R_MAP3 records (the records the device encodes from the angles).
+// R_MAP3 records (the records the device encodes from the angles).  With last
+// = false the records are the first piece of a longer stream: pending pulls
+// are applied in an identity pass and the last chunk closes with R_NEXT, so
+// the next piece starts on a chunk boundary.
 void build_stream(const HostPlan &plan, bool backward, std::vector<Rec> *out, int k0 = 0,
-                  int k1 = -1, std::vector<int32_t> *enc = nullptr);
+                  int k1 = -1, std::vector<int32_t> *enc = nullptr, bool last = true);
 
 // Signed permutation codes of the single-qubit Clifford opcodes on (X, Y, Z).
 uint32_t clifford_perm_code(int op);

@@ -61,6 +61,10 @@ constexpr int kThreadedStreamPasses = 2048;
 struct DevStreamBuf {
     std::vector<Rec> host;
     std::vector<int32_t> enc;
+    // a long stream is built as two pieces at once: the second piece (its
+    // encoded positions already offset) is uploaded right behind the first
+    std::vector<Rec> tail;
+    std::vector<int32_t> tail_enc;
     Rec *dev = nullptr;
     const int32_t *enc_dev = nullptr;
     int n_chunks = 0;
@@ -248,7 +252,8 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     const std::vector<DevStreamBuf *> streams = P.all_streams();
     size_t b_streams = 0;
     for (const DevStreamBuf *S : streams)
-        b_streams += align256(S->host.size() * sizeof(Rec)) + align256(S->enc.size() * 4);
+        b_streams += align256((S->host.size() + S->tail.size()) * sizeof(Rec)) +
+                     align256((S->enc.size() + S->tail_enc.size()) * 4);
     const size_t total = b_pass + b_ops + b_maps + b_midx + b_raw + b_pptr + b_prot + b_tabs +
                          b_streams;
     RC(c->dalloc(P.buf, total, c->st));
@@ -259,12 +264,20 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     size_t off = 0;
     // large pieces are copied into the staging buffer by the host pool
     std::vector<std::function<void()>> copies;
-    auto put = [&](const void *src, size_t bytes, size_t span) {
-        if (bytes >= ((size_t)1 << 18)) {
-            char *dst = h + off;
-            copies.push_back([dst, src, bytes] { std::memcpy(dst, src, bytes); });
-        } else if (bytes) {
-            std::memcpy(h + off, src, bytes);
+    // [src, bytes) then [src2, bytes2) at the next `span` bytes of the buffer
+    auto put = [&](const void *src, size_t bytes, size_t span, const void *src2 = nullptr,
+                   size_t bytes2 = 0) {
+        size_t o = off;
+        for (int k = 0; k < 2; ++k) {
+            const void *from = k ? src2 : src;
+            const size_t b = k ? bytes2 : bytes;
+            if (b >= ((size_t)1 << 18)) {
+                char *dst = h + o;
+                copies.push_back([dst, from, b] { std::memcpy(dst, from, b); });
+            } else if (b) {
+                std::memcpy(h + o, from, b);
+            }
+            o += b;
         }
         const size_t at = off;
         off += span;
@@ -279,10 +292,11 @@ int upload_plan(stab_ctx *c, DevPlan &P) {
     P.param_rot = (const int32_t *)put(H.param_rot.data(), H.param_rot.size() * 4, b_prot);
     P.prog.tabs = (const DevTab *)put(H.tabs.data(), H.tabs.size() * sizeof(DevTab), b_tabs);
     for (DevStreamBuf *S : streams) {
-        S->dev = (Rec *)put(S->host.data(), S->host.size() * sizeof(Rec),
-                            align256(S->host.size() * sizeof(Rec)));
-        S->enc_dev = (const int32_t *)put(S->enc.data(), S->enc.size() * 4,
-                                          align256(S->enc.size() * 4));
+        const size_t rb = S->host.size() * sizeof(Rec), tb = S->tail.size() * sizeof(Rec);
+        S->dev = (Rec *)put(S->host.data(), rb, align256(rb + tb), S->tail.data(), tb);
+        const size_t eb = S->enc.size() * 4, teb = S->tail_enc.size() * 4;
+        S->enc_dev = (const int32_t *)put(S->enc.data(), eb, align256(eb + teb),
+                                          S->tail_enc.data(), teb);
     }
     P.prog.n_passes = (int32_t)n_pass;
     P.prog.n_ops = (int32_t)n_ops;
@@ -308,8 +322,9 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
             c->launches++;
         }
         for (DevStreamBuf *S : P.all_streams()) {
-            if (S->enc.empty()) continue;
-            CK(launch_encode_stream(S->dev, S->enc_dev, (int)S->enc.size(), P.prog.maps, th,
+            const int n_enc = (int)(S->enc.size() + S->tail_enc.size());
+            if (n_enc == 0) continue;
+            CK(launch_encode_stream(S->dev, S->enc_dev, n_enc, P.prog.maps, th,
                                     c->st));
             c->launches++;
         }
@@ -329,39 +344,76 @@ int encode_plan(stab_ctx *c, DevPlan &P) {
     return STAB_OK;
 }
 
-void make_stream_range(const DevPlan &P, DevStreamBuf &S, bool backward, int k0, int k1) {
-    build_stream(P.host, backward, &S.host, k0, k1, &S.enc);
-    S.n_chunks = (int)(S.host.size() / kChunkRecs);
-}
+// One instruction stream to build: passes [k0, k1) of the plan, forward or
+// (backward) walked from k1 - 1 down to k0.
+struct StreamSpec {
+    DevStreamBuf *S;
+    bool backward;
+    int k0, k1;
+};
 
-void make_stream(DevPlan &P, bool backward) {
-    make_stream_range(P, backward ? P.sb : P.sf, backward, 0, -1);
+// Streams of at least this many passes are built as two pieces at once.
+constexpr int kStreamPiecePasses = 4096;
+
+// Builds the streams, on the host pool when `threads` is set; there a long
+// stream is built as two pieces at once, the first ending in R_NEXT on a
+// chunk boundary (its pending pulls in an identity pass), the second in
+// S.tail -- the same passes, pulls and ops as the one-piece stream.
+void build_streams(const DevPlan &P, const std::vector<StreamSpec> &specs, bool threads) {
+    std::vector<std::function<void()>> jobs;
+    for (const StreamSpec &sp : specs) {
+        DevStreamBuf *S = sp.S;
+        S->tail.clear();
+        S->tail_enc.clear();
+        if (!threads || sp.k1 - sp.k0 < kStreamPiecePasses) {
+            jobs.push_back([&P, sp] {
+                build_stream(P.host, sp.backward, &sp.S->host, sp.k0, sp.k1, &sp.S->enc);
+            });
+            continue;
+        }
+        const int mid = sp.k0 + (sp.k1 - sp.k0) / 2;
+        const int a0 = sp.backward ? mid : sp.k0, a1 = sp.backward ? sp.k1 : mid;
+        const int b0 = sp.backward ? sp.k0 : mid, b1 = sp.backward ? mid : sp.k1;
+        jobs.push_back([&P, sp, a0, a1] {
+            build_stream(P.host, sp.backward, &sp.S->host, a0, a1, &sp.S->enc, false);
+        });
+        jobs.push_back([&P, sp, b0, b1] {
+            build_stream(P.host, sp.backward, &sp.S->tail, b0, b1, &sp.S->tail_enc);
+        });
+    }
+    if (threads) {
+        HostPool::run(jobs);
+    } else {
+        for (auto &j : jobs) j();
+    }
+    for (const StreamSpec &sp : specs) {
+        DevStreamBuf &S = *sp.S;
+        for (int32_t &e : S.tail_enc) e += (int32_t)S.host.size();
+        S.n_chunks = (int)((S.host.size() + S.tail.size()) / kChunkRecs);
+    }
 }
 
 // Forward and backward streams, built concurrently on host threads; with
 // split_frac > 0 (and enough passes) also the split streams cut at that
 // fraction of the passes.  A split gradient plan (grad) needs only the four
-// half streams, not the whole-circuit ones.
+// half streams, not the whole-circuit ones.  Below kThreadedStreamPasses
+// passes the streams are built on the calling thread: handing them to the
+// pool would cost more than the work.
 void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_parts = 2) {
     P.streams = true;
     const int np = (int)P.host.passes.size();
+    const bool threads = np >= kThreadedStreamPasses;
     if (!grad && n_parts >= 3) {
-        // K forward parts of equal pass counts (on up to four threads when long)
+        // K forward parts of equal pass counts
         P.sf = P.sb = P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
         P.parts.resize((size_t)n_parts);
         P.cuts.assign((size_t)n_parts + 1, 0);
         for (int k = 0; k <= n_parts; ++k) P.cuts[k] = (int)((int64_t)np * k / n_parts);
         P.split = P.cuts[1];
-        std::vector<std::function<void()>> jobs;
+        std::vector<StreamSpec> specs;
         for (int k = 0; k < n_parts; ++k)
-            jobs.push_back([&P, k] {
-                make_stream_range(P, P.parts[k], false, P.cuts[k], P.cuts[k + 1]);
-            });
-        if (np < kThreadedStreamPasses) {
-            for (auto &j : jobs) j();
-        } else {
-            HostPool::run(jobs);
-        }
+            specs.push_back({&P.parts[k], false, P.cuts[k], P.cuts[k + 1]});
+        build_streams(P, specs, threads);
         return;
     }
     P.parts.clear();
@@ -370,26 +422,18 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_
     // streams that are rebuilt keep their capacity; the others are released
     if (P.split < 0) P.h1 = P.h2 = P.h2b = DevStreamBuf();
     if (!(grad && P.split >= 0)) P.h1b = DevStreamBuf();
-    // below kThreadedStreamPasses passes the streams are built on the calling
-    // thread: handing them to the pool would cost more than the work
-    const bool threads = np >= kThreadedStreamPasses;
-    auto run_all = [threads](std::vector<std::function<void()>> jobs) {
-        if (!threads) {
-            for (auto &j : jobs) j();
-            return;
-        }
-        HostPool::run(jobs);
-    };
     if (grad && P.split >= 0) {
         P.sf = P.sb = DevStreamBuf();
-        run_all({[&P] { make_stream_range(P, P.h1b, true, 0, P.split); },
-                 [&P] { make_stream_range(P, P.h1, false, 0, P.split); },
-                 [&P, np] { make_stream_range(P, P.h2, false, P.split, np); },
-                 [&P, np] { make_stream_range(P, P.h2b, true, P.split, np); }});
+        build_streams(P,
+                      {{&P.h1b, true, 0, P.split},
+                       {&P.h1, false, 0, P.split},
+                       {&P.h2, false, P.split, np},
+                       {&P.h2b, true, P.split, np}},
+                      threads);
         return;
     }
     if (P.split < 0) {
-        run_all({[&P] { make_stream(P, false); }, [&P] { make_stream(P, true); }});
+        build_streams(P, {{&P.sf, false, 0, np}, {&P.sb, true, 0, np}}, threads);
         return;
     }
     // A split plan reads the halves: the generators (n <= 4) and the density
@@ -399,12 +443,10 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_
     P.sb = DevStreamBuf();
     const bool whole_fwd = P.host_n > 4;
     if (!whole_fwd) P.sf = DevStreamBuf();
-    std::vector<std::function<void()>> jobs = {
-        [&P] { make_stream_range(P, P.h1, false, 0, P.split); },
-        [&P, np] { make_stream_range(P, P.h2, false, P.split, np); },
-        [&P, np] { make_stream_range(P, P.h2b, true, P.split, np); }};
-    if (whole_fwd) jobs.push_back([&P] { make_stream(P, false); });
-    run_all(std::move(jobs));
+    std::vector<StreamSpec> specs = {
+        {&P.h1, false, 0, P.split}, {&P.h2, false, P.split, np}, {&P.h2b, true, P.split, np}};
+    if (whole_fwd) specs.push_back({&P.sf, false, 0, np});
+    build_streams(P, specs, threads);
 }
 
 void no_streams(DevPlan &P) {
@@ -882,6 +924,46 @@ void stab_default_opts(stab_opts *o) {
 
 int stab_version(void) { return STAB_VERSION; }
 
+namespace {
+
+// What a kernel applies from a stream, in order: every pull record (last
+// listed first), then, for a pass with ops, its header (pull count cleared)
+// and its op records.  False when the stream is malformed (a record that is
+// not a header where one is due, a pass straddling a chunk, no R_END) or its
+// encoded positions are not those of its R_ROT / R_MAP3 records.
+bool stream_actions(const std::vector<Rec> &s, const std::vector<int32_t> &enc,
+                    std::vector<Rec> *out) {
+    std::vector<int32_t> pos;
+    size_t r = 0;
+    while (r < s.size()) {
+        const Rec &h = s[r];
+        if (h.kind == R_END) return pos == enc;
+        if (h.kind == R_NEXT) {
+            r = (r / kChunkRecs + 1) * kChunkRecs;
+            continue;
+        }
+        const size_t len = 1 + (size_t)h.param + (size_t)h.gate;
+        if (h.kind != R_PASS || h.param < 0 || h.gate < 0 ||
+            r / kChunkRecs != (r + len - 1) / kChunkRecs || r + len > s.size())
+            return false;
+        for (int k = h.param; k > 0; --k) out->push_back(s[r + (size_t)k]);
+        if (h.gate > 0) {
+            Rec hh = h;
+            hh.param = 0;
+            out->push_back(hh);
+            for (int k = 0; k < h.gate; ++k) {
+                const size_t i = r + 1 + (size_t)h.param + (size_t)k;
+                if (s[i].kind == R_ROT || s[i].kind == R_MAP3) pos.push_back((int32_t)i);
+                out->push_back(s[i]);
+            }
+        }
+        r += len;
+    }
+    return false;
+}
+
+}  // namespace
+
 int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, int mode) {
     if (n < 1 || n > STAB_MAX_QUBITS) return STAB_E_RANGE;
     if (mode < 0 || mode > 3) return STAB_E_RANGE;
@@ -905,6 +987,25 @@ int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_param
         build_stream(a, backward, &sa);
         build_stream(b, backward, &sb);
         ok = ok && same(sa, sb);
+    }
+    // one-piece against two-piece streams, compared as what a kernel applies:
+    // pulls in application order, passes with ops (identity passes only pull)
+    DevPlan P;
+    P.host = std::move(b);
+    const int np = (int)P.host.passes.size();
+    for (bool backward : {false, true}) {
+        DevStreamBuf one, two;
+        build_streams(P, {{&one, backward, 0, np}}, false);
+        build_streams(P, {{&two, backward, 0, np}}, true);
+        std::vector<Rec> joined = two.host;
+        joined.insert(joined.end(), two.tail.begin(), two.tail.end());
+        std::vector<int32_t> enc = two.enc;
+        enc.insert(enc.end(), two.tail_enc.begin(), two.tail_enc.end());
+        std::vector<Rec> fa, fb;
+        ok = ok && two.host.size() % kChunkRecs == 0 &&
+             (size_t)two.n_chunks * kChunkRecs == joined.size() &&
+             stream_actions(one.host, one.enc, &fa) && stream_actions(joined, enc, &fb) &&
+             same(fa, fb);
     }
     return ok ? STAB_OK : STAB_E_STATE;
 }

@@ -43,7 +43,9 @@ def test_host_only_calls():
 
 def test_chunked_planner_equals_sequential():
     # host-only: long gate lists are planned in parallel chunks; the plan and
-    # its instruction streams must be byte-identical to the sequential ones
+    # its instruction streams must be byte-identical to the sequential ones,
+    # and streams built as two pieces at once must apply the same pulls and
+    # passes in the same order as the one-piece streams
     import numpy as np
     from paper_2502_10685_gb300 import _lib, workloads as W
     L = _lib.load()
