@@ -312,10 +312,17 @@ void build_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, Plan
                       offsetof(stab_gate, param), "RawGate mirrors stab_gate");
     P.raw.resize((size_t)m);
     if (m > 0) std::memcpy(P.raw.data(), gates, (size_t)m * sizeof(RawGate));   // flags are 0
+    // (plans that turn every wire run into a map emit no rotation ops and
+    // need only the count)
     std::vector<int32_t> &rot_ordinal = P.rot_ordinal;
-    rot_ordinal.resize((size_t)m);
     int32_t nr = 0;
-    for (int64_t i = 0; i < m; ++i) rot_ordinal[i] = is_rotation(gates[i].op) ? nr++ : -1;
+    if (mode == PLAN_ROWS || mode == PLAN_PLAIN_ROWS) {
+        rot_ordinal.clear();
+        for (int64_t i = 0; i < m; ++i) nr += is_rotation(gates[i].op);
+    } else {
+        rot_ordinal.resize((size_t)m);
+        for (int64_t i = 0; i < m; ++i) rot_ordinal[i] = is_rotation(gates[i].op) ? nr++ : -1;
+    }
     P.n_rot = nr;
     if (mode == PLAN_GRAD) {
         P.param_ptr.assign((size_t)n_params + 1, 0);
