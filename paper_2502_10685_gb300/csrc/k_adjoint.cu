@@ -138,41 +138,53 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, doubl
     }
 }
 
+// Rotations of a tile group: the gradient dots a launch accumulates.
+int group_rotations(const TileGroup &tg) {
+    int n_acc = 0;
+    for (int j = 0; j < tg.n_pass; ++j) n_acc += tg.n_rot[j];
+    return n_acc;
+}
+
 // Tile-fused adjoint sweep: up to kTileMaxPasses wire passes on at most
 // kTileWires wires, applied backward (tg.inverse = 1; forward with 0) to the
 // pair (lambda, rho) held as two shared-memory tiles (pair[0 .. 4^n) =
-// lambda, pair[4^n ..) = rho).  The
-// group's ops are staged in shared memory once per launch.  Every rotation's
-// gradient dot is reduced within each warp per pass (lane 0 adds it to its
-// warp's slot, tile after tile), and over the warps in a fixed order at the
-// end; the result goes to partials[gate][block].
+// lambda, pair[4^n ..) = rho).  The group's ops are staged in shared memory
+// once per launch.  Each thread adds every rotation's gradient dot of its
+// group to its own shared-memory accumulator (tile after tile), so the op
+// chain carries no reduction; at the end each rotation's accumulators are
+// summed over the threads in a fixed order and the result goes to
+// partials[gate][block].
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src, double *pair,
                                                               int n, TileGroup tg,
                                                               const DevOp *ops,
                                                               double *partials) {
     extern __shared__ double sm[];
-    constexpr int W = kAdjThreads / 32;
     const uint32_t T = 1u << tg.tile_bits;
+    const int nt = (int)blockDim.x;
     double *tl = sm, *tr = sm + T;
-    double *red = tr + T;                            // kTileMaxPasses x R x W
-    DevOp *sops = reinterpret_cast<DevOp *>(red + kTileMaxPasses * R * W);   // kAdjStagedOps
+    DevOp *sops = reinterpret_cast<DevOp *>(tr + T);                   // kAdjStagedOps
     uint32_t *offs = reinterpret_cast<uint32_t *>(sops + kAdjStagedOps);
-    __shared__ int s_first[kTileMaxPasses], s_nrot[kTileMaxPasses];
-    __shared__ int s_staged;
+    double *acc = reinterpret_cast<double *>(offs + T);                // rotations x threads
+    __shared__ int s_first[kTileMaxPasses], s_nrot[kTileMaxPasses], s_rbase[kTileMaxPasses];
+    __shared__ int s_staged, s_nacc;
     for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
         offs[e] = (uint32_t)deposit_runs(e, tg.tile_runs);
-    for (int k = threadIdx.x; k < kTileMaxPasses * R * W; k += blockDim.x) red[k] = 0.0;
     if (threadIdx.x == 0) {
         int total = 0;
         for (int j = 0; j < tg.n_pass; ++j) total += tg.n_ops[j];
         s_staged = total <= kAdjStagedOps;
-        int at = 0;
+        int at = 0, rb = 0;
         for (int j = 0; j < tg.n_pass; ++j) {
             s_first[j] = s_staged ? at : (int)tg.first[j];
             at += tg.n_ops[j];
             s_nrot[j] = tg.n_rot[j];
+            s_rbase[j] = rb;
+            rb += tg.n_rot[j];
         }
+        s_nacc = rb;
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < s_nacc * nt; k += blockDim.x) acc[k] = 0.0;
     __syncthreads();
     const bool staged = s_staged != 0;
     if (staged) {
@@ -213,6 +225,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
             const int n_ops = tg.n_ops[j];
             const DevOp *po = pops + s_first[j];
             const int n_rot = s_nrot[j];
+            double *my_acc = acc + (size_t)s_rbase[j] * nt + threadIdx.x;
             // one group per thread (the launch has T / 4 threads): each
             // rotation's dot is reduced over the warp right away, so no
             // per-slot accumulator array is carried through the op loop
@@ -231,9 +244,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
                 for (int k = n_ops - 1; k >= 0; --k) {
                     const DevOp op = po[k];
                     if (op.kind == K_ROT) {
-                        double d = pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
-                        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-                        if (lane == 0) red[(j * R + slot) * W + warp] += d;
+                        my_acc[slot * nt] += pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
                         --slot;
                     }
                     apply_op1(lx_, ly_, lz_, op, nullptr, 1);
@@ -248,9 +259,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
                     apply_op1(lx_, ly_, lz_, op, nullptr, 0);
                     apply_op1(rx_, ry_, rz_, op, nullptr, 0);
                     if (op.kind == K_ROT) {
-                        double d = pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
-                        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-                        if (lane == 0) red[(j * R + slot) * W + warp] += d;
+                        my_acc[slot * nt] += pair_dot(op.axis, lx_, ly_, lz_, rx_, ry_, rz_);
                         ++slot;
                     }
                 }
@@ -267,16 +276,21 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
         }
         __syncthreads();
     }
-    const int nw = (int)(blockDim.x >> 5);
-    for (int k = threadIdx.x; k < tg.n_pass * R; k += blockDim.x) {
-        const int j = k / R, r = k % R;
-        if (r >= s_nrot[j]) continue;
+    // rotation r (pass j, slot r - s_rbase[j]) by warp r mod warps: each lane
+    // sums its threads' accumulators in order, then a fixed shuffle tree
+    const int nw = nt >> 5;
+    for (int r = warp; r < s_nacc; r += nw) {
         double total = 0.0;
-        for (int w = 0; w < nw; ++w) total += red[k * W + w];
-        DevPass p{};
-        p.n_ops = tg.n_ops[j];
-        p.first = s_first[j];
-        partials[(size_t)rot_gate(p, pops, r) * gridDim.x + blockIdx.x] = total;
+        for (int t = lane; t < nt; t += 32) total += acc[(size_t)r * nt + t];
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (lane == 0) {
+            int j = 0;
+            while (j + 1 < tg.n_pass && s_rbase[j + 1] <= r) ++j;
+            DevPass p{};
+            p.n_ops = tg.n_ops[j];
+            p.first = s_first[j];
+            partials[(size_t)rot_gate(p, pops, r - s_rbase[j]) * gridDim.x + blockIdx.x] = total;
+        }
     }
 }
 
@@ -320,19 +334,31 @@ cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &
     return cudaGetLastError();
 }
 
-size_t adjoint_tile_smem(int tile_bits) {
+namespace {
+
+int adjoint_tile_threads(int tile_bits) {
+    int threads = (int)((1u << tile_bits) / 4);
+    if (threads > kAdjThreads) threads = kAdjThreads;
+    if (threads < 32) threads = 32;
+    return threads;
+}
+
+}  // namespace
+
+size_t adjoint_tile_smem(int tile_bits, int n_rot) {
     const size_t T = (size_t)1 << tile_bits;
-    return 2 * T * sizeof(double) + (size_t)kTileMaxPasses * R * (kAdjThreads / 32) * sizeof(double) +
-           kAdjStagedOps * sizeof(DevOp) + T * sizeof(uint32_t);
+    return 2 * T * sizeof(double) + kAdjStagedOps * sizeof(DevOp) + T * sizeof(uint32_t) +
+           (size_t)n_rot * adjoint_tile_threads(tile_bits) * sizeof(double);
 }
 
 cudaError_t launch_adjoint_tile(const double *src_pair, double *dst_pair, int n,
                                 const TileGroup &tg, const DevOp *ops, double *partials,
                                 cudaStream_t st) {
-    int threads = (int)((1u << tg.tile_bits) / 4);
-    if (threads > kAdjThreads) threads = kAdjThreads;
-    if (threads < 32) threads = 32;
-    k_adjoint_tile<<<adjoint_stream_blocks(n), threads, adjoint_tile_smem(tg.tile_bits), st>>>(
+    static SmemLimit lim;
+    const size_t smem = adjoint_tile_smem(tg.tile_bits, group_rotations(tg));
+    cudaError_t e = raise_smem_limit(k_adjoint_tile, smem, lim);
+    if (e != cudaSuccess) return e;
+    k_adjoint_tile<<<adjoint_stream_blocks(n), adjoint_tile_threads(tg.tile_bits), smem, st>>>(
         src_pair, dst_pair, n, tg, ops, partials);
     return cudaGetLastError();
 }

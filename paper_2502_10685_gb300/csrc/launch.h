@@ -241,7 +241,7 @@ cudaError_t launch_adjoint_wire(double *lam, double *rho, int n, const DevPass &
 // launch_adjoint_wire.
 constexpr int kAdjTileMaxN = 8;
 constexpr int kAdjTileBits = 9;
-size_t adjoint_tile_smem(int tile_bits);
+size_t adjoint_tile_smem(int tile_bits, int n_rot);   // n_rot: rotations of the group
 cudaError_t launch_adjoint_tile(const double *src_pair, double *dst_pair, int n,
                                 const TileGroup &tg, const DevOp *ops, double *partials,
                                 cudaStream_t st);
