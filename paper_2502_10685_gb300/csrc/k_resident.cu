@@ -315,9 +315,10 @@ __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double
                     ++n_rot;
                 }
             }
-            if (n_rot > 0) {
+            // only the pass's rotations are reduced (n_rot is uniform over the CTA)
 #pragma unroll
-                for (int s = 0; s < R; ++s) {
+            for (int s = 0; s < R; ++s) {
+                if (s < n_rot) {
                     double v = part[s];
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                     if (lane == 0) red[warp * R + s] = v;
