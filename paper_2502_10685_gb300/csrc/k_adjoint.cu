@@ -124,11 +124,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_wire(double *lam, doubl
     }
     if (n_rot == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // only the pass's rotations are reduced (n_rot is uniform over the grid)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        double v = part[r];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp * R + r] = v;
+        if (r < n_rot) {
+            double v = part[r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp * R + r] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x < n_rot) {
