@@ -199,19 +199,25 @@ int stab_grad(stab_ctx *ctx, const stab_term *O, int64_t n_terms, double *expect
  * STAB_KERNEL_STREAMED.
  *  n, gates (m records), thetas (n_params), O (n_terms terms): host memory,
  *    meaning as in stab_load_circuit and stab_expect; out: host double.
- *  stream: cudaStream_t to queue on (NULL = the legacy default stream); the
- *    call waits for its own work before returning.
+ *  stream: cudaStream_t to queue on (NULL = the legacy default stream of
+ *    the current device); it must belong to the current device
+ *    (STAB_E_INVAL otherwise).  The call waits for its own work before
+ *    returning.
  * Everything the call needs on the device -- the planned passes, the angles,
  * the terms and two working vectors of 4^n doubles -- lives in one 16 MiB
  * workspace that the library holds as a static device array on every GPU
  * that loads it, until the process exits.  A problem that does not fit
  * (roughly n <= 9 for short circuits; fewer qubits for very long ones)
  * returns STAB_E_RANGE.  The first call on a device looks up the workspace's
- * device address with that device current; make that first call before any
- * stream capture.  All calls share the workspace: calls whose work overlaps
- * on the GPU (other threads, other streams) race and give wrong results, so
- * serialize them.  Errors: as stab_load_circuit and stab_expect, STAB_E_RANGE
- * (too large), STAB_E_CUDA. */
+ * device address with that device current and keeps it for the life of the
+ * process, so the call is not supported after cudaDeviceReset() of a device
+ * it has run on.  Every call copies from host memory and synchronizes its
+ * stream, so it must not be called while its stream (or, in global capture
+ * mode, any stream) is being captured.  All calls share the workspace: calls
+ * whose work overlaps on the GPU (other threads, other streams) race and give
+ * wrong results, so serialize them.  Errors: as stab_load_circuit and
+ * stab_expect, STAB_E_RANGE (too large), STAB_E_INVAL (stream of another
+ * device), STAB_E_CUDA. */
 int stab_expect_static(int n, const stab_gate *gates, int64_t m, const double *thetas,
                        int64_t n_params, const stab_term *O, int64_t n_terms, double *out,
                        void *stream);
@@ -275,13 +281,34 @@ int stab_batch_destroy(stab_batch *b);
 /* ---------------------------------------------------------------- serving */
 /* A request server with continuous batching: requests (an expectation value
  * or an adjoint gradient of one circuit) are queued as they arrive and
- * admitted, first come first served, whenever a slot and enough HBM budget
- * are free; each admitted request runs on its own pooled context and
- * streams, so the work of all admitted requests overlaps on the device, and
- * requests join and leave while others are running.  Contexts keep their
- * device vectors between requests.  The paper has no counterpart (it
- * evaluates one circuit per call). */
+ * admitted whenever a slot and enough HBM budget are free; requests join
+ * while others are running and leave as soon as they finish.  The paper has
+ * no counterpart (it evaluates one circuit per call).  Two engines run the
+ * admitted requests:
+ *  - STAB_SERVE_ITERATE (default): requests of n <= 8 are advanced together
+ *    by one persistent kernel launch per iteration; each launch moves every
+ *    admitted request a slice of its instruction streams further (the same
+ *    amount of work per request: iter_chunks chunks of 4 KiB at n = 4, a
+ *    quarter of that per extra qubit, at least one), its vectors staying in
+ *    its own device memory between launches.  New requests join at the next
+ *    launch.  Larger requests run as in STAB_SERVE_CONTEXTS, beside them.
+ *  - STAB_SERVE_CONTEXTS: each admitted request runs on its own pooled
+ *    context and streams, so the kernels of all admitted requests overlap on
+ *    the device; contexts keep their device vectors between requests.
+ * Within an engine a result does not depend on the other requests or on
+ * when the request was admitted (its passes run in the same order on the
+ * same data whatever the slicing); the two engines use different kernels and
+ * agree to rounding. */
 typedef struct stab_server stab_server;
+
+/* Admission order.  FIFO: the oldest queued request.  SHORTEST: the queued
+ * request with the least estimated work (gates x 4^n, three times that for a
+ * gradient), oldest first among equals -- unless the oldest queued request
+ * has waited longer than aging_s, which is then admitted first, so a large
+ * request waits at most about aging_s plus the time for budget to free up. */
+enum stab_serve_policy { STAB_SERVE_FIFO = 0, STAB_SERVE_SHORTEST = 1 };
+
+enum stab_serve_engine { STAB_SERVE_ITERATE = 0, STAB_SERVE_CONTEXTS = 1 };
 
 typedef struct stab_server_opts {
     int32_t device;        /* CUDA device ordinal, -1 = current */
@@ -289,13 +316,18 @@ typedef struct stab_server_opts {
     int64_t hbm_budget;    /* bytes of request state admitted at once (0 = 32 GiB) */
     int32_t planners;      /* host threads that plan and launch requests (0 = 4) */
     int32_t policy;        /* stab_serve_policy: which queued request is admitted next */
+    int32_t engine;        /* stab_serve_engine */
+    int32_t iter_chunks;   /* ITERATE: chunks per slice at n = 4 (0 = 64) */
+    int32_t iter_smem_kb;  /* ITERATE: KiB of shared memory per CTA for vectors (0 = 64, <= 200);
+                              a request whose working vectors fit runs in shared memory,
+                              others in their own device memory */
+    int32_t reserved;
+    double aging_s;        /* SHORTEST: aging bound in seconds (0 = 4 s, < 0 = none) */
+    stab_alloc_fn alloc;   /* device memory of the server, its contexts and requests; NULL:
+                              cudaMallocAsync / cudaFreeAsync (both NULL or both set) */
+    stab_free_fn free;
+    void *alloc_user;
 } stab_server_opts;
-
-/* Admission order.  FIFO: the oldest queued request.  SHORTEST: the queued
- * request with the least estimated work (gates x 4^n, three times that for a
- * gradient), oldest first among equals; small requests then wait less, large
- * ones may wait until the queue drains. */
-enum stab_serve_policy { STAB_SERVE_FIFO = 0, STAB_SERVE_SHORTEST = 1 };
 
 enum stab_request_kind { STAB_REQ_EXPECT = 0, STAB_REQ_GRAD = 1 };
 
@@ -319,11 +351,14 @@ typedef struct stab_result {
     double done_s;           /* results on the host */
 } stab_result;
 
-/* Admission footprint of a request: max(n 4^n 8, 4^n 8 x (4 for <O>, 8 for a
- * gradient: the vectors of the split sweeps)) bytes plus 64 bytes per gate,
+/* Admission footprint of a request: max(n 4^n 8, 4^n 8 x (4 for <O>, 12 for
+ * a gradient: the vectors of the split sweeps)) bytes plus 96 bytes per gate,
  * plus the streamed adjoint's per-CTA partial sums above n = 6. */
 int64_t stab_request_footprint(const stab_request *req);
 
+/* opts may be NULL (all defaults).  Errors: STAB_E_INVAL (unknown policy or
+ * engine, iter_chunks < 0, iter_smem_kb outside [0, 200], only one of alloc /
+ * free set), STAB_E_CUDA. */
 int stab_server_create(const stab_server_opts *opts, stab_server **out);
 
 /* Queues a copy of *req; *id identifies it.  Invalid requests are accepted
@@ -479,6 +514,21 @@ int stab_selftest_bounded_wait(int64_t polls);
  * order as the one-piece streams; STAB_E_STATE when any of this fails.
  * Errors: STAB_E_INVAL / STAB_E_RANGE (gates as for stab_load_circuit, mode). */
 int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, int mode);
+
+/* ---------------------------------------------------------------- FP64 peak */
+/* Measures the FP64 rate of the current device, the roofline of the rotation
+ * passes (three FMAs per rotated pair on data that stays on chip, so the FP64
+ * pipe, not HBM, bounds them; Sec. II-A's per-gate work).  kind 0: every
+ * thread of a full-occupancy grid runs eight independent DFMA chains; kind 1:
+ * every warp runs four independent chains of the 8x8x4 FP64 matrix
+ * instruction.  iters: chain steps per thread (1 .. 2^30; about 8192 gives a
+ * launch of a few tens of milliseconds on a GB300).  One untimed warm-up
+ * launch, then one launch timed with CUDA events on a stream the call creates.
+ * *tflops receives the achieved TFLOP/s (2 flops per FMA), *ms (may be NULL)
+ * the timed launch's duration.  Allocates 2 KiB of device memory for the
+ * duration of the call.  Errors: STAB_E_INVAL (kind, tflops NULL),
+ * STAB_E_RANGE (iters), STAB_E_CUDA. */
+int stab_probe_fp64(int kind, int64_t iters, double *tflops, double *ms);
 
 #ifdef __cplusplus
 }

@@ -57,7 +57,10 @@ class StabBatchItem(ctypes.Structure):
 class StabServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("planners", ctypes.c_int32),
-                ("policy", ctypes.c_int32)]
+                ("policy", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("iter_chunks", ctypes.c_int32), ("iter_smem_kb", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("aging_s", ctypes.c_double),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 
 class StabRequest(ctypes.Structure):
@@ -149,6 +152,7 @@ def load(build_if_missing: bool = True):
             "stab_sparse_generator": (i32, [vp, i32, i64, vp, ctypes.POINTER(i64),
                                             ctypes.POINTER(StabSparseInfo)]),
             "stab_sparse_order_history": (i32, [vp, vp, i64, ctypes.POINTER(i64)]),
+            "stab_probe_fp64": (i32, [i32, i64, dp, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

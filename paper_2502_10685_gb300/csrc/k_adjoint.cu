@@ -230,8 +230,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_tile(const double *src,
             const int n_rot = s_nrot[j];
             double *my_acc = acc + (size_t)s_rbase[j] * nt + threadIdx.x;
             // one group per thread (the launch has T / 4 threads): each
-            // rotation's dot is reduced over the warp right away, so no
-            // per-slot accumulator array is carried through the op loop
+            // rotation's dot is added to this thread's own shared-memory
+            // accumulator (my_acc); every rotation is summed over the threads
+            // once, in a fixed order, at the end of the launch
             const uint32_t g = threadIdx.x;
             const bool live = g < T / 4;
             uint32_t b = ((g >> lo) << (lo + 1)) | (g & ((1u << lo) - 1u));

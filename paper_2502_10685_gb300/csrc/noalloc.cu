@@ -36,7 +36,10 @@ std::mutex g_ws_mu;
 void *g_ws_addr[64] = {};
 
 // Device address of the workspace on the current device, looked up once per
-// device (with that device current) by the first call on it.
+// device (with that device current) by the first call on it.  The address
+// is cached for the life of the process: a cudaDeviceReset() recreates the
+// device's context and leaves the cached address stale, so this entry point
+// is not supported after a reset of a device it has already run on.
 int workspace_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -96,10 +99,22 @@ extern "C" int stab_expect_static(int n, const stab_gate *gates, int64_t m, cons
     const size_t total = b_ops + b_maps + b_midx + b_raw + b_th + b_terms + b_res + 2 * vec;
     if (total > kStaticBytes) return STAB_E_RANGE;   // does not fit the 16 MiB workspace
 
+    cudaStream_t s = (cudaStream_t)stream;
+    // the workspace is the current device's; a stream of another device
+    // would run these kernels against a pointer it cannot use
+    if (s != nullptr) {
+        int cur_dev = 0, st_dev = 0;
+        cudaError_t de = cudaGetDevice(&cur_dev);
+        if (de == cudaSuccess) de = cudaStreamGetDevice(s, &st_dev);
+        if (de != cudaSuccess) {
+            record_cuda_error(de);
+            return STAB_E_CUDA;
+        }
+        if (st_dev != cur_dev) return STAB_E_INVAL;
+    }
     void *ws = nullptr;
     rc = workspace_address(&ws);
     if (rc != STAB_OK) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
     char *base = (char *)ws;
     size_t off = 0;
     auto carve = [&](size_t bytes) {

@@ -186,6 +186,16 @@ def stab_launch_count(h) -> int:
 
 # ---------------------------------------------------------------- class
 
+def stab_probe_fp64(kind: str = "dfma", iters: int = 8192) -> Tuple[float, float]:
+    """FP64 rate of the current device: (TFLOP/s, ms of the timed launch);
+    kind "dfma" (independent DFMA chains) or "dmma" (8x8x4 FP64 matrix
+    instruction chains)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    check(_lib.load().stab_probe_fp64({"dfma": 0, "dmma": 1}[kind], int(iters),
+                                      ctypes.byref(tf), ctypes.byref(ms)), "stab_probe_fp64")
+    return tf.value, ms.value
+
+
 class Stab:
     """One context: n qubits, a loaded circuit, its generators and observables.
 
@@ -509,15 +519,42 @@ class Server:
     """
 
     POLICIES = {"fifo": 0, "shortest": 1}
+    ENGINES = {"iterate": 0, "contexts": 1}
 
     def __init__(self, device: int = 0, max_active: int = 0, hbm_budget: int = 0,
-                 planners: int = 0, policy: str = "fifo"):
+                 planners: int = 0, policy: str = "fifo", engine: str = "iterate",
+                 iter_chunks: int = 0, iter_smem_kb: int = 0, aging_s: float = 0.0,
+                 torch_memory: bool = True):
         o = StabServerOpts()
         o.device = device
         o.max_active = max_active
         o.hbm_budget = hbm_budget
         o.planners = planners
         o.policy = self.POLICIES[policy]
+        o.engine = self.ENGINES[engine]
+        o.iter_chunks = iter_chunks
+        o.iter_smem_kb = iter_smem_kb
+        o.aging_s = aging_s
+        self._keep = []
+        if torch_memory:
+            # device memory of the server's requests and contexts from
+            # PyTorch's caching allocator; the library hands a block back only
+            # after the work that used it has completed
+            import torch
+
+            def _alloc(nbytes, st, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), device))
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, st, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            a, f = _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
+            self._keep += [a, f]
+            o.alloc = a
+            o.free = f
         h = ctypes.c_void_p()
         check(_lib.load().stab_server_create(ctypes.byref(o), ctypes.byref(h)),
               "stab_server_create")

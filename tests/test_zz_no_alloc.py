@@ -6,16 +6,17 @@ framework whose allocator owns the device.  stab_expect_static runs the
 streamed expectation path on a fixed workspace the library declares as a
 static device array.  This test calls it through the C interface twice in a
 row, on two different circuits, and checks each value against stab_expect
-(streamed kernels) within the tolerance of the other parity tests; a second
-call that agreed only because it reused the first call's leftovers would
-fail here.  It also checks that a problem too large for the workspace is
-refused with STAB_E_RANGE.
+(streamed kernels) and against the CPU oracle within the tolerance of the
+other parity tests; a second call that agreed only because it reused the
+first call's leftovers would fail here.  It also checks that a problem too
+large for the workspace is refused with STAB_E_RANGE.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2502_10685_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -50,7 +51,9 @@ def test_static_expect_matches_stab_expect_on_two_calls_in_a_row():
         s.load_circuit(c.gates, c.thetas)
         ref = s.expect(obs)
         s.close()
-        assert abs(val - ref) <= 1e-12 * sum(abs(a) for a, _ in obs)
+        tol = 1e-12 * sum(abs(a) for a, _ in obs)
+        assert abs(val - ref) <= tol
+        assert abs(val - oracle.expect(c.n, c.gates, c.thetas, obs)) <= tol
 
 
 def test_static_expect_refuses_problems_beyond_the_workspace():
