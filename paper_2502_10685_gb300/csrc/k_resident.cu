@@ -233,117 +233,6 @@ __global__ void __launch_bounds__(kColThreads, 1) k_transfer_cols(const Rec *str
 
 // ---------------------------------------------------------------- adjoint
 
-__device__ __forceinline__ double pair_dot(int axis, double lx, double ly, double lz, double rx,
-                                           double ry, double rz) {
-    // d<O>/d theta on the pair (u, v): l_v r_u - l_u r_v; (u, v) = (Y, Z) for
-    // R_x, (Z, X) for R_y, (X, Y) for R_z
-    if (axis == AX_X) return fma(lz, ry, -ly * rz);
-    if (axis == AX_Y) return fma(lx, rz, -lz * rx);
-    return fma(ly, rx, -lx * ry);
-}
-
-// The pair (lambda, rho) through chunks [c0, c1) of a gradient stream, with
-// each rotation's dot <lambda_j, G_j rho_j> taken at its post-gate pair (G_j
-// the generator of the rotation on its pairs) and written to grad_rot at the
-// rotation's ordinal.  fwd = false: a backward stream -- the pair holds the
-// post-gate values when an inverse op comes up, so dot, then apply; fwd =
-// true: a forward stream (lambda_j = M_j lambda_{j-1} because every map is
-// orthogonal) -- apply, then dot.  On return lam / rho point at the results;
-// false when a staging wait gave up.
-template <int N>
-__device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double *&lam,
-                                              double *&lam_n, double *&rho, double *&rho_n,
-                                              double *grad_rot, int32_t *status,
-                                              unsigned char *smem, const bool fwd) {
-    using C = SCfg<N, 1>;
-    int *gslot = reinterpret_cast<int *>(smem + kOffSlot);
-    double *red = reinterpret_cast<double *>(smem + kOffRed);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int c = c0; c < c1; ++c) {
-        if (!st.wait(c, status)) return false;
-        const Rec *Rr = st.chunk(c);
-        int r = 0;
-        while (true) {
-            const Rec h = Rr[r];
-            if (h.kind != R_PASS) break;
-            const Rec *pulls = Rr + r + 1;
-            const Rec *ops = pulls + h.param;
-            const int n_pull = h.param, n_ops = h.gate, q = h.q;
-            double part[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) part[k] = 0.0;
-#pragma unroll
-            for (int k = 0; k < C::GPT; ++k) {
-                const uint32_t g = threadIdx.x + k * C::T;
-                if (g < (uint32_t)C::G) {
-                    uint32_t ii, ix, iy, iz;
-                    group_idx<N>(g, q, ii, ix, iy, iz);
-                    const double li = pulled<N>(lam, ii, pulls, n_pull);
-                    const double ri = pulled<N>(rho, ii, pulls, n_pull);
-                    double lx = pulled<N>(lam, ix, pulls, n_pull);
-                    double ly = pulled<N>(lam, iy, pulls, n_pull);
-                    double lz = pulled<N>(lam, iz, pulls, n_pull);
-                    double rx = pulled<N>(rho, ix, pulls, n_pull);
-                    double ry = pulled<N>(rho, iy, pulls, n_pull);
-                    double rz = pulled<N>(rho, iz, pulls, n_pull);
-                    int slot = 0;
-                    for (int j = 0; j < n_ops; ++j) {
-                        if (fwd) {
-                            apply_recs(lx, ly, lz, ops + j, 1);
-                            apply_recs(rx, ry, rz, ops + j, 1);
-                        }
-                        if (ops[j].kind == R_ROT) {
-                            const double d = pair_dot(ops[j].axis, lx, ly, lz, rx, ry, rz);
-#pragma unroll
-                            for (int s = 0; s < R; ++s)
-                                if (s == slot) part[s] += d;
-                            ++slot;
-                        }
-                        if (!fwd) {
-                            apply_recs(lx, ly, lz, ops + j, 1);
-                            apply_recs(rx, ry, rz, ops + j, 1);
-                        }
-                    }
-                    lam_n[ii] = li; lam_n[ix] = lx; lam_n[iy] = ly; lam_n[iz] = lz;
-                    rho_n[ii] = ri; rho_n[ix] = rx; rho_n[iy] = ry; rho_n[iz] = rz;
-                }
-            }
-            int n_rot = 0;
-            for (int j = 0; j < n_ops; ++j) {
-                if (ops[j].kind == R_ROT) {
-                    if (threadIdx.x == 0) gslot[n_rot] = ops[j].gate;
-                    ++n_rot;
-                }
-            }
-            // only the pass's rotations are reduced (n_rot is uniform over the CTA)
-#pragma unroll
-            for (int s = 0; s < R; ++s) {
-                if (s < n_rot) {
-                    double v = part[s];
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                    if (lane == 0) red[warp * R + s] = v;
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x < n_rot) {
-                double total = 0.0;
-                for (int w = 0; w < C::W; ++w) total += red[w * R + threadIdx.x];
-                grad_rot[gslot[threadIdx.x]] = total;
-            }
-            double *t = lam;
-            lam = lam_n;
-            lam_n = t;
-            t = rho;
-            rho = rho_n;
-            rho_n = t;
-            __syncthreads();
-            r += 1 + n_pull + n_ops;
-        }
-        st.release(c);
-    }
-    return true;
-}
-
 template <int N>
 __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamArgs a) {
     using C = SCfg<N, 1>;

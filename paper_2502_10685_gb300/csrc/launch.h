@@ -106,6 +106,55 @@ struct BatchArgs {
                                // others in the slab (0: kMaxResidentQubits)
 };
 
+// One slice of one unit of the serving iteration kernel (k_serve): a vector
+// (or an adjoint pair) of one admitted request carried through a contiguous
+// range of chunks of one of its instruction streams.  The request's state
+// vectors live in its own device memory between launches; a slice starts
+// from them (or from its initial value) and writes them back.
+enum ServeKind : int8_t {
+    SV_VEC = 0,        // one vector through a stream (forward or backward)
+    SV_PAIR_BWD = 1,   // (lambda, rho) through a backward gradient stream, dots then ops
+    SV_PAIR_FWD = 2,   // (lambda, rho) through a forward gradient stream, ops then dots
+};
+
+struct ServeUnit {             // 80 bytes
+    const Rec *stream;         // first chunk of the slice
+    int32_t n_chunks;          // chunks of the slice
+    int8_t n;                  // qubits (1 .. kServeMaxQubits)
+    int8_t kind;               // ServeKind
+    int8_t init;               // INIT_RHO0 / INIT_TERMS (first slice of a vector), INIT_LOAD
+    int8_t flags;              // SF_LAST | SF_ROWS
+    const DevTerm *terms;      // INIT_TERMS
+    int32_t n_terms;
+    int32_t pad;
+    const double *src;         // INIT_LOAD: the vector (SV_VEC) or lambda (pairs)
+    const double *src2;        // INIT_LOAD, pairs: rho
+    double *state;             // persistent state: SV_VEC [v | spare] (2 x 4^n doubles),
+                               // pairs [lambda | rho | spare | spare] (4 x 4^n)
+    double *grad_rot;          // pairs: the dots, by rotation ordinal
+    double *xfree_out;         // SF_LAST: x-free sum of the vector (SV_VEC) or of lambda
+    int64_t reserved;
+};
+static_assert(sizeof(ServeUnit) == 80, "ServeUnit layout");
+
+constexpr int kServeMaxQubits = 8;
+constexpr int SF_LAST = 1;     // the slice ends the unit's stream
+constexpr int SF_ROWS = 2;     // SV_VEC at n <= 4: every wire pass one 3x3 map (lane quads)
+
+struct ServeArgs {
+    const ServeUnit *units;
+    int32_t n_units;
+    int32_t *counter;          // next unit to take (zeroed before the launch)
+    int32_t *status;
+    int32_t smem_buf;          // bytes of shared memory for state buffers: a unit whose
+                               // buffers (2 or 4 x 4^n doubles) fit runs in shared memory
+};
+
+int serve_threads();
+size_t serve_smem_bytes(int smem_buf);
+cudaError_t serve_occupancy(size_t smem, int *ctas_per_sm);
+cudaError_t launch_serve(const ServeArgs &a, int grid, size_t smem, cudaStream_t s);
+
 size_t batch_smem_bytes(int max_n_in_smem);
 int batch_threads();
 cudaError_t batch_occupancy(size_t smem, int *ctas_per_sm);

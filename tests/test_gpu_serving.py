@@ -1,6 +1,9 @@
-"""Continuous-batching server: every result is the same served in a mix as
+"""Continuous-batching server, both engines (the iteration engine that
+advances every admitted request by a slice per persistent launch, and the
+per-request context engine): every result is the same served in a mix as
 computed alone, and matches the oracle; requests join while others run; a
-request that can never fit and a malformed request fail alone."""
+request that can never fit and a malformed request fail alone; the aging
+bound of shortest-work-first admission."""
 import time
 
 import numpy as np
@@ -48,9 +51,13 @@ def alone(stab, c, kind, obs):
     return r
 
 
-def test_served_results_equal_alone_and_oracle(stab):
+ENGINES = ["iterate", "contexts"]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_served_results_equal_alone_and_oracle(stab, engine):
     reqs = request_mix(3, 40)
-    srv = stab.Server(max_active=8)
+    srv = stab.Server(max_active=8, engine=engine)
     ids = []
     for k, (c, kind, obs) in enumerate(reqs):
         ids.append(srv.submit(c, kind, obs))
@@ -69,12 +76,13 @@ def test_served_results_equal_alone_and_oracle(stab):
         assert r["submit_s"] <= r["admit_s"] <= r["done_s"]
 
 
-def test_requests_join_while_others_run(stab):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_requests_join_while_others_run(stab, engine):
     # a small budget forces queueing: later requests wait for earlier ones to
     # release budget, then are admitted while others are still running
     reqs = request_mix(4, 24)
     fps = [stab.Server.footprint(c, k, o) for c, k, o in reqs]
-    srv = stab.Server(max_active=4, hbm_budget=max(fps) * 3)
+    srv = stab.Server(max_active=4, hbm_budget=max(fps) * 3, engine=engine)
     ids = [srv.submit(c, k, o) for c, k, o in reqs]
     res = [srv.wait(i, timeout_s=300) for i in ids]
     st = srv.stats()
@@ -91,11 +99,13 @@ def test_requests_join_while_others_run(stab):
     assert overlap
 
 
-def test_oversized_and_malformed_requests_fail_alone(stab):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_oversized_and_malformed_requests_fail_alone(stab, engine):
     good = W.layered_ansatz(4, 100, seed=1)
     big = W.layered_ansatz(10, 50, seed=2)
     bad = W.Circuit(3, W.gates_from_list([("CX", 1, 1)]), np.zeros(0))
-    srv = stab.Server(hbm_budget=stab.Server.footprint(big, "expect", W.obs_chain(10)) - 1)
+    srv = stab.Server(hbm_budget=stab.Server.footprint(big, "expect", W.obs_chain(10)) - 1,
+                      engine=engine)
     i_big = srv.submit(big, "expect", W.obs_chain(10))
     i_bad = srv.submit(bad, "expect", W.obs_chain(3))
     i_good = srv.submit(good, "grad", W.obs_chain(4))
@@ -108,14 +118,15 @@ def test_oversized_and_malformed_requests_fail_alone(stab):
     assert np.abs(r_good["grads"] - g_ref).max() <= 1e-12 * l1(W.obs_chain(4))
 
 
-def test_serving_trace_c5_sampled(stab):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_serving_trace_c5_sampled(stab, engine):
     """The serving workload's own trace (Poisson 2,000/s, n 4..12, depth
     log-uniform 100..60,000, seed 1005): its first 48 requests through the
     server as the bench submits them; those the oracle checks quickly
     (4^n m small) against the oracle -- <O>, and for gradient requests
     sampled slots by the parameter shift."""
     trace = W.serving_trace(48, seed=1005)
-    srv = stab.Server(max_active=64)
+    srv = stab.Server(max_active=64, engine=engine)
     ids = [srv.submit(r.circuit, r.kind, r.observable) for r in trace]
     res = [srv.wait(i, timeout_s=600) for i in ids]
     srv.close()
@@ -139,15 +150,16 @@ def test_serving_trace_c5_sampled(stab):
     assert checked >= 6
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("policy", ["fifo", "shortest"])
-def test_admission_order(stab, policy):
+def test_admission_order(stab, policy, engine):
     """One slot: while a blocker runs, a large request and six small ones
     queue.  FIFO admits the large one first; shortest-work-first admits the
     small ones first.  Results are the same under either order."""
     blocker = W.layered_ansatz(9, 1500, seed=1)
     large = W.layered_ansatz(8, 3000, seed=2)
     small = [W.layered_ansatz(3, 40 + k, seed=10 + k) for k in range(6)]
-    srv = stab.Server(max_active=1, policy=policy)
+    srv = stab.Server(max_active=1, policy=policy, engine=engine, aging_s=-1.0)
     ib = srv.submit(blocker, "expect", W.obs_chain(9))
     il = srv.submit(large, "expect", W.obs_chain(8))
     isml = [srv.submit(c, "expect", W.obs_chain(3)) for c in small]
@@ -162,3 +174,100 @@ def test_admission_order(stab, policy):
         assert all(r["done_s"] <= rl["admit_s"] for r in rs)
     for c, r in zip(small, rs):
         assert abs(r["expect"] - oracle.expect(3, c.gates, c.thetas, W.obs_chain(3))) <= 1e-12 * l1(W.obs_chain(3))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_served_large_gradient_against_oracle(stab, engine):
+    """An n = 9 gradient request served in a mix of smaller ones: its <O> and
+    sampled slots against the oracle's parameter shift, the others against
+    the oracle's <O>."""
+    big = W.layered_ansatz(9, 300, seed=909)
+    obs = W.obs_chain(9)
+    small = request_mix(5, 8)
+    srv = stab.Server(max_active=8, engine=engine)
+    ids = [srv.submit(c, k, o) for c, k, o in small[:4]]
+    ib = srv.submit(big, "grad", obs)
+    ids += [srv.submit(c, k, o) for c, k, o in small[4:]]
+    rb = srv.wait(ib, timeout_s=300)
+    rest = [srv.wait(i, timeout_s=300) for i in ids]
+    srv.close()
+    assert rb["status"] == 0 and all(r["status"] == 0 for r in rest)
+    tol = 1e-12 * l1(obs)
+    assert abs(rb["expect"] - oracle.expect(9, big.gates, big.thetas, obs)) <= tol
+    rot = [i for i, g in enumerate(big.gates) if int(g["op"]) in W.ROTATIONS]
+    rng = np.random.default_rng(19)
+    for gi in rng.choice(rot, size=3, replace=False):
+        slot = int(big.gates[gi]["param"])
+        want = oracle.psr_grad_gate(9, big.gates, big.thetas, obs, int(gi))
+        assert abs(rb["grads"][slot] - want) <= tol
+    for (c, kind, o), r in zip(small[:4] + small[4:], rest):
+        if 4 ** c.n * c.m <= 3e7:
+            assert abs(r["expect"] - oracle.expect(c.n, c.gates, c.thetas, o)) <= 1e-12 * l1(o)
+
+
+def test_iteration_engine_alone_equals_mix_bit_for_bit(stab):
+    """The iteration engine runs each request's passes in the same order on
+    the same data whatever else shares the launches and however the work is
+    sliced: every result (expectation and every gradient entry) served in a
+    mix of 32 requests of n = 2..8 equals, bit for bit, the same request served
+    alone with another slice size; all match the oracle and the context engine."""
+    rng = np.random.default_rng(77)
+    reqs = []
+    for k in range(32):
+        n = int(rng.integers(2, 9))
+        m = int(rng.integers(30, 700 if n <= 6 else 250))
+        c = W.layered_ansatz(n, m, seed=7700 + k)
+        reqs.append((c, "grad" if k % 2 else "expect", W.obs_chain(n)))
+    srv = stab.Server(max_active=64, engine="iterate", iter_chunks=16)
+    ids = []
+    for k, (c, kind, obs) in enumerate(reqs):
+        ids.append(srv.submit(c, kind, obs))
+        if k % 8 == 7:
+            time.sleep(0.005)
+    mix = [srv.wait(i, timeout_s=300) for i in ids]
+    srv.close()
+    ctx = stab.Server(max_active=64, engine="contexts")
+    cids = [ctx.submit(c, kind, obs) for c, kind, obs in reqs]
+    via_ctx = [ctx.wait(i, timeout_s=300) for i in cids]
+    ctx.close()
+    for (c, kind, obs), r, rc in zip(reqs, mix, via_ctx):
+        assert r["status"] == 0 and rc["status"] == 0
+        one = stab.Server(max_active=1, engine="iterate", iter_chunks=3)
+        a = one.wait(one.submit(c, kind, obs), timeout_s=300)
+        one.close()
+        assert a["status"] == 0
+        assert a["expect"] == r["expect"]
+        tol = 1e-12 * l1(obs)
+        assert abs(r["expect"] - oracle.expect(c.n, c.gates, c.thetas, obs)) <= tol
+        assert abs(r["expect"] - rc["expect"]) <= tol
+        if kind == "grad":
+            np.testing.assert_array_equal(a["grads"], r["grads"])
+            assert np.abs(r["grads"] - rc["grads"]).max() <= tol
+            rot = [i for i, g in enumerate(c.gates) if int(g["op"]) in W.ROTATIONS]
+            if rot and 4 ** c.n * c.m <= 2e7:
+                gi = int(rot[len(rot) // 2])
+                want = oracle.psr_grad_gate(c.n, c.gates, c.thetas, obs, gi)
+                assert abs(r["grads"][int(c.gates[gi]["param"])] - want) <= tol
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_shortest_first_with_aging_admits_the_oldest(stab, engine):
+    """One slot, shortest-work-first with a 1 ms aging bound: while a blocker
+    runs, a large request and six small ones queue; when the slot frees, the
+    large request has waited past the bound and is admitted before the small
+    ones (without the bound it would come last)."""
+    blocker = W.layered_ansatz(9, 1500, seed=1)
+    large = W.layered_ansatz(8, 3000, seed=2)
+    small = [W.layered_ansatz(3, 40 + k, seed=10 + k) for k in range(6)]
+    srv = stab.Server(max_active=1, policy="shortest", engine=engine, aging_s=1e-3)
+    ib = srv.submit(blocker, "expect", W.obs_chain(9))
+    il = srv.submit(large, "expect", W.obs_chain(8))
+    isml = [srv.submit(c, "expect", W.obs_chain(3)) for c in small]
+    rb = srv.wait(ib, timeout_s=300)
+    rl = srv.wait(il, timeout_s=300)
+    rs = [srv.wait(i, timeout_s=300) for i in isml]
+    srv.close()
+    assert rb["status"] == 0 and rl["status"] == 0 and all(r["status"] == 0 for r in rs)
+    assert all(rl["done_s"] <= r["admit_s"] for r in rs)
+    assert abs(rl["expect"] - oracle.expect(8, large.gates, large.thetas, W.obs_chain(8))) <= \
+        1e-12 * l1(W.obs_chain(8))

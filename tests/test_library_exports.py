@@ -59,3 +59,44 @@ def test_chunked_planner_equals_sequential():
             rc = L.stab_selftest_plan(c.n, g.ctypes.data, len(g), c.n_params, mode)
             assert rc == 0, (c.n, len(g), mode, rc)
     assert L.stab_selftest_plan(2, g.ctypes.data, len(g), c.n_params, 7) != 0
+
+
+def test_server_options_rejected_on_the_host():
+    # host-only: malformed server options are refused before any device call
+    import ctypes
+    from paper_2502_10685_gb300 import _lib
+    L = _lib.load()
+    for field, value in (("policy", 7), ("engine", 5), ("iter_chunks", -1),
+                         ("iter_smem_kb", 201)):
+        o = _lib.StabServerOpts()
+        setattr(o, field, value)
+        h = ctypes.c_void_p()
+        assert L.stab_server_create(ctypes.byref(o), ctypes.byref(h)) == -1, field
+        assert not h.value
+    # only one of the two allocator hooks
+    o = _lib.StabServerOpts()
+    keep = _lib.ALLOC_FN(lambda n, s, u: None)
+    o.alloc = keep
+    h = ctypes.c_void_p()
+    assert L.stab_server_create(ctypes.byref(o), ctypes.byref(h)) == -1
+
+
+def test_request_footprint_counts_the_split_sweep_vectors():
+    # host-only: max(n, 12) vectors of 4^n doubles for a gradient (half sweeps
+    # and two (lambda, rho) pairs with spares), max(n, 4) for an expectation,
+    # plus 96 B per gate
+    import ctypes
+    from paper_2502_10685_gb300 import _lib
+    L = _lib.load()
+    r = _lib.StabRequest()
+    r.n, r.m = 3, 1000
+    r.kind = 0
+    assert L.stab_request_footprint(ctypes.byref(r)) == 4 * 8 * 4 ** 3 + 96 * 1000
+    r.n = 8
+    assert L.stab_request_footprint(ctypes.byref(r)) == 8 * 8 * 4 ** 8 + 96 * 1000
+    r.kind = 1
+    assert L.stab_request_footprint(ctypes.byref(r)) >= 12 * 8 * 4 ** 8 + 96 * 1000
+    r.n, r.kind = 12, 0
+    assert L.stab_request_footprint(ctypes.byref(r)) == 12 * 8 * 4 ** 12 + 96 * 1000
+    r.n = 13
+    assert L.stab_request_footprint(ctypes.byref(r)) == 0
