@@ -16,9 +16,16 @@ per step on the context stream, L2 flushed between steps.
 e2e:   the public host-buffer calls (stab_apply_circuit from host arrays,
 stab_expect from host terms, stab_get_generators into host memory), wall
 clock, transfers inside the timed region.
+roofline: the generator launch against the FP64 rate measured on the same GPU
+in the same run (stab_probe_fp64, DFMA chains), the pipe that bounds it.
+sub:   bounded measurements of the other configurations in the same run, each
+with its own clock record: the 4,096-circuit uneven batch against one launch
+per circuit and the plain form, the n = 8 10,000-gate adjoint gradient
+against batched parameter shift and the plain form, and the first requests
+of the Poisson serving trace through both server engines and the plain form.
 
 --impl reference times the CPU oracle (the plain FP64 C implementation used by
-the tests) on the same workload on the host cores.
+the tests) on the same workload on all host cores.
 """
 from __future__ import annotations
 
@@ -26,6 +33,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -38,8 +46,6 @@ if ROOT not in sys.path:
 
 METRIC = "Pauli-coefficient updates/s"
 UNIT = "updates/s"
-SMS = 152
-FP64_FLOP_PER_CLK_SM = 4.0    # 2 DFMA per clock per SM (1.25 TFLOP/s nominal at 2.07 GHz)
 
 
 def workload_spec(name):
@@ -128,44 +134,77 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gpu_uuid(dev):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return str(dev.index if hasattr(dev, "index") else dev)
+
+
 # ---------------------------------------------------------------- oracle timing
 
-def oracle_step(c, obs, threads):
-    """One full workload step on the CPU oracle: the n generators and <O>, one
-    thread per vector (ctypes releases the GIL)."""
-    import concurrent.futures as cf
-    import numpy as np
+def host_cpu():
+    """(nproc, CPU model) of the host the oracle runs on."""
+    nproc = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return nproc, model or platform.processor() or platform.machine()
+
+
+def oracle_units(c, obs):
+    """The step's independent oracle jobs: each generator forward, <O> backward."""
     import oracle
-    N = 4 ** c.n
 
     def gen(k):
-        return oracle.forward(c.n, c.gates, c.thetas, oracle.generator(c.n, k))
+        return lambda: oracle.forward(c.n, c.gates, c.thetas, oracle.generator(c.n, k))
 
-    def exp_():
-        return oracle.expect(c.n, c.gates, c.thetas, obs)
-
-    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        futs = [ex.submit(gen, k) for k in range(c.n)] + [ex.submit(exp_)]
-        res = [f.result() for f in futs]
-    return res
+    return [gen(k) for k in range(c.n)] + [lambda: oracle.expect(c.n, c.gates, c.thetas, obs)]
 
 
-def cpu_baseline(c, obs, budget_s=12.0):
+def run_oracle_jobs(jobs, threads):
+    """Runs the jobs on `threads` host threads (ctypes releases the GIL);
+    returns the wall time in seconds."""
+    import concurrent.futures as cf
+    t0 = time.perf_counter()
+    if threads <= 1:
+        for j in jobs:
+            j()
+    else:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            for f in [ex.submit(j) for j in jobs]:
+                f.result()
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(c, obs, runs=5):
+    """The oracle on the host, two modes, median of `runs` each: one core (one
+    full step, its n + 1 vectors one after another) and all cores (nproc
+    steps' worth of independent vectors on nproc threads, the paper's
+    one-vector-per-core scheme)."""
     import oracle
     oracle.build()
-    threads = min(c.n + 1, os.cpu_count() or 1)
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        oracle_step(c, obs, threads)
-        reps += 1
-        if time.perf_counter() - t0 > budget_s or reps >= 50:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": units_per_step(c) * reps / dt, "unit": UNIT, "cores": threads,
-            "kind": "oracle",
-            "sample": "%d full steps of the workload (%d generators + 1 observable) on %d threads"
-                      % (reps, c.n, threads)}
+    nproc, model = host_cpu()
+    units = oracle_units(c, obs)
+    one = [run_oracle_jobs(units, 1) for _ in range(runs)]
+    jobs = units * nproc
+    many = [run_oracle_jobs(jobs, nproc) for _ in range(runs)]
+    v1 = units_per_step(c) / statistics.median(one)
+    vn = units_per_step(c) * nproc / statistics.median(many)
+    return {"value": vn, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": "all cores: %d full steps (%d vectors) on %d threads; one core: one full "
+                      "step; median of %d runs each" % (nproc, len(jobs), nproc, runs),
+            "single_core": {"value": v1, "ms_per_step": statistics.median(one) * 1e3},
+            "all_cores": {"value": vn, "threads": nproc,
+                          "ms_per_step": statistics.median(many) * 1e3 / nproc},
+            "host": {"nproc": nproc, "cpu_model": model}, "runs": runs, "statistic": "median"}
 
 
 def run_reference(args):
@@ -175,14 +214,12 @@ def run_reference(args):
     c, obs = workload_spec(args.workload)
     import oracle
     oracle.build()
-    threads = min(c.n + 1, os.cpu_count() or 1)
-    # each step is one bounded full step of the workload (the oracle is slow)
-    for _ in range(args.warmup):
-        oracle_step(c, obs, threads)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(c, obs, threads)
-    dt = time.perf_counter() - t0
+    nproc, model = host_cpu()
+    units = oracle_units(c, obs)
+    # warm-up steps, then the timed steps: every step's vectors are
+    # independent jobs spread over all host cores
+    run_oracle_jobs(units * args.warmup, nproc)
+    dt = run_oracle_jobs(units * args.steps, nproc)
     value = units_per_step(c) * args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
@@ -190,8 +227,10 @@ def run_reference(args):
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": c.n, "gates": c.m, "vectors_per_step": c.n + 1},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "%d steps of the full workload" % args.steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                         "sample": "%d full steps of the workload, their %d vectors on %d threads"
+                                   % (args.steps, len(units) * args.steps, nproc),
+                         "host": {"nproc": nproc, "cpu_model": model}},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -211,6 +250,20 @@ def combine_ranks(local_ms, units_per_rank, world, dist=None, device=None):
     return total_ms, units_per_rank * world / (total_ms / 1e3)
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def fp64_peak():
+    """FP64 rate of this GPU, measured now: DFMA chains (the pipe the rotation
+    passes use) and FP64 matrix-instruction chains, best of three launches."""
+    from paper_2502_10685_gb300 import stab
+    dfma = max(stab.stab_probe_fp64("dfma", 8192)[0] for _ in range(3))
+    dmma = max(stab.stab_probe_fp64("dmma", 2048)[0] for _ in range(3))
+    return dfma, dmma
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -228,6 +281,9 @@ def run_ours(args):
 
     from paper_2502_10685_gb300 import stab
     c, obs = workload_spec(args.workload)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # the roofline's denominator, measured on this GPU before the timed region
+    peak_dfma, peak_dmma = fp64_peak()
     # all work of this process is queued on one dedicated stream
     torch.cuda.set_stream(torch.cuda.Stream(dev))
     s = stab.Stab(c.n, device=local)
@@ -247,12 +303,7 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        uuid = str(local)
-    clocks = ClockSampler(uuid)
+    clocks = ClockSampler(gpu_uuid(dev))
     clocks.start()
     time.sleep(0.3)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
@@ -305,8 +356,6 @@ def run_ours(args):
     assert abs(val - got) <= 1e-12, (val, got)
 
     # ---- roofline of the dominant kernel (the generator launch)
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    peak = SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     gen_avg_s = statistics.mean(gen_ms) / 1e3
     achieved = algorithmic_flops_generators(c) / gen_avg_s / 1e12
     cut, gen_units, _ = s.split_info()
@@ -321,7 +370,7 @@ def run_ours(args):
         else:
             kernel = "k_batch (split: %d units) + k_apply_transfer" % gen_units
         executed = ((c.n + 1) * cut + (4 ** c.n - 1) * (n_passes - cut)) / (c.n * n_passes)
-        active_sms = min(SMS, c.n + 128 if c.n == 4 else gen_units)
+        active_sms = min(sms, c.n + 128 if c.n == 4 else gen_units)
         note = ("one circuit: the generators split at pass %d of %d; the n first-part "
                 "vectors and the 4^n-1 basis columns run at once (%s); passes are "
                 "sequential within a vector" % (cut, n_passes,
@@ -332,17 +381,19 @@ def run_ours(args):
         executed = 1.0
         active_sms = c.n
         note = "one circuit: n independent vectors, one CTA each; passes are sequential"
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_dfma, "unit": "TFLOP/s",
+                "frac": achieved / peak_dfma,
                 # DRAM bytes of the generator phase's two launches from one ncu
                 # capture of this workload (k_batch 1,803,776 + k_transfer_cols
                 # 1,589,248 B read, the staged half-streams; 0 B written)
                 "traffic": 3393024.0 if (c.n == 4 and c.m == 60200) else None,
                 "kernel": kernel, "launch_ms": gen_avg_s * 1e3,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x sampled SM clock",
+                "peak_source": "of measured: FP64 DFMA chains on this GPU in this run "
+                               "(stab_probe_fp64, best of 3; %d SMs)" % sms,
+                "peak_dmma_tflops": peak_dmma,
                 "active_sms": active_sms,
                 "executed_per_algorithmic": executed,
-                "executed_frac": achieved * executed / peak,
+                "executed_frac": achieved * executed / peak_dfma,
                 "note": note}
 
     # the plain GPU form: one launch per circuit, one pass per gate, no fusion, same step
@@ -357,10 +408,11 @@ def run_ours(args):
             sp.set_params(th_dev)
             sp.run_generators()
             sp.expect_async(out_p)
-        pstep()
+        for _ in range(2):
+            pstep()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
+        e0, e1 = _events()
+        reps = 10
         e0.record(st)
         for _ in range(reps):
             pstep()
@@ -369,7 +421,7 @@ def run_ours(args):
         pms = e0.elapsed_time(e1) / reps
         assert abs(float(out_p[0].item()) - got) <= 1e-10
         plain = {"value": units_per_step(c) / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
-                 "speedup": pms / (total_ms / args.steps),
+                 "speedup": pms / (total_ms / args.steps), "steps": reps,
                  "form": "one launch per circuit, one pass per gate, no fusion (STAB_KERNEL_PLAIN)"}
         sp.close()
 
@@ -391,9 +443,18 @@ def run_ours(args):
                    "reasons": clk.get("reasons"), "samples": clk.get("samples")},
         "expect": got,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(c, obs, budget_s=args.cpu_budget)
     s.close()
+    del flush
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(c, obs)
+    if rank == 0 and world == 1 and not args.no_sub:
+        # the other configurations, bounded, each with its own clock record
+        line["sub"] = {
+            "c3_batch": measure_batch(steps=3, warmup=1, with_cpu=False),
+            "c4_grad": measure_grad(steps=10, warmup=3, psr_slots=64, with_cpu=False),
+            "c5_serve": measure_serve(requests=args.sub_requests),
+        }
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -403,30 +464,18 @@ def run_ours(args):
 
 # ---------------------------------------------------------------- other configurations
 
-def _events():
-    import torch
-    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-
-def run_batch(args):
+def measure_batch(steps, warmup, with_cpu, small=False, world=1, rank=0, local=0, dist=None):
     """Uneven batch: 4,096 circuits (n ~ U{2..8}, depth ~ U[100, 20000]) including
     the 2m parameter-shift copies of a 6-qubit 2,000-gate circuit, one
     persistent launch per step; compared with one fused launch per circuit and
-    the plain form, one pass per gate (both timed on a seeded sample, scaled by
-    updates)."""
+    the plain form, one pass per gate (both timed on a seeded sample of 16
+    circuits, scaled by updates)."""
     import numpy as np
     import torch
-    import torch.distributed as dist
     from paper_2502_10685_gb300 import stab, units, workloads as W
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_stream(torch.cuda.Stream())
     st = torch.cuda.current_stream()
-    if args.workload == "batch-small":
+    if small:
         # a small batch for profiler captures: 96 circuits, n ~ U{6..8}, 300..600 gates
         all_items = W.uneven_batch(96 * world, seed=1013, n_range=(6, 8), depth_range=(300, 600),
                                    psr_base=None)
@@ -442,14 +491,14 @@ def run_batch(args):
     create_s = time.perf_counter() - t0
     upd = sum((it.circuit.n if it.kind == "generators" else 1) * it.circuit.m * 4 ** it.circuit.n
               for it in items)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run()
     torch.cuda.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(gpu_uuid(torch.device("cuda", local)))
     clocks.start()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         e0, e1 = _events()
         e0.record(st)
@@ -458,7 +507,8 @@ def run_batch(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     clk = clocks.stop()
-    ms, _ = combine_ranks(sum(times) / len(times), 0, world, dist if world > 1 else None,
+    del flush
+    ms, _ = combine_ranks(sum(times) / len(times), 0, world, dist,
                           torch.device("cuda", local))
     forms = {}
     rng = np.random.default_rng(0)
@@ -491,28 +541,25 @@ def run_batch(args):
             "extrapolated_ms": est, "batch_speedup": est / ms, "sample_circuits": len(sample)}
     info = b.info()
     # every item's <O> (NaN for generator items) back on rank 0, in item order
-    full = units.gather_to_root(mine, [float(x) for x in b.expectations()], len(all_items),
-                                dist if world > 1 else None)
+    full = units.gather_to_root(mine, [float(x) for x in b.expectations()], len(all_items), dist)
     b.close()
-    if world > 1:
-        dist.destroy_process_group()
-    if rank != 0:
-        return 0
     total_upd = sum(costs)
     line = {
         "metric": "circuits/s", "value": len(all_items) / (ms / 1e3), "unit": "circuits/s",
-        "n_gpus": world, "scaling": "weak", "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": world, "scaling": "weak", "steps": steps, "warmup": warmup,
         "ms_per_step": ms,
         "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "circuits": len(all_items),
+        "config": {"workload": "batch-small" if small else "batch-c3",
+                   "circuits": len(all_items),
                    "circuits_rank0": len(items), "units": info["units"],
                    "grid": info["grid"], "ctas_per_sm": info["ctas_per_sm"],
                    "smem_max_n": info["smem_max_n"],
                    "partition": "longest processing time first on coefficient updates",
                    "l2": "flushed between steps"},
         "updates_per_s": total_upd / (ms / 1e3), "create_s": create_s, "vs_forms": forms,
-        "results_gathered": sum(1 for x in full if x is not None), "clocks": clk}
-    if world == 1 and not args.no_cpu_baseline and len(items) >= 12:
+        "results_gathered": sum(1 for x in full if x is not None) if full else None,
+        "clocks": clk}
+    if world == 1 and with_cpu and len(items) >= 12:
         # the oracle on a seeded sample of small items, scaled by updates
         import oracle
         oracle.build()
@@ -534,14 +581,34 @@ def run_batch(args):
                                 "kind": "oracle",
                                 "sample": "12 seeded items with 4^n m <= 2e7, one core, scaled "
                                           "to the batch by coefficient updates"}
-    print(json.dumps(line))
+    return line
+
+
+def run_batch(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = measure_batch(args.steps, args.warmup, not args.no_cpu_baseline,
+                         small=args.workload == "batch-small", world=world, rank=rank,
+                         local=local, dist=dist if world > 1 else None)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
     return 0
 
 
-def run_grad(args):
+def measure_grad(steps, warmup, psr_slots, with_cpu):
     """n=8, 10,000-gate layered ansatz, O = sum Z_i Z_{i+1} + 0.5 sum X_i: all
-    gradients by one adjoint sweep, vs parameter shift (2 evaluations per
-    slot) in one batched launch, timed on 64 slots and scaled to all."""
+    gradients by one adjoint sweep, against parameter shift (2 evaluations per
+    slot) in one batched launch, timed on psr_slots slots and scaled to all,
+    and against the plain form's parameter shift (each shifted circuit one
+    pass per gate), timed on 2 slots and scaled."""
     import numpy as np
     import torch
     from paper_2502_10685_gb300 import stab, workloads as W
@@ -554,13 +621,13 @@ def run_grad(args):
     s.set_observable(obs)
     g = torch.zeros(c.n_params, dtype=torch.float64, device="cuda")
     e = torch.zeros(8, dtype=torch.float64, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         s.grad_async(e, g)
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = ClockSampler(gpu_uuid(torch.device("cuda", torch.cuda.current_device())))
     clocks.start()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0, e1 = _events()
         e0.record(st)
         s.grad_async(e, g)
@@ -572,7 +639,7 @@ def run_grad(args):
     grads = g.cpu().numpy()
     # parameter shift on a sample of slots, batched
     rng = np.random.default_rng(1)
-    js = rng.choice(c.n_params, size=64, replace=False)
+    js = rng.choice(c.n_params, size=psr_slots, replace=False)
     items = []
     for j in js:
         for sgn in (1.0, -1.0):
@@ -595,15 +662,43 @@ def run_grad(args):
     l1 = sum(abs(a) for a, _ in obs)
     assert err <= 1e-10 * l1, err
     psr_all_ms = psr_ms * c.n_params / len(js)
+    # the plain form's parameter shift: each shifted circuit one pass per gate
+    sp = stab.Stab(8, kernel="plain")
+    sp.load_circuit(c.gates, c.thetas)
+    sp.set_observable(obs)
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    sp.expect_async(out)
+    torch.cuda.synchronize()
+    plain_vals = []
+    e0, e1 = _events()
+    e0.record(st)
+    for j in js[:2]:
+        for sgn in (1.0, -1.0):
+            th = c.thetas.copy()
+            th[j] += sgn * math.pi / 2
+            sp.set_params(th)
+            sp.expect_async(out)
+            plain_vals.append(out[0].clone())
+    e1.record(st)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) * c.n_params / 2
+    pv = [float(v) for v in plain_vals]
+    perr = max(abs((pv[2 * k] - pv[2 * k + 1]) / 2 - grads[js[k]]) for k in range(2))
+    assert perr <= 1e-10 * l1, perr
+    sp.close()
     s.close()
     line = {
         "metric": "gradient time", "value": adj_ms, "unit": "ms", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": adj_ms,
+        "steps": steps, "warmup": warmup, "ms_per_step": adj_ms,
         "higher_is_better": False, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "grad-c4", "n": 8, "gates": c.m, "params": c.n_params},
         "psr_batched_ms_all_params": psr_all_ms, "adjoint_speedup": psr_all_ms / adj_ms,
+        "psr_sample_slots": int(psr_slots),
+        "plain_form_psr_ms_all_params": plain_ms, "adjoint_speedup_vs_plain": plain_ms / adj_ms,
+        "plain_form": "parameter shift, each shifted circuit one launch sequence of one pass "
+                      "per gate (STAB_KERNEL_PLAIN); 2 slots timed, scaled to all",
         "max_abs_diff_vs_psr_sample": err, "clocks": clk}
-    if not args.no_cpu_baseline:
+    if with_cpu:
         # the oracle's parameter shift of one slot (two full propagations),
         # scaled to every slot: the CPU way to these gradients
         import oracle
@@ -616,7 +711,11 @@ def run_grad(args):
                                 "kind": "oracle",
                                 "sample": "parameter shift of one slot (2 propagations of the "
                                           "full circuit), scaled to all %d slots" % c.n_params}
-    print(json.dumps(line))
+    return line
+
+
+def run_grad(args):
+    print(json.dumps(measure_grad(args.steps, args.warmup, 64, not args.no_cpu_baseline)))
     return 0
 
 
@@ -658,65 +757,137 @@ def run_grad_n(args):
     return 0
 
 
+def _percentiles(lat):
+    import numpy as np
+    lat = np.asarray(lat)
+    return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+
+
+def serve_trace(reqs, mine, form, max_active, aging_s, device=0):
+    """Submits reqs[i] for i in mine at their arrival times and waits for all.
+    form: ("iterate" | "contexts", policy) through stab.Server, or "plain":
+    one request at a time in arrival order, each on a context of the plain
+    form (one pass per gate; gradients by the library's streamed adjoint, the
+    plain form having none of its own), results to the host before the next
+    starts.  Returns (per request (latency s, <O>), makespan s, clocks)."""
+    import torch
+    from paper_2502_10685_gb300 import stab
+    clocks = ClockSampler(gpu_uuid(torch.device("cuda", device)))
+    clocks.start()
+    if form == "plain":
+        ctxs = {}
+        t0 = time.perf_counter()
+        out = []
+        for i in mine:
+            r = reqs[i]
+            delay = r.arrival_s - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            c = r.circuit
+            sx = ctxs.get(c.n)
+            if sx is None:
+                sx = ctxs[c.n] = stab.Stab(c.n, kernel="plain", device=device)
+            sx.load_circuit(c.gates, c.thetas)
+            if r.kind == "expect":
+                val = sx.expect(r.observable)
+            else:
+                val, _ = sx.grad(r.observable)
+            out.append((time.perf_counter() - t0 - r.arrival_s, val))
+        span = time.perf_counter() - t0
+        for sx in ctxs.values():
+            sx.close()
+        return out, span, clocks.stop()
+    engine, policy = form
+    srv = stab.Server(max_active=max_active, policy=policy, engine=engine, aging_s=aging_s,
+                      device=device)
+    t0 = time.perf_counter()
+    ids = []
+    for i in mine:
+        r = reqs[i]
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(r.circuit, r.kind, r.observable))
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    clk = clocks.stop()
+    assert all(x["status"] == 0 for x in res)
+    span = (max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)) if res else 0.0
+    return [(x["done_s"] - x["submit_s"], x["expect"]) for x in res], span, clk
+
+
+def serve_summary(reqs, out, span):
+    p50, p99 = _percentiles([x[0] for x in out])
+    upd = sum((1 if r.kind == "expect" else 2) * r.circuit.m * 4 ** r.circuit.n for r in reqs)
+    return {"p50_s": p50, "p99_s": p99, "circuits_per_s": len(reqs) / span, "makespan_s": span,
+            "updates_per_s": upd / span}
+
+
+def measure_serve(requests, max_active=256, aging_s=4.0):
+    """The first `requests` requests of the Poisson serving trace (2,000 req/s,
+    n ~ U{4..12}, depth log-uniform [100, 60,000], 50/50 <O> / gradient, seed
+    1005), through the iteration engine and the context engine (both
+    shortest-work-first with the aging bound) and the plain form, each with
+    its own clock record; latency = completion - arrival."""
+    from paper_2502_10685_gb300 import workloads as W
+    reqs = W.serving_trace(requests, seed=1005)
+    mine = list(range(len(reqs)))
+    forms = {}
+    vals = {}
+    for name, form in (("iterate", ("iterate", "shortest")), ("contexts", ("contexts", "shortest")),
+                       ("plain", "plain")):
+        out, span, clk = serve_trace(reqs, mine, form, max_active, aging_s)
+        forms[name] = dict(serve_summary(reqs, out, span), clocks=clk)
+        vals[name] = [x[1] for x in out]
+    worst = max(abs(a - b) for k in ("contexts", "plain")
+                for a, b in zip(vals["iterate"], vals[k]))
+    it = forms["iterate"]
+    return {
+        "metric": "p50/p99 latency", "value": it["p50_s"], "unit": "s", "p99_s": it["p99_s"],
+        "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve-c5", "requests": len(reqs), "rate_per_s": 2000,
+                   "max_active": max_active, "policy": "shortest estimated work first, aging "
+                   "bound %g s" % aging_s, "engine": "iteration (n <= 8), contexts above"},
+        "circuits_per_s": it["circuits_per_s"], "makespan_s": it["makespan_s"],
+        "forms": forms,
+        "speedup_vs_plain_circuits_per_s": it["circuits_per_s"] / forms["plain"]["circuits_per_s"],
+        "max_abs_diff_between_forms": worst, "clocks": it["clocks"]}
+
+
 def run_serve(args):
-    """Poisson trace (2,000 req/s), n ~ U{4..12}, depth log-uniform [100, 60000],
-    50/50 <O> / gradient requests, submitted at their arrival times to the
-    continuous-batching server; latency = completion - arrival.  The line's
-    value uses shortest-estimated-work-first admission; the same trace in FIFO
-    order is reported beside it.  With several ranks each request is routed,
-    in arrival order, to the rank with the least work assigned so far (the
-    same routing on every rank, no exchange), every rank serves its share on
-    its GPU, and the per-request results are gathered to rank 0 (the trace is
-    fixed: strong scaling)."""
+    """Serving trace: the line of measure_serve on one GPU; with several ranks
+    each request is routed, in arrival order, to the rank with the least work
+    assigned so far (the same routing on every rank, no exchange), every rank
+    serves its share on its GPU through the iteration engine, and the
+    per-request results are gathered to rank 0 (the trace is fixed: strong
+    scaling)."""
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2502_10685_gb300 import stab, units, workloads as W
+    from paper_2502_10685_gb300 import units, workloads as W
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if world == 1:
+        print(json.dumps(measure_serve(args.requests, args.max_active, args.aging)))
+        return 0
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     reqs = W.serving_trace(args.requests, seed=1005)
     # a gradient sweeps about three vectors where <O> sweeps one
     costs = [units.unit_cost(r.circuit.n, r.circuit.m, 1 if r.kind == "expect" else 3)
              for r in reqs]
     route = units.route_in_arrival_order(costs, world)
     mine = [i for i, r in enumerate(route) if r == rank]
-
-    def serve(policy):
-        srv = stab.Server(max_active=args.max_active, policy=policy, device=local)
-        t0 = time.perf_counter()
-        ids = []
-        for i in mine:
-            r = reqs[i]
-            delay = r.arrival_s - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            ids.append(srv.submit(r.circuit, r.kind, r.observable))
-        res = [srv.wait(i) for i in ids]
-        srv.close()
-        assert all(x["status"] == 0 for x in res)
-        span = (max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)) if res else 0.0
-        out = [(x["done_s"] - x["submit_s"], x["expect"]) for x in res]
-        full = units.gather_to_root(mine, out, len(reqs), dist if world > 1 else None)
-        spans = [span] * world
-        if world > 1:
-            dist.all_gather_object(spans, span)
-        return full, max(spans)
-
-    full, span = serve("shortest")
-    full2, span2 = serve("fifo")
-    if world > 1:
-        dist.destroy_process_group()
+    out, span, clk = serve_trace(reqs, mine, ("iterate", "shortest"), args.max_active, args.aging,
+                                 device=local)
+    full = units.gather_to_root(mine, out, len(reqs), dist)
+    spans = [span] * world
+    dist.all_gather_object(spans, span)
+    dist.destroy_process_group()
     if rank != 0:
         return 0
     lat = np.array([x[0] for x in full])
-    lat2 = np.array([x[0] for x in full2])
-    # the same request gives the same numbers under either order
-    worst = max(abs(a[1] - b[1]) for a, b in zip(full, full2))
-    upd = sum((1 if r.kind == "expect" else 2) * r.circuit.m * 4 ** r.circuit.n for r in reqs)
     print(json.dumps({
         "metric": "p50/p99 latency", "value": float(np.percentile(lat, 50)), "unit": "s",
         "p99_s": float(np.percentile(lat, 99)), "n_gpus": world, "higher_is_better": False,
@@ -724,10 +895,7 @@ def run_serve(args):
         "config": {"workload": "serve-c5", "requests": len(reqs), "rate_per_s": 2000,
                    "max_active": args.max_active, "policy": "shortest estimated work first",
                    "routing": "arrival order, least assigned work"},
-        "circuits_per_s": len(reqs) / span, "updates_per_s": upd / span, "makespan_s": span,
-        "fifo": {"p50_s": float(np.percentile(lat2, 50)), "p99_s": float(np.percentile(lat2, 99)),
-                 "makespan_s": span2, "circuits_per_s": len(reqs) / span2},
-        "max_abs_diff_between_orders": worst}))
+        "circuits_per_s": len(reqs) / max(spans), "makespan_s": max(spans), "clocks": clk}))
     return 0
 
 
@@ -738,6 +906,7 @@ def run_expect(args):
     import torch
     from paper_2502_10685_gb300 import stab, workloads as W
     n, m = (int(v) for v in args.workload[len("expect-n"):].split("-"))
+    peak, _ = fp64_peak()
     torch.cuda.set_stream(torch.cuda.Stream())
     st = torch.cuda.current_stream()
     c = W.layered_ansatz(n, m, seed=1000 + n)
@@ -762,14 +931,44 @@ def run_expect(args):
     ms = tot / args.steps
     n_rot = int(sum(1 for g in c.gates if g["op"] in W.ROTATIONS))
     flops = n_rot * 1.5 * 4 ** n
-    peak = SMS * FP64_FLOP_PER_CLK_SM * 2070.0e6 / 1e12
     s.close()
     print(json.dumps({
         "metric": METRIC, "value": m * 4 ** n / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "gates": m, "vectors_per_step": 1},
-        "fp64_tflops": flops / (ms / 1e3) / 1e12, "fp64_frac_of_peak": flops / (ms / 1e3) / 1e12 / peak}))
+        "fp64_tflops": flops / (ms / 1e3) / 1e12, "fp64_frac_of_peak": flops / (ms / 1e3) / 1e12 / peak,
+        "peak_source": "of measured: DFMA chains on this GPU (stab_probe_fp64)"}))
+    return 0
+
+
+def run_fp64_peak(args):
+    """The FP64 rates of this GPU (the roofline denominators of the rotation
+    passes): DFMA and FP64 matrix-instruction chains at two launch lengths,
+    with the clocks seen during the probes."""
+    import torch
+    from paper_2502_10685_gb300 import stab
+    dev = torch.device("cuda", 0)
+    props = torch.cuda.get_device_properties(dev)
+    clocks = ClockSampler(gpu_uuid(dev))
+    clocks.start()
+    time.sleep(0.3)
+    rows = []
+    for kind, iters in (("dfma", 4096), ("dfma", 16384), ("dmma", 1024), ("dmma", 4096)):
+        for _ in range(3):
+            tf, ms = stab.stab_probe_fp64(kind, iters)
+            rows.append({"kind": kind, "iters": iters, "tflops": tf, "ms": ms})
+    clk = clocks.stop()
+    best = {k: max(r["tflops"] for r in rows if r["kind"] == k) for k in ("dfma", "dmma")}
+    mhz = clk.get("sm_mhz") or 2070.0
+    print(json.dumps({
+        "metric": "FP64 TFLOP/s", "value": best["dfma"], "unit": "TFLOP/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fp64-peak", "sms": props.multi_processor_count,
+                   "gpu": props.name},
+        "dmma_tflops": best["dmma"],
+        "dfma_per_clk_per_sm": best["dfma"] * 1e12 / 2 / props.multi_processor_count / (mhz * 1e6),
+        "runs": rows, "clocks": clk}))
     return 0
 
 
@@ -861,7 +1060,6 @@ def run_sparse(args):
     backward as a list (its order reaches ~5e6 terms).  Metric: term-gate
     updates/s (sum over steps of the list length times the gates the step
     applies).  The oracle is timed on the same circuit with fewer rotations."""
-    import numpy as np
     import oracle
     import torch
     from paper_2502_10685_gb300 import stab, workloads as W
@@ -957,10 +1155,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="layered-n4-60200")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default line: skip the batch, gradient and serving sub-measurements")
+    ap.add_argument("--sub-requests", type=int, default=64,
+                    help="default line: serving trace length of the sub-measurement")
     ap.add_argument("--requests", type=int, default=200, help="serve-c5: trace length")
-    ap.add_argument("--max-active", type=int, default=64, help="serve-c5: admitted at once")
+    ap.add_argument("--max-active", type=int, default=256, help="serve-c5: admitted at once")
+    ap.add_argument("--aging", type=float, default=4.0, help="serve-c5: aging bound (s)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -976,6 +1178,8 @@ def main():
         return run_serve(args)
     if args.workload.startswith("expect-n"):
         return run_expect(args)
+    if args.workload == "fp64-peak":
+        return run_fp64_peak(args)
     if args.workload == "paper-sweep":
         return run_paper_sweep(args)
     if args.workload == "sparse-n32":
