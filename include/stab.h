@@ -285,7 +285,7 @@ int stab_batch_destroy(stab_batch *b);
  * while others are running and leave as soon as they finish.  The paper has
  * no counterpart (it evaluates one circuit per call).  Two engines run the
  * admitted requests:
- *  - STAB_SERVE_ITERATE (default): requests of n <= 8 are advanced together
+ *  - STAB_SERVE_ITERATE (default): requests of n <= iter_max_n are advanced together
  *    by one persistent kernel launch per iteration; each launch moves every
  *    admitted request a slice of its instruction streams further (the same
  *    amount of work per request: iter_chunks chunks of 4 KiB at n = 4, a
@@ -318,10 +318,12 @@ typedef struct stab_server_opts {
     int32_t policy;        /* stab_serve_policy: which queued request is admitted next */
     int32_t engine;        /* stab_serve_engine */
     int32_t iter_chunks;   /* ITERATE: chunks per slice at n = 4 (0 = 64) */
-    int32_t iter_smem_kb;  /* ITERATE: KiB of shared memory per CTA for vectors (0 = 64, <= 200);
+    int32_t iter_smem_kb;  /* ITERATE: KiB of shared memory per CTA for vectors (0 = 32, <= 200);
                               a request whose working vectors fit runs in shared memory,
                               others in their own device memory */
-    int32_t reserved;
+    int32_t iter_max_n;    /* ITERATE: largest n the iteration engine takes (0 = 6, 1 .. 8);
+                              larger requests run on contexts (one CTA per vector leaves a
+                              4^7 or 4^8 vector latency-bound) */
     double aging_s;        /* SHORTEST: aging bound in seconds (0 = 4 s, < 0 = none) */
     stab_alloc_fn alloc;   /* device memory of the server, its contexts and requests; NULL:
                               cudaMallocAsync / cudaFreeAsync (both NULL or both set) */
@@ -514,6 +516,72 @@ int stab_selftest_bounded_wait(int64_t polls);
  * order as the one-piece streams; STAB_E_STATE when any of this fails.
  * Errors: STAB_E_INVAL / STAB_E_RANGE (gates as for stab_load_circuit, mode). */
 int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, int mode);
+
+/* ---------------------------------------------------------------- path tuner */
+/* How a context of n qubits with the STAB_KERNEL_AUTO kernel runs, for one GPU
+ * model.  The paper has no counterpart (its CPU pipeline has one form).  The
+ * values are picked by timing the candidates on a probe circuit (a layered
+ * ansatz: R_x, R_y, R_z on every qubit, then a CNOT ring) on the GPU the
+ * first time an AUTO context of that n is created in the process, and kept
+ * in a process-wide cache keyed by the GPU's name and n.  Environment:
+ * STAB_PATH_TUNE=0 leaves the built-in defaults in place of tuning (entries
+ * already in the cache are still used); STAB_PATH_CACHE=<file> loads the cache
+ * from that file before the first lookup and writes it back after each
+ * tuning. */
+typedef struct stab_path_choice {
+    int32_t resident;          /* n <= 6: 1 = each vector resident in shared memory on one CTA,
+                                  0 = vectors streamed through HBM (grid-wide passes) */
+    int32_t resident_adjoint;  /* n <= 6: 1 = gradients by the resident adjoint, 0 = streamed */
+    double gen_cut;            /* n <= 4: where the generators' split sweep cuts the plan, as a
+                                  fraction of its passes (0.3 .. 0.7) */
+    int64_t tile_limit;        /* streamed plans: consecutive wire passes share one tile-fused
+                                  launch while vectors x 4^n <= tile_limit, else one launch
+                                  per pass (>= 0) */
+    int32_t tuned;             /* 1: measured on this GPU model; 0: the built-in defaults */
+    int32_t reserved;
+} stab_path_choice;
+
+/* The built-in defaults for n qubits: resident and resident_adjoint 1,
+ * gen_cut 0.56 at n = 4 (0.5 below), tile_limit 2^17, tuned 0.
+ * Errors: STAB_E_RANGE (n), STAB_E_INVAL (out NULL). */
+int stab_path_defaults(int n, stab_path_choice *out);
+
+/* The cached choice for (gpu_name, n).  Errors: STAB_E_STATE (no entry),
+ * STAB_E_RANGE (n), STAB_E_INVAL (NULL pointer). */
+int stab_path_lookup(const char *gpu_name, int n, stab_path_choice *out);
+
+/* Stores a choice for (gpu_name, n), replacing any entry; later AUTO contexts
+ * of that n on a GPU of that name use it.  gpu_name: at most 255 bytes, no
+ * tab or newline.  Errors: STAB_E_INVAL (a value outside its range, a bad
+ * name), STAB_E_RANGE (n). */
+int stab_path_store(const char *gpu_name, int n, const stab_path_choice *choice);
+
+/* Empties the cache (host only). */
+int stab_path_clear(void);
+
+/* Writes every cached entry to a text file (one line per entry: name, n,
+ * resident, resident_adjoint, gen_cut, tile_limit and tuned, tab-separated),
+ * or reads such a file into the cache; a
+ * file with a malformed line is rejected whole (STAB_E_INVAL) and leaves the
+ * cache as it was.  Errors: STAB_E_INVAL (path NULL, malformed file),
+ * STAB_E_STATE (the file cannot be opened). */
+int stab_path_save(const char *path);
+int stab_path_load(const char *path);
+
+/* Measures the candidates for n qubits on CUDA device `device` now, stores
+ * the result under that GPU's name and writes it to *out (may be NULL).
+ * Candidates: n = 4: gen_cut in {0.50, 0.53, 0.56, 0.59, 0.62} (time of the
+ * generators of a 6,000-gate probe); n = 5, 6: resident against streamed for
+ * <O> and, separately, for the gradient (2,000-gate probe); n = 7 .. 9: tiles
+ * against one launch per pass, for one vector (<O>) and for n vectors (the
+ * generators), giving tile_limit = the largest of those launch sizes where
+ * tiles won (0 when neither); n <= 3 and n >= 10 have nothing measured and
+ * keep the defaults (marked tuned).  Takes tens of milliseconds.
+ * Errors: STAB_E_RANGE (n), STAB_E_CUDA, STAB_E_NOMEM. */
+int stab_path_tune(int device, int n, stab_path_choice *out);
+
+/* The choice a context runs with (the defaults for kernels other than AUTO). */
+int stab_path_current(stab_ctx *ctx, stab_path_choice *out);
 
 /* ---------------------------------------------------------------- FP64 peak */
 /* Measures the FP64 rate of the current device, the roofline of the rotation

@@ -59,7 +59,7 @@ class StabServerOpts(ctypes.Structure):
                 ("hbm_budget", ctypes.c_int64), ("planners", ctypes.c_int32),
                 ("policy", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("iter_chunks", ctypes.c_int32), ("iter_smem_kb", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("aging_s", ctypes.c_double),
+                ("iter_max_n", ctypes.c_int32), ("aging_s", ctypes.c_double),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 
@@ -79,6 +79,12 @@ class StabSparseInfo(ctypes.Structure):
     _fields_ = [("order_final", ctypes.c_int64), ("order_max", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("dense_gates", ctypes.c_int64),
                 ("regrows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class StabPathChoice(ctypes.Structure):
+    _fields_ = [("resident", ctypes.c_int32), ("resident_adjoint", ctypes.c_int32),
+                ("gen_cut", ctypes.c_double), ("tile_limit", ctypes.c_int64),
+                ("tuned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def lib_path() -> str:
@@ -153,6 +159,14 @@ def load(build_if_missing: bool = True):
                                             ctypes.POINTER(StabSparseInfo)]),
             "stab_sparse_order_history": (i32, [vp, vp, i64, ctypes.POINTER(i64)]),
             "stab_probe_fp64": (i32, [i32, i64, dp, dp]),
+            "stab_path_defaults": (i32, [i32, ctypes.POINTER(StabPathChoice)]),
+            "stab_path_lookup": (i32, [ctypes.c_char_p, i32, ctypes.POINTER(StabPathChoice)]),
+            "stab_path_store": (i32, [ctypes.c_char_p, i32, ctypes.POINTER(StabPathChoice)]),
+            "stab_path_clear": (i32, []),
+            "stab_path_save": (i32, [ctypes.c_char_p]),
+            "stab_path_load": (i32, [ctypes.c_char_p]),
+            "stab_path_tune": (i32, [i32, i32, ctypes.POINTER(StabPathChoice)]),
+            "stab_path_current": (i32, [vp, ctypes.POINTER(StabPathChoice)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

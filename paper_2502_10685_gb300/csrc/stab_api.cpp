@@ -15,6 +15,7 @@
 #include "launch.h"
 #include "host_pool.h"
 #include "planner.h"
+#include "tuner.h"
 
 using namespace stab;
 
@@ -127,6 +128,7 @@ struct stab_ctx {
     int device = 0;
     int kernel = STAB_KERNEL_AUTO;
     int fuse = 1;
+    stab_path_choice choice{};         // AUTO: the path tuner's choice for this n and GPU
     cudaStream_t st = nullptr;
     cudaStream_t aux = nullptr;
     cudaStream_t aux2 = nullptr;       // second branch of the split adjoint
@@ -218,13 +220,15 @@ struct stab_ctx {
     }
     size_t vec_bytes() const { return (sizeof(double) << (2 * n)); }
     bool use_resident() const {
-        return (kernel == STAB_KERNEL_AUTO || kernel == STAB_KERNEL_RESIDENT ||
-                kernel == STAB_KERNEL_PLAIN) &&
-               n <= kMaxResidentQubits;
+        const bool k = kernel == STAB_KERNEL_AUTO ? choice.resident != 0
+                                                  : (kernel == STAB_KERNEL_RESIDENT ||
+                                                     kernel == STAB_KERNEL_PLAIN);
+        return k && n <= kMaxResidentQubits;
     }
     bool use_resident_adjoint() const {
-        return (kernel == STAB_KERNEL_AUTO || kernel == STAB_KERNEL_RESIDENT) &&
-               n <= kMaxResidentAdjoint;
+        const bool k = kernel == STAB_KERNEL_AUTO ? choice.resident_adjoint != 0
+                                                  : kernel == STAB_KERNEL_RESIDENT;
+        return k && n <= kMaxResidentAdjoint;
     }
     PlanMode fwd_mode() const {
         const bool rows = use_resident() && resident_lanes_per_group(n) == 4;
@@ -768,9 +772,10 @@ int run_streamed(stab_ctx *c, const DevPlan &P, double **cur, double **alt, int 
     if (k1 < 0) k1 = (int)passes.size();
     const int np = k1 - k0;   // passes [k0, k1), walked backward when inverse
     // tiles pay where a launch is small (launch-bound: few vectors, n <= 8); larger
-    // launches are FP64-bound and run faster one wire per launch
+    // launches are FP64-bound and run faster one wire per launch; the limit is
+    // the path tuner's (measured per GPU model)
     const bool fuse_tiles = P.host.mode != PLAN_PLAIN && P.host.mode != PLAN_PLAIN_ROWS &&
-                            ((uint64_t)n_vec << (2 * c->n)) <= (1ull << 17);
+                            ((uint64_t)n_vec << (2 * c->n)) <= (uint64_t)c->choice.tile_limit;
     std::vector<const DevPass *> group;
     std::vector<int> wires;
     // with tiles, a Clifford gather is folded into the loads of the next group
@@ -1045,7 +1050,9 @@ const char *stab_error_string(int s) {
     }
 }
 
-int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
+namespace {
+
+int create_ctx(int n, const stab_opts *opts, const stab_path_choice *forced, stab_ctx **out) {
     if (!out) return STAB_E_INVAL;
     *out = nullptr;
     if (n < 1 || n > STAB_MAX_QUBITS) return STAB_E_RANGE;
@@ -1055,19 +1062,30 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
     if (o.kernel < STAB_KERNEL_AUTO || o.kernel > STAB_KERNEL_PLAIN) return STAB_E_INVAL;
     if (o.kernel == STAB_KERNEL_RESIDENT && n > kMaxResidentQubits) return STAB_E_RANGE;
     if ((o.alloc == nullptr) != (o.free == nullptr)) return STAB_E_INVAL;
+    int dev = o.device;
+    cudaError_t e = cudaSuccess;
+    if (dev < 0) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        return STAB_E_CUDA;
+    }
+    // the path the context runs: the tuner's choice for AUTO (measured on
+    // first use of this n on this GPU model), the defaults otherwise
+    stab_path_choice choice;
+    stab_path_defaults(n, &choice);
+    if (forced) choice = *forced;
+    else if (o.kernel == STAB_KERNEL_AUTO && o.fuse) RC(resolve_path_choice(dev, n, &o, &choice));
     stab_ctx *c = new (std::nothrow) stab_ctx();
     if (!c) return STAB_E_NOMEM;
     c->n = n;
     c->fwd.host_n = c->grad.host_n = n;
     c->kernel = o.kernel;
     c->fuse = o.fuse;
+    c->choice = choice;
     c->alloc = o.alloc;
     c->free = o.free;
     c->user = o.alloc_user;
-    int dev = o.device;
-    cudaError_t e = cudaSuccess;
-    if (dev < 0) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaSetDevice(dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
         c->device = dev;
@@ -1101,6 +1119,28 @@ int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
         return STAB_E_CUDA;
     }
     *out = c;
+    return STAB_OK;
+}
+
+}  // namespace
+
+}  // extern "C"
+
+int stab::create_with_choice(int n, const stab_opts *opts, const stab_path_choice *choice,
+                             stab_ctx **out) {
+    if (!choice) return STAB_E_INVAL;
+    return create_ctx(n, opts, choice, out);
+}
+
+extern "C" {
+
+int stab_create(int n, const stab_opts *opts, stab_ctx **out) {
+    return create_ctx(n, opts, nullptr, out);
+}
+
+int stab_path_current(stab_ctx *c, stab_path_choice *out) {
+    if (!c || !out) return STAB_E_INVAL;
+    *out = c->choice;
     return STAB_OK;
 }
 
@@ -1155,12 +1195,12 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
     if (c->use_resident()) {
         // split streams for the resident sweeps: generators through the
         // transfer matrix of the second part (n <= 4), expectations meeting in
-        // the middle.  The cut balances the two parts' pass times: at half the
-        // passes for n <= 3 (every unit has an SM to itself); at n = 4, where
-        // k_transfer_cols takes ~780 cycles per pass against ~610 for a
-        // first-part unit alone on its SM, at 0.56 (measured optimum).
+        // the middle.  The cut balances the two parts' pass times; at n = 4,
+        // where k_transfer_cols carries two columns per CTA at a different
+        // pass rate than a first-part unit alone on its SM, the path tuner
+        // times candidate cuts (n <= 3: every unit has an SM to itself, half).
         const bool split = c->kernel == STAB_KERNEL_AUTO && c->fuse;
-        const double cut = transfer_cols_ctas(c->n) > 0 ? 0.56 : 0.5;
+        const double cut = c->choice.gen_cut;
         make_streams(c->fwd, split ? cut : 0.0, false, split ? chain_parts(c) : 2);
     }
     else no_streams(c->fwd);

@@ -16,8 +16,8 @@ from typing import Iterable, Optional, Sequence, Tuple
 import numpy as np
 
 from . import _lib
-from ._lib import (StabBatchItem, StabError, StabGate, StabOpts, StabRequest, StabResult,
-                   StabServerOpts, StabSparseInfo, StabTerm, check)
+from ._lib import (StabBatchItem, StabError, StabGate, StabOpts, StabPathChoice, StabRequest,
+                   StabResult, StabServerOpts, StabSparseInfo, StabTerm, check)
 
 KERNELS = {"auto": 0, "resident": 1, "streamed": 2, "plain": 3}
 GATE_DTYPE = np.dtype([("op", "u1"), ("q0", "u1"), ("q1", "u1"), ("flags", "u1"),
@@ -196,6 +196,33 @@ def stab_probe_fp64(kind: str = "dfma", iters: int = 8192) -> Tuple[float, float
     return tf.value, ms.value
 
 
+def _choice_dict(c: StabPathChoice) -> dict:
+    return {"resident": c.resident, "resident_adjoint": c.resident_adjoint,
+            "gen_cut": c.gen_cut, "tile_limit": c.tile_limit, "tuned": c.tuned}
+
+
+def stab_path_tune(device: int, n: int) -> dict:
+    """Measures the path choices for n qubits on `device` now (and caches them)."""
+    c = StabPathChoice()
+    check(_lib.load().stab_path_tune(device, n, ctypes.byref(c)), "stab_path_tune")
+    return _choice_dict(c)
+
+
+def stab_path_lookup(gpu_name: str, n: int) -> Optional[dict]:
+    c = StabPathChoice()
+    rc = _lib.load().stab_path_lookup(gpu_name.encode(), n, ctypes.byref(c))
+    if rc == -7:
+        return None
+    check(rc, "stab_path_lookup")
+    return _choice_dict(c)
+
+
+def stab_path_store(gpu_name: str, n: int, choice: dict) -> None:
+    c = StabPathChoice(**{k: choice[k] for k in ("resident", "resident_adjoint", "gen_cut",
+                                                  "tile_limit", "tuned")})
+    check(_lib.load().stab_path_store(gpu_name.encode(), n, ctypes.byref(c)), "stab_path_store")
+
+
 class Stab:
     """One context: n qubits, a loaded circuit, its generators and observables.
 
@@ -315,6 +342,12 @@ class Stab:
 
     def launch_count(self) -> int:
         return stab_launch_count(self.h)
+
+    def path_choice(self) -> dict:
+        """The path this context runs with (the tuner's choice for AUTO)."""
+        c = StabPathChoice()
+        check(_lib.load().stab_path_current(self.h, ctypes.byref(c)), "stab_path_current")
+        return _choice_dict(c)
 
 
 # ---------------------------------------------------------------- batches
@@ -523,8 +556,8 @@ class Server:
 
     def __init__(self, device: int = 0, max_active: int = 0, hbm_budget: int = 0,
                  planners: int = 0, policy: str = "fifo", engine: str = "iterate",
-                 iter_chunks: int = 0, iter_smem_kb: int = 0, aging_s: float = 0.0,
-                 torch_memory: bool = True):
+                 iter_chunks: int = 0, iter_smem_kb: int = 0, iter_max_n: int = 0,
+                 aging_s: float = 0.0, torch_memory: bool = True):
         o = StabServerOpts()
         o.device = device
         o.max_active = max_active
@@ -534,6 +567,7 @@ class Server:
         o.engine = self.ENGINES[engine]
         o.iter_chunks = iter_chunks
         o.iter_smem_kb = iter_smem_kb
+        o.iter_max_n = iter_max_n
         o.aging_s = aging_s
         self._keep = []
         if torch_memory:

@@ -1,0 +1,113 @@
+"""Path tuner on the GPU: stab_path_tune measures a valid choice for every
+tuned size, AUTO contexts created afterwards run with the cached choice, and
+every candidate a choice can select gives the oracle's results (generators,
+<O>, gradients) -- so whichever the tuner picks on a given GPU, parity holds."""
+import numpy as np
+import pytest
+
+import layout
+import oracle
+from paper_2502_10685_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2502_10685_gb300 import _lib, stab
+    yield stab
+    # forced entries must not leak into later tests: they re-tune on demand
+    _lib.load().stab_path_clear()
+
+
+def gpu_name():
+    import torch
+    return torch.cuda.get_device_name(0)
+
+
+def l1(obs):
+    return sum(abs(a) for a, _ in obs)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 7, 8, 9, 10])
+def test_tune_gives_a_valid_choice_that_auto_contexts_use(S, n):
+    c = S.stab_path_tune(0, n)
+    assert c["tuned"] == 1
+    assert c["resident"] in (0, 1) and c["resident_adjoint"] in (0, 1)
+    assert 0.3 <= c["gen_cut"] <= 0.7 and c["tile_limit"] >= 0
+    if n == 4:
+        assert c["gen_cut"] in (0.50, 0.53, 0.56, 0.59, 0.62)
+    if n >= 7:
+        E = 4 ** n
+        assert c["tile_limit"] in ((0, E, n * E) if n <= 9 else (1 << 17,))
+    assert S.stab_path_lookup(gpu_name(), n) == c
+    s = S.Stab(n)
+    assert s.path_choice() == c
+    s.close()
+    # other kernels keep the defaults
+    s = S.Stab(n, kernel="streamed")
+    assert s.path_choice()["tuned"] == 0
+    s.close()
+
+
+@pytest.mark.parametrize("cut", [0.50, 0.62])
+def test_generator_cut_candidates_match_oracle(S, cut):
+    n = 4
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": cut,
+                                      "tile_limit": 1 << 17, "tuned": 1})
+    c = W.layered_ansatz(n, 3000, seed=4401)
+    s = S.Stab(n)
+    assert s.path_choice()["gen_cut"] == cut
+    s.apply_circuit(c.gates, c.thetas)
+    cut_pass, _, _ = s.split_info()
+    n_pass = s.plan_info()[1]
+    assert cut_pass == int(n_pass * cut)
+    got = layout.lib_to_paper(n, s.generators())
+    s.close()
+    assert np.abs(got - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n", [5, 6])
+@pytest.mark.parametrize("resident", [0, 1])
+def test_resident_and_streamed_candidates_match_oracle(S, n, resident):
+    S.stab_path_store(gpu_name(), n, {"resident": resident, "resident_adjoint": resident,
+                                      "gen_cut": 0.5, "tile_limit": 1 << 17, "tuned": 1})
+    c = W.layered_ansatz(n, 500, seed=4500 + n)
+    obs = W.obs_chain(n)
+    s = S.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    assert s.plan_info()[2] == (1 if resident else 2)    # RESIDENT / STREAMED
+    e, g = s.grad(obs)
+    e2 = s.expect(obs)
+    s.run_generators()
+    gens = layout.lib_to_paper(n, s.generators())
+    s.close()
+    tol = 1e-12 * l1(obs)
+    ref = oracle.expect(n, c.gates, c.thetas, obs)
+    assert abs(e - ref) <= tol and abs(e2 - ref) <= tol
+    assert np.abs(gens - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12
+    rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+    for gi in (rot[3], rot[len(rot) // 2], rot[-2]):
+        want = oracle.psr_grad_gate(n, c.gates, c.thetas, obs, gi)
+        assert abs(g[int(c.gates[gi]["param"])] - want) <= tol
+
+
+@pytest.mark.parametrize("n", [7, 8])
+@pytest.mark.parametrize("tiles", [False, True])
+def test_tile_limit_candidates_match_oracle(S, n, tiles):
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": 0.5,
+                                      "tile_limit": (n * 4 ** n) if tiles else 0, "tuned": 1})
+    c = W.layered_ansatz(n, 150, seed=4700 + n)
+    obs = W.obs_chain(n)
+    s = S.Stab(n)
+    s.apply_circuit(c.gates, c.thetas)
+    gens = layout.lib_to_paper(n, s.generators())
+    e = s.expect(obs)
+    s.close()
+    for k in (0, n - 1):
+        want = oracle.forward(n, c.gates, c.thetas, oracle.generator(n, k))
+        assert np.abs(gens[k] - want).max() <= 1e-12
+    assert abs(e - oracle.expect(n, c.gates, c.thetas, obs)) <= 1e-12 * l1(obs)
