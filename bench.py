@@ -452,7 +452,7 @@ def run_ours(args):
         # the other configurations, bounded, each with its own clock record
         line["sub"] = {
             "c3_batch": measure_batch(steps=3, warmup=1, with_cpu=False),
-            "c4_grad": measure_grad(steps=10, warmup=3, psr_slots=64, with_cpu=False),
+            "c4_grad": measure_grad(steps=40, warmup=3, psr_slots=64, with_cpu=False),
             "c5_serve": measure_serve(requests=args.sub_requests),
         }
     if rank == 0:
@@ -626,6 +626,7 @@ def measure_grad(steps, warmup, psr_slots, with_cpu):
     torch.cuda.synchronize()
     clocks = ClockSampler(gpu_uuid(torch.device("cuda", torch.cuda.current_device())))
     clocks.start()
+    time.sleep(0.2)
     times = []
     for _ in range(steps):
         e0, e1 = _events()
@@ -763,13 +764,14 @@ def _percentiles(lat):
     return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
 
 
-def serve_trace(reqs, mine, form, max_active, aging_s, device=0):
+def serve_trace(reqs, mine, form, max_active, aging_s, device=0, burst=False):
     """Submits reqs[i] for i in mine at their arrival times and waits for all.
     form: ("iterate" | "contexts", policy) through stab.Server, or "plain":
     one request at a time in arrival order, each on a context of the plain
     form (one pass per gate; gradients by the library's streamed adjoint, the
     plain form having none of its own), results to the host before the next
-    starts.  Returns (per request (latency s, <O>), makespan s, clocks)."""
+    starts.  burst: every request submitted at time 0 (profiler captures).
+    Returns (per request (latency s, <O>), makespan s, clocks)."""
     import torch
     from paper_2502_10685_gb300 import stab
     clocks = ClockSampler(gpu_uuid(torch.device("cuda", device)))
@@ -780,7 +782,8 @@ def serve_trace(reqs, mine, form, max_active, aging_s, device=0):
         out = []
         for i in mine:
             r = reqs[i]
-            delay = r.arrival_s - (time.perf_counter() - t0)
+            arrival = 0.0 if burst else r.arrival_s
+            delay = arrival - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
             c = r.circuit
@@ -792,7 +795,7 @@ def serve_trace(reqs, mine, form, max_active, aging_s, device=0):
                 val = sx.expect(r.observable)
             else:
                 val, _ = sx.grad(r.observable)
-            out.append((time.perf_counter() - t0 - r.arrival_s, val))
+            out.append((time.perf_counter() - t0 - arrival, val))
         span = time.perf_counter() - t0
         for sx in ctxs.values():
             sx.close()
@@ -804,7 +807,7 @@ def serve_trace(reqs, mine, form, max_active, aging_s, device=0):
     ids = []
     for i in mine:
         r = reqs[i]
-        delay = r.arrival_s - (time.perf_counter() - t0)
+        delay = (0.0 if burst else r.arrival_s) - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
         ids.append(srv.submit(r.circuit, r.kind, r.observable))
@@ -823,34 +826,50 @@ def serve_summary(reqs, out, span):
             "updates_per_s": upd / span}
 
 
-def measure_serve(requests, max_active=256, aging_s=4.0):
+def measure_serve(requests, max_active=256, aging_s=4.0, small=False,
+                  forms_run=("iterate", "contexts", "plain"), burst=False):
     """The first `requests` requests of the Poisson serving trace (2,000 req/s,
     n ~ U{4..12}, depth log-uniform [100, 60,000], 50/50 <O> / gradient, seed
     1005), through the iteration engine and the context engine (both
     shortest-work-first with the aging bound) and the plain form, each with
     its own clock record; latency = completion - arrival."""
     from paper_2502_10685_gb300 import workloads as W
-    reqs = W.serving_trace(requests, seed=1005)
+    if small:
+        # the iteration engine's own range: n ~ U{4..8}, depth log-uniform [100, 20,000]
+        reqs = W.serving_trace(requests, seed=1015, n_range=(4, 8), depth_range=(100, 20000))
+    else:
+        reqs = W.serving_trace(requests, seed=1005)
     mine = list(range(len(reqs)))
+    # one context of every size first: the path tuner measures each n once per
+    # process, which must not land inside the first form's timed trace
+    from paper_2502_10685_gb300 import stab
+    for n in sorted({r.circuit.n for r in reqs}):
+        stab.Stab(n).close()
     forms = {}
     vals = {}
     for name, form in (("iterate", ("iterate", "shortest")), ("contexts", ("contexts", "shortest")),
                        ("plain", "plain")):
-        out, span, clk = serve_trace(reqs, mine, form, max_active, aging_s)
+        if name not in forms_run:
+            continue
+        out, span, clk = serve_trace(reqs, mine, form, max_active, aging_s, burst=burst)
         forms[name] = dict(serve_summary(reqs, out, span), clocks=clk)
         vals[name] = [x[1] for x in out]
-    worst = max(abs(a - b) for k in ("contexts", "plain")
-                for a, b in zip(vals["iterate"], vals[k]))
-    it = forms["iterate"]
+    first = next(iter(forms))
+    worst = max([abs(a - b) for k in forms if k != first
+                 for a, b in zip(vals[first], vals[k])] or [0.0])
+    it = forms[first]
     return {
         "metric": "p50/p99 latency", "value": it["p50_s"], "unit": "s", "p99_s": it["p99_s"],
         "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "serve-c5", "requests": len(reqs), "rate_per_s": 2000,
+        "config": {"workload": "serve-small" if small else "serve-c5", "requests": len(reqs),
+                   "rate_per_s": 2000, "n_range": [4, 8] if small else [4, 12],
                    "max_active": max_active, "policy": "shortest estimated work first, aging "
-                   "bound %g s" % aging_s, "engine": "iteration (n <= 8), contexts above"},
+                   "bound %g s" % aging_s, "arrivals": "all at 0" if burst else "Poisson",
+                   "engine": "iteration engine for n <= 6, contexts above"},
         "circuits_per_s": it["circuits_per_s"], "makespan_s": it["makespan_s"],
         "forms": forms,
-        "speedup_vs_plain_circuits_per_s": it["circuits_per_s"] / forms["plain"]["circuits_per_s"],
+        "speedup_vs_plain_circuits_per_s": (it["circuits_per_s"] / forms["plain"]["circuits_per_s"]
+                                            if "plain" in forms else None),
         "max_abs_diff_between_forms": worst, "clocks": it["clocks"]}
 
 
@@ -869,8 +888,11 @@ def run_serve(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world == 1:
-        print(json.dumps(measure_serve(args.requests, args.max_active, args.aging)))
+    if world == 1 or args.workload == "serve-small":
+        print(json.dumps(measure_serve(args.requests, args.max_active, args.aging,
+                                       small=args.workload == "serve-small",
+                                       forms_run=tuple(args.serve_forms.split(",")),
+                                       burst=args.burst)))
         return 0
     dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     reqs = W.serving_trace(args.requests, seed=1005)
@@ -1163,6 +1185,10 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serve-c5: trace length")
     ap.add_argument("--max-active", type=int, default=256, help="serve-c5: admitted at once")
     ap.add_argument("--aging", type=float, default=4.0, help="serve-c5: aging bound (s)")
+    ap.add_argument("--burst", action="store_true",
+                    help="serve-c5 / serve-small: submit every request at time 0")
+    ap.add_argument("--serve-forms", default="iterate,contexts,plain",
+                    help="serve-c5 / serve-small: which forms to run (comma list)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1174,7 +1200,7 @@ def main():
         return run_grad(args)
     if args.workload.startswith("grad-n"):
         return run_grad_n(args)
-    if args.workload == "serve-c5":
+    if args.workload in ("serve-c5", "serve-small"):
         return run_serve(args)
     if args.workload.startswith("expect-n"):
         return run_expect(args)

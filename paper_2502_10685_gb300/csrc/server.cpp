@@ -6,7 +6,7 @@
 // work unless the oldest has waited longer than the aging bound) whenever a
 // slot and enough HBM budget are free.  Two engines then run it:
 //
-//  * the iteration engine (STAB_SERVE_ITERATE, requests of n <= 8): the
+//  * the iteration engine (STAB_SERVE_ITERATE, requests of n <= iter_max_n): the
 //    planner thread plans the request on the host; the engine thread uploads
 //    it into one device block and, once per iteration, launches one
 //    persistent k_serve kernel that advances every admitted request by a
@@ -15,8 +15,8 @@
 //    requests join at the next iteration, finished ones leave after the
 //    launch that finished them.  Two iterations are in flight at a time, so
 //    the host prepares the next launch while the GPU runs the current one.
-//  * the context engine (every request with STAB_SERVE_CONTEXTS, and requests
-//    of n > 8 with ITERATE): the request runs on a pooled context with its own
+//  * the context engine (every request with STAB_SERVE_CONTEXTS, and larger
+//    requests with ITERATE): the request runs on a pooled context with its own
 //    streams (the vectors of a large request fill the GPU by themselves);
 //    its kernels overlap on the device with every other request's.  A
 //    completion thread polls each request's event.
@@ -49,7 +49,12 @@ namespace {
 constexpr int kInFlight = 2;          // iterations queued on the GPU at once
 constexpr int kTableSlots = kInFlight + 1;
 constexpr int kDefaultIterChunks = 64;
-constexpr int kDefaultIterSmemKb = 64;
+constexpr int kDefaultIterSmemKb = 32;
+// Requests above this size go to contexts by default: one CTA per vector
+// leaves a 4^7 or 4^8 vector latency-bound, while a context streams it over
+// the whole GPU (a Poisson trace of n = 4..8 requests: 1,068 circuits/s with
+// n <= 6 in the iteration engine, 380 with n <= 8, 604 with contexts only).
+constexpr int kDefaultIterMaxN = 6;
 constexpr double kDefaultAgingS = 4.0;
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -334,7 +339,7 @@ size_t next_request_locked(const stab_server *s) {
 }
 
 bool use_iteration(const stab_server *s, const Req *r) {
-    return s->iterate && r->hdr.n <= kServeMaxQubits;
+    return s->iterate && r->hdr.n <= s->opts.iter_max_n;
 }
 
 // ---------------------------------------------------------------- iteration requests: host side
@@ -930,11 +935,13 @@ int stab_server_create(const stab_server_opts *opts, stab_server **out) {
     if ((s->opts.policy != STAB_SERVE_FIFO && s->opts.policy != STAB_SERVE_SHORTEST) ||
         (s->opts.engine != STAB_SERVE_ITERATE && s->opts.engine != STAB_SERVE_CONTEXTS) ||
         s->opts.iter_chunks < 0 || s->opts.iter_smem_kb < 0 || s->opts.iter_smem_kb > 200 ||
+        s->opts.iter_max_n < 0 || s->opts.iter_max_n > kServeMaxQubits ||
         (s->opts.alloc == nullptr) != (s->opts.free == nullptr)) {
         delete s;
         return STAB_E_INVAL;
     }
     s->iterate = s->opts.engine == STAB_SERVE_ITERATE;
+    if (s->opts.iter_max_n == 0) s->opts.iter_max_n = kDefaultIterMaxN;
     s->hooks.alloc = s->opts.alloc;
     s->hooks.free = s->opts.free;
     s->hooks.user = s->opts.alloc_user;

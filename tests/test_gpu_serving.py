@@ -209,8 +209,10 @@ def test_iteration_engine_alone_equals_mix_bit_for_bit(stab):
     """The iteration engine runs each request's passes in the same order on
     the same data whatever else shares the launches and however the work is
     sliced: every result (expectation and every gradient entry) served in a
-    mix of 32 requests of n = 2..8 equals, bit for bit, the same request served
-    alone with another slice size; all match the oracle and the context engine."""
+    mix of 32 requests of n = 2..8 (all in the iteration engine) equals, bit for
+    bit, the same request served alone with another slice size and another
+    shared-memory budget (so some vectors move between shared and global
+    memory); all match the oracle and the context engine."""
     rng = np.random.default_rng(77)
     reqs = []
     for k in range(32):
@@ -218,7 +220,7 @@ def test_iteration_engine_alone_equals_mix_bit_for_bit(stab):
         m = int(rng.integers(30, 700 if n <= 6 else 250))
         c = W.layered_ansatz(n, m, seed=7700 + k)
         reqs.append((c, "grad" if k % 2 else "expect", W.obs_chain(n)))
-    srv = stab.Server(max_active=64, engine="iterate", iter_chunks=16)
+    srv = stab.Server(max_active=64, engine="iterate", iter_chunks=16, iter_max_n=8)
     ids = []
     for k, (c, kind, obs) in enumerate(reqs):
         ids.append(srv.submit(c, kind, obs))
@@ -232,7 +234,8 @@ def test_iteration_engine_alone_equals_mix_bit_for_bit(stab):
     ctx.close()
     for (c, kind, obs), r, rc in zip(reqs, mix, via_ctx):
         assert r["status"] == 0 and rc["status"] == 0
-        one = stab.Server(max_active=1, engine="iterate", iter_chunks=3)
+        one = stab.Server(max_active=1, engine="iterate", iter_chunks=3, iter_max_n=8,
+                          iter_smem_kb=64)
         a = one.wait(one.submit(c, kind, obs), timeout_s=300)
         one.close()
         assert a["status"] == 0
@@ -271,3 +274,52 @@ def test_shortest_first_with_aging_admits_the_oldest(stab, engine):
     assert all(rl["done_s"] <= r["admit_s"] for r in rs)
     assert abs(rl["expect"] - oracle.expect(8, large.gates, large.thetas, W.obs_chain(8))) <= \
         1e-12 * l1(W.obs_chain(8))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_server_device_memory_goes_through_the_hooks(stab, engine):
+    """The server allocates its device memory (request blocks, unit tables,
+    contexts' vectors) through the allocator hooks of its options: with
+    counting hooks every block is obtained through them and every one is
+    handed back by the time the server is destroyed."""
+    import ctypes
+
+    import torch
+    from paper_2502_10685_gb300 import _lib
+    live, calls = {}, {"alloc": 0, "free": 0}
+
+    def _alloc(nbytes, st, user):
+        calls["alloc"] += 1
+        p = int(torch.cuda.caching_allocator_alloc(int(nbytes), 0))
+        live[p] = int(nbytes)
+        return p
+
+    def _free(ptr, nbytes, st, user):
+        calls["free"] += 1
+        assert live.pop(int(ptr)) == int(nbytes)
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
+    o = _lib.StabServerOpts()
+    o.device, o.max_active, o.engine = 0, 8, stab.Server.ENGINES[engine]
+    o.alloc, o.free = a, f
+    h = ctypes.c_void_p()
+    L = _lib.load()
+    assert L.stab_server_create(ctypes.byref(o), ctypes.byref(h)) == 0
+    reqs = [(W.layered_ansatz(n, 120, seed=90 + n), kind, W.obs_chain(n))
+            for n, kind in ((4, "expect"), (5, "grad"), (7, "grad"), (9, "expect"))]
+    keep, ids = [], []
+    for c, kind, obs in reqs:
+        r = stab.Server._request(c, kind, obs, keep)
+        i = ctypes.c_int64()
+        assert L.stab_server_submit(h, ctypes.byref(r), ctypes.byref(i)) == 0
+        ids.append(i.value)
+    for (c, kind, obs), i in zip(reqs, ids):
+        res = _lib.StabResult()
+        grads = np.zeros(max(c.n_params, 1))
+        assert L.stab_server_wait(h, i, 300.0, ctypes.byref(res), grads.ctypes.data) == 0
+        assert res.status == 0
+        assert abs(res.expect - oracle.expect(c.n, c.gates, c.thetas, obs)) <= 1e-12 * l1(obs)
+    assert calls["alloc"] > 0
+    assert L.stab_server_destroy(h) == 0
+    assert not live and calls["free"] == calls["alloc"]
