@@ -384,9 +384,10 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_dfma, "unit": "TFLOP/s",
                 "frac": achieved / peak_dfma,
                 # DRAM bytes of the generator phase's two launches from one ncu
-                # capture of this workload (k_batch 1,803,776 + k_transfer_cols
-                # 1,589,248 B read, the staged half-streams; 0 B written)
-                "traffic": 3393024.0 if (c.n == 4 and c.m == 60200) else None,
+                # capture of this workload at this cut (k_batch 1,803,776 +
+                # k_transfer_cols 1,589,248 B read, the staged half-streams;
+                # 0 B written); another cut stages other streams
+                "traffic": 3393024.0 if (c.n == 4 and c.m == 60200 and cut == 10535) else None,
                 "kernel": kernel, "launch_ms": gen_avg_s * 1e3,
                 "peak_source": "of measured: FP64 DFMA chains on this GPU in this run "
                                "(stab_probe_fp64, best of 3; %d SMs)" % sms,

@@ -7,6 +7,9 @@
   oracle's backward propagation.
 * n = 10 gradients and n = 11 generators and <O> on layered circuits of a few
   hundred gates; n = 12 <O> on a 400-gate circuit.
+* Deep circuits: the adjoint over the paper-scale 60,200 gates at n = 4 (the
+  1e-10 tolerance of circuits of 60K gates and more) and over 20,000 gates at
+  n = 6, against the oracle's parameter shift.
 
 Tolerances as in the other parity tests: generators max |a - b| <= 1e-12
 (unit 2-norm), <O> and gradients within 1e-12 * sum |o_P|.  The oracle runs
@@ -134,3 +137,39 @@ def test_n12_expectation_400_gates_against_oracle(stab):
     s.close()
     ref = oracle.expect(n, c.gates, c.thetas, obs)
     assert abs(got - ref) <= 1e-12 * l1(obs)
+
+
+def test_deep_gradient_n4_60200_against_oracle_psr(stab):
+    """The paper-scale depth: n = 4, the 60,200-gate layered ansatz.  The
+    adjoint carries lambda and rho backward through the inverse maps over
+    all 60,200 gates; its entries on 8 sampled slots against the oracle's
+    parameter shift (the 1e-10 tolerance of circuits of 60K gates and more),
+    and <O> against the oracle."""
+    c = W.layered_ansatz(4, 60200, seed=1002)
+    obs = W.obs_chain(4)
+    s = stab.Stab(4)
+    s.load_circuit(c.gates, c.thetas)
+    e, g = s.grad(obs)
+    s.close()
+    sg = slot_gates(c)
+    rng = np.random.default_rng(43)
+    keys = sorted(sg)
+    # both ends of the circuit and around the middle, where the split sweeps meet
+    picks = [keys[0], keys[1], keys[len(keys) // 2 - 1], keys[len(keys) // 2],
+             keys[len(keys) // 2 + 1], keys[-2], keys[-1]]
+    picks += [int(k) for k in rng.choice(keys, size=1)]
+    jobs = [lambda: oracle.expect(4, c.gates, c.thetas, obs)]
+    jobs += [(lambda gi=sg[k]: oracle.psr_grad_gate(4, c.gates, c.thetas, obs, gi))
+             for k in picks]
+    ref = oracle_jobs(jobs)
+    tol = 1e-10 * l1(obs)
+    assert abs(e - ref[0]) <= tol
+    for k, want in zip(picks, ref[1:]):
+        assert abs(g[k] - want) <= tol, (k, g[k], want)
+
+
+def test_deep_gradient_n6_20000_against_oracle_psr(stab):
+    """n = 6, 20,000 gates (the deepest circuits of the batch workload): the
+    adjoint against the oracle's parameter shift on 4 sampled slots."""
+    c = W.layered_ansatz(6, 20000, seed=1006)
+    check_grad_against_oracle(stab, c, W.obs_chain(6), 4, seed=44)

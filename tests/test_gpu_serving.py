@@ -323,3 +323,26 @@ def test_server_device_memory_goes_through_the_hooks(stab, engine):
     assert calls["alloc"] > 0
     assert L.stab_server_destroy(h) == 0
     assert not live and calls["free"] == calls["alloc"]
+
+
+def test_iteration_engine_deep_gradient_against_oracle(stab):
+    """A 60,200-gate n = 4 gradient request through the iteration engine
+    (hundreds of slices per unit, both phases of the split sweeps): <O> and
+    sampled slots against the oracle's parameter shift, within the 1e-10
+    tolerance of circuits of 60K gates and more."""
+    c = W.layered_ansatz(4, 60200, seed=1002)
+    obs = W.obs_chain(4)
+    srv = stab.Server(max_active=4, engine="iterate", iter_chunks=8)
+    small = W.layered_ansatz(5, 300, seed=3)
+    i_small = srv.submit(small, "grad", W.obs_chain(5))
+    i_deep = srv.submit(c, "grad", obs)
+    r = srv.wait(i_deep, timeout_s=300)
+    r_small = srv.wait(i_small, timeout_s=300)
+    srv.close()
+    assert r["status"] == 0 and r_small["status"] == 0
+    tol = 1e-10 * l1(obs)
+    assert abs(r["expect"] - oracle.expect(4, c.gates, c.thetas, obs)) <= tol
+    rot = [i for i, g in enumerate(c.gates) if int(g["op"]) in W.ROTATIONS]
+    for gi in (rot[0], rot[len(rot) // 2], rot[-1]):
+        want = oracle.psr_grad_gate(4, c.gates, c.thetas, obs, gi)
+        assert abs(r["grads"][int(c.gates[gi]["param"])] - want) <= tol
