@@ -216,3 +216,16 @@ def test_chain_edges(stab, n, m):
     got = layout.lib_to_paper(n, s.generators())
     assert np.abs(got - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12
     s.close()
+
+
+def test_fp64_probe_measures_a_plausible_rate(stab):
+    """The roofline's denominator: DFMA and FP64 MMA chains give a positive
+    rate below the GPU's nominal FP64 peak (152 SMs x 4 flop/clk x 2.07 GHz
+    = 1.26 TFLOP/s on a GB300, with a margin for other parts), and a longer
+    launch takes proportionally longer."""
+    tf1, ms1 = stab.stab_probe_fp64("dfma", 1024)
+    tf2, ms2 = stab.stab_probe_fp64("dfma", 4096)
+    tm, _ = stab.stab_probe_fp64("dmma", 512)
+    for tf in (tf1, tf2, tm):
+        assert 0.05 < tf < 3.0
+    assert 2.5 < ms2 / ms1 < 6.0

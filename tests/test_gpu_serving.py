@@ -346,3 +346,34 @@ def test_iteration_engine_deep_gradient_against_oracle(stab):
     for gi in (rot[0], rot[len(rot) // 2], rot[-1]):
         want = oracle.psr_grad_gate(4, c.gates, c.thetas, obs, gi)
         assert abs(r["grads"][int(c.gates[gi]["param"])] - want) <= tol
+
+
+def test_iteration_engine_degenerate_requests(stab):
+    """Requests the iteration engine must handle without a special path: the
+    identity circuit (empty streams), a Clifford-only gradient (no slots),
+    one qubit, an observable with an identity term, repeated strings and an
+    empty one, random mixed circuits of every opcode with shared slots --
+    each against the oracle (gradients by the oracle's parameter shift)."""
+    ident = W.Circuit(3, np.zeros(0, dtype=W.GATE_DTYPE), np.zeros(0))
+    cliff = W.random_circuit(4, 120, seed=31, clifford_only=True)
+    one = W.random_circuit(1, 40, seed=32)
+    mixed = W.random_circuit(5, 200, seed=33, shared_params=6)
+    obs3 = [(2.5, "III"), (0.5, "ZIZ"), (0.25, "ZIZ"), (-1.0, "XYZ")]
+    cases = [(ident, "expect", obs3), (ident, "grad", obs3), (cliff, "grad", W.obs_chain(4)),
+             (cliff, "expect", W.obs_chain(4)), (one, "grad", [(1.0, "Z"), (0.5, "X")]),
+             (one, "expect", [(1.0, "Y")]), (mixed, "grad", W.random_observable(5, 6, seed=34)),
+             (W.layered_ansatz(3, 90, seed=35), "expect", [])]
+    srv = stab.Server(max_active=16, engine="iterate", iter_chunks=2)
+    ids = [srv.submit(c, kind, obs) for c, kind, obs in cases]
+    res = [srv.wait(i, timeout_s=120) for i in ids]
+    srv.close()
+    for (c, kind, obs), r in zip(cases, res):
+        assert r["status"] == 0
+        tol = 1e-12 * max(l1(obs), 1.0)
+        want = oracle.expect(c.n, c.gates, c.thetas, obs) if obs else 0.0
+        assert abs(r["expect"] - want) <= tol, (c.n, kind, r["expect"], want)
+        if kind == "grad":
+            assert len(r["grads"]) == c.n_params
+            if c.n_params:
+                ref = oracle.psr_grad(c.n, c.gates, c.thetas, obs)
+                assert np.abs(r["grads"] - ref).max() <= tol

@@ -100,3 +100,15 @@ def test_request_footprint_counts_the_split_sweep_vectors():
     assert L.stab_request_footprint(ctypes.byref(r)) == 12 * 8 * 4 ** 12 + 96 * 1000
     r.n = 13
     assert L.stab_request_footprint(ctypes.byref(r)) == 0
+
+
+def test_fp64_probe_rejects_bad_arguments_on_the_host():
+    # host-only: argument checks come before any device call
+    import ctypes
+    from paper_2502_10685_gb300 import _lib
+    L = _lib.load()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    assert L.stab_probe_fp64(2, 1024, ctypes.byref(tf), ctypes.byref(ms)) == -1
+    assert L.stab_probe_fp64(0, 1024, None, ctypes.byref(ms)) == -1
+    assert L.stab_probe_fp64(0, 0, ctypes.byref(tf), ctypes.byref(ms)) == -2
+    assert L.stab_probe_fp64(1, (1 << 30) + 1, ctypes.byref(tf), ctypes.byref(ms)) == -2
