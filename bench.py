@@ -827,8 +827,42 @@ def serve_summary(reqs, out, span):
             "updates_per_s": upd / span}
 
 
+def serve_cpu_baseline(reqs, sample=8):
+    """The oracle on the trace, one core: its update rate measured on a seeded
+    sample of the trace's small requests (4^n m <= 2e7; <O> = one backward
+    propagation, a gradient = the parameter shift of one slot, two
+    propagations), then every request of the trace costed at that rate (a
+    gradient two propagations per slot: the oracle has no adjoint)."""
+    import numpy as np
+    import oracle
+    from paper_2502_10685_gb300 import workloads as W
+    oracle.build()
+    cand = [r for r in reqs if 4 ** r.circuit.n * r.circuit.m <= 2e7]
+    rng = np.random.default_rng(5)
+    pick = [cand[i] for i in rng.choice(len(cand), size=min(sample, len(cand)), replace=False)]
+    t0 = time.perf_counter()
+    upd = 0
+    for r in pick:
+        c = r.circuit
+        rot = [i for i, g in enumerate(c.gates) if int(g["op"]) in W.ROTATIONS]
+        if r.kind == "grad" and rot:
+            oracle.psr_grad_gate(c.n, c.gates, c.thetas, r.observable, rot[0])
+            upd += 2 * c.m * 4 ** c.n
+        else:
+            oracle.expect(c.n, c.gates, c.thetas, r.observable)
+            upd += c.m * 4 ** c.n
+    rate = upd / (time.perf_counter() - t0)
+    work = sum((2 * max(r.circuit.n_params, 1) if r.kind == "grad" else 1) * r.circuit.m *
+               4 ** r.circuit.n for r in reqs)
+    nproc, model = host_cpu()
+    return {"value": len(reqs) / (work / rate), "unit": "circuits/s", "cores": 1,
+            "kind": "oracle", "host": {"nproc": nproc, "cpu_model": model},
+            "sample": "%d seeded requests with 4^n m <= 2e7 on one core (%.3g updates/s), the whole "
+                      "trace costed at that rate, gradients by parameter shift" % (len(pick), rate)}
+
+
 def measure_serve(requests, max_active=256, aging_s=4.0, small=False,
-                  forms_run=("iterate", "contexts", "plain"), burst=False):
+                  forms_run=("iterate", "contexts", "plain"), burst=False, with_cpu=False):
     """The first `requests` requests of the Poisson serving trace (2,000 req/s,
     n ~ U{4..12}, depth log-uniform [100, 60,000], 50/50 <O> / gradient, seed
     1005), through the iteration engine and the context engine (both
@@ -859,7 +893,7 @@ def measure_serve(requests, max_active=256, aging_s=4.0, small=False,
     worst = max([abs(a - b) for k in forms if k != first
                  for a, b in zip(vals[first], vals[k])] or [0.0])
     it = forms[first]
-    return {
+    line = {
         "metric": "p50/p99 latency", "value": it["p50_s"], "unit": "s", "p99_s": it["p99_s"],
         "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "serve-small" if small else "serve-c5", "requests": len(reqs),
@@ -872,6 +906,9 @@ def measure_serve(requests, max_active=256, aging_s=4.0, small=False,
         "speedup_vs_plain_circuits_per_s": (it["circuits_per_s"] / forms["plain"]["circuits_per_s"]
                                             if "plain" in forms else None),
         "max_abs_diff_between_forms": worst, "clocks": it["clocks"]}
+    if with_cpu:
+        line["cpu_baseline"] = serve_cpu_baseline(reqs)
+    return line
 
 
 def run_serve(args):
@@ -893,7 +930,7 @@ def run_serve(args):
         print(json.dumps(measure_serve(args.requests, args.max_active, args.aging,
                                        small=args.workload == "serve-small",
                                        forms_run=tuple(args.serve_forms.split(",")),
-                                       burst=args.burst)))
+                                       burst=args.burst, with_cpu=not args.no_cpu_baseline)))
         return 0
     dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     reqs = W.serving_trace(args.requests, seed=1005)
