@@ -259,6 +259,11 @@ int stab_batch_create(const stab_batch_item *items, int64_t count, const stab_op
 /* Queues one evaluation of every item (asynchronous). */
 int stab_batch_run(stab_batch *b);
 
+/* The same call under the name of the batch step of the propagation path
+ * (all items of a created batch, parameter-shift copies included, in one
+ * persistent launch). */
+int stab_apply_batch(stab_batch *b);
+
 /* After stab_batch_run: <O> of every item into out[0 .. count) (host; NaN for
  * generator items).  Synchronizes.  Errors: STAB_E_STATE (never run),
  * STAB_E_TIMEOUT. */
@@ -378,6 +383,11 @@ int stab_server_wait(stab_server *s, int64_t id, double timeout_s, stab_result *
 
 /* *done = 1 when request id has completed (it stays known until waited for). */
 int stab_server_poll(stab_server *s, int64_t id, int32_t *done);
+
+/* stab_server_submit and stab_server_poll under the names of the serving
+ * step of the propagation path. */
+int stab_serve_submit(stab_server *s, const stab_request *req, int64_t *id);
+int stab_serve_poll(stab_server *s, int64_t id, int32_t *done);
 
 /* Counters: requests submitted, completed, admitted now, bytes admitted now. */
 int stab_server_stats(stab_server *s, int64_t *submitted, int64_t *completed, int64_t *active,

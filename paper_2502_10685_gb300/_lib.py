@@ -124,6 +124,9 @@ def load(build_if_missing: bool = True):
             "stab_batch_create": (i32, [ctypes.POINTER(StabBatchItem), i64,
                                         ctypes.POINTER(StabOpts), ctypes.POINTER(vp)]),
             "stab_batch_run": (i32, [vp]),
+            "stab_apply_batch": (i32, [vp]),
+            "stab_serve_submit": (i32, [vp, ctypes.POINTER(StabRequest), ctypes.POINTER(i64)]),
+            "stab_serve_poll": (i32, [vp, i64, ctypes.POINTER(ctypes.c_int32)]),
             "stab_batch_expectations": (i32, [vp, dp]),
             "stab_batch_generators": (i32, [vp, i64, dp, i32]),
             "stab_batch_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),

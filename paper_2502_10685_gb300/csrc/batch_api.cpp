@@ -521,6 +521,8 @@ int stab_batch_run(stab_batch *b) {
     return STAB_OK;
 }
 
+int stab_apply_batch(stab_batch *b) { return stab_batch_run(b); }
+
 static int batch_status(stab_batch *b) {
     int32_t h = 0;
     BCK(cudaMemcpyAsync(&h, (int32_t *)b->counter.p + 32, 4, cudaMemcpyDeviceToHost, b->st));

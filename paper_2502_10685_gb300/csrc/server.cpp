@@ -1026,6 +1026,14 @@ int stab_server_poll(stab_server *s, int64_t id, int32_t *done) {
     return STAB_OK;
 }
 
+int stab_serve_submit(stab_server *s, const stab_request *req, int64_t *id) {
+    return stab_server_submit(s, req, id);
+}
+
+int stab_serve_poll(stab_server *s, int64_t id, int32_t *done) {
+    return stab_server_poll(s, id, done);
+}
+
 int stab_server_stats(stab_server *s, int64_t *submitted, int64_t *completed, int64_t *active,
                       int64_t *bytes_in_use) {
     if (!s) return STAB_E_INVAL;

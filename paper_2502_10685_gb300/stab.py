@@ -416,7 +416,7 @@ class Batch:
         self._keep = [x for x in self._keep if not isinstance(x, np.ndarray)]
 
     def run(self) -> None:
-        check(_lib.load().stab_batch_run(self.h), "stab_batch_run")
+        check(_lib.load().stab_apply_batch(self.h), "stab_apply_batch")
 
     def expectations(self) -> np.ndarray:
         out = np.empty(len(self.items))

@@ -312,8 +312,14 @@ def test_server_device_memory_goes_through_the_hooks(stab, engine):
     for c, kind, obs in reqs:
         r = stab.Server._request(c, kind, obs, keep)
         i = ctypes.c_int64()
-        assert L.stab_server_submit(h, ctypes.byref(r), ctypes.byref(i)) == 0
+        assert L.stab_serve_submit(h, ctypes.byref(r), ctypes.byref(i)) == 0
         ids.append(i.value)
+    done = ctypes.c_int32(0)
+    deadline = time.time() + 300
+    while not done.value and time.time() < deadline:    # the last request, by polling
+        assert L.stab_serve_poll(h, ids[-1], ctypes.byref(done)) == 0
+        time.sleep(0.001)
+    assert done.value == 1
     for (c, kind, obs), i in zip(reqs, ids):
         res = _lib.StabResult()
         grads = np.zeros(max(c.n_params, 1))
