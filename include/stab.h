@@ -581,12 +581,15 @@ int stab_path_load(const char *path);
 /* Measures the candidates for n qubits on CUDA device `device` now, stores
  * the result under that GPU's name and writes it to *out (may be NULL).
  * Candidates: n = 4: gen_cut in {0.50, 0.53, 0.56, 0.59, 0.62} (time of the
- * generators of a 6,000-gate probe); n = 5, 6: resident against streamed for
+ * generators of a 24,000-gate probe); n = 5, 6: resident against streamed for
  * <O> and, separately, for the gradient (2,000-gate probe); n = 7 .. 9: tiles
  * against one launch per pass, for one vector (<O>) and for n vectors (the
  * generators), giving tile_limit = the largest of those launch sizes where
  * tiles won (0 when neither); n <= 3 and n >= 10 have nothing measured and
- * keep the defaults (marked tuned).  Takes tens of milliseconds.
+ * keep the defaults (marked tuned).  Each candidate takes the best of five
+ * timed calls; a candidate replaces the default only when it is more than 2 %
+ * faster, so timing noise does not flip a choice.  Takes up to about a tenth
+ * of a second.
  * Errors: STAB_E_RANGE (n), STAB_E_CUDA, STAB_E_NOMEM. */
 int stab_path_tune(int device, int n, stab_path_choice *out);
 
