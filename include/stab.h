@@ -322,7 +322,7 @@ typedef struct stab_server_opts {
     int32_t planners;      /* host threads that plan and launch requests (0 = 4) */
     int32_t policy;        /* stab_serve_policy: which queued request is admitted next */
     int32_t engine;        /* stab_serve_engine */
-    int32_t iter_chunks;   /* ITERATE: chunks per slice at n = 4 (0 = 64) */
+    int32_t iter_chunks;   /* ITERATE: chunks per slice at n = 4 (0 = 32) */
     int32_t iter_smem_kb;  /* ITERATE: KiB of shared memory per CTA for vectors (0 = 32, <= 200);
                               a request whose working vectors fit runs in shared memory,
                               others in their own device memory */
