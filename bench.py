@@ -765,7 +765,7 @@ def _percentiles(lat):
     return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
 
 
-def serve_trace(reqs, mine, form, max_active, aging_s, device=0, burst=False):
+def serve_trace(reqs, mine, form, max_active, aging_s, device=0, burst=False, server_kw=None):
     """Submits reqs[i] for i in mine at their arrival times and waits for all.
     form: ("iterate" | "contexts", policy) through stab.Server, or "plain":
     one request at a time in arrival order, each on a context of the plain
@@ -803,7 +803,7 @@ def serve_trace(reqs, mine, form, max_active, aging_s, device=0, burst=False):
         return out, span, clocks.stop()
     engine, policy = form
     srv = stab.Server(max_active=max_active, policy=policy, engine=engine, aging_s=aging_s,
-                      device=device)
+                      device=device, **(server_kw or {}))
     t0 = time.perf_counter()
     ids = []
     for i in mine:
@@ -862,7 +862,8 @@ def serve_cpu_baseline(reqs, sample=8):
 
 
 def measure_serve(requests, max_active=256, aging_s=4.0, small=False,
-                  forms_run=("iterate", "contexts", "plain"), burst=False, with_cpu=False):
+                  forms_run=("iterate", "contexts", "plain"), burst=False, with_cpu=False,
+                  server_kw=None):
     """The first `requests` requests of the Poisson serving trace (2,000 req/s,
     n ~ U{4..12}, depth log-uniform [100, 60,000], 50/50 <O> / gradient, seed
     1005), through the iteration engine and the context engine (both
@@ -886,7 +887,8 @@ def measure_serve(requests, max_active=256, aging_s=4.0, small=False,
                        ("plain", "plain")):
         if name not in forms_run:
             continue
-        out, span, clk = serve_trace(reqs, mine, form, max_active, aging_s, burst=burst)
+        out, span, clk = serve_trace(reqs, mine, form, max_active, aging_s, burst=burst,
+                                     server_kw=server_kw if name == "iterate" else None)
         forms[name] = dict(serve_summary(reqs, out, span), clocks=clk)
         vals[name] = [x[1] for x in out]
     first = next(iter(forms))
@@ -900,7 +902,8 @@ def measure_serve(requests, max_active=256, aging_s=4.0, small=False,
                    "rate_per_s": 2000, "n_range": [4, 8] if small else [4, 12],
                    "max_active": max_active, "policy": "shortest estimated work first, aging "
                    "bound %g s" % aging_s, "arrivals": "all at 0" if burst else "Poisson",
-                   "engine": "iteration engine for n <= 6, contexts above"},
+                   "engine": "iteration engine for n <= 6, contexts above",
+                   "iteration_engine_options": server_kw or "defaults"},
         "circuits_per_s": it["circuits_per_s"], "makespan_s": it["makespan_s"],
         "forms": forms,
         "speedup_vs_plain_circuits_per_s": (it["circuits_per_s"] / forms["plain"]["circuits_per_s"]
@@ -930,7 +933,11 @@ def run_serve(args):
         print(json.dumps(measure_serve(args.requests, args.max_active, args.aging,
                                        small=args.workload == "serve-small",
                                        forms_run=tuple(args.serve_forms.split(",")),
-                                       burst=args.burst, with_cpu=not args.no_cpu_baseline)))
+                                       burst=args.burst, with_cpu=not args.no_cpu_baseline,
+                                       server_kw={k: v for k, v in (
+                                           ("iter_chunks", args.iter_chunks),
+                                           ("iter_smem_kb", args.iter_smem_kb),
+                                           ("iter_max_n", args.iter_max_n)) if v})))
         return 0
     dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     reqs = W.serving_trace(args.requests, seed=1005)
@@ -1225,6 +1232,12 @@ def main():
     ap.add_argument("--aging", type=float, default=4.0, help="serve-c5: aging bound (s)")
     ap.add_argument("--burst", action="store_true",
                     help="serve-c5 / serve-small: submit every request at time 0")
+    ap.add_argument("--iter-chunks", type=int, default=0,
+                    help="serve workloads: the iteration engine's chunks per slice at n = 4")
+    ap.add_argument("--iter-smem-kb", type=int, default=0,
+                    help="serve workloads: KiB of shared memory per CTA for vectors")
+    ap.add_argument("--iter-max-n", type=int, default=0,
+                    help="serve workloads: largest n the iteration engine takes")
     ap.add_argument("--serve-forms", default="iterate,contexts,plain",
                     help="serve-c5 / serve-small: which forms to run (comma list)")
     args = ap.parse_args()
