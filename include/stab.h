@@ -124,7 +124,11 @@ typedef struct stab_ctx stab_ctx;
 
 /* Creates a context for n qubits (1 <= n <= STAB_MAX_QUBITS).  opts may be
  * NULL.  The context owns the device vectors: n generators of 4^n doubles and
- * the work vectors of expectation and gradient calls.
+ * the work vectors of expectation and gradient calls.  The first AUTO context
+ * of each n in the process may run the path tuner (stab_path_tune) on the
+ * device, on streams of its own, allocating through opts' hooks; it
+ * synchronizes, so do not create contexts while work on the device must not
+ * be waited for (for instance during a global-mode stream capture).
  * Errors: STAB_E_RANGE (n), STAB_E_INVAL (out NULL), STAB_E_CUDA, STAB_E_NOMEM. */
 int stab_create(int n, const stab_opts *opts, stab_ctx **out);
 

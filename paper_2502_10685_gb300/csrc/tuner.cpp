@@ -197,12 +197,13 @@ int time_op(int device, const stab_opts *like, const Probe &P, const stab_path_c
     stab_opts o;
     stab_default_opts(&o);
     if (like) {
-        // the creating context's allocator hooks and stream
+        // the creating context's allocator hooks; the probes run on streams
+        // of their own, so nothing lands on the caller's stream (or in a
+        // capture running on it), and every block is handed back after a
+        // synchronize
         o.alloc = like->alloc;
         o.free = like->free;
         o.alloc_user = like->alloc_user;
-        o.stream = like->stream;
-        o.stream_given = like->stream_given;
     }
     o.device = device;
     stab_ctx *c = nullptr;
