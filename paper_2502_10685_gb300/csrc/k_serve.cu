@@ -151,8 +151,6 @@ __global__ void __launch_bounds__(kServeThreads, 4) k_serve(ServeArgs a) {
 
 }  // namespace
 
-int serve_threads() { return kServeThreads; }
-
 size_t serve_smem_bytes(int smem_buf) { return kSmemHeader + (size_t)(smem_buf > 0 ? smem_buf : 0); }
 
 cudaError_t serve_occupancy(size_t smem, int *ctas_per_sm) {

@@ -150,7 +150,6 @@ struct ServeArgs {
                                // buffers (2 or 4 x 4^n doubles) fit runs in shared memory
 };
 
-int serve_threads();
 size_t serve_smem_bytes(int smem_buf);
 cudaError_t serve_occupancy(size_t smem, int *ctas_per_sm);
 cudaError_t launch_serve(const ServeArgs &a, int grid, size_t smem, cudaStream_t s);
