@@ -15,9 +15,11 @@
 // Each CTA takes units from a counter (the host orders them by the work of
 // their slices, largest first).  A unit whose buffers fit the launch's shared
 // memory loads its vectors there at the start of the slice and stores them
-// back at the end; larger ones (n = 7, 8, or pairs at n = 6) work on the
-// request's own buffers in global memory, which stay in L2 while the CTA
-// works on them.  The pass code is the one of the resident and batch kernels.
+// back at the end; larger ones (with the server's default 32 KiB budget:
+// vectors and pairs of n = 6, and n = 7, 8 when the engine takes them) work
+// on the request's own buffers in global memory, which stay in L2 while the
+// CTA works on them.  The pass code is the one of the resident and batch
+// kernels.
 #include <cuda_runtime.h>
 
 #include "resident.cuh"
