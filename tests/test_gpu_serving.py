@@ -383,3 +383,37 @@ def test_iteration_engine_degenerate_requests(stab):
             if c.n_params:
                 ref = oracle.psr_grad(c.n, c.gates, c.thetas, obs)
                 assert np.abs(r["grads"] - ref).max() <= tol
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_wait_timeout_then_result_and_destroy_with_requests_in_flight(stab, engine):
+    """A wait that gives up (timeout) leaves the request running: a later wait
+    returns its result.  Destroying the server with requests still queued or
+    running waits for them and releases everything (no hang, no fault)."""
+    from paper_2502_10685_gb300._lib import StabError
+    big = W.layered_ansatz(8, 6000, seed=71)
+    srv = stab.Server(max_active=1, engine=engine)
+    i_big = srv.submit(big, "grad", W.obs_chain(8))
+    i_next = srv.submit(W.layered_ansatz(4, 300, seed=72), "expect", W.obs_chain(4))
+    with pytest.raises(StabError) as err:
+        srv.wait(i_next, timeout_s=1e-4)          # still queued behind the large request
+    assert err.value.code == -4                     # STAB_E_TIMEOUT
+    r = srv.wait(i_next, timeout_s=300)
+    assert r["status"] == 0
+    c4 = W.layered_ansatz(4, 300, seed=72)
+    assert abs(r["expect"] - oracle.expect(4, c4.gates, c4.thetas, W.obs_chain(4))) <= \
+        1e-12 * l1(W.obs_chain(4))
+    assert srv.wait(i_big, timeout_s=300)["status"] == 0
+    # now leave work behind: queued and running requests at destroy time
+    for k in range(6):
+        srv.submit(W.layered_ansatz(5 + k % 3, 2000, seed=80 + k), "grad", W.obs_chain(5 + k % 3))
+    t0 = time.time()
+    srv.close()
+    assert time.time() - t0 < 120
+    # the device is still usable afterwards
+    s = stab.Stab(3)
+    c3 = W.layered_ansatz(3, 50, seed=90)
+    s.load_circuit(c3.gates, c3.thetas)
+    assert abs(s.expect(W.obs_chain(3)) - oracle.expect(3, c3.gates, c3.thetas, W.obs_chain(3))) \
+        <= 1e-12 * l1(W.obs_chain(3))
+    s.close()
