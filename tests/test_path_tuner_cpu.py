@@ -111,3 +111,33 @@ def test_malformed_file_rejected_whole(L, tmp_path):
         rc, c = lookup(L, "Kept", 5)
         assert rc == 0 and c.resident == 0                      # the cache as it was
     assert L.stab_path_load(str(tmp_path / "missing.tsv").encode()) == -7
+
+
+def test_cache_file_named_by_the_environment_is_read_at_first_lookup(tmp_path):
+    """STAB_PATH_CACHE: a fresh process reads the named file before its first
+    lookup (so a tuned choice carries over between processes); a malformed
+    file is ignored and the cache starts empty."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    good = tmp_path / "paths.tsv"
+    good.write_text("NVIDIA GB300\t6\t0\t0\t0.5\t131072\t1\nNVIDIA GB300\t4\t1\t1\t0.59\t131072\t1\n")
+    bad = tmp_path / "bad.tsv"
+    bad.write_text("NVIDIA GB300\t6\t0\t0\t0.5\n")
+    code = ("import ctypes, sys; sys.path.insert(0, %r)\n"
+            "from paper_2502_10685_gb300 import _lib\n"
+            "L = _lib.load(build_if_missing=False)\n"
+            "c = _lib.StabPathChoice()\n"
+            "rc6 = L.stab_path_lookup(b'NVIDIA GB300', 6, ctypes.byref(c)); r6 = c.resident\n"
+            "rc4 = L.stab_path_lookup(b'NVIDIA GB300', 4, ctypes.byref(c)); cut = c.gen_cut\n"
+            "print(rc6, r6, rc4, cut)\n" % root)
+    env = dict(os.environ, STAB_PATH_CACHE=str(good))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.split() == ["0", "0", "0", "0.59"]
+    env = dict(os.environ, STAB_PATH_CACHE=str(bad))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.split()[0] == "-7" and out.stdout.split()[2] == "-7"
