@@ -229,3 +229,43 @@ def test_fp64_probe_measures_a_plausible_rate(stab):
     for tf in (tf1, tf2, tm):
         assert 0.05 < tf < 3.0
     assert 2.5 < ms2 / ms1 < 6.0
+
+
+def test_no_device_memory_growth_over_repeated_use(stab):
+    """Contexts, batches and servers created, used and destroyed over and over:
+    every block taken through the PyTorch allocator hooks is handed back
+    (torch's allocated bytes return to where they started) and the device's
+    free memory does not drift."""
+    import torch
+    from paper_2502_10685_gb300 import workloads as W2
+
+    def cycle(k):
+        c = W2.layered_ansatz(5, 300, seed=500 + k)
+        s = stab.Stab(5)
+        s.apply_circuit(c.gates, c.thetas)
+        s.generators()
+        s.grad(W2.obs_chain(5))
+        s.close()
+        items = [W2.BatchItem(W2.layered_ansatz(n, 200, seed=510 + k + n), "expect",
+                              W2.obs_chain(n)) for n in (3, 6, 8)]
+        b = stab.Batch(items)
+        b.run()
+        b.expectations()
+        b.close()
+        srv = stab.Server(max_active=4)
+        ids = [srv.submit(W2.layered_ansatz(n, 150, seed=520 + k + n), kind, W2.obs_chain(n))
+               for n, kind in ((4, "grad"), (6, "expect"), (9, "grad"))]
+        for i in ids:
+            assert srv.wait(i, timeout_s=120)["status"] == 0
+        srv.close()
+
+    cycle(0)                                   # first use: tuning, pools, caches
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in range(1, 9):
+        cycle(k)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 < (256 << 20), (free0 - free1)
