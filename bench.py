@@ -937,7 +937,8 @@ def run_serve(args):
                                        server_kw={k: v for k, v in (
                                            ("iter_chunks", args.iter_chunks),
                                            ("iter_smem_kb", args.iter_smem_kb),
-                                           ("iter_max_n", args.iter_max_n)) if v})))
+                                           ("iter_max_n", args.iter_max_n),
+                                           ("iter_slice_us", args.iter_slice_us)) if v})))
         return 0
     dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     reqs = W.serving_trace(args.requests, seed=1005)
@@ -1238,6 +1239,8 @@ def main():
                     help="serve workloads: KiB of shared memory per CTA for vectors")
     ap.add_argument("--iter-max-n", type=int, default=0,
                     help="serve workloads: largest n the iteration engine takes")
+    ap.add_argument("--iter-slice-us", type=float, default=0.0,
+                    help="serve workloads: target slice length (us; < 0: static budgets)")
     ap.add_argument("--serve-forms", default="iterate,contexts,plain",
                     help="serve-c5 / serve-small: which forms to run (comma list)")
     args = ap.parse_args()

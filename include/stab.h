@@ -296,8 +296,9 @@ int stab_batch_destroy(stab_batch *b);
  * admitted requests:
  *  - STAB_SERVE_ITERATE (default): requests of n <= iter_max_n are advanced together
  *    by one persistent kernel launch per iteration; each launch moves every
- *    admitted request a slice of its instruction streams further (the same
- *    amount of work per request: iter_chunks chunks of 4 KiB at n = 4, a
+ *    admitted request a slice of its instruction streams further (as many
+ *    4 KiB chunks as take about iter_slice_us by the measured cost of its
+ *    kind of unit; before a kind is measured, iter_chunks chunks at n = 4, a
  *    quarter of that per extra qubit, at least one), its vectors staying in
  *    its own device memory between launches.  New requests join at the next
  *    launch.  Larger requests run as in STAB_SERVE_CONTEXTS, beside them.
@@ -338,6 +339,13 @@ typedef struct stab_server_opts {
                               cudaMallocAsync / cudaFreeAsync (both NULL or both set) */
     stab_free_fn free;
     void *alloc_user;
+    double iter_slice_us;  /* ITERATE: target length of one unit's slice in microseconds (0 =
+                              400; < 0 = the static budget of iter_chunks only).  The launch
+                              records how long every slice took; per kind of unit (n, vector or
+                              pair, in shared memory or not) the engine keeps an estimate of a
+                              chunk's cost and gives each unit as many chunks as fill the
+                              target, so the units of one launch end together; until a kind
+                              has been measured it gets the static budget. */
 } stab_server_opts;
 
 enum stab_request_kind { STAB_REQ_EXPECT = 0, STAB_REQ_GRAD = 1 };

@@ -60,7 +60,8 @@ class StabServerOpts(ctypes.Structure):
                 ("policy", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("iter_chunks", ctypes.c_int32), ("iter_smem_kb", ctypes.c_int32),
                 ("iter_max_n", ctypes.c_int32), ("aging_s", ctypes.c_double),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+                ("iter_slice_us", ctypes.c_double)]
 
 
 class StabRequest(ctypes.Structure):

@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kServeThreads, 4) k_serve(ServeArgs a) {
         __syncthreads();
         if (u >= a.n_units) break;
         const ServeUnit U = a.units[u];
+        const long long t0 = clock64();
         switch (U.n) {
         case 1: serve_unit<1>(U, a.smem_buf, st, smem, a.status, ok); break;
         case 2: serve_unit<2>(U, a.smem_buf, st, smem, a.status, ok); break;
@@ -148,6 +149,9 @@ __global__ void __launch_bounds__(kServeThreads, 4) k_serve(ServeArgs a) {
         case 8: serve_unit<8>(U, a.smem_buf, st, smem, a.status, ok); break;
         default: break;
         }
+        // the slice's length, for the host's estimate of what a chunk of this
+        // kind of unit costs (every thread has passed the slice's last barrier)
+        if (a.unit_cycles && threadIdx.x == 0) a.unit_cycles[u] = (int64_t)(clock64() - t0);
     }
 }
 

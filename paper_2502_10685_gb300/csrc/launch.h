@@ -148,6 +148,7 @@ struct ServeArgs {
     int32_t *status;
     int32_t smem_buf;          // bytes of shared memory for state buffers: a unit whose
                                // buffers (2 or 4 x 4^n doubles) fit runs in shared memory
+    int64_t *unit_cycles;      // per unit: SM clock cycles its slice took (may be null)
 };
 
 size_t serve_smem_bytes(int smem_buf);

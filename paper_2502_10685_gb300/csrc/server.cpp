@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -58,6 +59,8 @@ constexpr int kDefaultIterSmemKb = 32;
 // n <= 6 in the iteration engine, 380 with n <= 8, 604 with contexts only).
 constexpr int kDefaultIterMaxN = 6;
 constexpr double kDefaultAgingS = 4.0;
+constexpr double kDefaultIterSliceUs = 400.0;
+constexpr int kCostClasses = (kServeMaxQubits + 1) * 3 * 2;
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -454,6 +457,8 @@ struct Flight {
     cudaEvent_t ev = nullptr;
     int slot = 0;
     std::vector<IterReq *> finishing;
+    std::vector<int16_t> keys;       // per unit slice: its cost class (see Engine::key)
+    std::vector<int32_t> chunks;     // per unit slice: chunks it ran
 };
 
 struct Engine {
@@ -466,7 +471,15 @@ struct Engine {
     // unit tables, one per slot: pinned copy, device copy, capacity
     ServeUnit *h_tab[kTableSlots] = {};
     ServeUnit *d_tab[kTableSlots] = {};
+    int64_t *h_cyc[kTableSlots] = {};      // per unit slice: SM cycles it took (pinned)
+    int64_t *d_cyc[kTableSlots] = {};
     int cap[kTableSlots] = {};
+    // Adaptive slices: per cost class (n, vector / rows vector / pair, in shared
+    // memory or not) an estimate of the SM cycles one chunk takes, learned from
+    // the slices' measured lengths; a unit then gets as many chunks as fill the
+    // target slice length (0 = no estimate yet: the static budget).
+    double est[kCostClasses] = {};
+    double target_cycles = 0.0;
     int32_t *d_words = nullptr;         // counters [0, kTableSlots), status at 32
     int32_t *h_status = nullptr;        // pinned, one per slot
     int64_t iterations = 0;
@@ -488,6 +501,15 @@ struct Engine {
         }
         grid_max = sms * std::min(occ, 4);
         if (s->opts.iter_chunks > 0) iter_chunks = s->opts.iter_chunks;
+        // the target slice length: iter_slice_us of SM clock (0: the default;
+        // < 0: static budgets only)
+        int khz = 0;
+        if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, s->device) != cudaSuccess) {
+            (void)cudaGetLastError();
+            khz = 0;
+        }
+        const double us = s->opts.iter_slice_us == 0.0 ? kDefaultIterSliceUs : s->opts.iter_slice_us;
+        target_cycles = (us > 0.0 && khz > 0) ? us * (double)khz / 1000.0 : 0.0;
         d_words = (int32_t *)s->hooks.get(256, st);
         if (!d_words) return STAB_E_NOMEM;
         if (cudaMemsetAsync(d_words, 0, 256, st) != cudaSuccess ||
@@ -502,7 +524,9 @@ struct Engine {
         if (st) cudaStreamSynchronize(st);
         for (int k = 0; k < kTableSlots; ++k) {
             if (d_tab[k]) s->hooks.put(d_tab[k], (size_t)cap[k] * sizeof(ServeUnit), st);
+            if (d_cyc[k]) s->hooks.put(d_cyc[k], (size_t)cap[k] * sizeof(int64_t), st);
             if (h_tab[k]) cudaFreeHost(h_tab[k]);
+            if (h_cyc[k]) cudaFreeHost(h_cyc[k]);
         }
         if (d_words) s->hooks.put(d_words, 256, st);
         if (st) cudaStreamSynchronize(st);
@@ -511,12 +535,29 @@ struct Engine {
         if (st) cudaStreamDestroy(st);
     }
 
-    // Chunks a unit of n qubits runs per iteration: the same work (chunks x
+    // Cost class of a unit: n, its kind (vector, rows vector, pair) and whether
+    // its vectors fit the launch's shared memory.
+    int key(int n, int kind, bool rows) const {
+        const size_t E = (size_t)1 << (2 * n);
+        const int k = kind != SV_VEC ? 2 : (rows ? 1 : 0);
+        const bool smem = (kind != SV_VEC ? 4 : 2) * E * sizeof(double) <= (size_t)smem_buf;
+        return (n * 3 + k) * 2 + (smem ? 1 : 0);
+    }
+
+    // Chunks a unit runs per iteration.  Static budget: the same work (chunks x
     // 4^n, twice that for a pair) for every unit, iter_chunks chunks at n = 4.
-    int budget(int n, int kind) const {
-        const int64_t w = (int64_t)iter_chunks << 8;
-        int64_t c = w >> (2 * n);
-        if (kind != SV_VEC) c /= 2;
+    // Adaptive (a target slice length and an estimate for the unit's class):
+    // as many chunks as take about the target length, so the units of one
+    // launch end together whatever their size and residency.
+    int budget(int n, int kind, bool rows) const {
+        const double e = target_cycles > 0.0 ? est[key(n, kind, rows)] : 0.0;
+        int64_t c;
+        if (e > 0.0) {
+            c = (int64_t)(target_cycles / e + 0.5);
+        } else {
+            c = ((int64_t)iter_chunks << 8) >> (2 * n);
+            if (kind != SV_VEC) c /= 2;
+        }
         return (int)std::max<int64_t>(1, std::min<int64_t>(c, 4096));
     }
 
@@ -635,6 +676,15 @@ struct Engine {
             status = STAB_E_TIMEOUT;
             h_status[f.slot] = 0;
             cudaMemsetAsync(d_words + 32, 0, 4, st);
+        } else {
+            // what a chunk of each class cost in this launch (running mean
+            // weighted toward recent launches)
+            for (size_t k = 0; k < f.keys.size(); ++k) {
+                const double per = (double)h_cyc[f.slot][k] / (double)std::max(1, f.chunks[k]);
+                if (per <= 0.0) continue;
+                double &e = est[f.keys[k]];
+                e = e > 0.0 ? 0.75 * e + 0.25 * per : per;
+            }
         }
         for (IterReq *it : f.finishing) finish(it, status);
     }
@@ -650,13 +700,19 @@ struct Engine {
         int c = std::max(256, cap[slot]);
         while (c < n_units) c *= 2;
         if (d_tab[slot]) s->hooks.put(d_tab[slot], (size_t)cap[slot] * sizeof(ServeUnit), st);
+        if (d_cyc[slot]) s->hooks.put(d_cyc[slot], (size_t)cap[slot] * sizeof(int64_t), st);
         if (h_tab[slot]) cudaFreeHost(h_tab[slot]);
+        if (h_cyc[slot]) cudaFreeHost(h_cyc[slot]);
         d_tab[slot] = nullptr;
+        d_cyc[slot] = nullptr;
         h_tab[slot] = nullptr;
+        h_cyc[slot] = nullptr;
         cap[slot] = 0;
         d_tab[slot] = (ServeUnit *)s->hooks.get((size_t)c * sizeof(ServeUnit), st);
-        if (!d_tab[slot]) return STAB_E_NOMEM;
-        if (cudaMallocHost(&h_tab[slot], (size_t)c * sizeof(ServeUnit)) != cudaSuccess) {
+        d_cyc[slot] = (int64_t *)s->hooks.get((size_t)c * sizeof(int64_t), st);
+        if (!d_tab[slot] || !d_cyc[slot]) return STAB_E_NOMEM;
+        if (cudaMallocHost(&h_tab[slot], (size_t)c * sizeof(ServeUnit)) != cudaSuccess ||
+            cudaMallocHost(&h_cyc[slot], (size_t)c * sizeof(int64_t)) != cudaSuccess) {
             (void)cudaGetLastError();
             return STAB_E_NOMEM;
         }
@@ -670,6 +726,7 @@ struct Engine {
         struct Item {
             ServeUnit su;
             int64_t cost;
+            int16_t key;
         };
         std::vector<Item> items;
         std::vector<IterReq *> finishing, still;
@@ -679,7 +736,7 @@ struct Engine {
             for (int k = 0; k < it->n_units; ++k) {
                 IterUnit &u = it->u[k];
                 if (u.pos >= u.n_chunks) continue;
-                const int take = std::min(budget(it->n, u.kind), u.n_chunks - u.pos);
+                const int take = std::min(budget(it->n, u.kind, u.rows), u.n_chunks - u.pos);
                 ServeUnit su{};
                 su.stream = u.stream + (size_t)u.pos * kChunkRecs;
                 su.n_chunks = take;
@@ -696,7 +753,11 @@ struct Engine {
                 su.state = u.state;
                 su.grad_rot = it->grad_rot;
                 su.xfree_out = u.xfree_out;
-                items.push_back({su, (int64_t)take * E * (u.kind == SV_VEC ? 1 : 2)});
+                // largest slice first: by the class's estimate when there is one
+                const int16_t kc = (int16_t)key(it->n, u.kind, u.rows);
+                const int64_t cost = est[kc] > 0.0 ? (int64_t)(take * est[kc])
+                                                    : (int64_t)take * E * (u.kind == SV_VEC ? 1 : 2);
+                items.push_back({su, cost, kc});
                 u.pos += take;
                 if (u.pos < u.n_chunks) left = true;
             }
@@ -726,7 +787,11 @@ struct Engine {
             a.counter = d_words + slot;
             a.status = d_words + 32;
             a.smem_buf = smem_buf;
+            a.unit_cycles = d_cyc[slot];
             if (e == cudaSuccess) e = launch_serve(a, std::min(grid_max, n_units), smem, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_cyc[slot], d_cyc[slot], (size_t)n_units * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st);
         }
         for (IterReq *it : finishing) {
             if (e != cudaSuccess) break;
@@ -753,6 +818,12 @@ struct Engine {
             return STAB_E_CUDA;
         }
         f.finishing = std::move(finishing);
+        f.keys.resize((size_t)n_units);
+        f.chunks.resize((size_t)n_units);
+        for (int k = 0; k < n_units; ++k) {
+            f.keys[(size_t)k] = items[(size_t)k].key;
+            f.chunks[(size_t)k] = items[(size_t)k].su.n_chunks;
+        }
         inflight.push_back(std::move(f));
         live.swap(still);
         ++iterations;
@@ -938,6 +1009,7 @@ int stab_server_create(const stab_server_opts *opts, stab_server **out) {
         (s->opts.engine != STAB_SERVE_ITERATE && s->opts.engine != STAB_SERVE_CONTEXTS) ||
         s->opts.iter_chunks < 0 || s->opts.iter_smem_kb < 0 || s->opts.iter_smem_kb > 200 ||
         s->opts.iter_max_n < 0 || s->opts.iter_max_n > kServeMaxQubits ||
+        !std::isfinite(s->opts.iter_slice_us) || s->opts.iter_slice_us > 1e6 ||
         (s->opts.alloc == nullptr) != (s->opts.free == nullptr)) {
         delete s;
         return STAB_E_INVAL;

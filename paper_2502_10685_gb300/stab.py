@@ -557,7 +557,7 @@ class Server:
     def __init__(self, device: int = 0, max_active: int = 0, hbm_budget: int = 0,
                  planners: int = 0, policy: str = "fifo", engine: str = "iterate",
                  iter_chunks: int = 0, iter_smem_kb: int = 0, iter_max_n: int = 0,
-                 aging_s: float = 0.0, torch_memory: bool = True):
+                 iter_slice_us: float = 0.0, aging_s: float = 0.0, torch_memory: bool = True):
         o = StabServerOpts()
         o.device = device
         o.max_active = max_active
@@ -568,6 +568,7 @@ class Server:
         o.iter_chunks = iter_chunks
         o.iter_smem_kb = iter_smem_kb
         o.iter_max_n = iter_max_n
+        o.iter_slice_us = iter_slice_us
         o.aging_s = aging_s
         self._keep = []
         if torch_memory:
