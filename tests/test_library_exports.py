@@ -67,7 +67,8 @@ def test_server_options_rejected_on_the_host():
     from paper_2502_10685_gb300 import _lib
     L = _lib.load()
     for field, value in (("policy", 7), ("engine", 5), ("iter_chunks", -1),
-                         ("iter_smem_kb", 201), ("iter_max_n", 9), ("iter_max_n", -1)):
+                         ("iter_smem_kb", 201), ("iter_max_n", 9), ("iter_max_n", -1),
+                         ("iter_slice_us", float("nan")), ("iter_slice_us", 2e6)):
         o = _lib.StabServerOpts()
         setattr(o, field, value)
         h = ctypes.c_void_p()
