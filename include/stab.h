@@ -555,16 +555,19 @@ typedef struct stab_path_choice {
                                   0 = vectors streamed through HBM (grid-wide passes) */
     int32_t resident_adjoint;  /* n <= 6: 1 = gradients by the resident adjoint, 0 = streamed */
     double gen_cut;            /* n <= 4: where the generators' split sweep cuts the plan, as a
-                                  fraction of its passes (0.3 .. 0.7) */
+                                  fraction of its passes (0.3 .. 0.7): the end of the first part */
     int64_t tile_limit;        /* streamed plans: consecutive wire passes share one tile-fused
                                   launch while vectors x 4^n <= tile_limit, else one launch
                                   per pass (>= 0) */
     int32_t tuned;             /* 1: measured on this GPU model; 0: the built-in defaults */
-    int32_t reserved;
+    int32_t gen_parts;         /* n = 4: 2 = the plan cut once at gen_cut (the generators through
+                                  one transfer matrix); 3 = a first part of gen_cut of the passes
+                                  and two equal parts after it (the generators through a chain of
+                                  two transfer matrices whose columns run four to an SM) */
 } stab_path_choice;
 
 /* The built-in defaults for n qubits: resident and resident_adjoint 1,
- * gen_cut 0.56 at n = 4 (0.5 below), tile_limit 2^17, tuned 0.
+ * gen_cut 0.56 at n = 4 (0.5 below), tile_limit 2^17, tuned 0, gen_parts 2.
  * Errors: STAB_E_RANGE (n), STAB_E_INVAL (out NULL). */
 int stab_path_defaults(int n, stab_path_choice *out);
 
@@ -582,7 +585,8 @@ int stab_path_store(const char *gpu_name, int n, const stab_path_choice *choice)
 int stab_path_clear(void);
 
 /* Writes every cached entry to a text file (one line per entry: name, n,
- * resident, resident_adjoint, gen_cut, tile_limit and tuned, tab-separated),
+ * resident, resident_adjoint, gen_cut, tile_limit, tuned and gen_parts,
+ * tab-separated),
  * or reads such a file into the cache; a
  * file with a malformed line is rejected whole (STAB_E_INVAL) and leaves the
  * cache as it was.  Errors: STAB_E_INVAL (path NULL, malformed file),
@@ -592,7 +596,8 @@ int stab_path_load(const char *path);
 
 /* Measures the candidates for n qubits on CUDA device `device` now, stores
  * the result under that GPU's name and writes it to *out (may be NULL).
- * Candidates: n = 4: gen_cut in {0.50, 0.53, 0.56, 0.59, 0.62} (time of the
+ * Candidates: n = 4: two parts with gen_cut in {0.50, 0.53, 0.56, 0.59, 0.62}
+ * and three parts with gen_cut in {0.43, 0.46, 0.49, 0.52} (time of the
  * generators of a 24,000-gate probe); n = 5, 6: resident against streamed for
  * <O> and, separately, for the gradient (2,000-gate probe); n = 7 .. 9: tiles
  * against one launch per pass, for one vector (<O>) and for n vectors (the

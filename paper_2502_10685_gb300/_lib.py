@@ -85,7 +85,7 @@ class StabSparseInfo(ctypes.Structure):
 class StabPathChoice(ctypes.Structure):
     _fields_ = [("resident", ctypes.c_int32), ("resident_adjoint", ctypes.c_int32),
                 ("gen_cut", ctypes.c_double), ("tile_limit", ctypes.c_int64),
-                ("tuned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tuned", ctypes.c_int32), ("gen_parts", ctypes.c_int32)]
 
 
 def lib_path() -> str:

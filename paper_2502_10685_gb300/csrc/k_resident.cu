@@ -140,32 +140,36 @@ __global__ void __launch_bounds__(256) k_apply_chain(const double *T, int n_mats
 // ---------------------------------------------------------------- transfer columns
 //
 // Columns of the transfer matrix T of a stream at n = 4: column j is the
-// basis string j carried through the stream's passes.  One CTA of 16 warps
-// carries two columns; each half (8 warps) owns one column, its own copy of
+// basis string j carried through the stream's passes.  One CTA of 8 H warps
+// carries H columns; each half (8 warps) owns one column, its own copy of
 // the staged stream and a named barrier, so the halves run independently and
-// one's loads and barriers overlap the other's FP64 work, as two CTAs on an
-// SM would.  For a pass on wire q the warp index holds the wire's (x_q, z_q)
+// one's loads and barriers overlap the others' FP64 work, as separate CTAs on
+// an SM would.  For a pass on wire q the warp index holds the wire's (x_q, z_q)
 // bits and the lane plus warp bit 0 the other six index bits, so the two warps
 // of the I slot do no FP64 work (those entries do not change) and the other
-// six compute one output row each from the group's X, Y, Z entries.  The
+// six compute one output row each from the group's X, Y, Z entries.  Pairs of
 // halves use mirrored slot maps: warp w = 8v + 4 b2 + 2 b1 + b0 runs on SMSP
-// w % 4 and holds slot (x, z) = (b1 ^ v, b2), so each SMSP has three working
-// warps -- nine warp-wide FP64 instructions per pass for both columns, where
-// two CTAs of the lane-per-entry form issue twelve.
-constexpr int kColThreads = 512;
+// w % 4 and holds slot (x, z) = (b1 ^ (v & 1), b2), so each SMSP has three
+// working warps per pair of halves -- nine warp-wide FP64 instructions per
+// pass for two columns, where two CTAs of the lane-per-entry form issue
+// twelve.  H = 2: the 255 columns of one transfer matrix on 128 CTAs; H = 4:
+// those of two matrices (two parts of a plan) on 128 CTAs, one per SM, with
+// every SM's FP64 pipe shared by four columns.
 constexpr int kColN = 4;
 constexpr int kColE = 1 << (2 * kColN);
 constexpr int kColHalf = (kOffRed + 127) / 128 * 128;   // one half's chunks + barriers
 
-__global__ void __launch_bounds__(kColThreads, 1) k_transfer_cols(const Rec *stream,
-                                                                   int n_chunks, double *tmat,
-                                                                   int32_t *status) {
+template <int H>
+__global__ void __launch_bounds__(256 * H, 1) k_transfer_cols(ColArgs a) {
     constexpr int N = kColN, E = kColE;
     extern __shared__ __align__(128) unsigned char smem[];
     const int w = threadIdx.x >> 5;
-    const int v = w >> 3;                             // this half's column
-    const int col = 1 + 2 * (int)blockIdx.x + v;
-    if (col >= E) return;                             // odd column count: the last half idles
+    const int v = w >> 3;                             // this half
+    // slot s of 256 per transfer matrix: the matrix s / 256, column 1 + s % 256
+    const int slot = H * (int)blockIdx.x + v;
+    const int part = slot / E;
+    const int col = 1 + slot % E;
+    if (part >= a.n_parts || col >= E) return;       // the 256th slot of a matrix idles
     const uint32_t tid = threadIdx.x & 255u;
     const uint32_t bar = 1u + (uint32_t)v;
     Stager st;
@@ -173,21 +177,24 @@ __global__ void __launch_bounds__(kColThreads, 1) k_transfer_cols(const Rec *str
     st.lead = (uint32_t)v * 256u;
     st.bar_id = bar;
     st.bar_n = 256;
-    st.s0 = stream;
+    // (selects, not an indexed read: the kernel parameters stay out of local memory)
+    const int n_chunks = part ? a.n_chunks[1] : a.n_chunks[0];
+    st.s0 = part ? a.stream[1] : a.stream[0];
     st.s1 = nullptr;
     st.n0 = n_chunks;
     st.n_total = n_chunks;
-    double *cur = reinterpret_cast<double *>(smem + 2 * kColHalf) + v * 2 * E;
+    double *tmat = a.tmat + (size_t)part * E * E;
+    double *cur = reinterpret_cast<double *>(smem + H * kColHalf) + v * 2 * E;
     double *nxt = cur + E;
     for (uint32_t i = tid; i < (uint32_t)E; i += 256u) cur[i] = (i == (uint32_t)col) ? 1.0 : 0.0;
     st.start();   // barrier of the half inside
-    const uint32_t sx = (uint32_t)(((w >> 1) & 1) ^ v), sz = (uint32_t)((w >> 2) & 1);
+    const uint32_t sx = (uint32_t)(((w >> 1) & 1) ^ (v & 1)), sz = (uint32_t)((w >> 2) & 1);
     const uint32_t g = (threadIdx.x & 31u) | ((uint32_t)(w & 1) << 5);
     const bool work = (sx | sz) != 0u;
     // slot 1 = X, 2 = Y, 3 = Z: row slot - 1 of the composed map
-    const uint32_t slot = sx ? (sz ? 2u : 1u) : 3u;
+    const uint32_t row = sx ? (sz ? 2u : 1u) : 3u;
     for (int c = 0; c < n_chunks; ++c) {
-        if (!st.wait(c, status)) return;
+        if (!st.wait(c, a.status)) return;
         const Rec *Rr = st.chunk(c);
         int r = 0;
         Rec h = Rr[0];
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_transfer_cols(const Rec *str
                     const double y = cur[base | (1u << q) | (1u << (N + q))];
                     const double z = cur[base | (1u << q)];
                     const double *m =
-                        reinterpret_cast<const double *>(Rr + r + 2 + n_pull) + 3 * (slot - 1u);
+                        reinterpret_cast<const double *>(Rr + r + 2 + n_pull) + 3 * (row - 1u);
                     out = fma(m[2], z, fma(m[1], y, m[0] * x));
                 } else {
                     out = cur[i];
@@ -402,19 +409,60 @@ cudaError_t launch_apply_chain(const double *T, int n_mats, const double *in, do
     return cudaGetLastError();
 }
 
+// <O> = sum of the terms' coeff x v[idx], in term order (one thread: an
+// observable has few terms).
+__global__ void k_terms_dot(const double *v, const DevTerm *terms, int n_terms, double *out) {
+    if (threadIdx.x != 0) return;
+    double acc = 0.0;
+    for (int k = 0; k < n_terms; ++k) acc += terms[k].coeff * v[terms[k].idx];
+    *out = acc;
+}
+
+cudaError_t launch_apply_transfer_chain(const double *T, int n_mats, const double *in,
+                                        double *out, double *tmp, int n_vec, int n,
+                                        const DevTerm *terms, int n_terms, double *dot_out,
+                                        cudaStream_t st) {
+    const int E = 1 << (2 * n);
+    if (n != kColN || n_mats < 1 || n_vec < 1 || (dot_out && n_vec != 1))
+        return cudaErrorInvalidValue;
+    // matrix s maps the previous vector into tmp (ping-pong between its two
+    // halves); the last one writes out (or the free half when out is null)
+    const size_t V = (size_t)n_vec * E;
+    const double *src = in;
+    double *dst = nullptr;
+    for (int s = 0; s < n_mats; ++s) {
+        const bool last = s == n_mats - 1;
+        dst = (last && out) ? out : tmp + (size_t)(s & 1) * V;
+        cudaError_t e = launch_apply_transfer(T + (size_t)s * E * E, src, dst, n_vec, n, st);
+        if (e != cudaSuccess) return e;
+        src = dst;
+    }
+    if (dot_out) {
+        k_terms_dot<<<1, 32, 0, st>>>(src, terms, n_terms, dot_out);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 int transfer_cols_ctas(int n) { return n == kColN ? kColE / 2 : 0; }
 
-cudaError_t launch_transfer_cols(const Rec *stream, int n_chunks, double *tmat, int n,
-                                 int32_t *status, cudaStream_t st) {
-    if (n != kColN) return cudaErrorInvalidValue;
+cudaError_t launch_transfer_cols(const ColArgs &a, int n, cudaStream_t st) {
+    if (n != kColN || a.n_parts < 1 || a.n_parts > 2) return cudaErrorInvalidValue;
     // more than half an SM's shared memory, so two of these CTAs never share
-    // an SM (the kernel needs two halves' chunks and barriers + 8 KiB)
+    // an SM (the kernel needs H halves' chunks and barriers + 4 KiB per half)
     const size_t smem = 116 * 1024;
-    static_assert(2 * kColHalf + 4 * kColE * sizeof(double) <= 116 * 1024, "column buffers");
-    static SmemLimit lim;
-    cudaError_t e = raise_smem_limit(k_transfer_cols, smem, lim);
-    if (e != cudaSuccess) return e;
-    k_transfer_cols<<<kColE / 2, kColThreads, smem, st>>>(stream, n_chunks, tmat, status);
+    static_assert(4 * kColHalf + 8 * kColE * sizeof(double) <= 116 * 1024, "column buffers");
+    static SmemLimit lim2, lim4;
+    cudaError_t e;
+    if (a.n_parts == 1) {
+        e = raise_smem_limit(k_transfer_cols<2>, smem, lim2);
+        if (e != cudaSuccess) return e;
+        k_transfer_cols<2><<<kColE / 2, 512, smem, st>>>(a);
+    } else {
+        e = raise_smem_limit(k_transfer_cols<4>, smem, lim4);
+        if (e != cudaSuccess) return e;
+        k_transfer_cols<4><<<kColE / 2, 1024, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

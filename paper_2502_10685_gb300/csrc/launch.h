@@ -213,8 +213,24 @@ int transfer_cols_ctas(int n);
 cudaError_t launch_apply_chain(const double *T, int n_mats, const double *in, double *out,
                                int n_vec, int n, const DevTerm *terms, int n_terms,
                                double *dot_out, cudaStream_t st);
-cudaError_t launch_transfer_cols(const Rec *stream, int n_chunks, double *tmat, int n,
-                                 int32_t *status, cudaStream_t st);
+// The columns of one or two transfer matrices (n_parts streams) at n = 4:
+// matrix p at tmat + p 16^n, column j at + j 4^n (column 0 is not written);
+// 128 CTAs of two (one matrix) or four (two matrices) columns each.
+struct ColArgs {
+    const Rec *stream[2];
+    int32_t n_chunks[2];
+    int32_t n_parts;
+    double *tmat;
+    int32_t *status;
+};
+cudaError_t launch_transfer_cols(const ColArgs &a, int n, cudaStream_t st);
+// out_k = T_{n_mats-1} ... T_0 in_k at n = 4 (one k_apply_transfer per matrix,
+// tmp: 2 x n_vec x 4^n doubles between them); with dot_out (n_vec = 1) also
+// <O> = sum of terms' coeff x the result[idx], in term order.  out may be null.
+cudaError_t launch_apply_transfer_chain(const double *T, int n_mats, const double *in,
+                                        double *out, double *tmp, int n_vec, int n,
+                                        const DevTerm *terms, int n_terms, double *dot_out,
+                                        cudaStream_t st);
 cudaError_t launch_apply_transfer(const double *T, const double *a, double *out, int n_vec,
                                   int n, cudaStream_t st);
 int resident_lanes_per_group(int n);

@@ -153,6 +153,7 @@ struct stab_ctx {
     DevBuf lam2, tmp3;               // second-branch buffers of the split sweeps
     DevBuf dotbuf;                   // partial sums of the split expectation's inner product
     DevBuf gmid;                     // split resident adjoint: rho, then lambda, at the cut
+    DevBuf chainbuf;                 // n = 4 chain of transfer matrices: intermediate vectors
     // split resident sweeps (n <= 6; see split_units): transfer matrix of the
     // second part (n <= 4), first-part generators, meeting vectors, basis
     // terms, batch units (generators; expectation), unit counters
@@ -403,16 +404,24 @@ void build_streams(const DevPlan &P, const std::vector<StreamSpec> &specs, bool 
 // half streams, not the whole-circuit ones.  Below kThreadedStreamPasses
 // passes the streams are built on the calling thread: handing them to the
 // pool would cost more than the work.
-void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_parts = 2) {
+void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_parts = 2,
+                  double first_frac = 0.0) {
     P.streams = true;
     const int np = (int)P.host.passes.size();
     const bool threads = np >= kThreadedStreamPasses;
     if (!grad && n_parts >= 3) {
-        // K forward parts of equal pass counts
+        // K forward parts of equal pass counts, or (first_frac > 0) a first
+        // part of that fraction of the passes and K - 1 equal parts after it
         P.sf = P.sb = P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
         P.parts.resize((size_t)n_parts);
         P.cuts.assign((size_t)n_parts + 1, 0);
-        for (int k = 0; k <= n_parts; ++k) P.cuts[k] = (int)((int64_t)np * k / n_parts);
+        if (first_frac > 0.0) {
+            const int c1 = (int)(np * first_frac);
+            for (int k = 1; k <= n_parts; ++k)
+                P.cuts[k] = c1 + (int)((int64_t)(np - c1) * (k - 1) / (n_parts - 1));
+        } else {
+            for (int k = 0; k <= n_parts; ++k) P.cuts[k] = (int)((int64_t)np * k / n_parts);
+        }
         P.split = P.cuts[1];
         std::vector<StreamSpec> specs;
         for (int k = 0; k < n_parts; ++k)
@@ -699,12 +708,27 @@ int split_run_g(stab_ctx *c) {
     a.status = (int32_t *)c->status.p;
     CK(cudaMemsetAsync(c->cnt.p, 0, 4, c->st));
     if (transfer_cols_ctas(c->n) > 0) {
-        // the first-part units and the columns of T at once, on two streams
+        // the first-part units and the columns of T (of both later parts in
+        // a three-part chain) at once, on two streams
         CK(cudaEventRecord(c->ev_fork, c->st));
         CK(cudaStreamWaitEvent(c->aux2, c->ev_fork, 0));
         CK(launch_batch(a, c->n_units_g, c->split_smem, c->st));
-        CK(launch_transfer_cols(c->fwd.h2.dev, c->fwd.h2.n_chunks, (double *)c->tmat.p, c->n,
-                                (int32_t *)c->status.p, c->aux2));
+        ColArgs ca{};
+        if (chain_mode(c)) {
+            ca.n_parts = (int)c->fwd.parts.size() - 1;
+            if (ca.n_parts > 2) return STAB_E_STATE;
+            for (int k = 0; k < ca.n_parts; ++k) {
+                ca.stream[k] = c->fwd.parts[(size_t)k + 1].dev;
+                ca.n_chunks[k] = c->fwd.parts[(size_t)k + 1].n_chunks;
+            }
+        } else {
+            ca.n_parts = 1;
+            ca.stream[0] = c->fwd.h2.dev;
+            ca.n_chunks[0] = c->fwd.h2.n_chunks;
+        }
+        ca.tmat = (double *)c->tmat.p;
+        ca.status = (int32_t *)c->status.p;
+        CK(launch_transfer_cols(ca, c->n, c->aux2));
         CK(cudaEventRecord(c->ev_join, c->aux2));
         CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
         c->launches++;
@@ -723,7 +747,13 @@ int split_apply(stab_ctx *c, int first, int n_vec, double *out, const DevTerm *t
                 double *dot_out, cudaStream_t s) {
     const size_t E = (size_t)1 << (2 * c->n);
     const double *in = (const double *)c->avec.p + (size_t)first * E;
-    if (chain_mode(c)) {
+    if (chain_mode(c) && transfer_cols_ctas(c->n) > 0) {
+        // n = 4: one matrix-vector product per part, through a scratch pair
+        RC(c->dalloc(c->chainbuf, 2 * (size_t)n_vec * E * 8, s));
+        CK(launch_apply_transfer_chain((const double *)c->tmat.p, (int)c->fwd.parts.size() - 1,
+                                       in, out, (double *)c->chainbuf.p, n_vec, c->n, terms,
+                                       n_terms, dot_out, s));
+    } else if (chain_mode(c)) {
         CK(launch_apply_chain((const double *)c->tmat.p, (int)c->fwd.parts.size() - 1, in, out,
                               n_vec, c->n, terms, n_terms, dot_out, s));
     } else {
@@ -1157,7 +1187,7 @@ int stab_destroy(stab_ctx *c) {
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
                       &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3,
                       &c->dotbuf, &c->tmat, &c->avec, &c->rmid, &c->lmid, &c->bterms,
-                      &c->units_g, &c->units_e, &c->cnt, &c->gmid};
+                      &c->units_g, &c->units_e, &c->cnt, &c->gmid, &c->chainbuf};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -1199,9 +1229,20 @@ int stab_load_circuit(stab_ctx *c, const stab_gate *gates, int64_t m, const doub
         // where k_transfer_cols carries two columns per CTA at a different
         // pass rate than a first-part unit alone on its SM, the path tuner
         // times candidate cuts (n <= 3: every unit has an SM to itself, half).
+        // At n = 4 the tuner may also cut the plan in three (a first part of
+        // gen_cut of the passes, then two equal parts whose transfer matrices
+        // share the SMs four columns to an SM).
         const bool split = c->kernel == STAB_KERNEL_AUTO && c->fuse;
         const double cut = c->choice.gen_cut;
-        make_streams(c->fwd, split ? cut : 0.0, false, split ? chain_parts(c) : 2);
+        const int np = (int)c->fwd.host.passes.size();
+        int parts = split ? chain_parts(c) : 2;
+        double first = 0.0;
+        if (split && transfer_cols_ctas(c->n) > 0 && c->choice.gen_parts == 3 &&
+            np >= 3 * kSplitMinPasses) {
+            parts = 3;
+            first = cut;
+        }
+        make_streams(c->fwd, split ? cut : 0.0, false, parts, first);
     }
     else no_streams(c->fwd);
     RC(upload_thetas_host(c, thetas));

@@ -50,7 +50,7 @@ bool choice_ok(const stab_path_choice &c) {
     return (c.resident == 0 || c.resident == 1) &&
            (c.resident_adjoint == 0 || c.resident_adjoint == 1) && std::isfinite(c.gen_cut) &&
            c.gen_cut >= 0.3 && c.gen_cut <= 0.7 && c.tile_limit >= 0 &&
-           (c.tuned == 0 || c.tuned == 1);
+           (c.tuned == 0 || c.tuned == 1) && (c.gen_parts == 2 || c.gen_parts == 3);
 }
 
 const char *cache_file() {
@@ -87,12 +87,12 @@ bool read_file(const char *path, std::map<std::pair<std::string, int>, stab_path
         }
         *tab = 0;
         stab_path_choice c{};
-        int n = 0, res = 0, radj = 0, tuned = 0;
+        int n = 0, res = 0, radj = 0, tuned = 0, parts = 0;
         long long tl = 0;
         double cut = 0.0;
         char tail = 0;
-        if (std::sscanf(tab + 1, "%d\t%d\t%d\t%lf\t%lld\t%d%c", &n, &res, &radj, &cut, &tl,
-                        &tuned, &tail) != 6) {
+        if (std::sscanf(tab + 1, "%d\t%d\t%d\t%lf\t%lld\t%d\t%d%c", &n, &res, &radj, &cut, &tl,
+                        &tuned, &parts, &tail) != 7) {
             ok = false;
             break;
         }
@@ -101,6 +101,7 @@ bool read_file(const char *path, std::map<std::pair<std::string, int>, stab_path
         c.gen_cut = cut;
         c.tile_limit = tl;
         c.tuned = tuned;
+        c.gen_parts = parts;
         if (!name_ok(line) || n < 1 || n > STAB_MAX_QUBITS || !choice_ok(c)) {
             ok = false;
             break;
@@ -116,9 +117,9 @@ bool write_file(const char *path) {
     if (!f) return false;
     for (const auto &kv : g_cache) {
         const stab_path_choice &c = kv.second;
-        std::fprintf(f, "%s\t%d\t%d\t%d\t%.17g\t%lld\t%d\n", kv.first.first.c_str(),
+        std::fprintf(f, "%s\t%d\t%d\t%d\t%.17g\t%lld\t%d\t%d\n", kv.first.first.c_str(),
                      kv.first.second, c.resident, c.resident_adjoint, c.gen_cut,
-                     (long long)c.tile_limit, c.tuned);
+                     (long long)c.tile_limit, c.tuned, c.gen_parts);
     }
     return std::fclose(f) == 0;
 }
@@ -285,19 +286,31 @@ int measure(int device, const stab_opts *like, int n, stab_path_choice *out) {
         const double def = d.gen_cut;
         float t_def = 0.0f, best = 1e30f;
         double best_cut = def;
-        for (double cut : {0.50, 0.53, 0.56, 0.59, 0.62}) {
+        int best_parts = 2;
+        struct Cand {
+            int parts;
+            double cut;
+        };
+        const Cand cands[] = {{2, 0.50}, {2, 0.53}, {2, 0.56}, {2, 0.59}, {2, 0.62},
+                              {3, 0.43}, {3, 0.46}, {3, 0.49}, {3, 0.52}};
+        for (const Cand &k : cands) {
             stab_path_choice c = d;
-            c.gen_cut = cut;
+            c.gen_cut = k.cut;
+            c.gen_parts = k.parts;
             float t = 0.0f;
             int rc = time_op(device, like, P, c, PR_GENS, &t);
             if (rc != STAB_OK) return rc;
-            if (cut == def) t_def = t;
+            if (k.parts == 2 && k.cut == def) t_def = t;
             if (t < best) {
                 best = t;
-                best_cut = cut;
+                best_cut = k.cut;
+                best_parts = k.parts;
             }
         }
-        d.gen_cut = clearly_faster(best, t_def) ? best_cut : def;
+        if (clearly_faster(best, t_def)) {
+            d.gen_cut = best_cut;
+            d.gen_parts = best_parts;
+        }
     } else if (n == 5 || n == 6) {
         P.m = 2000;
         probe_circuit(n, P.m, &P.g, &P.th);
@@ -395,6 +408,7 @@ int stab_path_defaults(int n, stab_path_choice *out) {
     c.gen_cut = n == 4 ? 0.56 : 0.5;
     c.tile_limit = (int64_t)1 << 17;
     c.tuned = 0;
+    c.gen_parts = 2;
     *out = c;
     return STAB_OK;
 }

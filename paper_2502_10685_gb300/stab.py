@@ -198,7 +198,8 @@ def stab_probe_fp64(kind: str = "dfma", iters: int = 8192) -> Tuple[float, float
 
 def _choice_dict(c: StabPathChoice) -> dict:
     return {"resident": c.resident, "resident_adjoint": c.resident_adjoint,
-            "gen_cut": c.gen_cut, "tile_limit": c.tile_limit, "tuned": c.tuned}
+            "gen_cut": c.gen_cut, "tile_limit": c.tile_limit, "tuned": c.tuned,
+            "gen_parts": c.gen_parts}
 
 
 def stab_path_tune(device: int, n: int) -> dict:
@@ -220,6 +221,7 @@ def stab_path_lookup(gpu_name: str, n: int) -> Optional[dict]:
 def stab_path_store(gpu_name: str, n: int, choice: dict) -> None:
     c = StabPathChoice(**{k: choice[k] for k in ("resident", "resident_adjoint", "gen_cut",
                                                   "tile_limit", "tuned")})
+    c.gen_parts = int(choice.get("gen_parts", 2))
     check(_lib.load().stab_path_store(gpu_name.encode(), n, ctypes.byref(c)), "stab_path_store")
 
 

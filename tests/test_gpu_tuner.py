@@ -39,7 +39,11 @@ def test_tune_gives_a_valid_choice_that_auto_contexts_use(S, n):
     assert c["resident"] in (0, 1) and c["resident_adjoint"] in (0, 1)
     assert 0.3 <= c["gen_cut"] <= 0.7 and c["tile_limit"] >= 0
     if n == 4:
-        assert c["gen_cut"] in (0.50, 0.53, 0.56, 0.59, 0.62)
+        assert (c["gen_parts"], c["gen_cut"]) in (
+            [(2, x) for x in (0.50, 0.53, 0.56, 0.59, 0.62)] +
+            [(3, x) for x in (0.43, 0.46, 0.49, 0.52)])
+    else:
+        assert c["gen_parts"] == 2
     if n >= 7:
         E = 4 ** n
         assert c["tile_limit"] in ((0, E, n * E) if n <= 9 else (1 << 17,))
@@ -111,3 +115,59 @@ def test_tile_limit_candidates_match_oracle(S, n, tiles):
         want = oracle.forward(n, c.gates, c.thetas, oracle.generator(n, k))
         assert np.abs(gens[k] - want).max() <= 1e-12
     assert abs(e - oracle.expect(n, c.gates, c.thetas, obs)) <= 1e-12 * l1(obs)
+
+
+@pytest.mark.parametrize("m,first", [(3000, 0.43), (3001, 0.52), (60200, 0.46)])
+def test_three_part_generator_split_matches_oracle(S, m, first):
+    """n = 4 with the plan cut in three (a first part of `first` of the passes,
+    two equal parts after it, the generators and rho_0 through the chain of
+    two transfer matrices): generators, <O> and the density matrix against
+    the oracle; the gradient (its own two-part adjoint) too."""
+    n = 4
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": first,
+                                      "tile_limit": 1 << 17, "tuned": 1, "gen_parts": 3})
+    c = W.layered_ansatz(n, m, seed=4410 + m)
+    obs = W.obs_chain(n)
+    s = S.Stab(n)
+    assert s.path_choice()["gen_parts"] == 3
+    s.apply_circuit(c.gates, c.thetas)
+    cut_pass, gen_units, _ = s.split_info()
+    n_pass = s.plan_info()[1]
+    n_mats = (gen_units - (n + 1)) // (4 ** n - 1)     # one transfer matrix per later part
+    assert n_mats == 2 and cut_pass == int(n_pass * first)
+    gens = layout.lib_to_paper(n, s.generators())
+    e = s.expect(obs)
+    rho = s.density_matrix()
+    eg, g = s.grad(obs)
+    s.close()
+    tol = (1e-10 if m >= 60000 else 1e-12)
+    assert np.abs(gens - oracle.generators(n, c.gates, c.thetas)).max() <= tol
+    ref = oracle.expect(n, c.gates, c.thetas, obs)
+    assert abs(e - ref) <= tol * l1(obs) and abs(eg - ref) <= tol * l1(obs)
+    # library rows and columns: bit q = qubit q; the oracle's: qubit 0 most significant
+    perm = [int(format(i, "0%db" % n)[::-1], 2) for i in range(2 ** n)]
+    assert np.abs(rho[np.ix_(perm, perm)] - oracle.density_matrix(n, c.gates, c.thetas)).max() \
+        <= tol
+    assert abs(np.trace(rho) - 1) <= tol
+    rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+    for gi in (rot[2], rot[len(rot) // 2]):
+        want = oracle.psr_grad_gate(n, c.gates, c.thetas, obs, gi)
+        assert abs(g[int(c.gates[gi]["param"])] - want) <= tol * l1(obs)
+
+
+def test_three_part_choice_on_a_short_plan_keeps_two_parts(S):
+    """Below three parts' minimum length the three-part choice cuts the plan
+    once, at gen_cut, and the results still match the oracle."""
+    n = 4
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": 0.46,
+                                      "tile_limit": 1 << 17, "tuned": 1, "gen_parts": 3})
+    c = W.layered_ansatz(n, 480, seed=4420)
+    s = S.Stab(n)
+    s.apply_circuit(c.gates, c.thetas)
+    cut_pass, gen_units, _ = s.split_info()
+    n_pass = s.plan_info()[1]
+    n_mats = (gen_units - (n + 1)) // (4 ** n - 1)
+    gens = layout.lib_to_paper(n, s.generators())
+    s.close()
+    assert 64 <= n_pass < 3 * 64 and n_mats == 1 and cut_pass == int(n_pass * 0.46)
+    assert np.abs(gens - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12

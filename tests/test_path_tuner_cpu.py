@@ -19,6 +19,7 @@ def L():
 def choice(**kw):
     c = _lib.StabPathChoice()
     c.resident, c.resident_adjoint, c.gen_cut, c.tile_limit, c.tuned = 1, 1, 0.5, 1 << 17, 1
+    c.gen_parts = 2
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -35,6 +36,7 @@ def test_defaults(L):
         c = _lib.StabPathChoice()
         assert L.stab_path_defaults(n, ctypes.byref(c)) == 0
         assert (c.resident, c.resident_adjoint, c.tile_limit, c.tuned) == (1, 1, 1 << 17, 0)
+        assert c.gen_parts == 2
         assert c.gen_cut == (0.56 if n == 4 else 0.5)
     c = _lib.StabPathChoice()
     assert L.stab_path_defaults(0, ctypes.byref(c)) == -2
@@ -64,7 +66,7 @@ def test_store_and_lookup_keyed_by_gpu_and_n(L):
 @pytest.mark.parametrize("bad", [dict(resident=2), dict(resident_adjoint=-1),
                                  dict(gen_cut=0.2), dict(gen_cut=0.71),
                                  dict(gen_cut=float("nan")), dict(tile_limit=-1),
-                                 dict(tuned=3)])
+                                 dict(tuned=3), dict(gen_parts=1), dict(gen_parts=4)])
 def test_store_rejects_values_out_of_range(L, bad):
     assert L.stab_path_store(b"GPU A", 4, ctypes.byref(choice(**bad))) == -1
     assert lookup(L, "GPU A", 4)[0] == -7
@@ -78,31 +80,33 @@ def test_store_rejects_bad_names_and_n(L):
 
 
 def test_file_round_trip(L, tmp_path):
-    L.stab_path_store(b"NVIDIA GB300", 4, ctypes.byref(choice(gen_cut=0.59)))
+    L.stab_path_store(b"NVIDIA GB300", 4, ctypes.byref(choice(gen_cut=0.46, gen_parts=3)))
     L.stab_path_store(b"NVIDIA GB300", 6, ctypes.byref(choice(resident=0, tile_limit=0)))
     L.stab_path_store(b"Other GPU", 8, ctypes.byref(choice(tile_limit=1 << 20, tuned=0)))
     f = str(tmp_path / "paths.tsv")
     assert L.stab_path_save(f.encode()) == 0
     lines = open(f).read().splitlines()
-    assert len(lines) == 3 and all(len(ln.split("\t")) == 7 for ln in lines)
+    assert len(lines) == 3 and all(len(ln.split("\t")) == 8 for ln in lines)
     L.stab_path_clear()
     assert lookup(L, "NVIDIA GB300", 4)[0] == -7
     assert L.stab_path_load(f.encode()) == 0
     rc, c = lookup(L, "NVIDIA GB300", 4)
-    assert rc == 0 and c.gen_cut == 0.59 and c.tuned == 1
+    assert rc == 0 and c.gen_cut == 0.46 and c.gen_parts == 3 and c.tuned == 1
     rc, c = lookup(L, "NVIDIA GB300", 6)
-    assert rc == 0 and c.resident == 0 and c.tile_limit == 0
+    assert rc == 0 and c.resident == 0 and c.tile_limit == 0 and c.gen_parts == 2
     rc, c = lookup(L, "Other GPU", 8)
     assert rc == 0 and c.tile_limit == 1 << 20 and c.tuned == 0
 
 
 def test_malformed_file_rejected_whole(L, tmp_path):
     L.stab_path_store(b"Kept", 5, ctypes.byref(choice(resident=0)))
-    good = "NVIDIA GB300\t4\t1\t1\t0.56\t131072\t1\n"
-    for bad in ("NVIDIA GB300\t4\t1\t1\t0.56\n",                  # fields missing
-                "NVIDIA GB300\t4\t1\t1\t0.56\t131072\t1\textra\n",  # a field too many
-                "NVIDIA GB300\t13\t1\t1\t0.56\t131072\t1\n",         # n out of range
-                "NVIDIA GB300\t4\t1\t1\t0.9\t131072\t1\n",           # cut out of range
+    good = "NVIDIA GB300\t4\t1\t1\t0.56\t131072\t1\t2\n"
+    for bad in ("NVIDIA GB300\t4\t1\t1\t0.56\n",                     # fields missing
+                "NVIDIA GB300\t4\t1\t1\t0.56\t131072\t1\n",           # the parts missing
+                "NVIDIA GB300\t4\t1\t1\t0.56\t131072\t1\t2\textra\n",  # a field too many
+                "NVIDIA GB300\t13\t1\t1\t0.56\t131072\t1\t2\n",         # n out of range
+                "NVIDIA GB300\t4\t1\t1\t0.9\t131072\t1\t2\n",           # cut out of range
+                "NVIDIA GB300\t4\t1\t1\t0.56\t131072\t1\t5\n",          # parts out of range
                 "no tab at all\n"):
         f = tmp_path / "bad.tsv"
         f.write_text(good + bad)
@@ -121,7 +125,8 @@ def test_cache_file_named_by_the_environment_is_read_at_first_lookup(tmp_path):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     good = tmp_path / "paths.tsv"
-    good.write_text("NVIDIA GB300\t6\t0\t0\t0.5\t131072\t1\nNVIDIA GB300\t4\t1\t1\t0.59\t131072\t1\n")
+    good.write_text("NVIDIA GB300\t6\t0\t0\t0.5\t131072\t1\t2\n"
+                    "NVIDIA GB300\t4\t1\t1\t0.59\t131072\t1\t2\n")
     bad = tmp_path / "bad.tsv"
     bad.write_text("NVIDIA GB300\t6\t0\t0\t0.5\n")
     code = ("import ctypes, sys; sys.path.insert(0, %r)\n"
