@@ -68,6 +68,12 @@ def units_per_step(c):
     return (c.n + 1) * c.m * 4 ** c.n
 
 
+# DRAM bytes read + written by the generator phase's launches (k_batch first
+# part + k_transfer_cols), per step, from one ncu capture of the 60,200-gate
+# n = 4 workload: keyed by (n, gates, cut pass, transfer matrices)
+GEN_TRAFFIC = {(4, 60200, 10535, 1): 3393024.0}
+
+
 def algorithmic_flops_generators(c):
     """FP64 flops of one generator launch: 6 per rotated pair (4^n / 4 pairs per
     rotation, per vector) and 15 per group for a composed 3x3 wire map."""
@@ -364,18 +370,21 @@ def run_ours(args):
         # the generators' persistent launch: n vectors through passes [0, cut)
         # and the 4^n - 1 transfer-matrix columns through [cut, P), then one
         # product; FP64 work executed per algorithmic flop, counted in passes
+        n_mats = (gen_units - (c.n + 1)) // (4 ** c.n - 1)
         if c.n == 4:
-            kernel = ("k_transfer_cols (255 columns, 2 per CTA) + k_batch (%d first-part "
-                      "units) + k_apply_transfer" % c.n)
+            kernel = ("k_transfer_cols (%d x 255 columns, %d per CTA) + k_batch (%d first-part "
+                      "units) + k_apply_transfer" % (n_mats, 2 * n_mats, c.n + 1))
         else:
             kernel = "k_batch (split: %d units) + k_apply_transfer" % gen_units
+        # every later part's columns together cover the passes after the cut once
         executed = ((c.n + 1) * cut + (4 ** c.n - 1) * (n_passes - cut)) / (c.n * n_passes)
-        active_sms = min(sms, c.n + 128 if c.n == 4 else gen_units)
-        note = ("one circuit: the generators split at pass %d of %d; the n first-part "
-                "vectors and the 4^n-1 basis columns run at once (%s); passes are "
-                "sequential within a vector" % (cut, n_passes,
-                                                 "two columns per CTA" if c.n == 4
-                                                 else "one CTA each"))
+        active_sms = min(sms, c.n + 1 + 128 if c.n == 4 else gen_units)
+        note = ("one circuit: the generators' first part ends at pass %d of %d, %d later "
+                "part(s) each through its transfer matrix; the n + 1 first-part vectors "
+                "and the basis columns run at once (%s); passes are sequential within a "
+                "vector" % (cut, n_passes, n_mats,
+                            "%d columns per CTA" % (2 * n_mats) if c.n == 4
+                            else "one CTA each"))
     else:
         kernel = "k_resident_stream (generators)"
         executed = 1.0
@@ -384,10 +393,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_dfma, "unit": "TFLOP/s",
                 "frac": achieved / peak_dfma,
                 # DRAM bytes of the generator phase's two launches from one ncu
-                # capture of this workload at this cut (k_batch 1,803,776 +
-                # k_transfer_cols 1,589,248 B read, the staged half-streams;
-                # 0 B written); another cut stages other streams
-                "traffic": 3393024.0 if (c.n == 4 and c.m == 60200 and cut == 10535) else None,
+                # capture of this workload with this split (the staged streams);
+                # another split stages other streams
+                "traffic": GEN_TRAFFIC.get((c.n, c.m, cut, n_mats if gen_units else 0)),
                 "kernel": kernel, "launch_ms": gen_avg_s * 1e3,
                 "peak_source": "of measured: FP64 DFMA chains on this GPU in this run "
                                "(stab_probe_fp64, best of 3; %d SMs)" % sms,
@@ -440,6 +448,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "vs_plain_form": plain,
         "roofline": roofline,
+        "path_choice": s.path_choice(),
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                    "reasons": clk.get("reasons"), "samples": clk.get("samples")},
         "expect": got,

@@ -597,7 +597,7 @@ int stab_path_load(const char *path);
 /* Measures the candidates for n qubits on CUDA device `device` now, stores
  * the result under that GPU's name and writes it to *out (may be NULL).
  * Candidates: n = 4: two parts with gen_cut in {0.50, 0.53, 0.56, 0.59, 0.62}
- * and three parts with gen_cut in {0.43, 0.46, 0.49, 0.52} (time of the
+ * and three parts with gen_cut in {0.43, 0.45, 0.47, 0.49, 0.51} (time of the
  * generators of a 24,000-gate probe); n = 5, 6: resident against streamed for
  * <O> and, separately, for the gradient (2,000-gate probe); n = 7 .. 9: tiles
  * against one launch per pass, for one vector (<O>) and for n vectors (the

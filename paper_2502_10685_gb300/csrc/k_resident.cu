@@ -193,6 +193,10 @@ __global__ void __launch_bounds__(256 * H, 1) k_transfer_cols(ColArgs a) {
     const bool work = (sx | sz) != 0u;
     // slot 1 = X, 2 = Y, 3 = Z: row slot - 1 of the composed map
     const uint32_t row = sx ? (sz ? 2u : 1u) : 3u;
+    // source index and sign through the last pull records walked, and the
+    // wire of the pass they preceded (-1: none yet)
+    uint32_t pj = 0, pneg = 0;
+    int pq = -1;
     for (int c = 0; c < n_chunks; ++c) {
         if (!st.wait(c, a.status)) return;
         const Rec *Rr = st.chunk(c);
@@ -203,9 +207,18 @@ __global__ void __launch_bounds__(256 * H, 1) k_transfer_cols(ColArgs a) {
             const uint32_t base = group_base32(g, N, q);
             const uint32_t i = base | (sz << q) | (sx << (N + q));
             if (n_pull > 0) {
-                // the pass's reads go through the preceding Clifford run
-                uint32_t neg = 0;
-                const uint32_t j = pull_recs(i, N, Rr + r + 1, n_pull, neg);
+                // the pass's reads go through the preceding Clifford run (the
+                // last one's index again when the run repeats on the same wire)
+                uint32_t neg = 0, j;
+                if (h.code == kPullRepeat && pq == q) {
+                    j = pj;
+                    neg = pneg;
+                } else {
+                    j = pull_recs(i, N, Rr + r + 1, n_pull, neg);
+                    pj = j;
+                    pneg = neg;
+                    pq = q;
+                }
                 nxt[i] = flip(cur[j], neg);
                 double *t = cur;
                 cur = nxt;
@@ -446,12 +459,15 @@ cudaError_t launch_apply_transfer_chain(const double *T, int n_mats, const doubl
 
 int transfer_cols_ctas(int n) { return n == kColN ? kColE / 2 : 0; }
 
+// more than half an SM's shared memory, so two of these CTAs never share an
+// SM (the kernel needs H halves' chunks and barriers + 4 KiB per half)
+constexpr size_t kColSmem = 116 * 1024;
+size_t transfer_cols_smem() { return kColSmem; }
+
 cudaError_t launch_transfer_cols(const ColArgs &a, int n, cudaStream_t st) {
     if (n != kColN || a.n_parts < 1 || a.n_parts > 2) return cudaErrorInvalidValue;
-    // more than half an SM's shared memory, so two of these CTAs never share
-    // an SM (the kernel needs H halves' chunks and barriers + 4 KiB per half)
-    const size_t smem = 116 * 1024;
-    static_assert(4 * kColHalf + 8 * kColE * sizeof(double) <= 116 * 1024, "column buffers");
+    const size_t smem = kColSmem;
+    static_assert(4 * kColHalf + 8 * kColE * sizeof(double) <= kColSmem, "column buffers");
     static SmemLimit lim2, lim4;
     cudaError_t e;
     if (a.n_parts == 1) {

@@ -224,6 +224,8 @@ struct ColArgs {
     int32_t *status;
 };
 cudaError_t launch_transfer_cols(const ColArgs &a, int n, cudaStream_t st);
+// Dynamic shared memory of a k_transfer_cols CTA (more than half an SM's).
+size_t transfer_cols_smem();
 // out_k = T_{n_mats-1} ... T_0 in_k at n = 4 (one k_apply_transfer per matrix,
 // tmp: 2 x n_vec x 4^n doubles between them); with dot_out (n_vec = 1) also
 // <O> = sum of terms' coeff x the result[idx], in term order.  out may be null.

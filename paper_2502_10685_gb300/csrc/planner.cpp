@@ -502,7 +502,8 @@ constexpr int kMaxPullPerPass = 64;
 struct StreamWriter {
     std::vector<Rec> *out;
     std::vector<int32_t> *enc;
-    int fill = 0;   // records used in the current chunk
+    int fill = 0;              // records used in the current chunk
+    std::vector<Rec> last;     // the previous pull pass's records, in stream order
 
     // Header of a pass with n_pull pull records and n_op op records; the
     // caller appends them.
@@ -523,9 +524,23 @@ struct StreamWriter {
         out->push_back(h);
         fill += need;
     }
-    // Pull records [b, e) of the applied two-qubit gates, last applied first.
+    // Pull records [b, e) of the applied two-qubit gates, last applied first;
+    // the pass's header (just written) gets kPullRepeat when they equal the
+    // previous pull pass's.
     void pulls(const Rec *b, const Rec *e) {
-        while (e != b) out->push_back(*--e);
+        if (e == b) return;
+        const size_t h = out->size() - 1;
+        bool same = (size_t)(e - b) == last.size();
+        for (size_t k = 0; same && k < last.size(); ++k) {
+            const Rec &p = *(e - 1 - k);
+            same = p.kind == last[k].kind && p.q == last[k].q && p.q1 == last[k].q1;
+        }
+        last.clear();
+        while (e != b) {
+            out->push_back(*--e);
+            last.push_back(out->back());
+        }
+        if (same) (*out)[h].code = kPullRepeat;
     }
     // R_END (the stream ends) or R_NEXT (another piece follows on the next
     // chunk; nothing when the piece is empty), then padding to the chunk end.

@@ -187,6 +187,10 @@ inline __device__ double *run_stream_reg4(Stager &st, int c0, int c1, double *cu
     int layout = 0;
     double v = cur[iA];
     double *rd = cur, *wr = nxt;   // last buffer read; the one the next write goes to
+    // this thread's source index and sign through the last pull records it
+    // walked, and the layout they were taken in (-1: none yet in this call)
+    uint32_t pj = 0, pneg = 0;
+    int play = -1;
     for (int c = c0; c < c1; ++c) {
         if (!st.wait(c, status)) return nullptr;
         const Rec *Rr = st.chunk(c);
@@ -199,8 +203,18 @@ inline __device__ double *run_stream_reg4(Stager &st, int c0, int c1, double *cu
             if (n_pull > 0 || want != layout) {
                 wr[layout ? iB : iA] = v;
                 __syncthreads();
-                uint32_t neg = 0;
-                const uint32_t j = pull_recs(want ? iB : iA, 4, Rr + r + 1, n_pull, neg);
+                uint32_t neg = 0, j;
+                if (n_pull > 0 && h.code == kPullRepeat && play == want) {
+                    j = pj;   // the same Clifford run as the last pull, same layout
+                    neg = pneg;
+                } else {
+                    j = pull_recs(want ? iB : iA, 4, Rr + r + 1, n_pull, neg);
+                    if (n_pull > 0) {
+                        pj = j;
+                        pneg = neg;
+                        play = want;
+                    }
+                }
                 v = flip(wr[j], neg);
                 double *tmp = rd;
                 rd = wr;

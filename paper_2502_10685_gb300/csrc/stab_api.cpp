@@ -153,7 +153,8 @@ struct stab_ctx {
     DevBuf lam2, tmp3;               // second-branch buffers of the split sweeps
     DevBuf dotbuf;                   // partial sums of the split expectation's inner product
     DevBuf gmid;                     // split resident adjoint: rho, then lambda, at the cut
-    DevBuf chainbuf;                 // n = 4 chain of transfer matrices: intermediate vectors
+    DevBuf chainbuf, chainbuf_e;     // n = 4 chain of transfer matrices: intermediate vectors
+                                     // of the context stream's products, of <O>'s (aux)
     // split resident sweeps (n <= 6; see split_units): transfer matrix of the
     // second part (n <= 4), first-part generators, meeting vectors, basis
     // terms, batch units (generators; expectation), unit counters
@@ -612,7 +613,12 @@ bool split_expect_ok(const stab_ctx *c) { return c->fwd.split >= 0; }
 
 int split_setup(stab_ctx *c, cudaStream_t s) {
     if (c->split_smem == 0) {
-        c->split_smem = batch_smem_bytes(c->n);
+        // n = 4: as much shared memory as a k_transfer_cols CTA takes, so a
+        // first-part unit (the critical path) never shares an SM's FP64 pipe
+        // with a CTA of columns running beside it
+        c->split_smem = transfer_cols_ctas(c->n) > 0
+                            ? std::max(batch_smem_bytes(c->n), transfer_cols_smem())
+                            : batch_smem_bytes(c->n);
         int occ = 0;
         CK(batch_occupancy(c->split_smem, &occ));
     }
@@ -749,9 +755,11 @@ int split_apply(stab_ctx *c, int first, int n_vec, double *out, const DevTerm *t
     const double *in = (const double *)c->avec.p + (size_t)first * E;
     if (chain_mode(c) && transfer_cols_ctas(c->n) > 0) {
         // n = 4: one matrix-vector product per part, through a scratch pair
-        RC(c->dalloc(c->chainbuf, 2 * (size_t)n_vec * E * 8, s));
+        // of the calling stream's own (<O> on aux may overlap the generators)
+        DevBuf &scratch = s == c->st ? c->chainbuf : c->chainbuf_e;
+        RC(c->dalloc(scratch, 2 * (size_t)n_vec * E * 8, s));
         CK(launch_apply_transfer_chain((const double *)c->tmat.p, (int)c->fwd.parts.size() - 1,
-                                       in, out, (double *)c->chainbuf.p, n_vec, c->n, terms,
+                                       in, out, (double *)scratch.p, n_vec, c->n, terms,
                                        n_terms, dot_out, s));
     } else if (chain_mode(c)) {
         CK(launch_apply_chain((const double *)c->tmat.p, (int)c->fwd.parts.size() - 1, in, out,
@@ -985,6 +993,7 @@ bool stream_actions(const std::vector<Rec> &s, const std::vector<int32_t> &enc,
         if (h.gate > 0) {
             Rec hh = h;
             hh.param = 0;
+            hh.code = 0;   // the repeated-pull hint is not an action
             out->push_back(hh);
             for (int k = 0; k < h.gate; ++k) {
                 const size_t i = r + 1 + (size_t)h.param + (size_t)k;
@@ -993,6 +1002,36 @@ bool stream_actions(const std::vector<Rec> &s, const std::vector<int32_t> &enc,
             }
         }
         r += len;
+    }
+    return false;
+}
+
+// Every pass header of a one-piece stream carries kPullRepeat exactly when
+// its pull records equal those of the previous pull pass.
+bool pull_repeat_flags_exact(const std::vector<Rec> &s) {
+    std::vector<Rec> last;
+    size_t r = 0;
+    while (r < s.size()) {
+        const Rec &h = s[r];
+        if (h.kind == R_END) return true;
+        if (h.kind == R_NEXT) {
+            r = (r / kChunkRecs + 1) * kChunkRecs;
+            continue;
+        }
+        if (h.kind != R_PASS || h.param < 0 || h.gate < 0) return false;
+        if (h.param > 0) {
+            bool same = (size_t)h.param == last.size();
+            for (int k = 0; same && k < h.param; ++k) {
+                const Rec &p = s[r + 1 + (size_t)k];
+                same = p.kind == last[(size_t)k].kind && p.q == last[(size_t)k].q &&
+                       p.q1 == last[(size_t)k].q1;
+            }
+            if (same != (h.code == kPullRepeat)) return false;
+            last.assign(s.begin() + (long)r + 1, s.begin() + (long)r + 1 + h.param);
+        } else if (h.code != 0) {
+            return false;
+        }
+        r += 1 + (size_t)h.param + (size_t)h.gate;
     }
     return false;
 }
@@ -1021,7 +1060,7 @@ int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_param
         std::vector<Rec> sa, sb;
         build_stream(a, backward, &sa);
         build_stream(b, backward, &sb);
-        ok = ok && same(sa, sb);
+        ok = ok && same(sa, sb) && pull_repeat_flags_exact(sa);
     }
     // one-piece against two-piece streams, compared as what a kernel applies:
     // pulls in application order, passes with ops (identity passes only pull)
@@ -1187,7 +1226,8 @@ int stab_destroy(stab_ctx *c) {
                       &c->rho, &c->tmp, &c->tmp2, &c->terms, &c->scal, &c->grad_rot,
                       &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3,
                       &c->dotbuf, &c->tmat, &c->avec, &c->rmid, &c->lmid, &c->bterms,
-                      &c->units_g, &c->units_e, &c->cnt, &c->gmid, &c->chainbuf};
+                      &c->units_g, &c->units_e, &c->cnt, &c->gmid, &c->chainbuf,
+                      &c->chainbuf_e};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);

@@ -131,6 +131,13 @@ struct Rec {            // 32 bytes
 };
 static_assert(sizeof(Rec) == 32, "Rec layout");
 
+// R_PASS header, code field: the pass's pull records equal those of the
+// stream's previous pull pass (a repeated Clifford run, as in layered
+// circuits).  A hint: a kernel that has pulled through that previous pass in
+// the same layout may reuse its source index and sign; any other reads the
+// records as usual.
+constexpr uint16_t kPullRepeat = 1;
+
 struct DevTerm {         // deduplicated observable term: index in the device layout
     double coeff;
     uint64_t idx;

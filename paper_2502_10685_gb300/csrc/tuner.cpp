@@ -292,7 +292,7 @@ int measure(int device, const stab_opts *like, int n, stab_path_choice *out) {
             double cut;
         };
         const Cand cands[] = {{2, 0.50}, {2, 0.53}, {2, 0.56}, {2, 0.59}, {2, 0.62},
-                              {3, 0.43}, {3, 0.46}, {3, 0.49}, {3, 0.52}};
+                              {3, 0.43}, {3, 0.45}, {3, 0.47}, {3, 0.49}, {3, 0.51}};
         for (const Cand &k : cands) {
             stab_path_choice c = d;
             c.gen_cut = k.cut;

@@ -454,3 +454,86 @@ def test_gradient_split_wire_path(stab, n, m):
     for gi in [rot[0], rot[-1]] + list(rng.choice(rot, size=2, replace=False)):
         want = oracle.psr_grad_gate(n, c.gates, c.thetas, obs, int(gi))
         assert abs(g[int(c.gates[gi]["param"])] - want) <= 1e-12 * obs_l1(obs)
+
+
+def ring_pattern_circuit(n_layers, seed):
+    """n = 4 layers of rotations whose wire order changes (so a layer's
+    Clifford run is pulled before wire 0, 1, 2 or 3), separated by Clifford
+    runs drawn from three rings in a pattern that repeats some runs and
+    alternates others: the streams' repeated-pull hints are set on some
+    passes and not on others, in both register layouts."""
+    rng = np.random.default_rng(seed)
+    rings = [[("CX", 0, 1), ("CX", 1, 2), ("CX", 2, 3), ("CX", 3, 0)],
+             [("CZ", 0, 2), ("CX", 3, 1)],
+             [("CX", 2, 0), ("CZ", 1, 3), ("CX", 0, 3)]]
+    orders = [(0, 1, 2, 3), (2, 3, 0, 1), (1, 0, 3, 2), (3, 2, 1, 0)]
+    pattern = [0, 0, 1, 0, 0, 2, 2, 1, 1, 0, 2, 0]
+    gates, n_params = [], 0
+    for L in range(n_layers):
+        order = orders[(L // 3) % len(orders)]
+        for q in order:
+            for op in ("RX", "RY", "RZ"):
+                gates.append((W.OPS[op], q, 0, 0, n_params))
+                n_params += 1
+        for op, a, b in rings[pattern[L % len(pattern)]]:
+            gates.append((W.OPS[op], a, b, 0, -1))
+    g = np.array(gates, dtype=W.GATE_DTYPE)
+    return W.Circuit(4, g, rng.uniform(0, 2 * np.pi, n_params))
+
+
+@pytest.mark.parametrize("form", ["resident", "split2", "split3"])
+def test_repeated_pull_reuse_matches_oracle(stab, form):
+    """A thread reuses its pull index and sign when a pass's Clifford run
+    repeats the previous one (register loop at n = 4, transfer-matrix
+    columns): generators, rho and <O> against the oracle on a circuit whose
+    runs repeat, alternate and precede different wires."""
+    from paper_2502_10685_gb300 import _lib
+    import torch
+    c = ring_pattern_circuit(240, seed=77)
+    obs = W.random_observable(4, 7, seed=78)
+    L1 = sum(abs(a) for a, _ in obs)
+    name = torch.cuda.get_device_name(0)
+    if form != "resident":
+        stab.stab_path_store(name, 4, {"resident": 1, "resident_adjoint": 1,
+                                       "gen_cut": 0.56 if form == "split2" else 0.47,
+                                       "tile_limit": 1 << 17, "tuned": 1,
+                                       "gen_parts": 2 if form == "split2" else 3})
+    try:
+        s = stab.Stab(4, kernel="resident" if form == "resident" else "auto")
+        s.apply_circuit(c.gates, c.thetas)
+        if form != "resident":
+            assert s.split_info()[0] > 0
+        gens = layout.lib_to_paper(4, s.generators())
+        e = s.expect(obs)
+        rho = s.density_matrix()
+        s.close()
+    finally:
+        _lib.load().stab_path_clear()
+    assert np.abs(gens - oracle.generators(4, c.gates, c.thetas)).max() <= 1e-12
+    assert abs(e - oracle.expect(4, c.gates, c.thetas, obs)) <= 1e-12 * L1
+    perm = _bitrev_perm(4)
+    assert np.abs(rho[np.ix_(perm, perm)] - oracle.density_matrix(4, c.gates, c.thetas)).max() \
+        <= 1e-12
+
+
+def test_repeated_pull_reuse_in_served_slices(stab):
+    """Serving slices start mid-stream, where a repeated-pull hint refers to a
+    pass of an earlier slice: the kernel must walk the records then.  n = 4
+    requests of the ring-pattern circuit through the iteration engine (small
+    slices) equal the oracle."""
+    c = ring_pattern_circuit(160, seed=79)
+    obs = W.random_observable(4, 5, seed=80)
+    L1 = sum(abs(a) for a, _ in obs)
+    srv = stab.Server(max_active=4, engine="iterate", iter_chunks=2)
+    ids = [srv.submit(c, kind, obs) for kind in ("expect", "grad", "expect")]
+    res = [srv.wait(i, timeout_s=300) for i in ids]
+    srv.close()
+    want = oracle.expect(4, c.gates, c.thetas, obs)
+    rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+    for r in res:
+        assert r["status"] == 0
+        assert abs(r["expect"] - want) <= 1e-12 * L1
+    g = res[1]["grads"]
+    for gi in (rot[1], rot[len(rot) // 2], rot[-3]):
+        assert abs(g[int(c.gates[gi]["param"])] - oracle.psr_grad_gate(4, c.gates, c.thetas, obs, gi)) \
+            <= 1e-12 * L1

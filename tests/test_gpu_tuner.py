@@ -41,7 +41,7 @@ def test_tune_gives_a_valid_choice_that_auto_contexts_use(S, n):
     if n == 4:
         assert (c["gen_parts"], c["gen_cut"]) in (
             [(2, x) for x in (0.50, 0.53, 0.56, 0.59, 0.62)] +
-            [(3, x) for x in (0.43, 0.46, 0.49, 0.52)])
+            [(3, x) for x in (0.43, 0.45, 0.47, 0.49, 0.51)])
     else:
         assert c["gen_parts"] == 2
     if n >= 7:
@@ -171,3 +171,36 @@ def test_three_part_choice_on_a_short_plan_keeps_two_parts(S):
     s.close()
     assert 64 <= n_pass < 3 * 64 and n_mats == 1 and cut_pass == int(n_pass * 0.46)
     assert np.abs(gens - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12
+
+
+def test_three_part_split_overlapped_async_calls_match_oracle(S):
+    """The bench's step with no host synchronisation between the calls: new
+    angles from device memory, the generators (context stream) and <O>
+    (auxiliary stream, through the same transfer matrices) overlap; each
+    step's generators and <O> match the oracle for that step's angles."""
+    import torch
+    n = 4
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": 0.49,
+                                      "tile_limit": 1 << 17, "tuned": 1, "gen_parts": 3})
+    c = W.layered_ansatz(n, 3000, seed=4430)
+    obs = W.obs_chain(n)
+    s = S.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    s.set_observable(obs)
+    rng = np.random.default_rng(4431)
+    thetas = [rng.uniform(0, 2 * np.pi, c.n_params) for _ in range(3)]
+    dev = [torch.tensor(t, dtype=torch.float64, device="cuda") for t in thetas]
+    outs = torch.zeros(len(dev), 8, dtype=torch.float64, device="cuda")
+    gens = []
+    for k, th in enumerate(dev):
+        s.set_params(th)
+        s.run_generators()
+        s.expect_async(outs[k])
+        gens.append(s.generators())           # synchronises the context stream only
+    torch.cuda.synchronize()
+    s.close()
+    for k, th in enumerate(thetas):
+        want = oracle.expect(n, c.gates, th, obs)
+        assert abs(float(outs[k, 0].item()) - want) <= 1e-12 * l1(obs), k
+        assert np.abs(layout.lib_to_paper(n, gens[k]) - oracle.generators(n, c.gates, th)).max() \
+            <= 1e-12, k

@@ -45,7 +45,9 @@ def test_chunked_planner_equals_sequential():
     # host-only: long gate lists are planned in parallel chunks; the plan and
     # its instruction streams must be byte-identical to the sequential ones,
     # and streams built as two pieces at once must apply the same pulls and
-    # passes in the same order as the one-piece streams
+    # passes in the same order as the one-piece streams; a pass header is
+    # flagged as a repeated pull exactly when its pull records equal the
+    # previous pull pass's
     import numpy as np
     from paper_2502_10685_gb300 import _lib, workloads as W
     L = _lib.load()
