@@ -71,7 +71,7 @@ def units_per_step(c):
 # DRAM bytes read + written by the generator phase's launches (k_batch first
 # part + k_transfer_cols), per step, from one ncu capture of the 60,200-gate
 # n = 4 workload: keyed by (n, gates, cut pass, transfer matrices)
-GEN_TRAFFIC = {(4, 60200, 10535, 1): 3393024.0}
+GEN_TRAFFIC = {(4, 60200, 10535, 1): 3393024.0, (4, 60200, 9218, 2): 3195136.0}
 
 
 def algorithmic_flops_generators(c):
@@ -1049,6 +1049,35 @@ def run_fp64_peak(args):
     return 0
 
 
+def run_pass_latency(args):
+    """Cycles per wire pass of the n = 4 register loop's pieces (one CTA, the
+    SM's cycle counter; stab_probe_pass): what bounds a lone vector of the
+    split generator sweep, against the FP64 pipe's six warp instructions per
+    SMSP per pass."""
+    import torch
+    from paper_2502_10685_gb300 import stab
+    dev = torch.device("cuda", 0)
+    clocks = ClockSampler(gpu_uuid(dev))
+    clocks.start()
+    time.sleep(0.3)
+    cases = [("register passes", 0, 256), ("+ layout switch every 2nd pass", 1, 256),
+             ("+ four-CNOT pull walk every 4th pass", 2, 256),
+             ("register passes, 128 threads", 0, 128),
+             ("two entries per thread, one barrier per 4 passes (pull merged)", 3, 128)]
+    rows = []
+    for name, pattern, threads in cases:
+        runs = [stab.stab_probe_pass(pattern, threads, 40000) for _ in range(3)]
+        rows.append({"case": name, "pattern": pattern, "threads": threads,
+                     "clk_per_pass": statistics.median(runs), "runs": runs})
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": "cycles per wire pass", "value": rows[2]["clk_per_pass"], "unit": "clk",
+        "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "pass-latency", "passes": 40000, "ctas": 1},
+        "rows": rows, "clocks": clk}))
+    return 0
+
+
 def run_paper_sweep(args):
     """The paper's experiment shape (Sec. V): time to the density matrix of
     the W_chain + ZXZ ansatz, n = 2, 3, 4, over #Layers (Repeats = 1) and
@@ -1269,6 +1298,8 @@ def main():
         return run_expect(args)
     if args.workload == "fp64-peak":
         return run_fp64_peak(args)
+    if args.workload == "pass-latency":
+        return run_pass_latency(args)
     if args.workload == "paper-sweep":
         return run_paper_sweep(args)
     if args.workload == "sparse-n32":

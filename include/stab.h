@@ -628,6 +628,24 @@ int stab_path_current(stab_ctx *ctx, stab_path_choice *out);
  * STAB_E_RANGE (iters), STAB_E_CUDA. */
 int stab_probe_fp64(int kind, int64_t iters, double *tflops, double *ms);
 
+/* Latency of the pieces of the n = 4 register pass loop (the loop a lone
+ * vector of a split generator sweep runs), on one CTA of the current device,
+ * by the SM's cycle counter.  A wire pass here is three shuffles that gather
+ * a lane's group (I, X, Y, Z slots of one wire in a warp's lanes) and the
+ * three dependent FP64 instructions of its row of a 3x3 rotation (Sec. III,
+ * the per-wire map of Rx, Ry, Rz); the map is orthogonal, so values stay
+ * bounded.  pattern 0: `passes` wire passes, one vector entry per thread;
+ * 1: plus a switch of the register layout through shared memory (write, one
+ * barrier, read) before every second pass; 2: plus a pull through a
+ * four-CNOT ring (Table I), walked record by record, at every fourth pass;
+ * 3 (threads = 128): two entries per thread, three register passes and one
+ * shared-memory pass merged with the ring's pull per four passes.  threads:
+ * 256 (a 4^4 vector) or 128.  passes: a multiple of 4 in [4, 2^24].  Writes
+ * the cycles per pass to *clk_per_pass.  Allocates under 3 KiB of device
+ * memory for the call.  Errors: STAB_E_INVAL (pattern, threads, NULL),
+ * STAB_E_RANGE (passes), STAB_E_CUDA. */
+int stab_probe_pass(int pattern, int threads, int64_t passes, double *clk_per_pass);
+
 #ifdef __cplusplus
 }
 #endif

@@ -163,6 +163,7 @@ def load(build_if_missing: bool = True):
                                             ctypes.POINTER(StabSparseInfo)]),
             "stab_sparse_order_history": (i32, [vp, vp, i64, ctypes.POINTER(i64)]),
             "stab_probe_fp64": (i32, [i32, i64, dp, dp]),
+            "stab_probe_pass": (i32, [i32, i32, i64, dp]),
             "stab_path_defaults": (i32, [i32, ctypes.POINTER(StabPathChoice)]),
             "stab_path_lookup": (i32, [ctypes.c_char_p, i32, ctypes.POINTER(StabPathChoice)]),
             "stab_path_store": (i32, [ctypes.c_char_p, i32, ctypes.POINTER(StabPathChoice)]),

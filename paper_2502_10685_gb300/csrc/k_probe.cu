@@ -1,4 +1,4 @@
-// k_probe.cu -- FP64 throughput probes.
+// k_probe.cu -- FP64 throughput probes and a pass-latency probe.
 //
 // The rotation passes of this library are bound by the FP64 pipe, not by
 // HBM (a pair costs three FMAs on 16 bytes that stay on chip for many
@@ -7,9 +7,19 @@
 // hand: independent DFMA chains in every thread of a full-occupancy grid, and
 // independent chains of the FP64 matrix instruction (8x8x4 per warp), whose
 // rate shows whether the tensor path would beat plain DFMA for this work.
+//
+// The pass-latency probe times, on one CTA and with the SM's cycle counter,
+// the pieces of the n = 4 register pass loop that bounds a lone vector (the
+// first part of a split generator sweep): a wire pass on a wire whose group
+// sits in a warp's lanes (three shuffles, then three dependent FP64
+// instructions per lane), a switch of the register layout through shared
+// memory, and a pull through a four-CNOT ring walked record by record.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "../../include/stab.h"
+#include "device_ops.cuh"
 #include "launch.h"
 
 namespace stab {
@@ -64,11 +74,159 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_dmma(int64_t iters, dou
     if (s == -1.0) sink[threadIdx.x] = s;
 }
 
+// ---------------------------------------------------------------- pass latency
+
+// The four index bits of lane/thread t in the two layouts of the probe: the
+// identity, and the low and high nibbles swapped (the two wire pairs trade
+// lane and warp positions, as in the register loop's layouts).
+__device__ __forceinline__ uint32_t probe_idx(uint32_t t, int layout) {
+    return layout ? (((t & 15u) << 4) | (t >> 4)) : t;
+}
+
+__device__ __forceinline__ double probe_row(const double *m, uint32_t slot, double x, double y,
+                                            double z) {
+    const double *mm = m + 3 * (slot - 1u);
+    return fma(mm[2], z, fma(mm[1], y, mm[0] * x));
+}
+
+// A wire pass on the lane-bit pair sh, sh + 1 of a warp: slot 0 (I) keeps its
+// entry, X, Y and Z get their row of the 3x3 map.
+__device__ __forceinline__ void probe_lane_pass(double &v, uint32_t lane, int sh,
+                                                const double *m) {
+    const uint32_t zb = (lane >> sh) & 1u, xb = (lane >> (sh + 1)) & 1u;
+    const uint32_t base = lane & ~(3u << sh);
+    const double x = __shfl_sync(0xffffffffu, v, base | (2u << sh));
+    const double y = __shfl_sync(0xffffffffu, v, base | (3u << sh));
+    const double z = __shfl_sync(0xffffffffu, v, base | (1u << sh));
+    if (xb | zb) v = probe_row(m, xb ? (zb ? 2u : 1u) : 3u, x, y, z);
+}
+
+// Patterns 0..2: one entry of a 4^4 vector per thread (256 threads; 128 runs
+// half a vector), `passes` wire passes alternating between the two lane-bit
+// pairs; 1 adds a layout switch (write, barrier, read) before every second
+// pass, 2 also walks a four-CNOT ring's pull records before every fourth.
+// Pattern 3 (128 threads): two entries per thread, so three wires' groups
+// lie within a warp (lane bits and the register); per layer three register
+// passes, then the fourth wire's pass read through the ring's pull from
+// shared memory -- one barrier per layer.  The map is a rotation, so every
+// entry stays bounded.  clk[0] = the CTA's cycles over the timed loop.
+template <int PATTERN>
+__global__ void k_probe_pass(int64_t passes, const double *mtab, double *sink, long long *clk) {
+    __shared__ double buf[2][256];
+    __shared__ Rec recs[4];
+    __shared__ double m[9];
+    const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
+    if (t < 9) m[t] = mtab[t];
+    if (t < 4) {
+        Rec r{};
+        r.kind = R_CX;
+        r.q = (uint8_t)t;
+        r.q1 = (uint8_t)((t + 1) & 3u);
+        recs[t] = r;
+    }
+    for (uint32_t i = t; i < 512u; i += blockDim.x) (&buf[0][0])[i] = 0.0;
+    double v = (t == 5u) ? 1.0 : 0.0, v1 = (t == 9u) ? 0.5 : 0.0;
+    __syncthreads();
+    const long long t0 = clock64();
+    if constexpr (PATTERN < 3) {
+        int layout = 0;
+        for (int64_t it = 0; it < passes; ++it) {
+            if (PATTERN >= 1 && (it & 1) == 0) {
+                double *b = buf[(it >> 1) & 1];
+                b[probe_idx(t, layout)] = v;
+                __syncthreads();
+                uint32_t j = probe_idx(t, layout ^ 1), neg = 0;
+                if (PATTERN == 2 && (it & 3) == 0) j = pull_recs(j, 4, recs, 4, neg);
+                v = flip(b[j], neg);
+                layout ^= 1;
+            }
+            probe_lane_pass(v, lane, 2 * (int)(it & 1), m);
+        }
+    } else {
+        const uint32_t i0 = lane | (w << 6), i1 = i0 | 32u;
+        for (int64_t it = 0; it < passes; it += 4) {
+            probe_lane_pass(v, lane, 0, m);
+            probe_lane_pass(v1, lane, 0, m);
+            probe_lane_pass(v, lane, 2, m);
+            probe_lane_pass(v1, lane, 2, m);
+            {   // lane bit 4 = x, the register = z
+                const double o0 = __shfl_xor_sync(0xffffffffu, v, 16);
+                const double o1 = __shfl_xor_sync(0xffffffffu, v1, 16);
+                const bool xl = (lane >> 4) & 1u;
+                const double X = xl ? v : o0, Y = xl ? v1 : o1, Z = xl ? o1 : v1;
+                if (xl) v = probe_row(m, 1u, X, Y, Z);
+                v1 = probe_row(m, xl ? 2u : 3u, X, Y, Z);
+            }
+            double *b = buf[(it >> 2) & 1];
+            b[i0] = v;
+            b[i1] = v1;
+            __syncthreads();
+            uint32_t n0 = 0, n1 = 0;
+            const uint32_t j0 = pull_recs(i0, 4, recs, 4, n0), j1 = pull_recs(i1, 4, recs, 4, n1);
+            // the fourth wire (bits 6 = z, 7 = x) at the pulled positions
+            const uint32_t g0 = j0 & 63u, s0 = (j0 >> 6) & 3u, g1 = j1 & 63u, s1 = (j1 >> 6) & 3u;
+            const double x0 = b[g0 | 128u], y0 = b[g0 | 192u], z0 = b[g0 | 64u], e0 = b[g0];
+            const double x1 = b[g1 | 128u], y1 = b[g1 | 192u], z1 = b[g1 | 64u], e1 = b[g1];
+            // slot code (bit 0 = z, bit 1 = x): 0 I, 1 Z, 2 X, 3 Y -> map row X 1, Y 2, Z 3
+            v = flip(s0 ? probe_row(m, s0 == 2u ? 1u : (s0 == 3u ? 2u : 3u), x0, y0, z0) : e0, n0);
+            v1 = flip(s1 ? probe_row(m, s1 == 2u ? 1u : (s1 == 3u ? 2u : 3u), x1, y1, z1) : e1, n1);
+        }
+    }
+    const long long t1 = clock64();
+    // never true for a rotation's bounded values; keeps the loop live
+    if (v + v1 == -1e300) sink[t] = v;
+    if (t == 0) clk[0] = t1 - t0;
+}
+
 }  // namespace
 
 }  // namespace stab
 
 using namespace stab;
+
+extern "C" int stab_probe_pass(int pattern, int threads, int64_t passes, double *clk_per_pass) {
+    if (!clk_per_pass || pattern < 0 || pattern > 3 || (threads != 128 && threads != 256) ||
+        (pattern == 3 && threads != 128))
+        return STAB_E_INVAL;
+    if (passes < 4 || passes > ((int64_t)1 << 24) || passes % 4 != 0) return STAB_E_RANGE;
+    cudaStream_t st = nullptr;
+    double *dm = nullptr, *sink = nullptr;
+    long long *dclk = nullptr;
+    long long hclk = 0;
+    // a rotation by 0.7 rad about the third axis
+    const double c = std::cos(0.7), s = std::sin(0.7);
+    const double hm[9] = {c, -s, 0.0, s, c, 0.0, 0.0, 0.0, 1.0};
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dm, sizeof hm, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&sink, 256 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dclk, sizeof(long long), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dm, hm, sizeof hm, cudaMemcpyHostToDevice, st);
+    auto launch = [&](int64_t n) {
+        switch (pattern) {
+        case 0: k_probe_pass<0><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
+        case 1: k_probe_pass<1><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
+        case 2: k_probe_pass<2><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
+        default: k_probe_pass<3><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
+        }
+        return cudaGetLastError();
+    };
+    if (e == cudaSuccess) e = launch(4);        // warm-up: code loaded
+    if (e == cudaSuccess) e = launch(passes);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hclk, dclk, sizeof hclk, cudaMemcpyDeviceToHost, st);
+    if (dm) cudaFreeAsync(dm, st);
+    if (sink) cudaFreeAsync(sink, st);
+    if (dclk) cudaFreeAsync(dclk, st);
+    const cudaError_t e2 = st ? cudaStreamSynchronize(st) : cudaSuccess;
+    if (st) cudaStreamDestroy(st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        record_cuda_error(e);
+        return STAB_E_CUDA;
+    }
+    *clk_per_pass = (double)hclk / (double)passes;
+    return STAB_OK;
+}
 
 extern "C" int stab_probe_fp64(int kind, int64_t iters, double *tflops, double *ms) {
     if (!tflops || (kind != 0 && kind != 1)) return STAB_E_INVAL;

@@ -196,6 +196,17 @@ def stab_probe_fp64(kind: str = "dfma", iters: int = 8192) -> Tuple[float, float
     return tf.value, ms.value
 
 
+def stab_probe_pass(pattern: int, threads: int = 256, passes: int = 40000) -> float:
+    """Cycles per pass of the n = 4 register pass loop's pieces on one CTA:
+    pattern 0 register passes, 1 + a layout switch every second pass, 2 + a
+    four-CNOT pull every fourth, 3 two entries per thread and one barrier per
+    four passes (threads = 128)."""
+    clk = ctypes.c_double()
+    check(_lib.load().stab_probe_pass(int(pattern), int(threads), int(passes),
+                                      ctypes.byref(clk)), "stab_probe_pass")
+    return clk.value
+
+
 def _choice_dict(c: StabPathChoice) -> dict:
     return {"resident": c.resident, "resident_adjoint": c.resident_adjoint,
             "gen_cut": c.gen_cut, "tile_limit": c.tile_limit, "tuned": c.tuned,

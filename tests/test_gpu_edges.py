@@ -231,6 +231,20 @@ def test_fp64_probe_measures_a_plausible_rate(stab):
     assert 2.5 < ms2 / ms1 < 6.0
 
 
+def test_pass_probe_measures_plausible_latencies(stab):
+    """The register pass loop's pieces: every pattern gives a positive cycle
+    count per pass, a wire pass costs at least the three dependent FP64
+    instructions' latency, and adding shared-memory round trips to the same
+    passes does not make them cheaper."""
+    c0 = stab.stab_probe_pass(0, 256, 4000)
+    c1 = stab.stab_probe_pass(1, 256, 4000)
+    c2 = stab.stab_probe_pass(2, 256, 4000)
+    c3 = stab.stab_probe_pass(3, 128, 4000)
+    for c in (c0, c1, c2, c3, stab.stab_probe_pass(0, 128, 4000)):
+        assert 30.0 < c < 1e5
+    assert c1 >= 0.95 * c0 and c2 >= 0.95 * c1
+
+
 def test_no_device_memory_growth_over_repeated_use(stab):
     """Contexts, batches and servers created, used and destroyed over and over:
     every block taken through the PyTorch allocator hooks is handed back
