@@ -1063,7 +1063,8 @@ def run_pass_latency(args):
     cases = [("register passes", 0, 256), ("+ layout switch every 2nd pass", 1, 256),
              ("+ four-CNOT pull walk every 4th pass", 2, 256),
              ("register passes, 128 threads", 0, 128),
-             ("two entries per thread, one barrier per 4 passes (pull merged)", 3, 128)]
+             ("two entries per thread, one barrier per 4 passes (pull merged)", 3, 128),
+             ("two-wire fused passes (per wire pass)", 4, 256)]
     rows = []
     for name, pattern, threads in cases:
         runs = [stab.stab_probe_pass(pattern, threads, 40000) for _ in range(3)]

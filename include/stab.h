@@ -639,7 +639,9 @@ int stab_probe_fp64(int kind, int64_t iters, double *tflops, double *ms);
  * barrier, read) before every second pass; 2: plus a pull through a
  * four-CNOT ring (Table I), walked record by record, at every fourth pass;
  * 3 (threads = 128): two entries per thread, three register passes and one
- * shared-memory pass merged with the ring's pull per four passes.  threads:
+ * shared-memory pass merged with the ring's pull per four passes; 4: two-wire
+ * fused passes (each 16-entry block of two wires through (1+M) (x) (1+M): up
+ * to nine products per output, counted as two wire passes).  threads:
  * 256 (a 4^4 vector) or 128.  passes: a multiple of 4 in [4, 2^24].  Writes
  * the cycles per pass to *clk_per_pass.  Allocates under 3 KiB of device
  * memory for the call.  Errors: STAB_E_INVAL (pattern, threads, NULL),

@@ -105,6 +105,12 @@ __device__ __forceinline__ void probe_lane_pass(double &v, uint32_t lane, int sh
 // half a vector), `passes` wire passes alternating between the two lane-bit
 // pairs; 1 adds a layout switch (write, barrier, read) before every second
 // pass, 2 also walks a four-CNOT ring's pull records before every fourth.
+// Pattern 4 (256 threads): two-wire fused passes -- each lane's 16-entry
+// block (the (z, x) bits of two wires in lane bits 0..3) goes through
+// (1 + M) (x) (1 + M) in one pass: up to nine source lanes and coefficients
+// per output (three with one I slot, one for I I), taken warp-uniformly as
+// nine shuffles and nine dependent FP64 instructions; `passes` counts wire
+// passes, two per fused pass.
 // Pattern 3 (128 threads): two entries per thread, so three wires' groups
 // lie within a warp (lane bits and the register); per layer three register
 // passes, then the fourth wire's pass read through the ring's pull from
@@ -127,8 +133,55 @@ __global__ void k_probe_pass(int64_t passes, const double *mtab, double *sink, l
     for (uint32_t i = t; i < 512u; i += blockDim.x) (&buf[0][0])[i] = 0.0;
     double v = (t == 5u) ? 1.0 : 0.0, v1 = (t == 9u) ? 0.5 : 0.0;
     __syncthreads();
+    // pattern 4: per block slot (s0 + 4 s1; slot code 0 I, 1 Z, 2 X, 3 Y by
+    // the (z, x) bits), nine (source slot, coefficient) terms, zero-padded
+    __shared__ uint32_t fsrc[16][9];
+    __shared__ double fcoef[16][9];
+    if (PATTERN == 4 && t < 16) {
+        const uint32_t s0 = t & 3u, s1 = t >> 2;
+        // map row of a slot code: X 1, Y 2, Z 3 (row - 1 indexes m)
+        auto row = [](uint32_t sc) { return sc == 2u ? 0u : (sc == 3u ? 1u : 2u); };
+        const uint32_t xyz[3] = {2u, 3u, 1u};   // slot codes of X, Y, Z
+        int k = 0;
+        if (s0 == 0u && s1 == 0u) {
+            fsrc[t][k] = t;
+            fcoef[t][k++] = 1.0;
+        } else if (s0 == 0u) {
+            for (int b = 0; b < 3; ++b) {
+                fsrc[t][k] = xyz[b] << 2;
+                fcoef[t][k++] = m[3 * row(s1) + (uint32_t)b];
+            }
+        } else if (s1 == 0u) {
+            for (int a = 0; a < 3; ++a) {
+                fsrc[t][k] = xyz[a];
+                fcoef[t][k++] = m[3 * row(s0) + (uint32_t)a];
+            }
+        } else {
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    fsrc[t][k] = xyz[a] | (xyz[b] << 2);
+                    fcoef[t][k++] = m[3 * row(s0) + (uint32_t)a] * m[3 * row(s1) + (uint32_t)b];
+                }
+        }
+        for (; k < 9; ++k) {
+            fsrc[t][k] = t;
+            fcoef[t][k] = 0.0;
+        }
+    }
+    __syncthreads();
     const long long t0 = clock64();
-    if constexpr (PATTERN < 3) {
+    if constexpr (PATTERN == 4) {
+        const uint32_t slot = lane & 15u, base = lane & 16u;
+        for (int64_t it = 0; it < passes; it += 2) {
+            double val[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) val[k] = __shfl_sync(0xffffffffu, v, base | fsrc[slot][k]);
+            double acc = fcoef[slot][0] * val[0];
+#pragma unroll
+            for (int k = 1; k < 9; ++k) acc = fma(fcoef[slot][k], val[k], acc);
+            v = acc;
+        }
+    } else if constexpr (PATTERN < 3) {
         int layout = 0;
         for (int64_t it = 0; it < passes; ++it) {
             if (PATTERN >= 1 && (it & 1) == 0) {
@@ -185,7 +238,7 @@ __global__ void k_probe_pass(int64_t passes, const double *mtab, double *sink, l
 using namespace stab;
 
 extern "C" int stab_probe_pass(int pattern, int threads, int64_t passes, double *clk_per_pass) {
-    if (!clk_per_pass || pattern < 0 || pattern > 3 || (threads != 128 && threads != 256) ||
+    if (!clk_per_pass || pattern < 0 || pattern > 4 || (threads != 128 && threads != 256) ||
         (pattern == 3 && threads != 128))
         return STAB_E_INVAL;
     if (passes < 4 || passes > ((int64_t)1 << 24) || passes % 4 != 0) return STAB_E_RANGE;
@@ -206,7 +259,8 @@ extern "C" int stab_probe_pass(int pattern, int threads, int64_t passes, double 
         case 0: k_probe_pass<0><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
         case 1: k_probe_pass<1><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
         case 2: k_probe_pass<2><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
-        default: k_probe_pass<3><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
+        case 3: k_probe_pass<3><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
+        default: k_probe_pass<4><<<1, threads, 0, st>>>(n, dm, sink, dclk); break;
         }
         return cudaGetLastError();
     };

@@ -200,7 +200,8 @@ def stab_probe_pass(pattern: int, threads: int = 256, passes: int = 40000) -> fl
     """Cycles per pass of the n = 4 register pass loop's pieces on one CTA:
     pattern 0 register passes, 1 + a layout switch every second pass, 2 + a
     four-CNOT pull every fourth, 3 two entries per thread and one barrier per
-    four passes (threads = 128)."""
+    four passes (threads = 128), 4 two-wire fused passes (cycles per wire
+    pass, two per fused pass)."""
     clk = ctypes.c_double()
     check(_lib.load().stab_probe_pass(int(pattern), int(threads), int(passes),
                                       ctypes.byref(clk)), "stab_probe_pass")

@@ -240,7 +240,7 @@ def test_pass_probe_measures_plausible_latencies(stab):
     c1 = stab.stab_probe_pass(1, 256, 4000)
     c2 = stab.stab_probe_pass(2, 256, 4000)
     c3 = stab.stab_probe_pass(3, 128, 4000)
-    for c in (c0, c1, c2, c3, stab.stab_probe_pass(0, 128, 4000)):
+    for c in (c0, c1, c2, c3, stab.stab_probe_pass(0, 128, 4000), stab.stab_probe_pass(4, 256, 4000)):
         assert 30.0 < c < 1e5
     assert c1 >= 0.95 * c0 and c2 >= 0.95 * c1
 

@@ -123,7 +123,7 @@ def test_pass_probe_rejects_bad_arguments_on_the_host():
     from paper_2502_10685_gb300 import _lib
     L = _lib.load()
     c = ctypes.c_double()
-    for pattern, threads in ((4, 256), (-1, 256), (0, 64), (0, 512), (3, 256)):
+    for pattern, threads in ((5, 256), (-1, 256), (0, 64), (0, 512), (3, 256)):
         assert L.stab_probe_pass(pattern, threads, 1024, ctypes.byref(c)) == -1
     assert L.stab_probe_pass(0, 256, 1024, None) == -1
     for passes in (0, 2, 1026, (1 << 24) + 4):
