@@ -121,8 +121,10 @@ __device__ void serve_unit(const ServeUnit &U, int smem_buf, Stager &st, unsigne
     else serve_pair<N>(U, smem_buf, st, smem, status, ok);
 }
 
-// Four CTAs per SM at most: the register bound matches the batch kernel's.
-__global__ void __launch_bounds__(kServeThreads, 4) k_serve(ServeArgs a) {
+// Three CTAs per SM: 80 registers, enough for every unit form without
+// spilling (at four CTAs per SM the 64-register bound spilled, and the n <= 8
+// serving trace ran about 8 % slower).
+__global__ void __launch_bounds__(kServeThreads, 3) k_serve(ServeArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_unit;
     Stager st;
