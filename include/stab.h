@@ -372,7 +372,10 @@ typedef struct stab_result {
 
 /* Admission footprint of a request: max(n 4^n 8, 4^n 8 x (4 for <O>, 12 for
  * a gradient: the vectors of the split sweeps)) bytes plus 96 bytes per gate,
- * plus the streamed adjoint's per-CTA partial sums above n = 6. */
+ * plus, for a gradient, the adjoint's partial dot sums: per CTA of the
+ * streamed sweep above n = 6, per thread of the resident sweep at n <= 5
+ * (8 bytes x gates x 32, 32, 32, 64, 256 threads at n = 1..5, while that
+ * stays within 256 MiB), as a bound on one per rotation. */
 int64_t stab_request_footprint(const stab_request *req);
 
 /* opts may be NULL (all defaults).  Errors: STAB_E_INVAL (unknown policy or

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
     double *rho_n = rho == rA ? rB : rA;
     double *lam = lA, *lam_n = lB;
     if (!adjoint_sweep<N>(st, a.n_fwd_chunks, st.n_total, lam, lam_n, rho, rho_n, a.grad_rot,
-                          a.status, smem, false))
+                          a.status, smem, false, a.partials))
         return;
     double acc = 0.0;
     for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_split(AdjointSplitArg
     __syncthreads();
     double *rho = rA, *rho_n = rB, *lam = lA, *lam_n = lB;
     const bool ok = adjoint_sweep<N>(st, 0, st.n_total, lam, lam_n, rho, rho_n, a.grad_rot,
-                                     a.status, smem, b == 1);
+                                     a.status, smem, b == 1, a.partials);
     if (!ok || b != 0) return;
     double acc = 0.0;
     for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
@@ -455,6 +455,18 @@ cudaError_t launch_apply_transfer_chain(const double *T, int n_mats, const doubl
         return cudaGetLastError();
     }
     return cudaSuccess;
+}
+
+int resident_adjoint_threads(int n) {
+    switch (n) {
+    case 1: return SCfg<1, 1>::T;
+    case 2: return SCfg<2, 1>::T;
+    case 3: return SCfg<3, 1>::T;
+    case 4: return SCfg<4, 1>::T;
+    case 5: return SCfg<5, 1>::T;
+    case 6: return SCfg<6, 1>::T;
+    default: return 0;
+    }
 }
 
 int transfer_cols_ctas(int n) { return n == kColN ? kColE / 2 : 0; }

@@ -60,6 +60,9 @@ struct AdjointSplitArgs {
     int32_t n_terms;
     double *rmid, *lmid;     // rho and lambda at the cut: phase 0 writes, phase 1 reads
     double *grad_rot;        // phase 1: one entry per rotation ordinal
+    double *partials;        // phase 1, optional: per-thread dots [rotation ordinal][threads]
+                             // (summed afterwards by k_reduce_partials); null: each pass
+                             // reduces its rotations' dots over the CTA into grad_rot
     double *expect_out;      // phase 1: <O>
     int32_t *status;
 };
@@ -72,9 +75,16 @@ struct AdjointStreamArgs {
     const DevTerm *terms;
     int32_t n_terms;
     double *grad_rot;        // one entry per rotation ordinal
+    double *partials;        // optional, as in AdjointSplitArgs
     double *expect_out;      // <O>
     int32_t *status;
 };
+// Threads of the resident adjoint kernels' CTA at n qubits (the row length
+// of their per-thread partials).
+int resident_adjoint_threads(int n);
+// Bytes of the resident adjoint's per-thread dot shares for n_rot rotations
+// at n qubits, or 0 where the sweeps reduce each pass's dots themselves.
+size_t resident_partial_bytes(int n, int64_t n_rot);
 
 // One unit of the persistent batch kernel: one vector of one circuit.
 struct BatchUnit {             // 64 bytes

@@ -266,12 +266,16 @@ __device__ __forceinline__ double pair_dot(int axis, double lx, double ly, doubl
 // orthogonal) -- apply, then dot.  On return lam / rho point at the results;
 // false when a staging wait gave up.  The block has T threads (a multiple
 // of 32), each taking groups threadIdx.x, + T, ...; each rotation's dot is
-// summed over a warp by shuffles, then over the warps in warp order.
+// summed over a warp by shuffles, then over the warps in warp order -- or,
+// with part_out, each thread stores its own share at part_out[ordinal * T +
+// thread] and the sweep does no reduction and no barrier for it (the caller
+// sums every rotation over the threads afterwards, in thread order).
 template <int N, int T = SCfg<N, 1>::T>
 __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double *&lam,
                                               double *&lam_n, double *&rho, double *&rho_n,
                                               double *grad_rot, int32_t *status,
-                                              unsigned char *smem, const bool fwd) {
+                                              unsigned char *smem, const bool fwd,
+                                              double *part_out = nullptr) {
     constexpr int G = SCfg<N, 1>::G;
     constexpr int GPT = (G + T - 1) / T;
     constexpr int W = T / 32;
@@ -327,27 +331,42 @@ __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double
                     rho_n[ii] = ri; rho_n[ix] = rx; rho_n[iy] = ry; rho_n[iz] = rz;
                 }
             }
-            int n_rot = 0;
-            for (int j = 0; j < n_ops; ++j) {
-                if (ops[j].kind == R_ROT) {
-                    if (threadIdx.x == 0) gslot[n_rot] = ops[j].gate;
-                    ++n_rot;
-                }
-            }
-            // only the pass's rotations are reduced (n_rot is uniform over the CTA)
+            if (part_out) {
+                // this thread's share of each of the pass's rotations
+                int slot = 0;
+                for (int j = 0; j < n_ops; ++j) {
+                    if (ops[j].kind == R_ROT) {
+                        double v = 0.0;
 #pragma unroll
-            for (int s = 0; s < R; ++s) {
-                if (s < n_rot) {
-                    double v = part[s];
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                    if (lane == 0) red[warp * R + s] = v;
+                        for (int s = 0; s < R; ++s)
+                            if (s == slot) v = part[s];
+                        part_out[(size_t)ops[j].gate * T + threadIdx.x] = v;
+                        ++slot;
+                    }
                 }
-            }
-            __syncthreads();
-            if (threadIdx.x < n_rot) {
-                double total = 0.0;
-                for (int w = 0; w < W; ++w) total += red[w * R + threadIdx.x];
-                grad_rot[gslot[threadIdx.x]] = total;
+            } else {
+                int n_rot = 0;
+                for (int j = 0; j < n_ops; ++j) {
+                    if (ops[j].kind == R_ROT) {
+                        if (threadIdx.x == 0) gslot[n_rot] = ops[j].gate;
+                        ++n_rot;
+                    }
+                }
+                // only the pass's rotations are reduced (n_rot is uniform over the CTA)
+#pragma unroll
+                for (int s = 0; s < R; ++s) {
+                    if (s < n_rot) {
+                        double v = part[s];
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                        if (lane == 0) red[warp * R + s] = v;
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x < n_rot) {
+                    double total = 0.0;
+                    for (int w = 0; w < W; ++w) total += red[w * R + threadIdx.x];
+                    grad_rot[gslot[threadIdx.x]] = total;
+                }
             }
             double *t = lam;
             lam = lam_n;

@@ -992,6 +992,10 @@ int64_t stab_request_footprint(const stab_request *q) {
     if (q->kind == STAB_REQ_GRAD && q->n > kMaxResidentAdjoint) {
         // per-CTA partial sums of the streamed adjoint: one per rotation and CTA
         fp += 8 * (q->m > 0 ? q->m : 0) * (int64_t)adjoint_stream_blocks(q->n);
+    } else if (q->kind == STAB_REQ_GRAD) {
+        // per-thread dot shares of the resident adjoint (at most one rotation
+        // per gate), where a context sweep keeps them
+        fp += (int64_t)resident_partial_bytes(q->n, q->m > 0 ? q->m : 0);
     }
     return fp;
 }

@@ -53,6 +53,22 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Resident plans with at least this many passes also get split streams.
 constexpr int kSplitMinPasses = 64;
+// Resident adjoint: per-thread dot shares while the CTA has at most this many
+// threads (n <= 5) and the shares take at most this many bytes.
+constexpr int kPartialThreads = 256;
+constexpr size_t kPartialBytes = (size_t)256 << 20;
+
+}  // namespace
+
+size_t stab::resident_partial_bytes(int n, int64_t n_rot) {
+    const int t = resident_adjoint_threads(n);
+    const size_t rows = (size_t)(n_rot > 0 ? n_rot : 0), cols = (size_t)(t > 0 ? t : 0);
+    const size_t bytes = rows * cols * sizeof(double);
+    return (t > 0 && t <= kPartialThreads && bytes <= kPartialBytes) ? bytes : 0;
+}
+
+namespace {
+
 // Plans of at least this many passes build their instruction streams on
 // several host threads.
 constexpr int kThreadedStreamPasses = 2048;
@@ -1519,6 +1535,19 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
     RC(c->dalloc(c->scal, 64 * sizeof(double), s));
     RC(c->dalloc(c->grad_rot, (size_t)(n_rot ? n_rot : 1) * sizeof(double), s));
     double *e_out = expect_dev ? expect_dev : (double *)c->scal.p + 1;
+    // the resident sweeps store each thread's dot share per rotation (no
+    // reduction on the sweep's critical path; one fixed-order sum after it)
+    // while the CTA has at most kPartialThreads threads and the shares fit
+    // kPartialBytes; otherwise each pass reduces its dots over the CTA
+    double *partials = nullptr;
+    const int part_threads = resident_adjoint_threads(n);
+    if (c->use_resident_adjoint()) {
+        const size_t bytes = resident_partial_bytes(n, n_rot);
+        if (bytes > 0) {
+            RC(c->dalloc(c->partials, bytes, s));
+            partials = (double *)c->partials.p;
+        }
+    }
     if (c->use_resident_adjoint() && c->grad.split >= 0) {
         // meet in the middle: rho_0 forward through the first part and O
         // backward through the second, then the pair at the cut backward
@@ -1536,6 +1565,7 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         a.rmid = (double *)c->gmid.p;
         a.lmid = (double *)c->gmid.p + E;
         a.grad_rot = (double *)c->grad_rot.p;
+        a.partials = partials;
         a.expect_out = e_out;
         a.status = (int32_t *)c->status.p;
         CK(launch_adjoint_split(n, a, s));
@@ -1546,6 +1576,10 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         a.phase = 1;
         CK(launch_adjoint_split(n, a, s));
         c->launches += 2;
+        if (partials) {
+            CK(launch_reduce_partials(partials, n_rot, part_threads, (double *)c->grad_rot.p, s));
+            c->launches++;
+        }
         if (c->n_params > 0) {
             CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
                                    c->grad.param_rot, (int)c->n_params, grads_dev, s));
@@ -1560,10 +1594,15 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
         a.terms = (const DevTerm *)c->terms.p;
         a.n_terms = nt;
         a.grad_rot = (double *)c->grad_rot.p;
+        a.partials = partials;
         a.expect_out = e_out;
         a.status = (int32_t *)c->status.p;
         CK(launch_adjoint_stream(n, a, s));
         c->launches++;
+        if (partials) {
+            CK(launch_reduce_partials(partials, n_rot, part_threads, (double *)c->grad_rot.p, s));
+            c->launches++;
+        }
         if (c->n_params > 0) {
             CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
                                    c->grad.param_rot, (int)c->n_params, grads_dev, s));

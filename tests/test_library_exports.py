@@ -95,6 +95,16 @@ def test_request_footprint_counts_the_split_sweep_vectors():
     r.n, r.m = 3, 1000
     r.kind = 0
     assert L.stab_request_footprint(ctypes.byref(r)) == 4 * 8 * 4 ** 3 + 96 * 1000
+    # gradients at n <= 5 add the resident sweep's per-thread dot shares (one
+    # row of its CTA's threads per gate, as a bound on the rotations)
+    r.kind = 1
+    for n, threads in ((3, 32), (4, 64), (5, 256)):
+        r.n = n
+        assert L.stab_request_footprint(ctypes.byref(r)) == \
+            12 * 8 * 4 ** n + 96 * 1000 + 8 * 1000 * threads
+    r.n = 6
+    assert L.stab_request_footprint(ctypes.byref(r)) == 12 * 8 * 4 ** 6 + 96 * 1000
+    r.kind = 0
     r.n = 8
     assert L.stab_request_footprint(ctypes.byref(r)) == 8 * 8 * 4 ** 8 + 96 * 1000
     r.kind = 1
