@@ -774,16 +774,19 @@ int split_apply(stab_ctx *c, int first, int n_vec, double *out, const DevTerm *t
         // of the calling stream's own (<O> on aux may overlap the generators)
         DevBuf &scratch = s == c->st ? c->chainbuf : c->chainbuf_e;
         RC(c->dalloc(scratch, 2 * (size_t)n_vec * E * 8, s));
-        CK(launch_apply_transfer_chain((const double *)c->tmat.p, (int)c->fwd.parts.size() - 1,
-                                       in, out, (double *)scratch.p, n_vec, c->n, terms,
-                                       n_terms, dot_out, s));
+        const int n_mats = (int)c->fwd.parts.size() - 1;
+        CK(launch_apply_transfer_chain((const double *)c->tmat.p, n_mats, in, out,
+                                       (double *)scratch.p, n_vec, c->n, terms, n_terms, dot_out,
+                                       s));
+        c->launches += n_mats + (dot_out ? 1 : 0);   // a product per matrix, then the dot
     } else if (chain_mode(c)) {
         CK(launch_apply_chain((const double *)c->tmat.p, (int)c->fwd.parts.size() - 1, in, out,
                               n_vec, c->n, terms, n_terms, dot_out, s));
+        c->launches++;
     } else {
         CK(launch_apply_transfer((const double *)c->tmat.p, in, out, n_vec, c->n, s));
+        c->launches++;
     }
-    c->launches++;
     return STAB_OK;
 }
 
