@@ -179,6 +179,10 @@ namespace stab {
 // The context's main stream (work queued by the asynchronous entry points is
 // complete once this stream is).
 cudaStream_t ctx_stream(stab_ctx *ctx);
+// Marks the context's split generator sweep as not made for its current
+// angles, so the next call that needs it runs it again (timing probes that
+// call the same entry point repeatedly).
+void ctx_forget_sweep(stab_ctx *ctx);
 
 // Density matrix from the forward-evolved coefficients of 2^n |0><0|:
 // rho (device, 2 x 4^n doubles, interleaved complex, row-major).

@@ -973,6 +973,9 @@ int ensure_grad_plan(stab_ctx *c) {
 }  // namespace
 
 cudaStream_t stab::ctx_stream(stab_ctx *c) { return c ? c->st : nullptr; }
+void stab::ctx_forget_sweep(stab_ctx *c) {
+    if (c) c->tx_gen = -1;
+}
 
 extern "C" {
 
@@ -1343,7 +1346,9 @@ int stab_run_generators(stab_ctx *c) {
     const size_t bytes = c->vec_bytes() * (size_t)n;
     RC(c->dalloc(c->gens, bytes, c->st));
     if (c->use_resident() && split_gens_ok(c)) {
-        RC(split_run_g(c));
+        // the split sweep for these angles may already have run (for <O> or
+        // the density matrix); then only the products with T remain
+        if (c->tx_gen != c->param_gen) RC(split_run_g(c));
         RC(split_apply(c, 0, n, (double *)c->gens.p, nullptr, 0, nullptr, c->st));
         c->gens_cur = (double *)c->gens.p;
     } else if (c->use_resident()) {
@@ -1812,9 +1817,10 @@ int stab_density_matrix(stab_ctx *c, double *out, int out_is_device) {
     RC(c->dalloc(c->rho, vb, c->st));
     double *r = (double *)c->rho.p;
     if (c->use_resident() && split_gens_ok(c)) {
-        // r = T r_1: rho_0 through the first part, then the second part's
-        // transfer matrix (built alongside, as for the generators)
-        RC(split_run_g(c));
+        // r = T r_1: rho_0 through the first part, then the later parts'
+        // transfer matrices (built alongside, as for the generators; reused
+        // when the sweep for these angles has run)
+        if (c->tx_gen != c->param_gen) RC(split_run_g(c));
         RC(split_apply(c, n, 1, r, nullptr, 0, nullptr, c->st));
     } else if (c->use_resident()) {
         StreamArgs a{};

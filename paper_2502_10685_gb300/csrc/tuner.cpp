@@ -233,7 +233,12 @@ int time_op(int device, const stab_opts *like, const Probe &P, const stab_path_c
         rc = STAB_E_CUDA;
     }
     auto call = [&]() {
-        if (op == PR_GENS) return stab_run_generators(c);
+        if (op == PR_GENS) {
+            // every timed call runs the whole sweep (a repeated call for the
+            // same angles would otherwise reuse the previous one)
+            ctx_forget_sweep(c);
+            return stab_run_generators(c);
+        }
         if (op == PR_EXPECT) return stab_expect_async(c, dev);
         return stab_grad_async(c, dev, dev + 8);
     };

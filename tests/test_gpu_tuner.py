@@ -204,3 +204,32 @@ def test_three_part_split_overlapped_async_calls_match_oracle(S):
         assert abs(float(outs[k, 0].item()) - want) <= 1e-12 * l1(obs), k
         assert np.abs(layout.lib_to_paper(n, gens[k]) - oracle.generators(n, c.gates, th)).max() \
             <= 1e-12, k
+
+
+def test_three_part_expectation_first_runs_the_sweep_itself(S):
+    """n = 4, three parts: <O> asked before any generators runs the split
+    sweep for the current angles itself (first part and both transfer
+    matrices); after new angles it must not reuse the old sweep; the
+    generators asked afterwards reuse the sweep <O> made."""
+    n = 4
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": 0.49,
+                                      "tile_limit": 1 << 17, "tuned": 1, "gen_parts": 3})
+    c = W.layered_ansatz(n, 2400, seed=4440)
+    obs = W.random_observable(n, 6, seed=4441)
+    s = S.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    assert (s.split_info()[1] - (n + 1)) // (4 ** n - 1) == 2
+    e1 = s.expect(obs)
+    th2 = np.random.default_rng(4442).uniform(0, 2 * np.pi, c.n_params)
+    s.set_params(th2)
+    e2 = s.expect(obs)
+    launches = s.launch_count()
+    s.run_generators()              # reuses the sweep <O> made: only the products run
+    ran = s.launch_count() - launches
+    gens = layout.lib_to_paper(n, s.generators())
+    s.close()
+    assert ran == 2                 # T2 then T3 on the first-part generators
+    tol = 1e-12 * l1(obs)
+    assert abs(e1 - oracle.expect(n, c.gates, c.thetas, obs)) <= tol
+    assert abs(e2 - oracle.expect(n, c.gates, th2, obs)) <= tol
+    assert np.abs(gens - oracle.generators(n, c.gates, th2)).max() <= 1e-12
