@@ -233,3 +233,45 @@ def test_three_part_expectation_first_runs_the_sweep_itself(S):
     assert abs(e1 - oracle.expect(n, c.gates, c.thetas, obs)) <= tol
     assert abs(e2 - oracle.expect(n, c.gates, th2, obs)) <= tol
     assert np.abs(gens - oracle.generators(n, c.gates, th2)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("family", ["random", "random-shared", "paper"])
+def test_three_part_split_on_other_circuit_families(S, family):
+    """The three-part split at n = 4 on circuits whose Clifford runs differ
+    from layer to layer (random gate mixes: pulls of every length, repeated
+    and not, before any wire), whose angle slots are shared by several gates,
+    and on the paper's W_chain + ZXZ shape with long per-wire runs: the
+    generators, <O> and the gradient against the oracle."""
+    n = 4
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": 0.49,
+                                      "tile_limit": 1 << 17, "tuned": 1, "gen_parts": 3})
+    if family == "random":
+        c = W.random_circuit(n, 4000, seed=4450)
+    elif family == "random-shared":
+        c = W.random_circuit(n, 4000, seed=4451, shared_params=17)
+    else:
+        c = W.paper_shaped_ansatz(n, 60, 20, seed=4452)
+    obs = W.random_observable(n, 6, seed=4453)
+    s = S.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    n_pass = s.plan_info()[1]
+    if n_pass >= 3 * 64:
+        assert (s.split_info()[1] - (n + 1)) // (4 ** n - 1) == 2
+    s.run_generators()
+    gens = layout.lib_to_paper(n, s.generators())
+    e = s.expect(obs)
+    eg, g = s.grad(obs)
+    s.close()
+    tol = 1e-12 * l1(obs)
+    assert np.abs(gens - oracle.generators(n, c.gates, c.thetas)).max() <= 1e-12
+    ref = oracle.expect(n, c.gates, c.thetas, obs)
+    assert abs(e - ref) <= tol and abs(eg - ref) <= tol
+    if family == "random-shared":
+        # every slot is read by many gates: the oracle's parameter shift per slot
+        want = oracle.psr_grad(n, c.gates, c.thetas, obs)
+        assert np.abs(g - want).max() <= tol
+    else:
+        rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+        for gi in (rot[1], rot[len(rot) // 2]):
+            want = oracle.psr_grad_gate(n, c.gates, c.thetas, obs, gi)
+            assert abs(g[int(c.gates[gi]["param"])] - want) <= tol, (family, gi)
