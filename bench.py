@@ -733,7 +733,9 @@ def run_grad(args):
 def run_grad_n(args):
     """All gradients by the adjoint on the layered ansatz with n, m from the
     workload name grad-n<N>-<M> (O = the ZZ chain + 0.5 X field); device time of
-    grad_async with CUDA events, L2 flushed between steps."""
+    a training step's set_params (angles from device memory) + grad_async with
+    CUDA events, L2 flushed between steps (new angles every step, so nothing
+    made for earlier angles is reused)."""
     import torch
     from paper_2502_10685_gb300 import stab, workloads as W
     n, m = (int(v) for v in args.workload[len("grad-n"):].split("-"))
@@ -745,8 +747,10 @@ def run_grad_n(args):
     s.set_observable(W.obs_chain(n))
     g = torch.zeros(max(1, c.n_params), dtype=torch.float64, device="cuda")
     e = torch.zeros(8, dtype=torch.float64, device="cuda")
+    th = torch.tensor(c.thetas, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
+        s.set_params(th)
         s.grad_async(e, g)
     torch.cuda.synchronize()
     times = []
@@ -754,6 +758,7 @@ def run_grad_n(args):
         flush.zero_()
         e0, e1 = _events()
         e0.record(st)
+        s.set_params(th)
         s.grad_async(e, g)
         e1.record(st)
         torch.cuda.synchronize()

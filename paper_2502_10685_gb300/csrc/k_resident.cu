@@ -422,6 +422,22 @@ cudaError_t launch_apply_chain(const double *T, int n_mats, const double *in, do
     return cudaGetLastError();
 }
 
+// out = T^T in at n = 4 (T stored by columns, column j at T + j 4^n): output
+// j is column j dotted with in -- the backward step through a part whose
+// forward transfer matrix is T, the maps being orthogonal.  A warp per
+// output, lanes over the column (coalesced), a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_apply_transfer_t(const double *T, const double *in,
+                                                          double *out) {
+    constexpr int E = kColE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 8 + warp;
+    const double *col = T + (size_t)j * E;
+    double acc = 0.0;
+    for (int i = lane; i < E; i += 32) acc = fma(col[i], in[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[j] = acc;
+}
+
 // <O> = sum of the terms' coeff x v[idx], in term order (one thread: an
 // observable has few terms).
 __global__ void k_terms_dot(const double *v, const DevTerm *terms, int n_terms, double *out) {
@@ -467,6 +483,13 @@ int resident_adjoint_threads(int n) {
     case 6: return SCfg<6, 1>::T;
     default: return 0;
     }
+}
+
+cudaError_t launch_apply_transfer_t(const double *T, const double *in, double *out, int n,
+                                    cudaStream_t st) {
+    if (n != kColN) return cudaErrorInvalidValue;
+    k_apply_transfer_t<<<kColE / 8, 256, 0, st>>>(T, in, out);
+    return cudaGetLastError();
 }
 
 int transfer_cols_ctas(int n) { return n == kColN ? kColE / 2 : 0; }

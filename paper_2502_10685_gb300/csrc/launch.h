@@ -240,6 +240,10 @@ struct ColArgs {
 cudaError_t launch_transfer_cols(const ColArgs &a, int n, cudaStream_t st);
 // Dynamic shared memory of a k_transfer_cols CTA (more than half an SM's).
 size_t transfer_cols_smem();
+// out = T^T in for one n = 4 transfer matrix (the backward step through its
+// part): 4^n outputs, each a column of T dotted with in.
+cudaError_t launch_apply_transfer_t(const double *T, const double *in, double *out, int n,
+                                    cudaStream_t st);
 // out_k = T_{n_mats-1} ... T_0 in_k at n = 4 (one k_apply_transfer per matrix,
 // tmp: 2 x n_vec x 4^n doubles between them); with dot_out (n_vec = 1) also
 // <O> = sum of terms' coeff x the result[idx], in term order.  out may be null.

@@ -169,6 +169,9 @@ struct stab_ctx {
     DevBuf lam2, tmp3;               // second-branch buffers of the split sweeps
     DevBuf dotbuf;                   // partial sums of the split expectation's inner product
     DevBuf gmid;                     // split resident adjoint: rho, then lambda, at the cut
+    DevBuf odense;                   // O as a dense vector, and a second vector for the
+                                     // transposed products of the aligned gradient
+    bool grad_aligned = false;       // the gradient plan's cut is the generators' first cut
     DevBuf chainbuf, chainbuf_e;     // n = 4 chain of transfer matrices: intermediate vectors
                                      // of the context stream's products, of <O>'s (aux)
     // split resident sweeps (n <= 6; see split_units): transfer matrix of the
@@ -422,7 +425,7 @@ void build_streams(const DevPlan &P, const std::vector<StreamSpec> &specs, bool 
 // passes the streams are built on the calling thread: handing them to the
 // pool would cost more than the work.
 void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_parts = 2,
-                  double first_frac = 0.0) {
+                  double first_frac = 0.0, int force_split = -1) {
     P.streams = true;
     const int np = (int)P.host.passes.size();
     const bool threads = np >= kThreadedStreamPasses;
@@ -449,6 +452,7 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_
     P.parts.clear();
     P.cuts.clear();
     P.split = (split_frac > 0.0 && np >= kSplitMinPasses) ? (int)(np * split_frac) : -1;
+    if (P.split >= 0 && force_split > 0 && force_split < np) P.split = force_split;
     // streams that are rebuilt keep their capacity; the others are released
     if (P.split < 0) P.h1 = P.h2 = P.h2b = DevStreamBuf();
     if (!(grad && P.split >= 0)) P.h1b = DevStreamBuf();
@@ -952,15 +956,61 @@ void reset_graphs(stab_ctx *c) {
     c->plan_gen++;
 }
 
+// Plans of one gate list in different modes hold the same sequence of units:
+// a P_CLIFF pass, or a maximal stretch of consecutive P_WIRE passes on one
+// wire (a gradient plan only cuts a wire's run into several passes).  Returns
+// the pass of plan B that starts the unit starting at pass k of plan A, or -1
+// when pass k starts no unit or the two plans' unit sequences differ (a run
+// that is the identity and holds no rotation makes no pass in some modes).
+bool unit_start(const HostPlan &P, size_t i) {
+    if (i == 0) return true;
+    const DevPass &p = P.passes[i], &q = P.passes[i - 1];
+    return p.type != P_WIRE || q.type != P_WIRE || p.q != q.q;
+}
+
+int aligned_pass(const HostPlan &A, int k, const HostPlan &B) {
+    if (k <= 0 || k >= (int)A.passes.size() || !unit_start(A, (size_t)k)) return -1;
+    // the units of both plans, as (type, wire), in order; the first pass of each in B
+    std::vector<uint16_t> ua, ub;
+    std::vector<int> start_b;
+    int unit_k = -1;
+    for (size_t i = 0; i < A.passes.size(); ++i)
+        if (unit_start(A, i)) {
+            if ((int)i == k) unit_k = (int)ua.size();
+            ua.push_back((uint16_t)(A.passes[i].type << 8 | A.passes[i].q));
+        }
+    for (size_t i = 0; i < B.passes.size(); ++i)
+        if (unit_start(B, i)) {
+            ub.push_back((uint16_t)(B.passes[i].type << 8 | B.passes[i].q));
+            start_b.push_back((int)i);
+        }
+    if (ua != ub || unit_k < 0) return -1;
+    return start_b[(size_t)unit_k];
+}
+
 int ensure_grad_plan(stab_ctx *c) {
     if (!c->grad.built) {
         build_plan(c->n, c->gates.data(), (int64_t)c->gates.size(), c->n_params, PLAN_GRAD,
                    &c->grad.host, !c->use_resident_adjoint());
         // resident adjoint: split at half the passes (the AUTO kernel; the
-        // RESIDENT choice keeps the single-CTA forward-then-reverse sweep)
-        if (c->use_resident_adjoint())
-            make_streams(c->grad, c->kernel == STAB_KERNEL_AUTO ? 0.5 : 0.0, true);
-        else no_streams(c->grad);
+        // RESIDENT choice keeps the single-CTA forward-then-reverse sweep) --
+        // or, at n = 4 with the generators' split sweep, at the gate where the
+        // generators' first part ends, so the pair at the cut comes from that
+        // sweep (see stab_grad_async)
+        c->grad_aligned = false;
+        if (c->use_resident_adjoint()) {
+            int forced = -1;
+            if (c->kernel == STAB_KERNEL_AUTO && c->use_resident() && split_gens_ok(c) &&
+                transfer_cols_ctas(c->n) > 0) {
+                const int k = aligned_pass(c->fwd.host, c->fwd.split, c->grad.host);
+                if (k > 0 && (int)c->grad.host.passes.size() >= kSplitMinPasses) forced = k;
+            }
+            make_streams(c->grad, c->kernel == STAB_KERNEL_AUTO ? 0.5 : 0.0, true, 2, 0.0,
+                         forced);
+            c->grad_aligned = forced > 0 && c->grad.split == forced;
+        } else {
+            no_streams(c->grad);
+        }
         c->g_grad.reset();
         c->plan_gen++;
         RC(upload_plan(c, c->grad));
@@ -1249,7 +1299,7 @@ int stab_destroy(stab_ctx *c) {
                       &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3,
                       &c->dotbuf, &c->tmat, &c->avec, &c->rmid, &c->lmid, &c->bterms,
                       &c->units_g, &c->units_e, &c->cnt, &c->gmid, &c->chainbuf,
-                      &c->chainbuf_e};
+                      &c->chainbuf_e, &c->odense};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -1556,7 +1606,50 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
             partials = (double *)c->partials.p;
         }
     }
-    if (c->use_resident_adjoint() && c->grad.split >= 0) {
+    if (c->use_resident_adjoint() && c->grad.split >= 0 && c->grad_aligned) {
+        // n = 4, cut where the generators' first part ends: rho_0 through the
+        // first part is that sweep's first-part vector, and lambda at the cut
+        // is O carried backward through the later parts, T_k^T (the maps being
+        // orthogonal) from the last part to the first; the sweep is reused
+        // when it was made for these angles.  Then the pair at the cut
+        // backward through the first part and forward through the rest.
+        if (c->tx_gen != c->param_gen) RC(split_run_g(c));
+        CK(cudaStreamWaitEvent(s, c->ev_tx, 0));
+        const size_t E = (size_t)1 << (2 * n);
+        RC(c->dalloc(c->odense, 2 * E * sizeof(double), s));
+        double *cur = (double *)c->odense.p, *nxt = cur + E;
+        CK(launch_fill(cur, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, s));
+        const int n_mats = chain_mode(c) ? (int)c->fwd.parts.size() - 1 : 1;
+        for (int k = n_mats - 1; k >= 0; --k) {
+            CK(launch_apply_transfer_t((const double *)c->tmat.p + (size_t)k * E * E, cur, nxt, n,
+                                       s));
+            std::swap(cur, nxt);
+        }
+        c->launches += 1 + n_mats;
+        AdjointSplitArgs a{};
+        a.stream[0] = c->grad.h1b.dev;
+        a.n_chunks[0] = c->grad.h1b.n_chunks;
+        a.stream[1] = c->grad.h2.dev;
+        a.n_chunks[1] = c->grad.h2.n_chunks;
+        a.phase = 1;
+        a.rmid = (double *)c->avec.p + (size_t)n * E;
+        a.lmid = cur;
+        a.grad_rot = (double *)c->grad_rot.p;
+        a.partials = partials;
+        a.expect_out = e_out;
+        a.status = (int32_t *)c->status.p;
+        CK(launch_adjoint_split(n, a, s));
+        c->launches++;
+        if (partials) {
+            CK(launch_reduce_partials(partials, n_rot, part_threads, (double *)c->grad_rot.p, s));
+            c->launches++;
+        }
+        if (c->n_params > 0) {
+            CK(launch_gather_grads((const double *)c->grad_rot.p, c->grad.param_ptr,
+                                   c->grad.param_rot, (int)c->n_params, grads_dev, s));
+            c->launches++;
+        }
+    } else if (c->use_resident_adjoint() && c->grad.split >= 0) {
         // meet in the middle: rho_0 forward through the first part and O
         // backward through the second, then the pair at the cut backward
         // through the first part and forward through the second

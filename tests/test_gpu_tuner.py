@@ -275,3 +275,51 @@ def test_three_part_split_on_other_circuit_families(S, family):
         for gi in (rot[1], rot[len(rot) // 2]):
             want = oracle.psr_grad_gate(n, c.gates, c.thetas, obs, gi)
             assert abs(g[int(c.gates[gi]["param"])] - want) <= tol, (family, gi)
+
+
+def with_identity_run(c, layer_gates=16, at_layer=40):
+    """c with an H H pair on wire 2 inserted between the first two CNOTs of
+    one layer's ring (n = 4: 12 rotation slots, then 4 CNOTs): a block of its
+    own whose only wire run is the identity and holds no rotation (gradient
+    plans make no pass of it, generator plans a map pass)."""
+    k = layer_gates * at_layer + 13
+    h = np.zeros(2, dtype=W.GATE_DTYPE)
+    h["op"] = W.OPS["H"]
+    h["q0"] = 2
+    h["param"] = -1
+    return W.Circuit(c.n, np.concatenate([c.gates[:k], h, c.gates[k:]]), c.thetas)
+
+
+@pytest.mark.parametrize("parts,cut", [(3, 0.49), (2, 0.56)])
+@pytest.mark.parametrize("identity_run", [False, True])
+def test_gradient_cut_at_the_generators_first_part(S, parts, cut, identity_run):
+    """n = 4: the gradient's cut sits where the generators' first part ends,
+    and the pair at the cut comes from the generators' split sweep (rho_0
+    through the first part; O backward through the later parts' transfer
+    matrices, transposed) -- run by the gradient itself when no sweep was made
+    for the current angles, reused when one was.  A circuit whose wire runs
+    differ between the plan modes (an identity run) keeps the meet-in-the-
+    middle sweep.  Both against the oracle's parameter shift."""
+    n = 4
+    S.stab_path_store(gpu_name(), n, {"resident": 1, "resident_adjoint": 1, "gen_cut": cut,
+                                      "tile_limit": 1 << 17, "tuned": 1, "gen_parts": parts})
+    c = W.layered_ansatz(n, 3200, seed=4460 + parts)
+    if identity_run:
+        c = with_identity_run(c)
+    obs = W.random_observable(n, 5, seed=4461)
+    tol = 1e-12 * l1(obs)
+    rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+    picks = (rot[0], rot[len(rot) // 2 - 1], rot[len(rot) // 2 + 3], rot[-1])
+    s = S.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    e1, g1 = s.grad(obs)                      # no sweep for these angles yet
+    th2 = np.random.default_rng(4462).uniform(0, 2 * np.pi, c.n_params)
+    s.set_params(th2)
+    s.run_generators()
+    e2, g2 = s.grad(obs)                      # the generators' sweep, reused
+    s.close()
+    for th, e, g in ((c.thetas, e1, g1), (th2, e2, g2)):
+        assert abs(e - oracle.expect(n, c.gates, th, obs)) <= tol
+        for gi in picks:
+            want = oracle.psr_grad_gate(n, c.gates, th, obs, gi)
+            assert abs(g[int(c.gates[gi]["param"])] - want) <= tol, gi
