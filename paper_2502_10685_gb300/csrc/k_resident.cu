@@ -297,15 +297,29 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
 //     sweeps it backward through the first part (stream 0) and also writes
 //     <O> (x-free sum of lambda_0), CTA 1 forward through the second part
 //     (stream 1); each rotation's dot lands in the part that holds it.
+//   with parts (phase 1 only): CTA b walks part b's stream from the part's
+//     own pair -- part 0 backward from its end, every later part forward
+//     from its start; CTA 0 writes <O>.
 template <int N>
 __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_split(AdjointSplitArgs a) {
     using C = SCfg<N, 1>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int b = blockIdx.x;
     Stager st;
-    st.s0 = b == 0 ? a.stream[0] : a.stream[1];
+    const double *rmid = a.rmid, *lmid = a.lmid;
+    bool fwd = b == 1;
+    if (a.parts) {
+        const AdjPart P = a.parts[b];
+        st.s0 = P.stream;
+        st.n0 = P.n_chunks;
+        rmid = P.rho;
+        lmid = P.lam;
+        fwd = P.forward != 0;
+    } else {
+        st.s0 = b == 0 ? a.stream[0] : a.stream[1];
+        st.n0 = b == 0 ? a.n_chunks[0] : a.n_chunks[1];
+    }
     st.s1 = nullptr;
-    st.n0 = b == 0 ? a.n_chunks[0] : a.n_chunks[1];
     st.n_total = st.n0;
     stager_setup(st, smem);
     double *red = reinterpret_cast<double *>(smem + kOffRed);
@@ -326,13 +340,13 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_split(AdjointSplitArg
         return;
     }
     for (int i = threadIdx.x; i < C::E; i += C::T) {
-        rA[i] = a.rmid[i];
-        lA[i] = a.lmid[i];
+        rA[i] = rmid[i];
+        lA[i] = lmid[i];
     }
     __syncthreads();
     double *rho = rA, *rho_n = rB, *lam = lA, *lam_n = lB;
     const bool ok = adjoint_sweep<N>(st, 0, st.n_total, lam, lam_n, rho, rho_n, a.grad_rot,
-                                     a.status, smem, b == 1, a.partials);
+                                     a.status, smem, fwd, a.partials);
     if (!ok || b != 0) return;
     double acc = 0.0;
     for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];
@@ -358,7 +372,7 @@ cudaError_t launch_adjoint_split_n(const AdjointSplitArgs &a, cudaStream_t s) {
     static SmemLimit lim;
     cudaError_t e = raise_smem_limit(k_adjoint_split<N>, smem, lim);
     if (e != cudaSuccess) return e;
-    k_adjoint_split<N><<<2, C::T, smem, s>>>(a);
+    k_adjoint_split<N><<<a.parts ? a.n_parts : 2, C::T, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -483,6 +497,49 @@ int resident_adjoint_threads(int n) {
     case 6: return SCfg<6, 1>::T;
     default: return 0;
     }
+}
+
+// The pairs at the cuts of a K-part split, n <= 3 (see launch.h): thread i
+// computes entry i of every product, summing in index order; the CTA syncs
+// between the steps of each chain.
+__global__ void __launch_bounds__(64) k_adjoint_pairs(const double *T, int K, int E,
+                                                      const double *r1, const double *o,
+                                                      double *pairs) {
+    const int i = threadIdx.x;
+    const size_t EE = (size_t)E * E;
+    auto lam = [&](int k) { return pairs + (size_t)(k - 1) * 2 * E; };
+    auto rho = [&](int k) { return pairs + (size_t)(k - 1) * 2 * E + E; };
+    if (i < E) rho(1)[i] = r1[i];
+    __syncthreads();
+    for (int k = 1; k + 1 <= K - 1; ++k) {
+        // rho_{k+1} = T_k rho_k: row i of T_k is entry i of every column
+        const double *Tk = T + (size_t)(k - 1) * EE;
+        if (i < E) {
+            double acc = 0.0;
+            for (int j = 0; j < E; ++j) acc = fma(Tk[(size_t)j * E + i], rho(k)[j], acc);
+            rho(k + 1)[i] = acc;
+        }
+        __syncthreads();
+    }
+    for (int k = K - 1; k >= 1; --k) {
+        // lambda_k = T_k^T lambda_{k+1} (lambda_K = o): column i of T_k
+        const double *Tk = T + (size_t)(k - 1) * EE;
+        const double *src = k == K - 1 ? o : lam(k + 1);
+        if (i < E) {
+            double acc = 0.0;
+            for (int j = 0; j < E; ++j) acc = fma(Tk[(size_t)i * E + j], src[j], acc);
+            lam(k)[i] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_adjoint_pairs(const double *T, int K, int n, const double *r1,
+                                 const double *o, double *pairs, cudaStream_t st) {
+    const int E = 1 << (2 * n);
+    if (n < 1 || n > 3 || K < 2) return cudaErrorInvalidValue;
+    k_adjoint_pairs<<<1, 64, 0, st>>>(T, K, E, r1, o, pairs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_apply_transfer_t(const double *T, const double *in, double *out, int n,

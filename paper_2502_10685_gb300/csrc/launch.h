@@ -50,6 +50,17 @@ struct StreamArgs {
     int32_t *status;         // set to a nonzero code when a bounded wait gives up
 };
 
+// One part of a many-part resident adjoint sweep (phase 1 of k_adjoint_split
+// with parts): the part's gradient stream, walked backward (the first part,
+// from its end) or forward (every later part, from its start), and the pair
+// (lambda, rho) where the walk starts.
+struct AdjPart {
+    const Rec *stream;
+    int32_t n_chunks;
+    int32_t forward;
+    const double *lam, *rho;
+};
+
 // Split resident adjoint (two CTAs, two launches; see k_adjoint_split).
 struct AdjointSplitArgs {
     const Rec *stream[2];    // phase 0: forward [0, cut), backward [cut, P); phase 1: backward
@@ -63,6 +74,8 @@ struct AdjointSplitArgs {
     double *partials;        // phase 1, optional: per-thread dots [rotation ordinal][threads]
                              // (summed afterwards by k_reduce_partials); null: each pass
                              // reduces its rotations' dots over the CTA into grad_rot
+    const AdjPart *parts;    // phase 1, optional (device array): one CTA per part, in place
+    int32_t n_parts;         // of stream[] and the pair (lmid, rmid); CTA 0 writes <O>
     double *expect_out;      // phase 1: <O>
     int32_t *status;
 };
@@ -82,6 +95,12 @@ struct AdjointStreamArgs {
 // Threads of the resident adjoint kernels' CTA at n qubits (the row length
 // of their per-thread partials).
 int resident_adjoint_threads(int n);
+// The pairs at the cuts of a K-part split at n <= 3, one CTA: rho_1 = r1,
+// rho_{k+1} = T_k rho_k, lambda_{K-1} = T_{K-1}^T o, lambda_k = T_k^T
+// lambda_{k+1}, with T_k (k = 1 .. K-1) at T + (k - 1) 16^n (by columns);
+// pairs = [lambda_1, rho_1, ..., lambda_{K-1}, rho_{K-1}], 4^n doubles each.
+cudaError_t launch_adjoint_pairs(const double *T, int K, int n, const double *r1,
+                                 const double *o, double *pairs, cudaStream_t st);
 // Bytes of the resident adjoint's per-thread dot shares for n_rot rotations
 // at n qubits, or 0 where the sweeps reduce each pass's dots themselves.
 size_t resident_partial_bytes(int n, int64_t n_rot);

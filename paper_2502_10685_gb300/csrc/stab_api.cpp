@@ -171,7 +171,10 @@ struct stab_ctx {
     DevBuf gmid;                     // split resident adjoint: rho, then lambda, at the cut
     DevBuf odense;                   // O as a dense vector, and a second vector for the
                                      // transposed products of the aligned gradient
-    bool grad_aligned = false;       // the gradient plan's cut is the generators' first cut
+    bool grad_aligned = false;       // the gradient plan's parts end where the generators' do
+    std::vector<int> grad_cuts;      // their pass boundaries in the gradient plan (K + 1)
+    DevBuf gpairs, gparts;           // the pairs at the cuts; the parts' descriptors
+    std::vector<AdjPart> gparts_host;
     DevBuf chainbuf, chainbuf_e;     // n = 4 chain of transfer matrices: intermediate vectors
                                      // of the context stream's products, of <O>'s (aux)
     // split resident sweeps (n <= 6; see split_units): transfer matrix of the
@@ -481,6 +484,23 @@ void make_streams(DevPlan &P, double split_frac = 0.0, bool grad = false, int n_
         {&P.h1, false, 0, P.split}, {&P.h2, false, P.split, np}, {&P.h2b, true, P.split, np}};
     if (whole_fwd) specs.push_back({&P.sf, false, 0, np});
     build_streams(P, specs, threads);
+}
+
+// Gradient streams of a many-part split at the pass boundaries `cuts` (K + 1
+// of them, 0 and P included): part 0 backward over [0, cuts[1]) (walked from
+// its end), part k >= 1 forward over [cuts[k], cuts[k + 1]).
+void make_grad_part_streams(DevPlan &P, const std::vector<int> &cuts) {
+    P.streams = true;
+    const int np = (int)P.host.passes.size();
+    const size_t K = cuts.size() - 1;
+    P.sf = P.sb = P.h1 = P.h2 = P.h2b = P.h1b = DevStreamBuf();
+    P.parts.resize(K);
+    P.cuts = cuts;
+    P.split = cuts[1];
+    std::vector<StreamSpec> specs;
+    for (size_t k = 0; k < K; ++k)
+        specs.push_back({&P.parts[k], k == 0, cuts[k], cuts[k + 1]});
+    build_streams(P, specs, np >= kThreadedStreamPasses);
 }
 
 void no_streams(DevPlan &P) {
@@ -998,22 +1018,57 @@ int ensure_grad_plan(stab_ctx *c) {
         // generators' first part ends, so the pair at the cut comes from that
         // sweep (see stab_grad_async)
         c->grad_aligned = false;
+        c->grad_cuts.clear();
         if (c->use_resident_adjoint()) {
-            int forced = -1;
+            // the generators' part boundaries, as passes of the gradient plan
+            const int npg = (int)c->grad.host.passes.size();
             if (c->kernel == STAB_KERNEL_AUTO && c->use_resident() && split_gens_ok(c) &&
-                transfer_cols_ctas(c->n) > 0) {
-                const int k = aligned_pass(c->fwd.host, c->fwd.split, c->grad.host);
-                if (k > 0 && (int)c->grad.host.passes.size() >= kSplitMinPasses) forced = k;
+                npg >= kSplitMinPasses) {
+                std::vector<int> fc = chain_mode(c)
+                                          ? c->fwd.cuts
+                                          : std::vector<int>{0, c->fwd.split,
+                                                             (int)c->fwd.host.passes.size()};
+                std::vector<int> gc = {0};
+                for (size_t k = 1; k + 1 < fc.size(); ++k) {
+                    const int g = aligned_pass(c->fwd.host, fc[k], c->grad.host);
+                    if (g <= gc.back()) break;
+                    gc.push_back(g);
+                }
+                if (gc.size() + 1 == fc.size() && gc.back() < npg) {
+                    gc.push_back(npg);
+                    c->grad_cuts = gc;
+                }
             }
-            make_streams(c->grad, c->kernel == STAB_KERNEL_AUTO ? 0.5 : 0.0, true, 2, 0.0,
-                         forced);
-            c->grad_aligned = forced > 0 && c->grad.split == forced;
+            if (!c->grad_cuts.empty()) make_grad_part_streams(c->grad, c->grad_cuts);
+            else make_streams(c->grad, c->kernel == STAB_KERNEL_AUTO ? 0.5 : 0.0, true);
+            c->grad_aligned = !c->grad_cuts.empty();
         } else {
             no_streams(c->grad);
         }
         c->g_grad.reset();
         c->plan_gen++;
         RC(upload_plan(c, c->grad));
+        if (c->grad_aligned) {
+            // the parts' descriptors: part 0 backward from the pair at the first
+            // cut, part k >= 1 forward from the pair at cut k
+            const int K = (int)c->grad_cuts.size() - 1;
+            const size_t E = (size_t)1 << (2 * c->n);
+            RC(c->dalloc(c->gpairs, (size_t)(K - 1) * 2 * E * sizeof(double), c->st));
+            RC(c->dalloc(c->gparts, (size_t)K * sizeof(AdjPart), c->st));
+            const double *pairs = (const double *)c->gpairs.p;
+            c->gparts_host.assign((size_t)K, AdjPart{});
+            for (int k = 0; k < K; ++k) {
+                AdjPart &q = c->gparts_host[(size_t)k];
+                const int at = k == 0 ? 1 : k;   // the pair this part starts from
+                q.stream = c->grad.parts[(size_t)k].dev;
+                q.n_chunks = c->grad.parts[(size_t)k].n_chunks;
+                q.forward = k > 0;
+                q.lam = pairs + (size_t)(at - 1) * 2 * E;
+                q.rho = q.lam + E;
+            }
+            CK(cudaMemcpyAsync(c->gparts.p, c->gparts_host.data(), (size_t)K * sizeof(AdjPart),
+                               cudaMemcpyHostToDevice, c->st));
+        }
     }
     if (!c->grad.encoded) RC(encode_plan(c, c->grad));
     CK(cudaEventRecord(c->ev_ready, c->st));
@@ -1299,7 +1354,7 @@ int stab_destroy(stab_ctx *c) {
                       &c->partials, &c->grads, &c->status, &c->gbuf, &c->lam2, &c->tmp3,
                       &c->dotbuf, &c->tmat, &c->avec, &c->rmid, &c->lmid, &c->bterms,
                       &c->units_g, &c->units_e, &c->cnt, &c->gmid, &c->chainbuf,
-                      &c->chainbuf_e, &c->odense};
+                      &c->chainbuf_e, &c->odense, &c->gpairs, &c->gparts};
     for (DevBuf *b : bufs) c->dfree(*b, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->stage) cudaFreeHost(c->stage);
@@ -1606,34 +1661,43 @@ int stab_grad_async(stab_ctx *c, double *expect_dev, double *grads_dev) {
             partials = (double *)c->partials.p;
         }
     }
-    if (c->use_resident_adjoint() && c->grad.split >= 0 && c->grad_aligned) {
-        // n = 4, cut where the generators' first part ends: rho_0 through the
-        // first part is that sweep's first-part vector, and lambda at the cut
-        // is O carried backward through the later parts, T_k^T (the maps being
-        // orthogonal) from the last part to the first; the sweep is reused
-        // when it was made for these angles.  Then the pair at the cut
-        // backward through the first part and forward through the rest.
+    if (c->use_resident_adjoint() && c->grad_aligned) {
+        // the gradient plan's parts end where the generators' split sweep cuts
+        // the circuit, so the pair at every cut comes from that sweep: rho_0
+        // through the first part is its first-part vector, rho at a later cut
+        // the next parts' transfer matrices applied to it, and lambda at a cut
+        // is O carried backward through the parts after it, T_k^T (the maps
+        // being orthogonal) from the last part to the first; the sweep is
+        // reused when it was made for these angles.  Then every part is swept
+        // at once: the first backward from its end, the others forward.
         if (c->tx_gen != c->param_gen) RC(split_run_g(c));
         CK(cudaStreamWaitEvent(s, c->ev_tx, 0));
-        const size_t E = (size_t)1 << (2 * n);
-        RC(c->dalloc(c->odense, 2 * E * sizeof(double), s));
-        double *cur = (double *)c->odense.p, *nxt = cur + E;
-        CK(launch_fill(cur, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, s));
-        const int n_mats = chain_mode(c) ? (int)c->fwd.parts.size() - 1 : 1;
-        for (int k = n_mats - 1; k >= 0; --k) {
-            CK(launch_apply_transfer_t((const double *)c->tmat.p + (size_t)k * E * E, cur, nxt, n,
-                                       s));
-            std::swap(cur, nxt);
+        const int K = (int)c->grad_cuts.size() - 1;
+        const size_t E = (size_t)1 << (2 * n), EE = E * E;
+        RC(c->dalloc(c->odense, E * sizeof(double), s));
+        double *o = (double *)c->odense.p;
+        CK(launch_fill(o, n, 1, INIT_TERMS, (const DevTerm *)c->terms.p, nt, s));
+        const double *T = (const double *)c->tmat.p;
+        const double *r1 = (const double *)c->avec.p + (size_t)n * E;
+        double *pairs = (double *)c->gpairs.p;
+        auto lam = [&](int k) { return pairs + (size_t)(k - 1) * 2 * E; };
+        if (n == 4) {
+            CK(cudaMemcpyAsync(lam(1) + E, r1, E * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            for (int k = 1; k + 1 <= K - 1; ++k)
+                CK(launch_apply_transfer(T + (size_t)(k - 1) * EE, lam(k) + E, lam(k + 1) + E, 1,
+                                         n, s));
+            for (int k = K - 1; k >= 1; --k)
+                CK(launch_apply_transfer_t(T + (size_t)(k - 1) * EE, k == K - 1 ? o : lam(k + 1),
+                                           lam(k), n, s));
+            c->launches += 1 + 2 * (K - 1) - 1;
+        } else {
+            CK(launch_adjoint_pairs(T, K, n, r1, o, pairs, s));
+            c->launches += 2;
         }
-        c->launches += 1 + n_mats;
         AdjointSplitArgs a{};
-        a.stream[0] = c->grad.h1b.dev;
-        a.n_chunks[0] = c->grad.h1b.n_chunks;
-        a.stream[1] = c->grad.h2.dev;
-        a.n_chunks[1] = c->grad.h2.n_chunks;
         a.phase = 1;
-        a.rmid = (double *)c->avec.p + (size_t)n * E;
-        a.lmid = cur;
+        a.parts = (const AdjPart *)c->gparts.p;
+        a.n_parts = K;
         a.grad_rot = (double *)c->grad_rot.p;
         a.partials = partials;
         a.expect_out = e_out;
