@@ -537,3 +537,33 @@ def test_repeated_pull_reuse_in_served_slices(stab):
     for gi in (rot[1], rot[len(rot) // 2], rot[-3]):
         assert abs(g[int(c.gates[gi]["param"])] - oracle.psr_grad_gate(4, c.gates, c.thetas, obs, gi)) \
             <= 1e-12 * L1
+
+
+@pytest.mark.parametrize("n,m", [(2, 6000), (3, 9000)])
+def test_many_part_gradient_against_oracle(stab, n, m):
+    """n <= 3, long circuits: the generators' chain cuts the plan into K >= 3
+    parts (10 at n = 2, 3 at n = 3); the gradient is cut into the same parts,
+    takes the pair at every cut from the chain's transfer matrices and sweeps
+    all parts at once.  Sampled slots (both ends and across the parts)
+    against the oracle's parameter shift, with the sweep run by the gradient
+    and reused after the generators at new angles."""
+    c = W.layered_ansatz(n, m, seed=630 + n)
+    obs = W.random_observable(n, 3, seed=63 + n)
+    l1 = sum(abs(a) for a, _ in obs)
+    s = stab.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    cut, vectors, _ = s.split_info()
+    assert cut > 0 and vectors >= n + 1 + 2 * (4 ** n - 1)       # a chain of >= 3 parts
+    e1, g1 = s.grad(obs)
+    th2 = np.random.default_rng(640 + n).uniform(0, 2 * np.pi, c.n_params)
+    s.set_params(th2)
+    s.run_generators()
+    e2, g2 = s.grad(obs)
+    s.close()
+    rot = [i for i, gt in enumerate(c.gates) if int(gt["op"]) in W.ROTATIONS]
+    picks = sorted({rot[0], rot[-1]} | {rot[(len(rot) * k) // 12] for k in range(1, 12)})
+    for th, e, g in ((c.thetas, e1, g1), (th2, e2, g2)):
+        assert abs(e - oracle.expect(n, c.gates, th, obs)) <= 1e-12 * l1
+        for gi in picks:
+            want = oracle.psr_grad_gate(n, c.gates, th, obs, gi)
+            assert abs(g[int(c.gates[gi]["param"])] - want) <= 1e-12 * l1, gi
