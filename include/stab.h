@@ -372,6 +372,9 @@ typedef struct stab_result {
 
 /* Admission footprint of a request: max(n 4^n 8, 4^n 8 x (4 for <O>, 12 for
  * a gradient: the vectors of the split sweeps)) bytes plus 96 bytes per gate,
+ * plus at n <= 4 the split sweep's transfer matrices (8 x 16^n bytes each: two
+ * at n = 4, up to min(49, 160 / (4^n - 1)) at n <= 3), its n + 1 first-part
+ * vectors and the pairs at the cuts (two vectors per matrix),
  * plus, for a gradient, the adjoint's partial dot sums: per CTA of the
  * streamed sweep above n = 6, per thread of the resident sweep at n <= 5
  * (8 bytes x gates x 32, 32, 32, 64, 256 threads at n = 1..5, while that

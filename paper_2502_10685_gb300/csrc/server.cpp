@@ -980,6 +980,17 @@ void completer_main(stab_server *s) {
 
 extern "C" {
 
+// n <= 4: the split sweep's transfer matrices (at most two at n = 4, one
+// per later part of the chain at n <= 3: bounded by 160 SMs' worth of
+// columns), its first-part vectors and the pairs at the cuts.
+static int64_t split_sweep_bytes(int n) {
+    if (n > 4) return 0;
+    const int64_t E = (int64_t)1 << (2 * n);
+    int64_t mats = n == 4 ? 2 : std::min<int64_t>(49, 160 / (E - 1));
+    if (mats < 1) mats = 1;
+    return 8 * (mats * E * E + (n + 1 + 2 * mats) * E);
+}
+
 int64_t stab_request_footprint(const stab_request *q) {
     if (!q || q->n < 1 || q->n > STAB_MAX_QUBITS) return 0;
     const int64_t vec = (int64_t)8 << (2 * q->n);
@@ -989,6 +1000,7 @@ int64_t stab_request_footprint(const stab_request *q) {
     const int64_t work = vec * (q->kind == STAB_REQ_GRAD ? 12 : 4);
     if (work > fp) fp = work;
     fp += 96 * (q->m > 0 ? q->m : 0);
+    fp += split_sweep_bytes(q->n);
     if (q->kind == STAB_REQ_GRAD && q->n > kMaxResidentAdjoint) {
         // per-CTA partial sums of the streamed adjoint: one per rotation and CTA
         fp += 8 * (q->m > 0 ? q->m : 0) * (int64_t)adjoint_stream_blocks(q->n);

@@ -84,24 +84,34 @@ def test_server_options_rejected_on_the_host():
     assert L.stab_server_create(ctypes.byref(o), ctypes.byref(h)) == -1
 
 
+def split_sweep_bytes(n):
+    # n <= 4: the transfer matrices, n + 1 first-part vectors, two pair vectors per matrix
+    if n > 4:
+        return 0
+    E = 4 ** n
+    mats = 2 if n == 4 else max(1, min(49, 160 // (E - 1)))
+    return 8 * (mats * E * E + (n + 1 + 2 * mats) * E)
+
+
 def test_request_footprint_counts_the_split_sweep_vectors():
     # host-only: max(n, 12) vectors of 4^n doubles for a gradient (half sweeps
     # and two (lambda, rho) pairs with spares), max(n, 4) for an expectation,
-    # plus 96 B per gate
+    # plus 96 B per gate, plus the split sweep's transfer matrices at n <= 4
     import ctypes
     from paper_2502_10685_gb300 import _lib
     L = _lib.load()
     r = _lib.StabRequest()
     r.n, r.m = 3, 1000
     r.kind = 0
-    assert L.stab_request_footprint(ctypes.byref(r)) == 4 * 8 * 4 ** 3 + 96 * 1000
+    assert L.stab_request_footprint(ctypes.byref(r)) == \
+        4 * 8 * 4 ** 3 + 96 * 1000 + split_sweep_bytes(3)
     # gradients at n <= 5 add the resident sweep's per-thread dot shares (one
     # row of its CTA's threads per gate, as a bound on the rotations)
     r.kind = 1
     for n, threads in ((3, 32), (4, 64), (5, 256)):
         r.n = n
         assert L.stab_request_footprint(ctypes.byref(r)) == \
-            12 * 8 * 4 ** n + 96 * 1000 + 8 * 1000 * threads
+            12 * 8 * 4 ** n + 96 * 1000 + 8 * 1000 * threads + split_sweep_bytes(n)
     r.n = 6
     assert L.stab_request_footprint(ctypes.byref(r)) == 12 * 8 * 4 ** 6 + 96 * 1000
     r.kind = 0
