@@ -257,6 +257,24 @@ __device__ __forceinline__ double pair_dot(int axis, double lx, double ly, doubl
     return fma(ly, rx, -lx * ry);
 }
 
+// One rotation record on the same pair slots of both vectors (lambda and
+// rho), as apply_rot does on one.
+__device__ __forceinline__ void rot_pair(const Rec &op, double &lx, double &ly, double &lz,
+                                         double &rx, double &ry, double &rz) {
+    const double t = op.t, s = op.s;
+    const uint32_t neg = op.code;
+    if (op.axis == AX_X) {
+        lift(ly, lz, t, s, neg);
+        lift(ry, rz, t, s, neg);
+    } else if (op.axis == AX_Y) {
+        lift(lz, lx, t, s, neg);
+        lift(rz, rx, t, s, neg);
+    } else {
+        lift(lx, ly, t, s, neg);
+        lift(rx, ry, t, s, neg);
+    }
+}
+
 // The pair (lambda, rho) through chunks [c0, c1) of a gradient stream, with
 // each rotation's dot <lambda_j, G_j rho_j> taken at its post-gate pair (G_j
 // the generator of the rotation on its pairs) and written to grad_rot at the
@@ -292,6 +310,55 @@ __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double
             const Rec *pulls = Rr + r + 1;
             const Rec *ops = pulls + h.param;
             const int n_pull = h.param, n_ops = h.gate, q = h.q;
+            if (GPT == 1 && part_out) {
+                // one group per thread, each dot's share stored as it comes:
+                // every op decoded once for both vectors, the group's four
+                // sources pulled once for both
+                const uint32_t g = threadIdx.x;
+                if (g < (uint32_t)G) {
+                    uint32_t ii, ix, iy, iz;
+                    group_idx<N>(g, q, ii, ix, iy, iz);
+                    uint32_t ji = ii, jx = ix, jy = iy, jz = iz;
+                    uint32_t ni = 0, nx = 0, ny = 0, nz = 0;
+                    if (n_pull > 0) {
+                        ji = pull_recs(ii, N, pulls, n_pull, ni);
+                        jx = pull_recs(ix, N, pulls, n_pull, nx);
+                        jy = pull_recs(iy, N, pulls, n_pull, ny);
+                        jz = pull_recs(iz, N, pulls, n_pull, nz);
+                    }
+                    const double li = flip(lam[ji], ni), ri = flip(rho[ji], ni);
+                    double lx = flip(lam[jx], nx), ly = flip(lam[jy], ny), lz = flip(lam[jz], nz);
+                    double rx = flip(rho[jx], nx), ry = flip(rho[jy], ny), rz = flip(rho[jz], nz);
+                    for (int j = 0; j < n_ops; ++j) {
+                        const Rec op = ops[j];
+                        if (op.kind == R_ROT) {
+                            double *share = part_out + (size_t)op.gate * T + threadIdx.x;
+                            if (!fwd) *share = pair_dot(op.axis, lx, ly, lz, rx, ry, rz);
+                            rot_pair(op, lx, ly, lz, rx, ry, rz);
+                            if (fwd) *share = pair_dot(op.axis, lx, ly, lz, rx, ry, rz);
+                        } else {
+                            apply_recs(lx, ly, lz, ops + j, 1);
+                            apply_recs(rx, ry, rz, ops + j, 1);
+                        }
+                    }
+                    lam_n[ii] = li; lam_n[ix] = lx; lam_n[iy] = ly; lam_n[iz] = lz;
+                    rho_n[ii] = ri; rho_n[ix] = rx; rho_n[iy] = ry; rho_n[iz] = rz;
+                } else {
+                    // a thread without a group (n <= 3): zero shares
+                    for (int j = 0; j < n_ops; ++j)
+                        if (ops[j].kind == R_ROT)
+                            part_out[(size_t)ops[j].gate * T + threadIdx.x] = 0.0;
+                }
+                double *t = lam;
+                lam = lam_n;
+                lam_n = t;
+                t = rho;
+                rho = rho_n;
+                rho_n = t;
+                __syncthreads();
+                r += 1 + n_pull + n_ops;
+                continue;
+            }
             double part[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) part[k] = 0.0;
