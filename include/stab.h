@@ -545,6 +545,19 @@ int stab_selftest_bounded_wait(int64_t polls);
  * Errors: STAB_E_INVAL / STAB_E_RANGE (gates as for stab_load_circuit, mode). */
 int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_params, int mode);
 
+/* Host-only check of the cut alignment between a circuit's generator plan
+ * (one 3x3 map per wire run) and its gradient plan (every rotation its own
+ * op): for every pass of the generator plan that starts a unit (a two-qubit
+ * pass, or the passes of one wire run), the gradient-plan pass the aligner
+ * maps it to must hold before it exactly the same rotations (by ordinal) and
+ * the same number of two-qubit gates; where the aligner refuses, the two
+ * plans' unit sequences must really differ.  *aligned receives how many
+ * passes were aligned (0 when the aligner refused).  STAB_OK, or
+ * STAB_E_STATE when a check fails.  Errors: STAB_E_INVAL / STAB_E_RANGE
+ * (gates as for stab_load_circuit). */
+int stab_selftest_align(int n, const stab_gate *gates, int64_t m, int64_t n_params,
+                        int64_t *aligned);
+
 /* ---------------------------------------------------------------- path tuner */
 /* How a context of n qubits with the STAB_KERNEL_AUTO kernel runs, for one GPU
  * model.  The paper has no counterpart (its CPU pipeline has one form).  The

@@ -1211,6 +1211,80 @@ int stab_selftest_plan(int n, const stab_gate *gates, int64_t m, int64_t n_param
     return ok ? STAB_OK : STAB_E_STATE;
 }
 
+namespace {
+
+// Rotation ordinals (sorted) and two-qubit gate count of passes [0, k) of a
+// plan: maps list their gates, rotation ops carry their ordinals.
+void prefix_content(const HostPlan &P, int k, std::vector<int32_t> *rots, int64_t *two_q) {
+    rots->clear();
+    *two_q = 0;
+    for (int i = 0; i < k; ++i) {
+        const DevPass &p = P.passes[(size_t)i];
+        for (int j = 0; j < p.n_ops; ++j) {
+            const DevOp &op = P.ops[p.first + (uint32_t)j];
+            if (p.type == P_CLIFF) {
+                ++*two_q;
+            } else if (op.kind == K_ROT) {
+                rots->push_back(op.gate);
+            } else if (op.kind == K_MAP3) {
+                const DevMap3 &mp = P.maps[(size_t)op.param];
+                for (int g = 0; g < mp.count; ++g) {
+                    const int32_t o = P.rot_ordinal[(size_t)P.map_gate_idx[(size_t)(mp.first + g)]];
+                    if (o >= 0) rots->push_back(o);
+                }
+            }
+        }
+    }
+    std::sort(rots->begin(), rots->end());
+}
+
+}  // namespace
+
+int stab_selftest_align(int n, const stab_gate *gates, int64_t m, int64_t n_params,
+                        int64_t *aligned) {
+    if (n < 1 || n > STAB_MAX_QUBITS) return STAB_E_RANGE;
+    std::string msg;
+    RC(validate_gates(n, gates, m, n_params, &msg));
+    HostPlan F, G;
+    build_plan(n, gates, m, n_params, PLAN_ROWS, &F, false, true);
+    build_plan(n, gates, m, n_params, PLAN_GRAD, &G, false, true);
+    // rotation ordinals of the generator plan's maps need the gate -> ordinal table
+    if (F.rot_ordinal.size() != (size_t)m) {
+        F.rot_ordinal.assign((size_t)m, -1);
+        int32_t nr = 0;
+        for (int64_t i = 0; i < m; ++i)
+            if (gates[i].op >= STAB_RX) F.rot_ordinal[(size_t)i] = nr++;
+    }
+    int64_t count = 0;
+    bool refused = false;
+    std::vector<int32_t> ra, rb;
+    int64_t qa = 0, qb = 0;
+    for (int k = 1; k < (int)F.passes.size(); ++k) {
+        if (!unit_start(F, (size_t)k)) continue;
+        const int g = aligned_pass(F, k, G);
+        if (g < 0) {
+            refused = true;
+            break;
+        }
+        prefix_content(F, k, &ra, &qa);
+        prefix_content(G, g, &rb, &qb);
+        if (ra != rb || qa != qb) return STAB_E_STATE;
+        ++count;
+    }
+    if (refused) {
+        // the aligner refuses only where the plans' unit sequences differ
+        std::vector<uint16_t> ua, ub;
+        for (size_t i = 0; i < F.passes.size(); ++i)
+            if (unit_start(F, i)) ua.push_back((uint16_t)(F.passes[i].type << 8 | F.passes[i].q));
+        for (size_t i = 0; i < G.passes.size(); ++i)
+            if (unit_start(G, i)) ub.push_back((uint16_t)(G.passes[i].type << 8 | G.passes[i].q));
+        if (ua == ub) return STAB_E_STATE;
+        count = 0;
+    }
+    if (aligned) *aligned = count;
+    return STAB_OK;
+}
+
 int stab_selftest_bounded_wait(int64_t polls) {
     if (polls < 0) return STAB_E_RANGE;
     cudaStream_t s = nullptr;

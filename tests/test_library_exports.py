@@ -148,3 +148,39 @@ def test_pass_probe_rejects_bad_arguments_on_the_host():
     assert L.stab_probe_pass(0, 256, 1024, None) == -1
     for passes in (0, 2, 1026, (1 << 24) + 4):
         assert L.stab_probe_pass(0, 256, passes, ctypes.byref(c)) == -2
+
+
+def test_gradient_cut_alignment_on_the_host():
+    # host-only: every generator-plan unit boundary maps to a gradient-plan
+    # pass with the same rotations and two-qubit gates before it; a circuit
+    # with a wire run that is the identity (no pass in the gradient plan) is
+    # refused, and only such a circuit
+    import ctypes
+    import numpy as np
+    from paper_2502_10685_gb300 import _lib, workloads as W
+    L = _lib.load()
+
+    def check(c):
+        g = np.ascontiguousarray(c.gates)
+        out = ctypes.c_int64()
+        rc = L.stab_selftest_align(c.n, g.ctypes.data, len(g), c.n_params, ctypes.byref(out))
+        assert rc == 0, (c.n, len(g), rc)
+        return out.value
+
+    for c in (W.layered_ansatz(4, 3000, seed=1), W.layered_ansatz(3, 2000, seed=2),
+              W.layered_ansatz(2, 1500, seed=3), W.layered_ansatz(5, 800, seed=4),
+              W.paper_shaped_ansatz(4, 20, 30, seed=5)):
+        assert check(c) > 0
+    for seed in range(6):
+        check(W.random_circuit(4, 1500, seed=100 + seed))
+        check(W.random_circuit(3, 1500, seed=200 + seed, shared_params=7))
+    # an H H pair between two CNOTs of a ring: a block whose one wire run is
+    # the identity -- the aligner must refuse (0 passes aligned)
+    c = W.layered_ansatz(4, 1600, seed=6)
+    h = np.zeros(2, dtype=W.GATE_DTYPE)
+    h["op"] = W.OPS["H"]
+    h["q0"] = 2
+    h["param"] = -1
+    k = 16 * 30 + 13
+    c2 = W.Circuit(4, np.concatenate([c.gates[:k], h, c.gates[k:]]), c.thetas)
+    assert check(c2) == 0
