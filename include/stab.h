@@ -186,7 +186,12 @@ int stab_expect_async(stab_ctx *ctx, double *out_dev);
 
 /* Adjoint gradient of the loaded observable: expect_dev (device, may be NULL)
  * receives <O>, grads_dev (device) n_params doubles.  Queued like
- * stab_expect_async. */
+ * stab_expect_async.  At n <= 4 (AUTO kernel, long circuits) the gradient is
+ * cut into the parts of the generators' split sweep and takes its vectors at
+ * the cuts from that sweep: when none was made for the current angles it is
+ * queued first on the context stream (as by stab_run_generators, whose
+ * results it leaves valid for reuse), then the gradient on the internal
+ * stream.  Same for stab_expect_async in that form. */
 int stab_grad_async(stab_ctx *ctx, double *expect_dev, double *grads_dev);
 
 /* Gradient of <O> with respect to every angle slot, by one adjoint reverse
