@@ -323,3 +323,31 @@ def test_gradient_cut_at_the_generators_first_part(S, parts, cut, identity_run):
         for gi in picks:
             want = oracle.psr_grad_gate(n, c.gates, th, obs, gi)
             assert abs(g[int(c.gates[gi]["param"])] - want) <= tol, gi
+
+
+@pytest.mark.parametrize("n,m", [(4, 3000), (3, 4000), (2, 4000)])
+def test_density_matrix_reuses_the_sweep_a_gradient_made(S, n, m):
+    """The gradient at n <= 4 runs the generators' split sweep for the current
+    angles; the density matrix asked next reuses it (rho_0 through the first
+    part and the parts' transfer matrices).  Both, and the generators, equal
+    the oracle; after new angles nothing made for the old ones is reused."""
+    c = W.layered_ansatz(n, m, seed=4470 + n)
+    obs = W.random_observable(n, 4, seed=4471 + n)
+    perm = [int(format(i, "0%db" % n)[::-1], 2) for i in range(2 ** n)]
+    s = S.Stab(n)
+    s.load_circuit(c.gates, c.thetas)
+    th2 = np.random.default_rng(4472 + n).uniform(0, 2 * np.pi, c.n_params)
+    got = []
+    for th in (c.thetas, th2):
+        s.set_params(th)
+        e, _ = s.grad(obs)
+        rho = s.density_matrix()
+        s.run_generators()
+        gens = layout.lib_to_paper(n, s.generators())
+        got.append((th, e, rho, gens))
+    s.close()
+    for th, e, rho, gens in got:
+        assert abs(e - oracle.expect(n, c.gates, th, obs)) <= 1e-12 * l1(obs)
+        assert np.abs(rho[np.ix_(perm, perm)] - oracle.density_matrix(n, c.gates, th)).max() \
+            <= 1e-12
+        assert np.abs(gens - oracle.generators(n, c.gates, th)).max() <= 1e-12
