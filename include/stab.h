@@ -194,6 +194,13 @@ int stab_expect_async(stab_ctx *ctx, double *out_dev);
  * stream.  Same for stab_expect_async in that form. */
 int stab_grad_async(stab_ctx *ctx, double *expect_dev, double *grads_dev);
 
+/* How the last gradient's plan is cut: *parts receives K >= 2 when it is cut
+ * into the K parts of the generators' split sweep (n <= 4; the pairs at the
+ * cuts come from that sweep), 1 when it uses the meet-in-the-middle or a
+ * streamed sweep, 0 before any gradient since the circuit was loaded.
+ * Errors: STAB_E_INVAL (ctx or parts NULL). */
+int stab_grad_parts(stab_ctx *ctx, int32_t *parts);
+
 /* Gradient of <O> with respect to every angle slot, by one adjoint reverse
  * sweep.  expect_out (may be NULL) receives <O>; grads_out receives n_params
  * doubles (host memory).  Errors as stab_expect. */

@@ -155,6 +155,7 @@ def load(build_if_missing: bool = True):
             "stab_selftest_bounded_wait": (i32, [i64]),
             "stab_selftest_plan": (i32, [i32, vp, i64, i64, i32]),
             "stab_selftest_align": (i32, [i32, vp, i64, i64, ctypes.POINTER(i64)]),
+            "stab_grad_parts": (i32, [vp, ctypes.POINTER(i32)]),
             "stab_sparse_create": (i32, [i32, i64, ctypes.POINTER(StabOpts), ctypes.POINTER(vp)]),
             "stab_sparse_destroy": (i32, [vp]),
             "stab_sparse_load_circuit": (i32, [vp, vp, i64, dp, i64]),

@@ -2115,6 +2115,12 @@ int stab_split_info(stab_ctx *c, int64_t *cut, int32_t *gen_units, int32_t *expe
 
 int64_t stab_launch_count(stab_ctx *c) { return c ? c->launches : 0; }
 
+int stab_grad_parts(stab_ctx *c, int32_t *parts) {
+    if (!c || !parts) return STAB_E_INVAL;
+    *parts = !c->grad.built ? 0 : c->grad_aligned ? (int32_t)c->grad_cuts.size() - 1 : 1;
+    return STAB_OK;
+}
+
 int stab_transfer_bytes(stab_ctx *c, int64_t *h2d, int64_t *d2h) {
     if (!c) return STAB_E_INVAL;
     if (h2d) *h2d = c->h2d_bytes;

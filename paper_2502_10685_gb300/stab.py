@@ -357,6 +357,13 @@ class Stab:
     def launch_count(self) -> int:
         return stab_launch_count(self.h)
 
+    def grad_parts(self) -> int:
+        """K >= 2: the last gradient was cut into the generators' K parts;
+        1: meet-in-the-middle or streamed; 0: no gradient since the load."""
+        k = ctypes.c_int32()
+        check(_lib.load().stab_grad_parts(self.h, ctypes.byref(k)), "stab_grad_parts")
+        return k.value
+
     def path_choice(self) -> dict:
         """The path this context runs with (the tuner's choice for AUTO)."""
         c = StabPathChoice()

@@ -555,6 +555,7 @@ def test_many_part_gradient_against_oracle(stab, n, m):
     cut, vectors, _ = s.split_info()
     assert cut > 0 and vectors >= n + 1 + 2 * (4 ** n - 1)       # a chain of >= 3 parts
     e1, g1 = s.grad(obs)
+    assert s.grad_parts() == 1 + (vectors - (n + 1)) // (4 ** n - 1)
     th2 = np.random.default_rng(640 + n).uniform(0, 2 * np.pi, c.n_params)
     s.set_params(th2)
     s.run_generators()

@@ -312,7 +312,10 @@ def test_gradient_cut_at_the_generators_first_part(S, parts, cut, identity_run):
     picks = (rot[0], rot[len(rot) // 2 - 1], rot[len(rot) // 2 + 3], rot[-1])
     s = S.Stab(n)
     s.load_circuit(c.gates, c.thetas)
+    assert s.grad_parts() == 0
     e1, g1 = s.grad(obs)                      # no sweep for these angles yet
+    # the generators' parts, or (unit sequences that differ) meet in the middle
+    assert s.grad_parts() == (1 if identity_run else parts)
     th2 = np.random.default_rng(4462).uniform(0, 2 * np.pi, c.n_params)
     s.set_params(th2)
     s.run_generators()
@@ -341,6 +344,7 @@ def test_density_matrix_reuses_the_sweep_a_gradient_made(S, n, m):
     for th in (c.thetas, th2):
         s.set_params(th)
         e, _ = s.grad(obs)
+        assert s.grad_parts() >= 2
         rho = s.density_matrix()
         s.run_generators()
         gens = layout.lib_to_paper(n, s.generators())

@@ -137,6 +137,15 @@ def test_fp64_probe_rejects_bad_arguments_on_the_host():
     assert L.stab_probe_fp64(1, (1 << 30) + 1, ctypes.byref(tf), ctypes.byref(ms)) == -2
 
 
+def test_grad_parts_rejects_null_on_the_host():
+    # host-only: argument checks come before any device call
+    import ctypes
+    from paper_2502_10685_gb300 import _lib
+    L = _lib.load()
+    k = ctypes.c_int32()
+    assert L.stab_grad_parts(None, ctypes.byref(k)) == -1
+
+
 def test_pass_probe_rejects_bad_arguments_on_the_host():
     # host-only: argument checks come before any device call
     import ctypes
