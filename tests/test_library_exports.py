@@ -183,6 +183,21 @@ def test_gradient_cut_alignment_on_the_host():
     for seed in range(6):
         check(W.random_circuit(4, 1500, seed=100 + seed))
         check(W.random_circuit(3, 1500, seed=200 + seed, shared_params=7))
+    # a wire run longer than one pass takes (16,384 gates): two consecutive
+    # passes on one wire in the generator plan, many in the gradient plan --
+    # still one unit in both
+    rng = np.random.default_rng(7)
+    layer = W.layered_ansatz(2, 400, seed=7)
+    long_run = np.zeros(20000, dtype=W.GATE_DTYPE)
+    long_run["op"] = rng.choice([W.OPS["RX"], W.OPS["RY"], W.OPS["RZ"]], size=20000)
+    long_run["q0"] = 0
+    long_run["param"] = np.arange(20000) + layer.n_params
+    cx = np.zeros(1, dtype=W.GATE_DTYPE)
+    cx["op"] = W.OPS["CX"]
+    cx["q0"], cx["q1"], cx["param"] = 0, 1, -1
+    gl = np.concatenate([layer.gates, cx, long_run, cx, layer.gates])
+    th = np.concatenate([layer.thetas, rng.uniform(0, 6.28, 20000)])
+    assert check(W.Circuit(2, gl, th)) > 0
     # an H H pair between two CNOTs of a ring: a block whose one wire run is
     # the identity -- the aligner must refuse (0 passes aligned)
     c = W.layered_ansatz(4, 1600, seed=6)
