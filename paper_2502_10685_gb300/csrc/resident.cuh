@@ -300,6 +300,12 @@ __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double
     int *gslot = reinterpret_cast<int *>(smem + kOffSlot);
     double *red = reinterpret_cast<double *>(smem + kOffRed);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // fast path: the group's four pulled sources and signs through the last
+    // pull records walked, and the wire of that pass (-1: none yet); kept at
+    // N <= 4 only, where the eight registers fit under the launch bound
+    constexpr bool kReuse = N <= 4;
+    uint32_t cj[4] = {0, 0, 0, 0}, cn[4] = {0, 0, 0, 0};
+    int cq = -1;
     for (int c = c0; c < c1; ++c) {
         if (!st.wait(c, status)) return false;
         const Rec *Rr = st.chunk(c);
@@ -320,11 +326,20 @@ __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double
                     group_idx<N>(g, q, ii, ix, iy, iz);
                     uint32_t ji = ii, jx = ix, jy = iy, jz = iz;
                     uint32_t ni = 0, nx = 0, ny = 0, nz = 0;
-                    if (n_pull > 0) {
+                    if (kReuse && n_pull > 0 && h.code == kPullRepeat && cq == q) {
+                        // the same Clifford run as the last pull, on the same wire
+                        ji = cj[0]; jx = cj[1]; jy = cj[2]; jz = cj[3];
+                        ni = cn[0]; nx = cn[1]; ny = cn[2]; nz = cn[3];
+                    } else if (n_pull > 0) {
                         ji = pull_recs(ii, N, pulls, n_pull, ni);
                         jx = pull_recs(ix, N, pulls, n_pull, nx);
                         jy = pull_recs(iy, N, pulls, n_pull, ny);
                         jz = pull_recs(iz, N, pulls, n_pull, nz);
+                        if (kReuse) {
+                            cj[0] = ji; cj[1] = jx; cj[2] = jy; cj[3] = jz;
+                            cn[0] = ni; cn[1] = nx; cn[2] = ny; cn[3] = nz;
+                            cq = q;
+                        }
                     }
                     const double li = flip(lam[ji], ni), ri = flip(rho[ji], ni);
                     double lx = flip(lam[jx], nx), ly = flip(lam[jy], ny), lz = flip(lam[jz], nz);
