@@ -280,8 +280,10 @@ __global__ void __launch_bounds__(SCfg<N, 1>::T) k_adjoint_stream(AdjointStreamA
     if (rho == nullptr) return;
     double *rho_n = rho == rA ? rB : rA;
     double *lam = lA, *lam_n = lB;
-    if (!adjoint_sweep<N>(st, a.n_fwd_chunks, st.n_total, lam, lam_n, rho, rho_n, a.grad_rot,
-                          a.status, smem, false, a.partials))
+    // no pull reuse at n = 5 here: with the forward sweep in the same kernel
+    // the eight cached registers spill
+    if (!adjoint_sweep<N, C::T, (N <= 4)>(st, a.n_fwd_chunks, st.n_total, lam, lam_n, rho,
+                                          rho_n, a.grad_rot, a.status, smem, false, a.partials))
         return;
     double acc = 0.0;
     for (int i = threadIdx.x; i < (1 << N); i += C::T) acc += lam[i];

@@ -288,7 +288,10 @@ __device__ __forceinline__ void rot_pair(const Rec &op, double &lx, double &ly, 
 // with part_out, each thread stores its own share at part_out[ordinal * T +
 // thread] and the sweep does no reduction and no barrier for it (the caller
 // sums every rotation over the threads afterwards, in thread order).
-template <int N, int T = SCfg<N, 1>::T>
+// REUSE: with part_out and one group per thread, a pass whose Clifford run
+// repeats the last pull on the same wire takes the group's pulled sources
+// and signs from registers (eight more registers a thread).
+template <int N, int T = SCfg<N, 1>::T, bool REUSE = (N <= 5)>
 __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double *&lam,
                                               double *&lam_n, double *&rho, double *&rho_n,
                                               double *grad_rot, int32_t *status,
@@ -301,9 +304,8 @@ __device__ __forceinline__ bool adjoint_sweep(Stager &st, int c0, int c1, double
     double *red = reinterpret_cast<double *>(smem + kOffRed);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // fast path: the group's four pulled sources and signs through the last
-    // pull records walked, and the wire of that pass (-1: none yet); kept at
-    // N <= 4 only, where the eight registers fit under the launch bound
-    constexpr bool kReuse = N <= 4;
+    // pull records walked, and the wire of that pass (-1: none yet)
+    constexpr bool kReuse = REUSE;
     uint32_t cj[4] = {0, 0, 0, 0}, cn[4] = {0, 0, 0, 0};
     int cq = -1;
     for (int c = c0; c < c1; ++c) {

@@ -258,8 +258,11 @@ def test_shortest_first_with_aging_admits_the_oldest(stab, engine):
     """One slot, shortest-work-first with a 1 ms aging bound: while a blocker
     runs, a large request and six small ones queue; when the slot frees, the
     large request has waited past the bound and is admitted before the small
-    ones (without the bound it would come last)."""
-    blocker = W.layered_ansatz(9, 1500, seed=1)
+    ones (without the bound it would come last).  The blocker is long enough
+    (15,000 gates at n = 9) that the large request has aged past the bound
+    when the slot frees; a blocker done within 1 ms of that submission would
+    rightly let a small request in first."""
+    blocker = W.layered_ansatz(9, 15000, seed=1)
     large = W.layered_ansatz(8, 3000, seed=2)
     small = [W.layered_ansatz(3, 40 + k, seed=10 + k) for k in range(6)]
     srv = stab.Server(max_active=1, policy="shortest", engine=engine, aging_s=1e-3)
@@ -271,6 +274,7 @@ def test_shortest_first_with_aging_admits_the_oldest(stab, engine):
     rs = [srv.wait(i, timeout_s=300) for i in isml]
     srv.close()
     assert rb["status"] == 0 and rl["status"] == 0 and all(r["status"] == 0 for r in rs)
+    assert rb["done_s"] - rl["submit_s"] > 1e-3   # the premise: the large one has aged
     assert all(rl["done_s"] <= r["admit_s"] for r in rs)
     assert abs(rl["expect"] - oracle.expect(8, large.gates, large.thetas, W.obs_chain(8))) <= \
         1e-12 * l1(W.obs_chain(8))
